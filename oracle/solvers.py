@@ -1,0 +1,136 @@
+"""Solvers driven by M (oracle, FP64): dynamics, stationary state, spectra, current.
+
+Paper passages followed:
+* Package architecture: dynamics by an ODE solver or by the propagator exp(M t);
+  stationary states by a linear solve.
+* Methods, "Numerical computation of the spectrum": the bosonic power spectrum
+  pi S(w) = -Re Tr[a^dag x] with (M - i w) x = a rho (even parity), and the density of
+  states pi A(w) = -Re{Tr[d x_+] + Tr[d^dag x_-]} with (M + i w) x_+ = d^dag rho and
+  (M - i w) x_- = d rho, M acting on odd-parity ADOs; only the tier-0 block enters the trace.
+* Methods, "Electronic current" (Eq. last): <I_alpha> = i e sum_{nu,h,sigma}
+  (-1)^{delta_{nu,-}} Tr[d_sigma^{nubar} rho^{(0,1,+)}_{alpha,nu,h,sigma}].
+
+Readings (the paper does not fix them):
+* Dynamics: classical fixed-step RK4 (the paper's adaptive ODE solvers are not specified).
+* Stationary state: the equation of the (0,0) element of the tier-0 ADO is replaced by the
+  normalisation Tr rho_sys = 1 (that equation is redundant because M preserves the trace).
+* b = O rho_n for every ADO n (left multiplication, no extra sign) in the spectra.
+* Residuals: r_ss = ||M x|| / ||x|| with Tr rho_sys = 1; linear solves ||b - A x|| / ||b||.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from .liouvillian import from_liouville, to_liouville
+
+
+def rk4(apply, x0: np.ndarray, dt: float, n_steps: int, save_every: int = 1,
+        observe=None):
+    """Classical RK4: x <- x + dt/6 (k1 + 2 k2 + 2 k3 + k4). Returns (x_end, snapshots)."""
+    observe = observe or (lambda v: v.copy())
+    x = x0.copy()
+    snaps = [observe(x)]
+    for s in range(n_steps):
+        k1 = apply(x)
+        k2 = apply(x + 0.5 * dt * k1)
+        k3 = apply(x + 0.5 * dt * k2)
+        k4 = apply(x + dt * k3)
+        x = x + (dt / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+        if (s + 1) % save_every == 0:
+            snaps.append(observe(x))
+    return x, snaps
+
+
+def propagate_expm(M, v0: np.ndarray, t: float) -> np.ndarray:
+    """exp(M t) v0 with a dense matrix exponential (tiny hierarchies only)."""
+    Md = M.toarray() if sp.issparse(M) else np.asarray(M)
+    return sla.expm(Md * t) @ v0
+
+
+def initial_vector(n_ado: int, rho0: np.ndarray) -> np.ndarray:
+    """All ADOs zero except the tier-0 one, which is rho0 (row-major blocks)."""
+    X = np.zeros((n_ado,) + rho0.shape, dtype=np.complex128)
+    X[0] = rho0
+    return X
+
+
+def steady_state(M, d: int) -> np.ndarray:
+    """Solve M x = 0 with Tr rho_sys = 1 by sparse LU; returns (N, d, d) blocks."""
+    A = sp.lil_matrix(M, dtype=np.complex128)
+    trace_row = np.zeros(M.shape[1], dtype=np.complex128)
+    trace_row[[i * d + i for i in range(d)]] = 1.0  # column stacking: (i,i) -> i*d + i
+    A[0, :] = trace_row
+    rhs = np.zeros(M.shape[0], dtype=np.complex128)
+    rhs[0] = 1.0
+    lu = spla.splu(sp.csc_matrix(A))
+    return from_liouville(lu.solve(rhs), d)
+
+
+def steady_residual(M, X: np.ndarray) -> float:
+    """r_ss = ||M x|| / ||x|| after normalising Tr rho_sys = 1."""
+    X = X / np.trace(X[0])
+    v = to_liouville(X)
+    return float(np.linalg.norm(M @ v) / np.linalg.norm(v))
+
+
+def left_multiply(op: np.ndarray, X: np.ndarray) -> np.ndarray:
+    """b_n = op rho_n for every ADO n."""
+    return np.einsum("ij,njk->nik", op, X)
+
+
+def dos(M_odd, X_ss: np.ndarray, dop: np.ndarray, omegas, return_solutions=False):
+    """Density of states A(w) of the mode dop (Methods, spectrum; fermionic case)."""
+    d = dop.shape[0]
+    bp = to_liouville(left_multiply(dop.conj().T, X_ss))
+    bm = to_liouville(left_multiply(dop, X_ss))
+    I = sp.identity(M_odd.shape[0], dtype=np.complex128, format="csc")
+    Mc = sp.csc_matrix(M_odd)
+    out = np.empty(len(omegas))
+    sols = []
+    for k, w in enumerate(omegas):
+        xp = spla.splu(Mc + 1j * w * I).solve(bp)
+        xm = spla.splu(Mc - 1j * w * I).solve(bm)
+        xp0 = from_liouville(xp[: d * d], d)[0]
+        xm0 = from_liouville(xm[: d * d], d)[0]
+        out[k] = -np.real(np.trace(dop @ xp0) + np.trace(dop.conj().T @ xm0)) / np.pi
+        if return_solutions:
+            sols.append((xp, xm))
+    return (out, sols) if return_solutions else out
+
+
+def psd(M_even, X_ss: np.ndarray, aop: np.ndarray, omegas):
+    """Power spectral density S(w) of the mode aop (Methods, spectrum; bosonic case)."""
+    d = aop.shape[0]
+    b = to_liouville(left_multiply(aop, X_ss))
+    I = sp.identity(M_even.shape[0], dtype=np.complex128, format="csc")
+    Mc = sp.csc_matrix(M_even)
+    out = np.empty(len(omegas))
+    for k, w in enumerate(omegas):
+        x = spla.splu(Mc - 1j * w * I).solve(b)
+        x0 = from_liouville(x[: d * d], d)[0]
+        out[k] = -np.real(np.trace(aop.conj().T @ x0)) / np.pi
+    return out
+
+
+def current(problem: dict, hier, X_ss: np.ndarray, baths_of_lead) -> float:
+    """<I_alpha> (e = 1) from the tier-1 fermionic ADOs of the baths that form lead alpha."""
+    from .hierarchy import flatten_exponents
+    from .liouvillian import op_power
+
+    _, fer = flatten_exponents(problem)
+    m0 = hier.bos[0]
+    total = 0j
+    for q, e in enumerate(fer):
+        if e.bath not in baths_of_lead:
+            continue
+        rho_q = X_ss[hier.index[(m0, (q,))]]
+        sign = 1 if e.nu == 1 else -1
+        total += sign * np.trace(op_power(e.op, -e.nu) @ rho_q)
+    return float(np.real(1j * total))
+
+
+def solve_residual(A, x: np.ndarray, b: np.ndarray) -> float:
+    return float(np.linalg.norm(b - A @ x) / np.linalg.norm(b))
