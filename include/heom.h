@@ -1,0 +1,213 @@
+/*
+ * heom.h -- C ABI of the GB300 HEOM library (libheom.so).
+ *
+ * The library applies the HEOM Liouvillian superoperator M of the hierarchical equations
+ * of motion (Eq. HEOM of arXiv 2306.07522 with the superoperators A, B, C, D, P_s defined
+ * below it) to the vector of all auxiliary density operators (ADOs), matrix-free on one
+ * GPU, and drives it in three solvers: RK4 time evolution, stationary states and spectra.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Complex numbers are (re, im) pairs of doubles (heom_c64, the memory layout of
+ *   torch.complex128 / std::complex<double>). FP32 device buffers are (re, im) float pairs
+ *   (torch.complex64).
+ * - Operators are d x d, row-major.
+ * - An ADO vector is a device buffer laid out [N][d][d][batch]: ADO n, row r, column c,
+ *   batch column b at element ((n*d + r)*d + c)*batch + b. With batch = 1 this is a plain
+ *   array of N row-major d x d blocks. ADO n = 0 is the reduced density matrix rho_sys.
+ * - ADO order (the "hierarchy dictionary", Fig. 1e): bosonic occupation vectors m
+ *   (|m| <= tier_b) by tier ascending then lexicographically descending, fermionic index
+ *   sets S (|S| <= tier_f) by size ascending then lexicographically ascending as sorted
+ *   tuples; ADO index = bosonic index * N_f + fermionic index. Exponents are numbered in
+ *   bath order, then in order within each bath; bosonic exponents come first
+ *   (0 .. K_b-1), fermionic ones after (K_b .. K_b+K_f-1) in the occupation arrays below.
+ * - Ownership: every input array is copied by the call that receives it. Device vectors are
+ *   caller-allocated and caller-owned; the library never frees them. A heom_hier owns its
+ *   device tables and workspace until heom_destroy.
+ * - Streams: every device entry point takes a CUDA stream (a cudaStream_t; 0 = legacy
+ *   default stream) and enqueues its work there. Solvers synchronise that stream before
+ *   they return (they read convergence flags on the host); heom_apply does not.
+ * - Errors: every call returns a heom_status. No exception crosses the ABI. On failure the
+ *   message of the last error on the calling thread is available from heom_last_error().
+ *   There is no CPU fallback: without a usable CUDA device the device entry points return
+ *   HEOM_ECUDA.
+ */
+#ifndef HEOM_H
+#define HEOM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } heom_c64;
+typedef struct heom_hier heom_hier;
+typedef struct CUstream_st *heom_stream; /* binary-compatible with cudaStream_t */
+
+typedef enum {
+    HEOM_OK = 0,
+    HEOM_EINVAL = 1,      /* invalid argument (message says which)                      */
+    HEOM_ENOMEM = 2,      /* host or device allocation failed                           */
+    HEOM_ECUDA = 3,       /* CUDA runtime error, or no usable device                    */
+    HEOM_ENOCONV = 4,     /* a solver reached max_iter; stats hold the last residual    */
+    HEOM_EBREAKDOWN = 5,  /* Krylov breakdown or a non-finite value in a solver         */
+    HEOM_ENOTSUP = 6      /* valid request this build does not implement               */
+} heom_status;
+
+/* Kinds of exponent lists (one per bath). Results: Eqs. C_beta_RI and C_beta_u; D_j. */
+typedef enum {
+    HEOM_BOSON_R = 0,   /* real part:       D X = c [V, X]                             */
+    HEOM_BOSON_I = 1,   /* imaginary part:  D X = i c {V, X}                           */
+    HEOM_BOSON_RI = 2,  /* both, real rates: D X = Re(c) [V, X] + i Im(c) {V, X}       */
+    HEOM_FERMION = 3    /* fermionic: A_q, C_q with eta = coef, gamma = rate            */
+} heom_kind;
+
+/* Arithmetic of a call. */
+typedef enum {
+    HEOM_FP64 = 0,   /* complex FP64 throughout (the plain path)                       */
+    HEOM_FP32 = 1,   /* complex FP32 storage and arithmetic                            */
+    HEOM_MIXED = 2   /* solvers: FP32 inner Krylov solves inside FP64 iterative
+                        refinement; FP64 residuals, dot products and normalisation      */
+} heom_prec;
+
+/* One bath = one coupling operator + its exponent list (Fig. 1b). */
+typedef struct {
+    int kind;               /* heom_kind                                                */
+    const heom_c64 *op;     /* d x d: V (bosonic, Hermitian) or d (fermionic annihilator) */
+    int n_exp;              /* number of exponents of this bath                         */
+    const heom_c64 *coef;   /* bosonic: c (R / I) or xi (RI); fermionic: eta             */
+    const heom_c64 *rate;   /* bosonic chi, fermionic gamma                              */
+    const int *nu;          /* fermionic only: +1 (d^dagger) / -1 (d) per exponent       */
+    const int *partner;     /* fermionic only: index within this bath of the exponent
+                               with the same (alpha, h, sigma) and opposite nu; must be an
+                               involution that flips nu                                  */
+} heom_bath;
+
+/* Per-solve statistics (one per batch column). */
+typedef struct {
+    int iterations;    /* Krylov iterations (inner ones summed over refinement sweeps) */
+    int refinements;   /* FP64 refinement sweeps (0 for HEOM_FP64 / HEOM_FP32)          */
+    double residual;   /* final FP64 residual, as defined by the solver                */
+    int status;        /* heom_status of this column                                   */
+} heom_solve_stats;
+
+/* ---------------------------------------------------------------- exponents (host) */
+
+/* Pade ([N-1/N], pade = 1) or Matsubara (pade = 0) constants of the Fermi (fermi = 1) or
+ * Bose (fermi = 0) function: 1/(e^x+1) ~ 1/2 - sum_j 2 kappa_j x/(x^2+zeta_j^2) and
+ * 1/(e^x-1) ~ 1/x - 1/2 + sum_j 2 kappa_j x/(x^2+zeta_j^2) (Methods, the two Pade forms;
+ * the constants are from the Pade spectrum decomposition the paper cites). kappa, zeta:
+ * caller arrays of n_poles doubles. n_poles in [0, 2000]. */
+heom_status heom_pade_constants(int n_poles, int fermi, int pade, double *kappa, double *zeta);
+
+/* Drude-Lorentz bosonic bath J(w) = 4 lam W w / (w^2 + W^2) (Methods, Eq. Drude-Lorentz):
+ * xi_1 = lam W [cot(W/2kT) - i], chi_1 = W; xi_l = -2 kappa_l kT 2 lam W zeta_l kT /
+ * (W^2 - (zeta_l kT)^2), chi_l = zeta_l kT. Writes n_poles+1 entries to xi and chi (RI
+ * kind exponents). kT > 0, W > 0. */
+heom_status heom_exp_drude_lorentz(double lam, double W, double kT, int n_poles, int pade,
+                                   heom_c64 *xi, heom_c64 *chi);
+
+/* Lorentzian fermionic lead J(w) = Gamma W^2/((w-mu)^2 + W^2) (Methods, Eq. Lorentz):
+ * eta_1 = (Gamma W/2) n(iW/kT) with n the Pade (or Matsubara) Fermi function,
+ * gamma_1 = W - nu i mu; eta_h = -i kappa_h kT Gamma W^2/(W^2 - (zeta_h kT)^2),
+ * gamma_h = zeta_h kT - nu i mu. Writes n_poles+1 entries to eta and gamma. nu = +1 | -1. */
+heom_status heom_exp_lorentz_fermion(double Gamma, double W, double mu, double kT,
+                                     int n_poles, int pade, int nu,
+                                     heom_c64 *eta, heom_c64 *gamma);
+
+/* ---------------------------------------------------------------- hierarchy */
+
+/* Enumerate the ADOs (Eq. HEOM multi-indices, Pauli exclusion for fermions, truncation at
+ * tier_b / tier_f), build the neighbour and sign tables of M for parity p = +1 (even) or
+ * -1 (odd), and copy tables, operators and coefficients to the current CUDA device.
+ * H: d x d Hermitian system Hamiltonian. flags: 0. On success *out owns everything.
+ * Errors: HEOM_EINVAL for d < 1, tiers < 0, non-finite inputs, a non-involutive partner
+ * map, nu not +-1, more than 64 fermionic exponents; HEOM_ENOMEM; HEOM_ECUDA. */
+heom_status heom_build_hierarchy(int d, const heom_c64 *H, int n_baths, const heom_bath *baths,
+                                 int tier_b, int tier_f, int parity, int flags,
+                                 heom_hier **out);
+
+/* Replace the parameter sets of a hierarchy by n_sets sets that share its structure
+ * (operators, exponent kinds, nu, partner map, tiers) and differ in H and in the
+ * exponent values: H [n_sets][d][d], coef [n_sets][K], rate [n_sets][K] with K = K_b + K_f
+ * in the global exponent order. Batch column b of every later call then uses parameter
+ * set b / (batch / n_sets); batch must be a multiple of n_sets. */
+heom_status heom_set_params(heom_hier *h, int n_sets, const heom_c64 *H,
+                            const heom_c64 *coef, const heom_c64 *rate);
+
+/* Sizes: number of ADOs, system dimension, bosonic / fermionic exponent counts, number of
+ * parameter sets, number of neighbour-table entries. Any pointer may be NULL. */
+heom_status heom_hier_info(const heom_hier *h, int64_t *n_ado, int *d, int *k_b, int *k_f,
+                           int *n_sets, int64_t *n_entries);
+
+/* Hierarchy dictionary (Fig. 1e). occ: K_b bosonic occupations then K_f fermionic 0/1
+ * occupations. heom_ado_index returns -1 in *idx for a multi-index outside the hierarchy. */
+heom_status heom_ado_index(const heom_hier *h, const int *occ, int64_t *idx);
+heom_status heom_ado_label(const heom_hier *h, int64_t idx, int *occ_out);
+
+/* Export the neighbour and sign tables (host copies, for inspection and tests).
+ * For ADO i the entries row_ptr[i] .. row_ptr[i+1]-1 each describe one term of Eq. HEOM:
+ *   (M X)_i += -i ( mult_l * a * O X_nb  +  mult_r * b * X_nb O )
+ * with exponent k, dir = +1 when X_nb is the ADO raised in k (A or B term: a = b = 1,
+ * O = V_k or d_k^{-nu_k}) and dir = -1 when it is lowered in k (D or C term: bosonic
+ * (a, b) = (c, c) | (ic, -ic) | (xi, xi^*) for kinds R | I | RI, O = V_k; fermionic
+ * a = eta_k, b = conj(eta_partner(k)), O = d_k^{nu_k}). The integers carry the tier
+ * multiplicity m_k, the parity sign (-1)^{delta_{p,-}}, the ordering sign
+ * (-1)^{#{r in S : r < k}} and the P_s sign p (-1)^n. Arrays: row_ptr [N+1]; nb, k, dir,
+ * mult_l, mult_r [n_entries]. */
+heom_status heom_export_tables(const heom_hier *h, int32_t *row_ptr, int32_t *nb, int32_t *k,
+                               int32_t *dir, int32_t *mult_l, int32_t *mult_r);
+
+void heom_destroy(heom_hier *h);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char *heom_last_error(void);
+
+/* ---------------------------------------------------------------- apply (the hot path) */
+
+/* y = M x for every batch column (Eq. HEOM right-hand side), matrix-free.
+ * x, y: device ADO vectors [N][d][d][batch], complex128 (prec = HEOM_FP64) or complex64
+ * (prec = HEOM_FP32); must not overlap. batch >= 1 and a multiple of n_sets.
+ * Enqueued on stream s; returns without synchronising. */
+heom_status heom_apply(const heom_hier *h, const void *x, void *y, int64_t batch, int prec,
+                       heom_stream s);
+
+/* ---------------------------------------------------------------- solvers */
+
+/* RK4 time evolution d/dt x = M x (fixed step dt, n_steps steps) of every batch column.
+ * ados: device ADO vector, in: state at t0, out: state at t0 + n_steps dt, complex128
+ * (HEOM_FP64) or complex64 (HEOM_FP32). If rho_traj is not NULL it receives the tier-0
+ * block (rho_sys, all batch columns) at steps 0, save_every, 2 save_every, ...:
+ * n_steps / save_every + 1 device blocks of [d][d][batch], same precision as ados.
+ * Library workspace is allocated on first use and kept in h. Synchronises s. */
+heom_status heom_evolve(heom_hier *h, void *ados, int64_t batch, double dt, int64_t n_steps,
+                        int64_t save_every, void *rho_traj, int prec, heom_stream s);
+
+/* Stationary state of every batch column: M x = 0 with Tr rho_sys = 1 (package
+ * architecture: stationary states by a linear solve; the trace condition is added to the
+ * (0,0) equation of the tier-0 ADO, which M leaves redundant because it preserves the
+ * trace). x0: optional device warm start (complex128, NULL for a cold start). x_out:
+ * device complex128 [N][d][d][batch]. Converged when ||M x||_2 / ||x||_2 <= tol for x
+ * normalised to Tr rho_sys = 1. prec: HEOM_FP64 (plain FP64 BiCGStab) or HEOM_MIXED
+ * (FP32 BiCGStab corrections inside FP64 iterative refinement). stats: host array of
+ * batch entries or NULL. Returns HEOM_ENOCONV if any column missed tol within max_iter
+ * Krylov iterations. Synchronises s. */
+heom_status heom_steady(heom_hier *h, const void *x0, void *x_out, int64_t batch, double tol,
+                        int max_iter, int prec, heom_solve_stats *stats, heom_stream s);
+
+/* Density of states of the fermionic mode op_d (Methods, numerical computation of the
+ * spectrum): for every omega, (M + i w) x_+ = d^dag rho and (M - i w) x_- = d rho with M
+ * of the odd-parity hierarchy `odd` and b built from every ADO of the even stationary
+ * state ss_ados (device complex128 [N][d][d], batch 1); pi A(w) = -Re{Tr[d x_+,0] +
+ * Tr[d^dag x_-,0]}. op_d: host d x d. omega: host [n_omega]; A_out: host [n_omega].
+ * Converged when ||b - (M -+ i w) x|| / ||b|| <= tol. prec as for heom_steady.
+ * stats: host array of 2*n_omega entries (x_+ then x_-) or NULL. Synchronises s. */
+heom_status heom_spectrum(heom_hier *odd, const void *ss_ados, const heom_c64 *op_d,
+                          const double *omega, int64_t n_omega, double tol, int max_iter,
+                          double *A_out, int prec, heom_solve_stats *stats, heom_stream s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HEOM_H */

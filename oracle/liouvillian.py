@@ -71,14 +71,20 @@ def damping(m, S, bos, fer) -> complex:
 # --------------------------------------------------------------------------------------
 
 
-def apply_loop(problem: dict, X: np.ndarray, hier=None) -> np.ndarray:
-    """Y = M X computed ADO by ADO from Eq. HEOM (target-ADO view)."""
+def apply_loop(problem: dict, X: np.ndarray, hier=None, only=None) -> np.ndarray:
+    """Y = M X computed ADO by ADO from Eq. HEOM (target-ADO view).
+
+    ``only``: optional list of ADO indices; then only those blocks of Y are computed (the
+    others stay zero), which lets a test sample very large hierarchies.
+    """
     H = problem["H"]
     p = problem["parity"]
     bos, fer = flatten_exponents(problem)
     hier = hier or problem_hierarchy(problem)
     Y = np.zeros_like(X)
-    for i, (m, S) in enumerate(hier.ados):
+    targets = range(hier.n_ado) if only is None else only
+    for i in targets:
+        m, S = hier.ados[i]
         n = len(S)
         X0 = X[i]
         acc = -1j * (H @ X0 - X0 @ H) - damping(m, S, bos, fer) * X0

@@ -1,0 +1,316 @@
+"""Python binding of libheom.so: argument marshalling only.
+
+Every function here forwards to the C ABI declared in ``include/heom.h`` under the same
+name (without the ``heom_`` prefix). Device buffers are torch tensors (PyTorch supplies
+device memory and streams); every step of the HEOM path runs in the library's CUDA kernels.
+There is no fallback: if ``libheom.so`` is missing or fails to load, importing this package
+raises, and every device entry point needs a CUDA device.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIBRARY_PATH = os.path.join(_HERE, "libheom.so")
+
+if not os.path.exists(LIBRARY_PATH):
+    raise ImportError(f"libheom.so is not built ({LIBRARY_PATH}); run "
+                      "`python -m paper_2306_07522_gb300.build` or __graft_entry__.build()")
+_lib = C.CDLL(LIBRARY_PATH)
+
+# ------------------------------------------------------------------------- ABI types
+OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EBREAKDOWN, ENOTSUP = range(7)
+BOSON_R, BOSON_I, BOSON_RI, FERMION = range(4)
+FP64, FP32, MIXED = range(3)
+KIND = {"R": BOSON_R, "I": BOSON_I, "RI": BOSON_RI, "F": FERMION}
+STATUS_NAMES = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA",
+                ENOCONV: "ENOCONV", EBREAKDOWN: "EBREAKDOWN", ENOTSUP: "ENOTSUP"}
+
+
+class c64(C.Structure):
+    _fields_ = [("re", C.c_double), ("im", C.c_double)]
+
+
+class Bath(C.Structure):
+    _fields_ = [("kind", C.c_int), ("op", C.POINTER(c64)), ("n_exp", C.c_int),
+                ("coef", C.POINTER(c64)), ("rate", C.POINTER(c64)),
+                ("nu", C.POINTER(C.c_int)), ("partner", C.POINTER(C.c_int))]
+
+
+class SolveStats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("refinements", C.c_int), ("residual", C.c_double),
+                ("status", C.c_int)]
+
+
+class HeomError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib.heom_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+
+
+_P = C.c_void_p
+_sig = {
+    "heom_pade_constants": [C.c_int, C.c_int, C.c_int, _P, _P],
+    "heom_exp_drude_lorentz": [C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, _P, _P],
+    "heom_exp_lorentz_fermion": [C.c_double, C.c_double, C.c_double, C.c_double, C.c_int,
+                                 C.c_int, C.c_int, _P, _P],
+    "heom_build_hierarchy": [C.c_int, _P, C.c_int, _P, C.c_int, C.c_int, C.c_int, C.c_int,
+                             C.POINTER(_P)],
+    "heom_set_params": [_P, C.c_int, _P, _P, _P],
+    "heom_hier_info": [_P, _P, _P, _P, _P, _P, _P],
+    "heom_ado_index": [_P, _P, _P],
+    "heom_ado_label": [_P, C.c_int64, _P],
+    "heom_export_tables": [_P, _P, _P, _P, _P, _P, _P],
+    "heom_apply": [_P, _P, _P, C.c_int64, C.c_int, _P],
+    "heom_evolve": [_P, _P, C.c_int64, C.c_double, C.c_int64, C.c_int64, _P, C.c_int, _P],
+    "heom_steady": [_P, _P, _P, C.c_int64, C.c_double, C.c_int, C.c_int, _P, _P],
+    "heom_spectrum": [_P, _P, _P, _P, C.c_int64, C.c_double, C.c_int, _P, C.c_int, _P, _P],
+}
+EXPORTED = sorted(list(_sig) + ["heom_destroy", "heom_last_error"])
+for _name, _args in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = C.c_int
+_lib.heom_destroy.argtypes = [_P]
+_lib.heom_destroy.restype = None
+_lib.heom_last_error.argtypes = []
+_lib.heom_last_error.restype = C.c_char_p
+
+
+def _check(status: int, where: str) -> int:
+    if status != OK:
+        raise HeomError(status, where)
+    return status
+
+
+def _c64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.complex128))
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _stream(stream=None):
+    if stream is not None:
+        return C.c_void_p(int(stream))
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------------------- exponents
+def pade_constants(n_poles: int, fermi: bool = True, pade: bool = True):
+    kappa = np.zeros(max(n_poles, 1))
+    zeta = np.zeros(max(n_poles, 1))
+    _check(_lib.heom_pade_constants(n_poles, int(fermi), int(pade), _ptr(kappa), _ptr(zeta)),
+           "heom_pade_constants")
+    return kappa[:n_poles], zeta[:n_poles]
+
+
+def exp_drude_lorentz(lam, W, kT, n_poles, pade=True):
+    xi = np.zeros(n_poles + 1, np.complex128)
+    chi = np.zeros(n_poles + 1, np.complex128)
+    _check(_lib.heom_exp_drude_lorentz(lam, W, kT, n_poles, int(pade), _ptr(xi), _ptr(chi)),
+           "heom_exp_drude_lorentz")
+    return xi, chi
+
+
+def exp_lorentz_fermion(Gamma, W, mu, kT, n_poles, pade=True, nu=1):
+    eta = np.zeros(n_poles + 1, np.complex128)
+    gam = np.zeros(n_poles + 1, np.complex128)
+    _check(_lib.heom_exp_lorentz_fermion(Gamma, W, mu, kT, n_poles, int(pade), nu, _ptr(eta),
+                                         _ptr(gam)), "heom_exp_lorentz_fermion")
+    return eta, gam
+
+
+def problem_from_model(model, parity: int = 1) -> dict:
+    """Raw problem (bath list with exponents) of a physical model, exponents from the library."""
+    baths = []
+    for V, p in model.boson_baths:
+        xi, chi = exp_drude_lorentz(p.lam, p.W, p.kT, p.n_poles, p.method == "pade")
+        baths.append(dict(kind="RI", op=_c64(V), coef=xi, rate=chi))
+    for dop, p in model.fermion_baths:
+        ep, gp = exp_lorentz_fermion(p.Gamma, p.W, p.mu, p.kT, p.n_poles, p.method == "pade", 1)
+        em, gm = exp_lorentz_fermion(p.Gamma, p.W, p.mu, p.kT, p.n_poles, p.method == "pade", -1)
+        h = len(ep)
+        baths.append(dict(kind="F", op=_c64(dop), coef=np.concatenate([ep, em]),
+                          rate=np.concatenate([gp, gm]),
+                          nu=np.array([1] * h + [-1] * h, np.int32),
+                          partner=np.array(list(range(h, 2 * h)) + list(range(h)), np.int32)))
+    return dict(d=model.d, H=_c64(model.H), baths=baths, tier_b=model.tier_b,
+                tier_f=model.tier_f, parity=parity)
+
+
+# ------------------------------------------------------------------------- hierarchy
+class Hierarchy:
+    """Owner of a ``heom_hier*`` (freed by ``heom_destroy`` when collected)."""
+
+    def __init__(self, handle, keep):
+        self._h = handle
+        self._keep = keep
+        n_ado, d, kb, kf, ns, ne = C.c_int64(), C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_int64()
+        _check(_lib.heom_hier_info(self._h, C.byref(n_ado), C.byref(d), C.byref(kb), C.byref(kf),
+                                   C.byref(ns), C.byref(ne)), "heom_hier_info")
+        self.n_ado, self.d, self.k_b, self.k_f = n_ado.value, d.value, kb.value, kf.value
+        self.n_sets, self.n_entries = ns.value, ne.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def refresh(self):
+        self.__init__(self._h, self._keep)
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _lib.heom_destroy(self._h)
+            self._h = None
+
+
+def build_hierarchy(problem: dict) -> Hierarchy:
+    d = int(problem["d"])
+    H = _c64(problem["H"])
+    keep = [H]
+    arr = (Bath * max(len(problem["baths"]), 1))()
+    for i, b in enumerate(problem["baths"]):
+        op = _c64(b["op"])
+        coef = _c64(b["coef"])
+        rate = _c64(b["rate"])
+        keep += [op, coef, rate]
+        arr[i].kind = KIND[b["kind"]]
+        arr[i].op = op.ctypes.data_as(C.POINTER(c64))
+        arr[i].n_exp = len(coef)
+        arr[i].coef = coef.ctypes.data_as(C.POINTER(c64))
+        arr[i].rate = rate.ctypes.data_as(C.POINTER(c64))
+        if b["kind"] == "F":
+            nu = np.ascontiguousarray(b["nu"], np.int32)
+            partner = np.ascontiguousarray(b["partner"], np.int32)
+            keep += [nu, partner]
+            arr[i].nu = nu.ctypes.data_as(C.POINTER(C.c_int))
+            arr[i].partner = partner.ctypes.data_as(C.POINTER(C.c_int))
+    out = C.c_void_p()
+    _check(_lib.heom_build_hierarchy(d, _ptr(H), len(problem["baths"]), C.cast(arr, C.c_void_p),
+                                     int(problem["tier_b"]), int(problem["tier_f"]),
+                                     int(problem.get("parity", 1)), 0, C.byref(out)),
+           "heom_build_hierarchy")
+    return Hierarchy(out, None)
+
+
+def set_params(h: Hierarchy, H, coef, rate):
+    """H [n_sets, d, d], coef / rate [n_sets, K] in the global exponent order."""
+    H = _c64(H)
+    coef = _c64(coef)
+    rate = _c64(rate)
+    n_sets = H.shape[0]
+    _check(_lib.heom_set_params(h.handle, n_sets, _ptr(H), _ptr(coef), _ptr(rate)),
+           "heom_set_params")
+    h.refresh()
+
+
+def ado_index(h: Hierarchy, occ) -> int:
+    occ = np.ascontiguousarray(occ, np.int32)
+    idx = C.c_int64()
+    _check(_lib.heom_ado_index(h.handle, _ptr(occ), C.byref(idx)), "heom_ado_index")
+    return idx.value
+
+
+def ado_label(h: Hierarchy, idx: int) -> np.ndarray:
+    out = np.zeros(h.k_b + h.k_f, np.int32)
+    _check(_lib.heom_ado_label(h.handle, idx, _ptr(out)), "heom_ado_label")
+    return out
+
+
+def export_tables(h: Hierarchy) -> dict:
+    E = h.n_entries
+    row_ptr = np.zeros(h.n_ado + 1, np.int32)
+    cols = {k: np.zeros(max(E, 1), np.int32) for k in ("nb", "k", "dir", "mult_l", "mult_r")}
+    _check(_lib.heom_export_tables(h.handle, _ptr(row_ptr), *[_ptr(cols[k]) for k in
+                                                              ("nb", "k", "dir", "mult_l", "mult_r")]),
+           "heom_export_tables")
+    out = {k: v[:E] for k, v in cols.items()}
+    out["row_ptr"] = row_ptr
+    return out
+
+
+# ------------------------------------------------------------------------- device calls
+def _prec_of(t) -> int:
+    import torch
+    if t.dtype == torch.complex128:
+        return FP64
+    if t.dtype == torch.complex64:
+        return FP32
+    raise TypeError("ADO vectors must be complex128 or complex64 tensors")
+
+
+def _batch_of(h: Hierarchy, t) -> int:
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("ADO vectors must be contiguous CUDA tensors")
+    if t.dim() == 3:
+        return 1
+    if t.dim() == 4:
+        return t.shape[3]
+    raise ValueError("ADO vector shape must be (N, d, d) or (N, d, d, batch)")
+
+
+def apply(h: Hierarchy, x, y, stream=None):
+    """y = M x (x, y: CUDA complex tensors (N, d, d[, batch]), same dtype)."""
+    prec = _prec_of(x)
+    if y.dtype != x.dtype or y.shape != x.shape:
+        raise ValueError("x and y must have the same shape and dtype")
+    _check(_lib.heom_apply(h.handle, _dptr(x), _dptr(y), _batch_of(h, x), prec, _stream(stream)),
+           "heom_apply")
+    return y
+
+
+def evolve(h: Hierarchy, ados, dt: float, n_steps: int, save_every: int = 0, stream=None):
+    """RK4 in place on ``ados``; returns the rho_sys snapshots (n_saves, d, d[, batch]) or None."""
+    import torch
+    prec = _prec_of(ados)
+    B = _batch_of(h, ados)
+    traj = None
+    if save_every:
+        shape = (n_steps // save_every + 1, h.d, h.d) + ((B,) if ados.dim() == 4 else ())
+        traj = torch.empty(shape, dtype=ados.dtype, device=ados.device)
+    _check(_lib.heom_evolve(h.handle, _dptr(ados), B, dt, n_steps, max(save_every, 1),
+                            _dptr(traj) if traj is not None else None, prec, _stream(stream)),
+           "heom_evolve")
+    return traj
+
+
+def _stats_list(arr):
+    return [dict(iterations=s.iterations, refinements=s.refinements, residual=s.residual,
+                 status=s.status) for s in arr]
+
+
+def steady(h: Hierarchy, x_out, x0=None, tol: float = 1e-8, max_iter: int = 2000,
+           prec: int = MIXED, stream=None, raise_on_error: bool = True):
+    """Stationary state into x_out (complex128). Returns (status, per-column stats)."""
+    B = _batch_of(h, x_out)
+    stats = (SolveStats * B)()
+    st = _lib.heom_steady(h.handle, _dptr(x0) if x0 is not None else None, _dptr(x_out), B, tol,
+                          max_iter, prec, C.cast(stats, C.c_void_p), _stream(stream))
+    if raise_on_error:
+        _check(st, "heom_steady")
+    return st, _stats_list(stats)
+
+
+def spectrum(odd: Hierarchy, ss, op_d, omegas, tol: float = 1e-8, max_iter: int = 2000,
+             prec: int = MIXED, stream=None, raise_on_error: bool = True):
+    """Density of states A(w) of mode op_d; returns (A, status, stats of x_+ then x_-)."""
+    op = _c64(op_d)
+    om = np.ascontiguousarray(omegas, np.float64)
+    A = np.zeros(len(om))
+    stats = (SolveStats * (2 * len(om)))()
+    st = _lib.heom_spectrum(odd.handle, _dptr(ss), _ptr(op), _ptr(om), len(om), tol, max_iter,
+                            _ptr(A), prec, C.cast(stats, C.c_void_p), _stream(stream))
+    if raise_on_error:
+        _check(st, "heom_spectrum")
+    return A, st, _stats_list(stats)

@@ -1,0 +1,685 @@
+// Host side of libheom: exponent helpers, ADO enumeration, neighbour/sign tables, device
+// upload, the hierarchy dictionary and error reporting.
+//
+// Paper passages: Eq. HEOM and its multi-index notation (which ADO couples to which, with
+// which sign), the definitions of A, B, C, D and P_s below it; Methods (exponents of the
+// Lorentzian and Drude-Lorentz baths). The enumeration here is combinatorial ranking
+// (compositions for bosons, the combinatorial number system for fermionic subsets), so a
+// neighbour's index is computed, not looked up.
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <new>
+
+#include "heom_internal.h"
+
+using heom::cx;
+using heom::DBuf;
+using heom::NbEntry;
+using heom::OccEntry;
+
+namespace heom {
+
+static thread_local std::string g_err;
+
+void set_error(const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+heom_status cuda_fail(cudaError_t e, const char *what) {
+    set_error("CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
+    return HEOM_ECUDA;
+}
+
+heom_status dalloc(DBuf &b, size_t bytes) {
+    dfree(b);
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        set_error("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? HEOM_ENOMEM : HEOM_ECUDA;
+    }
+    b.bytes = bytes;
+    return HEOM_OK;
+}
+
+void dfree(DBuf &b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+heom_status ensure_ws(DBuf &b, size_t bytes) {
+    if (b.bytes >= bytes && b.p) return HEOM_OK;
+    return dalloc(b, bytes);
+}
+
+}  // namespace heom
+
+using heom::set_error;
+
+// ======================================================================= exponents
+namespace {
+
+// Number of eigenvalues smaller than x of the symmetric tridiagonal matrix with zero
+// diagonal and off-diagonal b (Sturm sequence of the LDL^T pivots).
+int sturm_count(const std::vector<double> &b, double x) {
+    int n = (int)b.size() + 1, cnt = 0;
+    double q = -x;
+    if (q < 0) cnt++;
+    for (int i = 1; i < n; ++i) {
+        double prev = (q == 0.0) ? 1e-300 : q;
+        q = -x - b[i - 1] * b[i - 1] / prev;
+        if (q < 0) cnt++;
+    }
+    return cnt;
+}
+
+// The m largest eigenvalues, descending, by bisection (all eigenvalues lie in [-2max|b|, 2max|b|]).
+std::vector<double> top_eigs(const std::vector<double> &b, int m) {
+    int n = (int)b.size() + 1;
+    double bound = 0;
+    for (double v : b) bound = std::max(bound, 2.0 * std::fabs(v));
+    bound += 1e-12;
+    std::vector<double> out;
+    for (int j = 0; j < m; ++j) {
+        // eigenvalue of rank n-1-j (0-based ascending): smallest x with count(x) >= n-j
+        int target = n - j;
+        double lo = -bound, hi = bound;
+        for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(1.0, std::fabs(hi)); ++it) {
+            double mid = 0.5 * (lo + hi);
+            if (sturm_count(b, mid) >= target) hi = mid; else lo = mid;
+        }
+        out.push_back(0.5 * (lo + hi));
+    }
+    return out;
+}
+
+void decomposition(int N, bool fermi, bool pade, std::vector<double> &kappa,
+                   std::vector<double> &zeta) {
+    kappa.assign(N, 1.0);
+    zeta.assign(N, 0.0);
+    if (N == 0) return;
+    if (!pade) {  // Matsubara poles
+        for (int j = 1; j <= N; ++j) zeta[j - 1] = fermi ? (2 * j - 1) * M_PI : 2 * M_PI * j;
+        return;
+    }
+    auto bm = [fermi](int m) { return fermi ? 2.0 * m - 1.0 : 2.0 * m + 1.0; };
+    std::vector<double> off(2 * N - 1), off_t(std::max(0, 2 * N - 2));
+    for (int m = 1; m < 2 * N; ++m) off[m - 1] = 1.0 / std::sqrt(bm(m) * bm(m + 1));
+    for (int m = 1; m < 2 * N - 1; ++m) off_t[m - 1] = 1.0 / std::sqrt(bm(m + 1) * bm(m + 2));
+    std::vector<double> lam = top_eigs(off, N);
+    std::vector<double> lt = N > 1 ? top_eigs(off_t, N - 1) : std::vector<double>();
+    for (int j = 0; j < N; ++j) zeta[j] = 2.0 / lam[j];
+    for (int j = 0; j < N; ++j) {
+        double num = 1.0, den = 1.0;
+        for (double l : lt) {
+            double z = 2.0 / l;
+            num *= z * z - zeta[j] * zeta[j];
+        }
+        for (int k = 0; k < N; ++k)
+            if (k != j) den *= zeta[k] * zeta[k] - zeta[j] * zeta[j];
+        kappa[j] = 0.5 * N * bm(N + 1) * num / den;
+    }
+}
+
+}  // namespace
+
+extern "C" heom_status heom_pade_constants(int n_poles, int fermi, int pade, double *kappa,
+                                           double *zeta) {
+    if (n_poles < 0 || n_poles > 2000 || (n_poles > 0 && (!kappa || !zeta))) {
+        set_error("heom_pade_constants: n_poles must be in [0, 2000] with output arrays");
+        return HEOM_EINVAL;
+    }
+    std::vector<double> k, z;
+    decomposition(n_poles, fermi != 0, pade != 0, k, z);
+    for (int j = 0; j < n_poles; ++j) { kappa[j] = k[j]; zeta[j] = z[j]; }
+    return HEOM_OK;
+}
+
+extern "C" heom_status heom_exp_drude_lorentz(double lam, double W, double kT, int n_poles,
+                                              int pade, heom_c64 *xi, heom_c64 *chi) {
+    if (!(kT > 0) || !(W > 0) || !std::isfinite(lam) || n_poles < 0 || n_poles > 2000 || !xi ||
+        !chi) {
+        set_error("heom_exp_drude_lorentz: need kT > 0, W > 0, finite lam, n_poles in [0,2000]");
+        return HEOM_EINVAL;
+    }
+    std::vector<double> kap, zet;
+    decomposition(n_poles, false, pade != 0, kap, zet);
+    xi[0] = {lam * W / std::tan(W / (2.0 * kT)), -lam * W};
+    chi[0] = {W, 0.0};
+    for (int l = 0; l < n_poles; ++l) {
+        double zk = zet[l] * kT;
+        xi[l + 1] = {-2.0 * kap[l] * kT * 2.0 * lam * W * zk / (W * W - zk * zk), 0.0};
+        chi[l + 1] = {zk, 0.0};
+    }
+    return HEOM_OK;
+}
+
+extern "C" heom_status heom_exp_lorentz_fermion(double Gamma, double W, double mu, double kT,
+                                                int n_poles, int pade, int nu, heom_c64 *eta,
+                                                heom_c64 *gamma) {
+    if (!(kT > 0) || !(W > 0) || !std::isfinite(Gamma) || !std::isfinite(mu) || n_poles < 0 ||
+        n_poles > 2000 || (nu != 1 && nu != -1) || !eta || !gamma) {
+        set_error("heom_exp_lorentz_fermion: need kT > 0, W > 0, finite Gamma/mu, nu = +-1");
+        return HEOM_EINVAL;
+    }
+    std::vector<double> kap, zet;
+    decomposition(n_poles, true, pade != 0, kap, zet);
+    // n(x) at x = i W / kT of the truncated Fermi function 1/2 - sum 2 kappa x/(x^2+zeta^2)
+    std::complex<double> x(0.0, W / kT), n(0.5, 0.0);
+    for (int h = 0; h < n_poles; ++h) n -= 2.0 * kap[h] * x / (x * x + zet[h] * zet[h]);
+    std::complex<double> e1 = 0.5 * Gamma * W * n;
+    eta[0] = {e1.real(), e1.imag()};
+    gamma[0] = {W, -nu * mu};
+    for (int h = 0; h < n_poles; ++h) {
+        double zk = zet[h] * kT;
+        eta[h + 1] = {0.0, -kap[h] * kT * Gamma * W * W / (W * W - zk * zk)};
+        gamma[h + 1] = {zk, -nu * mu};
+    }
+    return HEOM_OK;
+}
+
+// ======================================================================= enumeration
+namespace {
+
+uint64_t binom(int n, int k) {
+    if (k < 0 || n < 0 || k > n) return 0;
+    k = std::min(k, n - k);
+    unsigned __int128 r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (unsigned __int128)(n - k + i) / i;
+    return (uint64_t)r;
+}
+
+// compositions of s into p >= 1 non-negative parts
+uint64_t ncomp(int s, int p) { return p <= 0 ? (s == 0) : binom(s + p - 1, p - 1); }
+
+struct Ranker {
+    int Kb, Kf, tb, tf;
+    std::vector<uint64_t> bos_off;  // bos_off[t] = # bosonic vectors of tier < t
+    std::vector<uint64_t> fer_off;  // fer_off[n] = # fermionic subsets of size < n
+    uint64_t Nb = 0, Nf = 0;
+
+    void init(int Kb_, int Kf_, int tb_, int tf_) {
+        Kb = Kb_; Kf = Kf_; tb = Kb_ > 0 ? tb_ : 0; tf = std::min(tf_, Kf_);
+        bos_off.assign(tb + 2, 0);
+        for (int t = 0; t <= tb; ++t) bos_off[t + 1] = bos_off[t] + (Kb > 0 ? ncomp(t, Kb) : (t == 0));
+        Nb = bos_off[tb + 1];
+        fer_off.assign(tf + 2, 0);
+        for (int n = 0; n <= tf; ++n) fer_off[n + 1] = fer_off[n] + binom(Kf, n);
+        Nf = fer_off[tf + 1];
+    }
+    // rank of m among all bosonic vectors (tier ascending, lex descending inside a tier)
+    int64_t rank_bos(const int *m) const {
+        int t = 0;
+        for (int i = 0; i < Kb; ++i) t += m[i];
+        if (t > tb) return -1;
+        uint64_t cnt = 0;
+        int rem = t;
+        for (int i = 0; i + 1 < Kb; ++i) {
+            for (int v = m[i] + 1; v <= rem; ++v) cnt += ncomp(rem - v, Kb - 1 - i);
+            rem -= m[i];
+        }
+        return (int64_t)(bos_off[t] + cnt);
+    }
+    // rank of the subset with bit mask S (size ascending, lex ascending inside a size)
+    int64_t rank_fer(uint64_t S) const {
+        int n = __builtin_popcountll(S);
+        if (n > tf) return -1;
+        uint64_t r = binom(Kf, n) - 1;
+        int i = 0;
+        for (int c = 0; c < Kf; ++c)
+            if (S >> c & 1ULL) { r -= binom(Kf - 1 - c, n - i); ++i; }
+        return (int64_t)(fer_off[n] + r);
+    }
+};
+
+// next bosonic vector of the same tier in lex-descending order; false at the end
+bool next_comp(std::vector<int> &m) {
+    int K = (int)m.size();
+    for (int i = K - 2; i >= 0; --i) {
+        if (m[i] > 0) {
+            int tail = 0;
+            for (int j = i + 1; j < K; ++j) { tail += m[j]; m[j] = 0; }
+            m[i] -= 1;
+            m[i + 1] = tail + 1;
+            return true;
+        }
+    }
+    return false;
+}
+
+bool finite(const heom_c64 &z) { return std::isfinite(z.re) && std::isfinite(z.im); }
+
+template <class T>
+heom_status upload(DBuf &b, const std::vector<T> &v) {
+    heom_status st = heom::dalloc(b, v.size() * sizeof(T));
+    if (st != HEOM_OK) return st;
+    if (!v.empty()) HEOM_CUDA(cudaMemcpy(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return HEOM_OK;
+}
+
+template <class R>
+std::vector<cx<R>> to_cx(const std::vector<heom_c64> &v) {
+    std::vector<cx<R>> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) o[i] = cx<R>{R(v[i].re), R(v[i].im)};
+    return o;
+}
+
+// bosonic (a, b) of D X = a V X - b X V for one exponent of the given kind
+void boson_ab(int kind, heom_c64 c, heom_c64 &a, heom_c64 &b) {
+    if (kind == HEOM_BOSON_R) { a = c; b = c; }
+    else if (kind == HEOM_BOSON_I) { a = {-c.im, c.re}; b = {c.im, -c.re}; }
+    else { a = c; b = {c.re, -c.im}; }
+}
+
+}  // namespace
+
+heom::DevView<double> heom_hier::view64() const {
+    heom::DevView<double> v{};
+    v.N = N; v.d = d; v.d2 = d2; v.K = K; v.n_sets = n_sets; v.nnzH = nnzH;
+    v.row_ptr = (const int32_t *)d_row_ptr.p; v.ent = (const NbEntry *)d_ent.p;
+    v.occ_ptr = (const int32_t *)d_occ_ptr.p; v.occ = (const OccEntry *)d_occ.p;
+    v.op_rptr = (const int32_t *)d_op_rptr.p; v.op_rcol = (const int32_t *)d_op_rcol.p;
+    v.op_rval = (const cx<double> *)d_op_rval64.p;
+    v.op_cptr = (const int32_t *)d_op_cptr.p; v.op_crow = (const int32_t *)d_op_crow.p;
+    v.op_cval = (const cx<double> *)d_op_cval64.p;
+    v.h_rptr = (const int32_t *)d_h_rptr.p; v.h_rcol = (const int32_t *)d_h_rcol.p;
+    v.h_rvi = (const int32_t *)d_h_rvi.p; v.h_cptr = (const int32_t *)d_h_cptr.p;
+    v.h_crow = (const int32_t *)d_h_crow.p; v.h_cvi = (const int32_t *)d_h_cvi.p;
+    v.h_val = (const cx<double> *)d_hval64.p;
+    v.coefL = (const cx<double> *)d_coefL64.p; v.coefR = (const cx<double> *)d_coefR64.p;
+    v.rate = (const cx<double> *)d_rate64.p; v.hdiag = (const cx<double> *)d_hdiag64.p;
+    v.floor = (const double *)d_floor64.p;
+    return v;
+}
+
+heom::DevView<float> heom_hier::view32() const {
+    heom::DevView<float> v{};
+    v.N = N; v.d = d; v.d2 = d2; v.K = K; v.n_sets = n_sets; v.nnzH = nnzH;
+    v.row_ptr = (const int32_t *)d_row_ptr.p; v.ent = (const NbEntry *)d_ent.p;
+    v.occ_ptr = (const int32_t *)d_occ_ptr.p; v.occ = (const OccEntry *)d_occ.p;
+    v.op_rptr = (const int32_t *)d_op_rptr.p; v.op_rcol = (const int32_t *)d_op_rcol.p;
+    v.op_rval = (const cx<float> *)d_op_rval32.p;
+    v.op_cptr = (const int32_t *)d_op_cptr.p; v.op_crow = (const int32_t *)d_op_crow.p;
+    v.op_cval = (const cx<float> *)d_op_cval32.p;
+    v.h_rptr = (const int32_t *)d_h_rptr.p; v.h_rcol = (const int32_t *)d_h_rcol.p;
+    v.h_rvi = (const int32_t *)d_h_rvi.p; v.h_cptr = (const int32_t *)d_h_cptr.p;
+    v.h_crow = (const int32_t *)d_h_crow.p; v.h_cvi = (const int32_t *)d_h_cvi.p;
+    v.h_val = (const cx<float> *)d_hval32.p;
+    v.coefL = (const cx<float> *)d_coefL32.p; v.coefR = (const cx<float> *)d_coefR32.p;
+    v.rate = (const cx<float> *)d_rate32.p; v.hdiag = (const cx<float> *)d_hdiag32.p;
+    v.floor = (const float *)d_floor32.p;
+    return v;
+}
+
+namespace {
+
+void free_all(heom_hier *h) {
+    DBuf *bufs[] = {&h->d_row_ptr, &h->d_ent, &h->d_occ_ptr, &h->d_occ, &h->d_op_rptr,
+                    &h->d_op_rcol, &h->d_op_cptr, &h->d_op_crow, &h->d_op_rval64,
+                    &h->d_op_cval64, &h->d_op_rval32, &h->d_op_cval32, &h->d_h_rptr,
+                    &h->d_h_rcol, &h->d_h_rvi, &h->d_h_cptr, &h->d_h_crow, &h->d_h_cvi,
+                    &h->d_hval64, &h->d_hval32, &h->d_coefL64, &h->d_coefL32, &h->d_coefR64,
+                    &h->d_coefR32, &h->d_rate64, &h->d_rate32, &h->d_hdiag64, &h->d_hdiag32,
+                    &h->d_floor64, &h->d_floor32, &h->ws, &h->ws_small};
+    for (DBuf *b : bufs) heom::dfree(*b);
+}
+
+// Upload the parameter-dependent arrays: H values on the shared pattern, (a, b) pairs,
+// rates, H diagonal and the damping floor, for n_sets sets.
+heom_status upload_params(heom_hier *h, int n_sets, const heom_c64 *H, const heom_c64 *coef,
+                          const heom_c64 *rate) {
+    const int d = h->d, K = h->K;
+    // H pattern: union of non-zeros over all sets
+    std::vector<char> nz(d * d, 0);
+    for (int s = 0; s < n_sets; ++s)
+        for (int i = 0; i < d * d; ++i)
+            if (H[s * d * d + i].re != 0.0 || H[s * d * d + i].im != 0.0) nz[i] = 1;
+    std::vector<int32_t> rptr(d + 1, 0), rcol, rvi, cptr(d + 1, 0), crow, cvi;
+    std::vector<int> vidx(d * d, -1);
+    int nnz = 0;
+    for (int r = 0; r < d; ++r) {
+        for (int c = 0; c < d; ++c)
+            if (nz[r * d + c]) { vidx[r * d + c] = nnz; rcol.push_back(c); rvi.push_back(nnz); ++nnz; }
+        rptr[r + 1] = nnz;
+    }
+    int cn = 0;
+    for (int c = 0; c < d; ++c) {
+        for (int r = 0; r < d; ++r)
+            if (nz[r * d + c]) { crow.push_back(r); cvi.push_back(vidx[r * d + c]); ++cn; }
+        cptr[c + 1] = cn;
+    }
+    std::vector<heom_c64> hval((size_t)n_sets * std::max(nnz, 1)), cl((size_t)n_sets * K),
+        cr((size_t)n_sets * K), rt((size_t)n_sets * K), hd((size_t)n_sets * d);
+    std::vector<double> fl(n_sets);
+    for (int s = 0; s < n_sets; ++s) {
+        for (int i = 0; i < d * d; ++i)
+            if (vidx[i] >= 0) hval[(size_t)s * nnz + vidx[i]] = H[(size_t)s * d * d + i];
+        for (int r = 0; r < d; ++r) hd[(size_t)s * d + r] = H[(size_t)s * d * d + r * d + r];
+        double floor = 0;
+        bool first = true;
+        for (int k = 0; k < K; ++k) {
+            heom_c64 c = coef[(size_t)s * K + k];
+            heom_c64 a, b;
+            if (k < h->K_b) {
+                boson_ab(h->exp_kind[k], c, a, b);
+            } else {
+                heom_c64 p = coef[(size_t)s * K + h->exp_partner[k]];
+                a = c;
+                b = {p.re, -p.im};
+            }
+            cl[(size_t)s * K + k] = a;
+            cr[(size_t)s * K + k] = b;
+            rt[(size_t)s * K + k] = rate[(size_t)s * K + k];
+            double re = rate[(size_t)s * K + k].re;
+            if (re > 0 && (first || re < floor)) { floor = re; first = false; }
+        }
+        fl[s] = first ? 1.0 : floor;
+    }
+    std::vector<float> fl32(fl.begin(), fl.end());
+    heom_status st;
+#define UP(buf, vec) if ((st = upload(h->buf, vec)) != HEOM_OK) return st
+    UP(d_h_rptr, rptr); UP(d_h_rcol, rcol); UP(d_h_rvi, rvi);
+    UP(d_h_cptr, cptr); UP(d_h_crow, crow); UP(d_h_cvi, cvi);
+    UP(d_hval64, to_cx<double>(hval)); UP(d_hval32, to_cx<float>(hval));
+    UP(d_coefL64, to_cx<double>(cl)); UP(d_coefL32, to_cx<float>(cl));
+    UP(d_coefR64, to_cx<double>(cr)); UP(d_coefR32, to_cx<float>(cr));
+    UP(d_rate64, to_cx<double>(rt)); UP(d_rate32, to_cx<float>(rt));
+    UP(d_hdiag64, to_cx<double>(hd)); UP(d_hdiag32, to_cx<float>(hd));
+    UP(d_floor64, fl); UP(d_floor32, fl32);
+#undef UP
+    h->nnzH = nnz;
+    h->n_sets = n_sets;
+    h->H0.assign(H, H + (size_t)n_sets * d * d);
+    return HEOM_OK;
+}
+
+}  // namespace
+
+extern "C" heom_status heom_build_hierarchy(int d, const heom_c64 *H, int n_baths,
+                                            const heom_bath *baths, int tier_b, int tier_f,
+                                            int parity, int flags, heom_hier **out) {
+    if (!out) { set_error("heom_build_hierarchy: out is NULL"); return HEOM_EINVAL; }
+    *out = nullptr;
+    if (d < 1 || d > 64 || !H || n_baths < 0 || (n_baths > 0 && !baths) || tier_b < 0 ||
+        tier_f < 0 || (parity != 1 && parity != -1) || flags != 0) {
+        set_error("heom_build_hierarchy: need 1 <= d <= 64, H, tiers >= 0, parity = +-1, flags 0");
+        return HEOM_EINVAL;
+    }
+    for (int i = 0; i < d * d; ++i)
+        if (!finite(H[i])) { set_error("heom_build_hierarchy: H has a non-finite entry"); return HEOM_EINVAL; }
+    heom_hier *h = new (std::nothrow) heom_hier();
+    if (!h) { set_error("heom_build_hierarchy: out of host memory"); return HEOM_ENOMEM; }
+    h->d = d; h->d2 = d * d; h->tier_b = tier_b; h->tier_f = tier_f; h->parity = parity;
+    cudaGetDevice(&h->device);
+
+    // ---- exponents: bosonic first (bath order), then fermionic (bath order)
+    std::vector<heom_c64> coef, rate;
+    std::vector<int> op_slot_of_bath(n_baths, -1);
+    std::vector<int> fer_first_global(n_baths, -1);
+    int n_ops = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int b = 0; b < n_baths; ++b) {
+            const heom_bath &B = baths[b];
+            bool fer = B.kind == HEOM_FERMION;
+            if (B.kind < 0 || B.kind > 3 || B.n_exp < 0 || (B.n_exp > 0 && (!B.coef || !B.rate)) || !B.op) {
+                set_error("heom_build_hierarchy: bath %d: bad kind, n_exp or NULL arrays", b);
+                delete h; return HEOM_EINVAL;
+            }
+            if ((pass == 0) == fer) continue;
+            for (int i = 0; i < d * d; ++i)
+                if (!finite(B.op[i])) { set_error("bath %d: non-finite operator", b); delete h; return HEOM_EINVAL; }
+            op_slot_of_bath[b] = n_ops;
+            for (int i = 0; i < d * d; ++i) h->ops.push_back(B.op[i]);
+            ++n_ops;
+            if (fer) {  // second slot: d^dagger
+                for (int r = 0; r < d; ++r)
+                    for (int c = 0; c < d; ++c) {
+                        heom_c64 z = B.op[c * d + r];
+                        h->ops.push_back({z.re, -z.im});
+                    }
+                ++n_ops;
+                if (!B.nu || !B.partner) { set_error("bath %d: fermionic bath needs nu and partner", b); delete h; return HEOM_EINVAL; }
+                fer_first_global[b] = (int)h->exp_kind.size();
+            }
+            for (int k = 0; k < B.n_exp; ++k) {
+                if (!finite(B.coef[k]) || !finite(B.rate[k])) {
+                    set_error("bath %d exponent %d: non-finite coefficient or rate", b, k);
+                    delete h; return HEOM_EINVAL;
+                }
+                h->exp_kind.push_back(B.kind);
+                h->exp_bath.push_back(b);
+                coef.push_back(B.coef[k]);
+                rate.push_back(B.rate[k]);
+                if (fer) {
+                    int p = B.partner[k];
+                    if (B.nu[k] != 1 && B.nu[k] != -1) { set_error("bath %d exponent %d: nu must be +-1", b, k); delete h; return HEOM_EINVAL; }
+                    if (p < 0 || p >= B.n_exp || B.partner[p] != k || B.nu[p] != -B.nu[k]) {
+                        set_error("bath %d exponent %d: partner map must be an involution flipping nu", b, k);
+                        delete h; return HEOM_EINVAL;
+                    }
+                    h->exp_nu.push_back(B.nu[k]);
+                    h->exp_partner.push_back(fer_first_global[b] + p);
+                } else {
+                    h->exp_nu.push_back(0);
+                    h->exp_partner.push_back(-1);
+                }
+            }
+            if (pass == 0) h->K_b += B.n_exp; else h->K_f += B.n_exp;
+        }
+    }
+    h->K = h->K_b + h->K_f;
+    h->n_ops = n_ops;
+    if (h->K_f > 64) { set_error("heom_build_hierarchy: at most 64 fermionic exponents"); delete h; return HEOM_EINVAL; }
+    if (h->K_b == 0) h->tier_b = 0;
+    if (h->K_f < h->tier_f) h->tier_f = h->K_f;
+    const int Kb = h->K_b, Kf = h->K_f;
+
+    // ---- enumerate
+    Ranker rk;
+    rk.init(Kb, Kf, h->tier_b, h->tier_f);
+    h->N_b = (int64_t)rk.Nb; h->N_f = (int64_t)rk.Nf;
+    if ((double)rk.Nb * (double)rk.Nf > 2.0e9) { set_error("heom_build_hierarchy: more than 2e9 ADOs"); delete h; return HEOM_EINVAL; }
+    h->N = h->N_b * h->N_f;
+    try {
+        h->bos.reserve(rk.Nb);
+        for (int t = 0; t <= h->tier_b; ++t) {
+            std::vector<int> m(Kb, 0);
+            if (Kb == 0) { if (t == 0) h->bos.push_back(m); continue; }
+            m[0] = t;
+            do { h->bos.push_back(m); } while (next_comp(m));
+        }
+        h->fer.reserve(rk.Nf);
+        for (int n = 0; n <= h->tier_f; ++n) {
+            if (n == 0) { h->fer.push_back(0); continue; }
+            std::vector<int> c(n);
+            for (int i = 0; i < n; ++i) c[i] = i;
+            while (true) {
+                uint64_t S = 0;
+                for (int v : c) S |= 1ULL << v;
+                h->fer.push_back(S);
+                int i = n - 1;
+                while (i >= 0 && c[i] == Kf - n + i) --i;
+                if (i < 0) break;
+                ++c[i];
+                for (int j = i + 1; j < n; ++j) c[j] = c[j - 1] + 1;
+            }
+        }
+        // ---- neighbour / sign tables
+        const int p = parity;
+        std::vector<int32_t> occ_ptr(h->N + 1, 0);
+        std::vector<OccEntry> occ;
+        h->row_ptr.assign(h->N + 1, 0);
+        std::vector<int> mm(Kb);
+        for (int64_t ib = 0; ib < h->N_b; ++ib) {
+            const std::vector<int> &m = h->bos[ib];
+            int tb = 0;
+            for (int v : m) tb += v;
+            for (int64_t jf = 0; jf < h->N_f; ++jf) {
+                const uint64_t S = h->fer[jf];
+                const int64_t i = ib * h->N_f + jf;
+                const int n = __builtin_popcountll(S);
+                const int sigma = ((n & 1) ? -p : p);
+                if (tb < h->tier_b) {
+                    for (int k = 0; k < Kb; ++k) {
+                        mm = m; mm[k] += 1;
+                        int64_t j = rk.rank_bos(mm.data()) * h->N_f + jf;
+                        h->ent.push_back({(int32_t)j, (int16_t)op_slot_of_bath[h->exp_bath[k]], (int16_t)k, 1, 1, -1, 0});
+                    }
+                }
+                for (int k = 0; k < Kb; ++k) {
+                    if (m[k] == 0) continue;
+                    mm = m; mm[k] -= 1;
+                    int64_t j = rk.rank_bos(mm.data()) * h->N_f + jf;
+                    h->ent.push_back({(int32_t)j, (int16_t)op_slot_of_bath[h->exp_bath[k]], (int16_t)k, -1,
+                                      (int16_t)m[k], (int16_t)(-m[k]), 0});
+                }
+                for (int q = 0; q < Kf; ++q) {
+                    const int g = Kb + q;
+                    const int slot = op_slot_of_bath[h->exp_bath[g]];
+                    const int nu = h->exp_nu[g];
+                    const int eps = (__builtin_popcountll(S & ((1ULL << q) - 1ULL)) & 1) ? -1 : 1;
+                    if (S >> q & 1ULL) {  // lowered neighbour: C term, O = d^{nu}
+                        int64_t j = ib * h->N_f + rk.rank_fer(S & ~(1ULL << q));
+                        h->ent.push_back({(int32_t)j, (int16_t)(slot + (nu == 1 ? 1 : 0)), (int16_t)g, -1,
+                                          (int16_t)(p * eps), (int16_t)(p * eps * sigma), 0});
+                    } else if (n < h->tier_f) {  // raised neighbour: A term, O = d^{-nu}
+                        int64_t j = ib * h->N_f + rk.rank_fer(S | (1ULL << q));
+                        h->ent.push_back({(int32_t)j, (int16_t)(slot + (nu == 1 ? 0 : 1)), (int16_t)g, 1,
+                                          (int16_t)(p * eps), (int16_t)(-p * eps * sigma), 0});
+                    }
+                }
+                h->row_ptr[i + 1] = (int32_t)h->ent.size();
+                for (int k = 0; k < Kb; ++k)
+                    if (m[k]) occ.push_back({(int16_t)k, (int16_t)m[k]});
+                for (int q = 0; q < Kf; ++q)
+                    if (S >> q & 1ULL) occ.push_back({(int16_t)(Kb + q), 1});
+                occ_ptr[i + 1] = (int32_t)occ.size();
+            }
+        }
+        h->E = (int64_t)h->ent.size();
+        if (h->E > INT32_MAX) { set_error("heom_build_hierarchy: table too large"); delete h; return HEOM_EINVAL; }
+        // ---- operators, CSR and CSC with absolute offsets
+        std::vector<int32_t> orp, orc, ocp, ocr;
+        std::vector<heom_c64> orv, ocv;
+        for (int o = 0; o < n_ops; ++o) {
+            const heom_c64 *A = &h->ops[(size_t)o * d * d];
+            orp.push_back((int32_t)orc.size());
+            for (int r = 0; r < d; ++r) {
+                for (int c = 0; c < d; ++c)
+                    if (A[r * d + c].re != 0.0 || A[r * d + c].im != 0.0) { orc.push_back(c); orv.push_back(A[r * d + c]); }
+                orp.push_back((int32_t)orc.size());
+            }
+            ocp.push_back((int32_t)ocr.size());
+            for (int c = 0; c < d; ++c) {
+                for (int r = 0; r < d; ++r)
+                    if (A[r * d + c].re != 0.0 || A[r * d + c].im != 0.0) { ocr.push_back(r); ocv.push_back(A[r * d + c]); }
+                ocp.push_back((int32_t)ocr.size());
+            }
+        }
+        heom_status st;
+#define UP(buf, vec) if ((st = upload(h->buf, vec)) != HEOM_OK) { free_all(h); delete h; return st; }
+        UP(d_row_ptr, h->row_ptr); UP(d_ent, h->ent); UP(d_occ_ptr, occ_ptr); UP(d_occ, occ);
+        UP(d_op_rptr, orp); UP(d_op_rcol, orc); UP(d_op_cptr, ocp); UP(d_op_crow, ocr);
+        UP(d_op_rval64, to_cx<double>(orv)); UP(d_op_cval64, to_cx<double>(ocv));
+        UP(d_op_rval32, to_cx<float>(orv)); UP(d_op_cval32, to_cx<float>(ocv));
+#undef UP
+        if ((st = upload_params(h, 1, H, coef.data(), rate.data())) != HEOM_OK) { free_all(h); delete h; return st; }
+    } catch (const std::bad_alloc &) {
+        set_error("heom_build_hierarchy: out of host memory");
+        free_all(h); delete h;
+        return HEOM_ENOMEM;
+    }
+    *out = h;
+    return HEOM_OK;
+}
+
+extern "C" heom_status heom_set_params(heom_hier *h, int n_sets, const heom_c64 *H,
+                                       const heom_c64 *coef, const heom_c64 *rate) {
+    if (!h || n_sets < 1 || !H || (h->K > 0 && (!coef || !rate))) {
+        set_error("heom_set_params: need a hierarchy, n_sets >= 1 and H/coef/rate arrays");
+        return HEOM_EINVAL;
+    }
+    for (size_t i = 0; i < (size_t)n_sets * h->d2; ++i)
+        if (!finite(H[i])) { set_error("heom_set_params: non-finite H"); return HEOM_EINVAL; }
+    for (size_t i = 0; i < (size_t)n_sets * h->K; ++i)
+        if (!finite(coef[i]) || !finite(rate[i])) { set_error("heom_set_params: non-finite exponent"); return HEOM_EINVAL; }
+    HEOM_CUDA(cudaSetDevice(h->device));
+    return upload_params(h, n_sets, H, coef, rate);
+}
+
+extern "C" heom_status heom_hier_info(const heom_hier *h, int64_t *n_ado, int *d, int *k_b,
+                                      int *k_f, int *n_sets, int64_t *n_entries) {
+    if (!h) { set_error("heom_hier_info: NULL hierarchy"); return HEOM_EINVAL; }
+    if (n_ado) *n_ado = h->N;
+    if (d) *d = h->d;
+    if (k_b) *k_b = h->K_b;
+    if (k_f) *k_f = h->K_f;
+    if (n_sets) *n_sets = h->n_sets;
+    if (n_entries) *n_entries = h->E;
+    return HEOM_OK;
+}
+
+extern "C" heom_status heom_ado_index(const heom_hier *h, const int *occ, int64_t *idx) {
+    if (!h || !occ || !idx) { set_error("heom_ado_index: NULL argument"); return HEOM_EINVAL; }
+    Ranker rk;
+    rk.init(h->K_b, h->K_f, h->tier_b, h->tier_f);
+    uint64_t S = 0;
+    for (int k = 0; k < h->K_b; ++k)
+        if (occ[k] < 0) { *idx = -1; return HEOM_OK; }
+    for (int q = 0; q < h->K_f; ++q) {
+        int v = occ[h->K_b + q];
+        if (v != 0 && v != 1) { *idx = -1; return HEOM_OK; }
+        if (v) S |= 1ULL << q;
+    }
+    int64_t ib = rk.rank_bos(occ), jf = rk.rank_fer(S);
+    *idx = (ib < 0 || jf < 0) ? -1 : ib * h->N_f + jf;
+    return HEOM_OK;
+}
+
+extern "C" heom_status heom_ado_label(const heom_hier *h, int64_t idx, int *occ_out) {
+    if (!h || !occ_out || idx < 0 || idx >= h->N) {
+        set_error("heom_ado_label: index out of range or NULL argument");
+        return HEOM_EINVAL;
+    }
+    const std::vector<int> &m = h->bos[idx / h->N_f];
+    uint64_t S = h->fer[idx % h->N_f];
+    for (int k = 0; k < h->K_b; ++k) occ_out[k] = m[k];
+    for (int q = 0; q < h->K_f; ++q) occ_out[h->K_b + q] = (int)(S >> q & 1ULL);
+    return HEOM_OK;
+}
+
+extern "C" heom_status heom_export_tables(const heom_hier *h, int32_t *row_ptr, int32_t *nb,
+                                          int32_t *k, int32_t *dir, int32_t *mult_l,
+                                          int32_t *mult_r) {
+    if (!h) { set_error("heom_export_tables: NULL hierarchy"); return HEOM_EINVAL; }
+    if (row_ptr) std::copy(h->row_ptr.begin(), h->row_ptr.end(), row_ptr);
+    for (int64_t t = 0; t < h->E; ++t) {
+        const NbEntry &e = h->ent[t];
+        if (nb) nb[t] = e.nb;
+        if (k) k[t] = e.k;
+        if (dir) dir[t] = e.dir;
+        if (mult_l) mult_l[t] = e.mult_l;
+        if (mult_r) mult_r[t] = e.mult_r;
+    }
+    return HEOM_OK;
+}
+
+extern "C" void heom_destroy(heom_hier *h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    free_all(h);
+    delete h;
+}
+
+extern "C" const char *heom_last_error(void) { return heom::g_err.c_str(); }

@@ -1,0 +1,171 @@
+// Internal declarations shared by the host code (heom_host.cpp) and the CUDA kernels.
+// Nothing here is part of the public ABI (include/heom.h).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/heom.h"
+
+#if defined(__CUDACC__)
+#define HD __host__ __device__ __forceinline__
+#else
+#define HD inline
+#endif
+
+namespace heom {
+
+// ------------------------------------------------------------------ complex arithmetic
+template <class R>
+struct alignas(2 * sizeof(R)) cx {
+    R re, im;
+};
+template <class R> HD cx<R> mk(R a, R b) { return cx<R>{a, b}; }
+template <class R> HD cx<R> operator+(cx<R> a, cx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <class R> HD cx<R> operator-(cx<R> a, cx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <class R> HD cx<R> operator*(cx<R> a, cx<R> b) {
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <class R> HD cx<R> operator*(R s, cx<R> a) { return {s * a.re, s * a.im}; }
+template <class R> HD cx<R> conj(cx<R> a) { return {a.re, -a.im}; }
+template <class R> HD cx<R> mul_i(cx<R> a) { return {-a.im, a.re}; }         // i a
+template <class R> HD cx<R> mul_mi(cx<R> a) { return {a.im, -a.re}; }        // -i a
+template <class R> HD R norm2(cx<R> a) { return a.re * a.re + a.im * a.im; }
+// acc += a * b
+template <class R> HD void fma_to(cx<R> &acc, cx<R> a, cx<R> b) {
+    acc.re += a.re * b.re - a.im * b.im;
+    acc.im += a.re * b.im + a.im * b.re;
+}
+template <class R> HD cx<R> cdiv(cx<R> a, cx<R> b) {
+    R den = b.re * b.re + b.im * b.im;
+    return {(a.re * b.re + a.im * b.im) / den, (a.im * b.re - a.re * b.im) / den};
+}
+template <class R, class S> HD cx<R> cast(cx<S> a) { return {R(a.re), R(a.im)}; }
+
+// ------------------------------------------------------------------ tables
+// One term of Eq. HEOM for a target ADO: (M X)_i += -i (mult_l a O X_nb + mult_r b X_nb O).
+struct NbEntry {
+    int32_t nb;      // neighbour ADO index
+    int16_t op;      // operator slot
+    int16_t k;       // global exponent index
+    int16_t dir;     // +1 raised neighbour (a = b = 1), -1 lowered neighbour (a, b from params)
+    int16_t mult_l;  // integer factor of the left product
+    int16_t mult_r;  // integer factor of the right product
+    int16_t pad;
+};
+static_assert(sizeof(NbEntry) == 16, "NbEntry must stay 16 bytes");
+
+struct OccEntry {  // damping term: count * rate_k
+    int16_t k;
+    int16_t count;
+};
+
+// Device view of a hierarchy in one precision (R = double or float).
+template <class R>
+struct DevView {
+    int64_t N;          // number of ADOs
+    int d, d2, K, n_sets, nnzH;
+    const int32_t *row_ptr;   // [N+1]
+    const NbEntry *ent;       // [E]
+    const int32_t *occ_ptr;   // [N+1]
+    const OccEntry *occ;      // [Eo]
+    const int32_t *op_rptr;   // [n_ops*(d+1)] absolute offsets into op_rcol/op_rval
+    const int32_t *op_rcol;
+    const cx<R> *op_rval;
+    const int32_t *op_cptr;   // [n_ops*(d+1)] absolute offsets into op_crow/op_cval
+    const int32_t *op_crow;
+    const cx<R> *op_cval;
+    const int32_t *h_rptr;    // [d+1]: H pattern by rows (union over parameter sets)
+    const int32_t *h_rcol;
+    const int32_t *h_rvi;     // value index into a set's H value array
+    const int32_t *h_cptr;    // [d+1]: the same pattern by columns
+    const int32_t *h_crow;
+    const int32_t *h_cvi;
+    const cx<R> *h_val;       // [n_sets][nnzH]
+    const cx<R> *coefL;       // [n_sets][K]
+    const cx<R> *coefR;       // [n_sets][K]
+    const cx<R> *rate;        // [n_sets][K]
+    const cx<R> *hdiag;       // [n_sets][d]   diagonal of H (preconditioner)
+    const R *floor;           // [n_sets]      damping floor for undamped ADOs (preconditioner)
+};
+
+// Optional modifiers of the apply used by the solvers (all may be null / zero).
+template <class R>
+struct ApplyMods {
+    const cx<R> *shift;   // [B]: y += shift_b x  (spectra: -+ i w)
+    R aug;                // steady state: y_(0,(0,0)) += aug * Tr x_0
+};
+
+// A device buffer owned by the library.
+struct DBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace heom
+
+// The opaque handle of the public ABI.
+struct heom_hier {
+    int device = 0;
+    int d = 0, d2 = 0, K_b = 0, K_f = 0, K = 0, tier_b = 0, tier_f = 0, parity = 1;
+    int n_sets = 1, n_ops = 0;
+    int64_t N = 0, N_b = 0, N_f = 0, E = 0;
+    // host copies (dictionary and table export)
+    std::vector<std::vector<int>> bos;      // bosonic occupation vectors in order
+    std::vector<uint64_t> fer;              // fermionic subsets (bit masks) in order
+    std::vector<int32_t> row_ptr;
+    std::vector<heom::NbEntry> ent;
+    std::vector<int> exp_kind;              // heom_kind per global exponent
+    std::vector<int> exp_bath;              // bath per global exponent
+    std::vector<int> exp_nu;                // fermionic nu per global exponent (0 for bosons)
+    std::vector<int> exp_partner;           // global index of the partner (fermions)
+    std::vector<heom_c64> ops;              // [n_ops][d][d]
+    std::vector<heom_c64> H0;               // [n_sets][d][d]
+    // device tables
+    heom::DBuf d_row_ptr, d_ent, d_occ_ptr, d_occ;
+    heom::DBuf d_op_rptr, d_op_rcol, d_op_cptr, d_op_crow, d_op_rval64, d_op_cval64,
+        d_op_rval32, d_op_cval32;
+    heom::DBuf d_h_rptr, d_h_rcol, d_h_rvi, d_h_cptr, d_h_crow, d_h_cvi;
+    int nnzH = 0;
+    // device parameters (per set), both precisions
+    heom::DBuf d_hval64, d_hval32, d_coefL64, d_coefL32, d_coefR64, d_coefR32, d_rate64,
+        d_rate32, d_hdiag64, d_hdiag32, d_floor64, d_floor32;
+    // solver workspace (grown on demand)
+    heom::DBuf ws;
+    heom::DBuf ws_small;
+    heom::DevView<double> view64() const;
+    heom::DevView<float> view32() const;
+};
+
+namespace heom {
+
+// error reporting (thread-local message)
+void set_error(const char *fmt, ...);
+heom_status cuda_fail(cudaError_t e, const char *what);
+
+#define HEOM_CUDA(call)                                   \
+    do {                                                  \
+        cudaError_t e__ = (call);                         \
+        if (e__ != cudaSuccess) return heom::cuda_fail(e__, #call); \
+    } while (0)
+
+heom_status dalloc(DBuf &b, size_t bytes);
+void dfree(DBuf &b);
+heom_status ensure_ws(DBuf &b, size_t bytes);
+
+// launch geometry shared by every row x column kernel: block (bx, by), grid (gx, gy)
+struct Geom {
+    dim3 grid, block;
+    int64_t rows, B;
+};
+Geom make_geom(int64_t rows, int64_t B, int max_blocks_x = 0);
+
+// kernels (heom_kernels.cu)
+template <class R>
+cudaError_t launch_apply(const DevView<R> &v, const cx<R> *x, cx<R> *y, int64_t B,
+                         const ApplyMods<R> &mods, cudaStream_t s);
+
+}  // namespace heom

@@ -1,0 +1,124 @@
+// Device building blocks shared by the kernels: the matrix-free HEOM apply at one point,
+// the block-local preconditioner and block reductions into per-column FP64 accumulators.
+#pragma once
+
+#include "heom_internal.h"
+
+namespace heom {
+
+// Per-column solver state; every field is FP64 (Krylov scalars, dots, residuals).
+struct ColState {
+    cx<double> rho_old, alpha, omega;      // BiCGStab scalars
+    cx<double> acc_rv, acc_ts, acc_tt, acc_rr;  // dot-product accumulators
+    double acc_nr;                          // ||r||^2 accumulator
+    double bnorm2;                          // ||b||^2
+    int active;                             // 1 while the column iterates
+    int flag;                               // breakdown marker
+};
+
+template <class R>
+__device__ __forceinline__ cx<R> ldc(const cx<R> *p) {
+    if constexpr (sizeof(R) == 8) {
+        double2 t = __ldg(reinterpret_cast<const double2 *>(p));
+        return cx<R>{t.x, t.y};
+    } else {
+        float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+        return cx<R>{t.x, t.y};
+    }
+}
+
+template <class R>
+__device__ __forceinline__ cx<R> damping_of(const DevView<R> &v, int64_t n, int set) {
+    cx<R> dmp{R(0), R(0)};
+    const int o1 = __ldg(v.occ_ptr + n + 1);
+    for (int o = __ldg(v.occ_ptr + n); o < o1; ++o) {
+        const int packed = __ldg(reinterpret_cast<const int *>(v.occ) + o);
+        const int k = (int)(int16_t)(packed & 0xffff);
+        const int cnt = (int)(int16_t)(packed >> 16);
+        dmp = dmp + R(cnt) * ldc(v.rate + (int64_t)set * v.K + k);
+    }
+    return dmp;
+}
+
+// (M X)[n][e][b]: Eq. HEOM evaluated at ADO n, element e = r*d + c, batch column b.
+// X points at the start of the ADO vector ([N][d2][B]).
+template <class R>
+__device__ __forceinline__ cx<R> apply_point(const DevView<R> &v, const cx<R> *__restrict__ X,
+                                             int64_t n, int e, int64_t b, int64_t B, int set,
+                                             const cx<R> &damp) {
+    const int d = v.d;
+    const int r = e / d, c = e - r * d;
+    const cx<R> *Xn = X + n * v.d2 * B + b;
+    const cx<R> x0 = Xn[(int64_t)e * B];
+    cx<R> acc{-(damp.re * x0.re - damp.im * x0.im), -(damp.re * x0.im + damp.im * x0.re)};
+    // system commutator: -i (H X - X H)
+    const cx<R> *hv = v.h_val + (int64_t)set * v.nnzH;
+    for (int j = __ldg(v.h_rptr + r), j1 = __ldg(v.h_rptr + r + 1); j < j1; ++j)
+        fma_to(acc, mul_mi(ldc(hv + __ldg(v.h_rvi + j))), Xn[(int64_t)(__ldg(v.h_rcol + j) * d + c) * B]);
+    for (int j = __ldg(v.h_cptr + c), j1 = __ldg(v.h_cptr + c + 1); j < j1; ++j)
+        fma_to(acc, mul_i(ldc(hv + __ldg(v.h_cvi + j))), Xn[(int64_t)(r * d + __ldg(v.h_crow + j)) * B]);
+    // couplings to the neighbouring ADOs
+    const int t1 = __ldg(v.row_ptr + n + 1);
+    for (int t = __ldg(v.row_ptr + n); t < t1; ++t) {
+        const int4 raw = __ldg(reinterpret_cast<const int4 *>(v.ent) + t);
+        const int nb = raw.x;
+        const int op = (int)(int16_t)(raw.y & 0xffff);
+        const int k = (int)(int16_t)(raw.y >> 16);
+        const int dir = (int)(int16_t)(raw.z & 0xffff);
+        const R ml = R((int16_t)(raw.z >> 16));
+        const R mr = R((int16_t)(raw.w & 0xffff));
+        cx<R> cl, cr;  // -i * mult * (a | b)
+        if (dir > 0) {
+            cl = cx<R>{R(0), -ml};
+            cr = cx<R>{R(0), -mr};
+        } else {
+            const int64_t pk = (int64_t)set * v.K + k;
+            cl = mul_mi(ml * ldc(v.coefL + pk));
+            cr = mul_mi(mr * ldc(v.coefR + pk));
+        }
+        const cx<R> *Xb = X + (int64_t)nb * v.d2 * B + b;
+        const int base = op * (d + 1);
+        for (int j = __ldg(v.op_rptr + base + r), j1 = __ldg(v.op_rptr + base + r + 1); j < j1; ++j)
+            fma_to(acc, cl * ldc(v.op_rval + j), Xb[(int64_t)(__ldg(v.op_rcol + j) * d + c) * B]);
+        for (int j = __ldg(v.op_cptr + base + c), j1 = __ldg(v.op_cptr + base + c + 1); j < j1; ++j)
+            fma_to(acc, cr * ldc(v.op_cval + j), Xb[(int64_t)(r * d + __ldg(v.op_crow + j)) * B]);
+    }
+    return acc;
+}
+
+// Inverse of the ADO-local diagonal: 1 / (-i (H_rr - H_cc) - damp + shift), the undamped
+// tier-0 ADO being given the smallest positive rate as damping so the inverse stays bounded.
+template <class R>
+__device__ __forceinline__ cx<R> precond_inv(const DevView<R> &v, int64_t n, int e, int set,
+                                             const cx<R> &damp, cx<R> shift) {
+    const int r = e / v.d, c = e - r * v.d;
+    const cx<R> hr = ldc(v.hdiag + (int64_t)set * v.d + r), hc = ldc(v.hdiag + (int64_t)set * v.d + c);
+    cx<R> loc = mul_mi(hr - hc) - damp + shift;
+    if (__ldg(v.occ_ptr + n) == __ldg(v.occ_ptr + n + 1)) loc.re -= __ldg(v.floor + set);
+    return cdiv(cx<R>{R(1), R(0)}, loc);
+}
+
+// Sum a per-thread FP64 complex value over threadIdx.y and atomically add it to acc[col].
+// Block is (bx, by) with by a power of two; every thread of the block must call this.
+__device__ __forceinline__ void block_add(double re, double im, double *acc_re, double *acc_im,
+                                          bool valid) {
+    __shared__ double sre[256], sim[256];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    sre[tid] = re;
+    sim[tid] = im;
+    __syncthreads();
+    for (int s = blockDim.y >> 1; s > 0; s >>= 1) {
+        if (threadIdx.y < s) {
+            sre[tid] += sre[tid + s * blockDim.x];
+            sim[tid] += sim[tid + s * blockDim.x];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.y == 0 && valid) {
+        atomicAdd(acc_re, sre[threadIdx.x]);
+        if (acc_im) atomicAdd(acc_im, sim[threadIdx.x]);
+    }
+    __syncthreads();
+}
+
+}  // namespace heom

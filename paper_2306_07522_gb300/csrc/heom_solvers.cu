@@ -1,0 +1,772 @@
+// Solvers driven by the HEOM apply (package architecture: dynamics, stationary states,
+// spectra): fixed-step RK4, batched right-preconditioned BiCGStab, FP64 iterative
+// refinement around FP32 BiCGStab corrections, and the density-of-states readout
+// (Methods, numerical computation of the spectrum).
+//
+// All batch columns are independent systems that iterate in lock-step; every Krylov scalar
+// lives on the device per column (ColState, FP64), so an iteration is five kernel launches
+// and no host round trip. The host reads the per-column residuals every few iterations to
+// retire converged columns.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "heom_kernels.cuh"
+
+namespace heom {
+
+// ------------------------------------------------------------------ block reduction
+template <int NV>
+__device__ __forceinline__ void reduce_add(double (&val)[NV], double *const (&dst)[NV],
+                                           bool valid) {
+    __shared__ double sh[NV][256];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) sh[i][tid] = val[i];
+    __syncthreads();
+    for (int s = blockDim.y >> 1; s > 0; s >>= 1) {
+        if (threadIdx.y < s) {
+#pragma unroll
+            for (int i = 0; i < NV; ++i) sh[i][tid] += sh[i][tid + s * blockDim.x];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.y == 0 && valid) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i)
+            if (dst[i]) atomicAdd(dst[i], sh[i][threadIdx.x]);
+    }
+}
+
+#define COLUMN_PROLOGUE                                                    \
+    const int64_t b = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;      \
+    const bool inb = b < B;                                                \
+    const int64_t rows = v.N * v.d2;                                       \
+    const int set = inb ? (int)(b / cps) : 0;                              \
+    (void)set;
+
+#define ROW_LOOP for (int64_t row = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; row < rows; \
+                      row += (int64_t)gridDim.x * blockDim.y)
+
+__device__ __forceinline__ bool designated() { return blockIdx.x == 0 && threadIdx.y == 0; }
+
+// ------------------------------------------------------------------ RK4
+// One fused stage of classical RK4: k = M z_in, then
+//   stage 1: acc = k,       z_out = y + dt/2 k
+//   stage 2: acc += 2k,     z_out = y + dt/2 k
+//   stage 3: acc += 2k,     z_out = y + dt k
+//   stage 4: y += dt/6 (acc + k)
+template <class R>
+__global__ void __launch_bounds__(256) k_rk4_stage(DevView<R> v, const cx<R> *__restrict__ z_in,
+                                                   cx<R> *__restrict__ z_out, cx<R> *y,
+                                                   cx<R> *__restrict__ acc, int64_t B,
+                                                   int64_t cps, R dt, int stage) {
+    COLUMN_PROLOGUE
+    if (!inb) return;
+    ROW_LOOP {
+        const int64_t n = row / v.d2;
+        const int e = (int)(row - n * v.d2);
+        const cx<R> k = apply_point(v, z_in, n, e, b, B, set, damping_of(v, n, set));
+        const int64_t i = row * B + b;
+        if (stage == 1) {
+            acc[i] = k;
+            z_out[i] = y[i] + (R(0.5) * dt) * k;
+        } else if (stage == 2) {
+            acc[i] = acc[i] + R(2) * k;
+            z_out[i] = y[i] + (R(0.5) * dt) * k;
+        } else if (stage == 3) {
+            acc[i] = acc[i] + R(2) * k;
+            z_out[i] = y[i] + dt * k;
+        } else {
+            y[i] = y[i] + (dt / R(6)) * (acc[i] + k);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ BiCGStab
+__global__ void k_state_init(ColState *st, int64_t B, const int *active) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    ColState c{};
+    c.rho_old = {1.0, 0.0};
+    c.alpha = {1.0, 0.0};
+    c.omega = {1.0, 0.0};
+    c.active = active ? active[b] : 1;
+    st[b] = c;
+}
+
+// r = b - A x (or r = b when x is zero), rh = r, p = v = 0; acc_rr = (rh, r), acc_nr = |r|^2,
+// bnorm2 = |b|^2.
+template <class R>
+__global__ void __launch_bounds__(256) k_bicg_init(DevView<R> v, const cx<R> *__restrict__ bb,
+                                                   const cx<R> *__restrict__ x, cx<R> *r,
+                                                   cx<R> *rh, cx<R> *p, cx<R> *vv, int64_t B,
+                                                   int64_t cps, ApplyMods<R> mods, int x_zero,
+                                                   ColState *st) {
+    COLUMN_PROLOGUE
+    const bool act = inb && st[b].active;
+    double nr = 0, nb = 0;
+    if (act) {
+        ROW_LOOP {
+            const int64_t i = row * B + b;
+            cx<R> ri = bb[i];
+            if (!x_zero) {
+                const int64_t n = row / v.d2;
+                const int e = (int)(row - n * v.d2);
+                cx<R> ax = apply_point(v, x, n, e, b, B, set, damping_of(v, n, set));
+                if (mods.shift) fma_to(ax, mods.shift[b], x[i]);
+                if (mods.aug != R(0) && row == 0) {
+                    cx<R> tr{R(0), R(0)};
+                    for (int q = 0; q < v.d; ++q) tr = tr + x[(int64_t)(q * v.d + q) * B + b];
+                    ax = ax + mods.aug * tr;
+                }
+                ri = ri - ax;
+            }
+            r[i] = ri;
+            rh[i] = ri;
+            p[i] = cx<R>{R(0), R(0)};
+            vv[i] = cx<R>{R(0), R(0)};
+            nr += (double)norm2(ri);
+            nb += (double)norm2(bb[i]);
+        }
+    }
+    double val[3] = {nr, nr, nb};
+    double *const dst[3] = {act ? &st[b].acc_rr.re : nullptr, act ? &st[b].acc_nr : nullptr,
+                            act ? &st[b].bnorm2 : nullptr};
+    reduce_add<3>(val, dst, act);
+}
+
+// p = r + beta (p - omega v), ph = P^-1 p, beta = (rho / rho_old)(alpha / omega)
+template <class R>
+__global__ void __launch_bounds__(256) k_bicg_p(DevView<R> v, const cx<R> *__restrict__ r,
+                                                cx<R> *p, const cx<R> *__restrict__ vv,
+                                                cx<R> *__restrict__ ph, int64_t B, int64_t cps,
+                                                const cx<R> *shift, int precond, ColState *st) {
+    COLUMN_PROLOGUE
+    if (!inb || !st[b].active) return;
+    const ColState c = st[b];
+    const cx<double> beta = cdiv(c.acc_rr, c.rho_old) * cdiv(c.alpha, c.omega);
+    const cx<R> bt = cast<R>(beta), om = cast<R>(c.omega);
+    const cx<R> sh = shift ? shift[b] : cx<R>{R(0), R(0)};
+    ROW_LOOP {
+        const int64_t i = row * B + b;
+        const cx<R> pi = r[i] + bt * (p[i] - om * vv[i]);
+        p[i] = pi;
+        if (precond) {
+            const int64_t n = row / v.d2;
+            const int e = (int)(row - n * v.d2);
+            ph[i] = pi * precond_inv(v, n, e, set, damping_of(v, n, set), sh);
+        } else {
+            ph[i] = pi;
+        }
+    }
+    if (designated()) st[b].acc_rv = {0.0, 0.0};
+}
+
+// out = A in (apply with shift / trace augmentation), plus FP64 dots against two vectors:
+//   mode 0 (v = A ph):  acc_rv += (rh, v)
+//   mode 1 (t = A sh):  acc_ts += (t, s), acc_tt += (t, t)
+template <class R>
+__global__ void __launch_bounds__(256) k_bicg_apply(DevView<R> v, const cx<R> *__restrict__ in,
+                                                    cx<R> *__restrict__ out,
+                                                    const cx<R> *__restrict__ w, int64_t B,
+                                                    int64_t cps, ApplyMods<R> mods, int mode,
+                                                    ColState *st) {
+    COLUMN_PROLOGUE
+    const bool act = inb && st[b].active;
+    double a_re = 0, a_im = 0, tt = 0;
+    if (act) {
+        ROW_LOOP {
+            const int64_t n = row / v.d2;
+            const int e = (int)(row - n * v.d2);
+            const int64_t i = row * B + b;
+            cx<R> y = apply_point(v, in, n, e, b, B, set, damping_of(v, n, set));
+            if (mods.shift) fma_to(y, mods.shift[b], in[i]);
+            if (mods.aug != R(0) && row == 0) {
+                cx<R> tr{R(0), R(0)};
+                for (int q = 0; q < v.d; ++q) tr = tr + in[(int64_t)(q * v.d + q) * B + b];
+                y = y + mods.aug * tr;
+            }
+            out[i] = y;
+            const cx<double> yd = cast<double>(y), wd = cast<double>(w[i]);
+            if (mode == 0) {  // (rh, v) = sum conj(rh) v
+                a_re += wd.re * yd.re + wd.im * yd.im;
+                a_im += wd.re * yd.im - wd.im * yd.re;
+            } else {          // (t, s) = sum conj(t) s ; (t, t)
+                a_re += yd.re * wd.re + yd.im * wd.im;
+                a_im += yd.re * wd.im - yd.im * wd.re;
+                tt += yd.re * yd.re + yd.im * yd.im;
+            }
+        }
+    }
+    if (mode == 0) {
+        double val[2] = {a_re, a_im};
+        double *const dst[2] = {act ? &st[b].acc_rv.re : nullptr, act ? &st[b].acc_rv.im : nullptr};
+        reduce_add<2>(val, dst, act);
+    } else {
+        double val[3] = {a_re, a_im, tt};
+        double *const dst[3] = {act ? &st[b].acc_ts.re : nullptr, act ? &st[b].acc_ts.im : nullptr,
+                                act ? &st[b].acc_tt.re : nullptr};
+        reduce_add<3>(val, dst, act);
+        if (act && designated()) {
+            st[b].acc_rr = {0.0, 0.0};
+            st[b].acc_nr = 0.0;
+        }
+    }
+}
+
+// alpha = rho / (rh, v); s = r - alpha v (in place in r); sh = P^-1 s
+template <class R>
+__global__ void __launch_bounds__(256) k_bicg_s(DevView<R> v, cx<R> *r, const cx<R> *__restrict__ vv,
+                                                cx<R> *__restrict__ sh, int64_t B, int64_t cps,
+                                                const cx<R> *shift, int precond, ColState *st) {
+    COLUMN_PROLOGUE
+    if (!inb || !st[b].active) return;
+    const ColState c = st[b];
+    const bool bad = norm2(c.acc_rv) == 0.0;
+    const cx<double> alpha = bad ? cx<double>{0.0, 0.0} : cdiv(c.acc_rr, c.acc_rv);
+    const cx<R> al = cast<R>(alpha);
+    const cx<R> shf = shift ? shift[b] : cx<R>{R(0), R(0)};
+    ROW_LOOP {
+        const int64_t i = row * B + b;
+        const cx<R> s = r[i] - al * vv[i];
+        r[i] = s;
+        if (precond) {
+            const int64_t n = row / v.d2;
+            const int e = (int)(row - n * v.d2);
+            sh[i] = s * precond_inv(v, n, e, set, damping_of(v, n, set), shf);
+        } else {
+            sh[i] = s;
+        }
+    }
+    if (designated()) {
+        st[b].alpha = alpha;
+        st[b].rho_old = c.acc_rr;
+        st[b].acc_ts = {0.0, 0.0};
+        st[b].acc_tt = {0.0, 0.0};
+        if (bad) st[b].flag = 1;
+    }
+}
+
+// omega = (t, s) / (t, t); x += alpha ph + omega sh; r = s - omega t;
+// acc_rr += (rh, r), acc_nr += |r|^2
+template <class R>
+__global__ void __launch_bounds__(256) k_bicg_x(int64_t rows, cx<R> *x, const cx<R> *__restrict__ ph,
+                                                const cx<R> *__restrict__ sh, cx<R> *r,
+                                                const cx<R> *__restrict__ t,
+                                                const cx<R> *__restrict__ rh, int64_t B,
+                                                ColState *st) {
+    const int64_t b = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+    const bool act = b < B && st[b].active;
+    double rr_re = 0, rr_im = 0, nr = 0;
+    cx<double> omega{0.0, 0.0};
+    if (act) {
+        const ColState c = st[b];
+        omega = c.acc_tt.re == 0.0 ? cx<double>{0.0, 0.0} : cdiv(c.acc_ts, c.acc_tt);
+        const cx<R> al = cast<R>(c.alpha), om = cast<R>(omega);
+        ROW_LOOP {
+            const int64_t i = row * B + b;
+            x[i] = x[i] + al * ph[i] + om * sh[i];
+            const cx<R> ri = r[i] - om * t[i];
+            r[i] = ri;
+            const cx<double> rd = cast<double>(ri), hd = cast<double>(rh[i]);
+            rr_re += hd.re * rd.re + hd.im * rd.im;
+            rr_im += hd.re * rd.im - hd.im * rd.re;
+            nr += rd.re * rd.re + rd.im * rd.im;
+        }
+    }
+    double val[3] = {rr_re, rr_im, nr};
+    double *const dst[3] = {act ? &st[b].acc_rr.re : nullptr, act ? &st[b].acc_rr.im : nullptr,
+                            act ? &st[b].acc_nr : nullptr};
+    reduce_add<3>(val, dst, act);
+    if (act && designated()) st[b].omega = omega;
+}
+
+// ------------------------------------------------------------------ refinement helpers
+// r64 = b - A x64 in FP64 with |r|^2 -> acc_nr and |b|^2 -> bnorm2 of the outer state
+__global__ void __launch_bounds__(256) k_residual64(DevView<double> v, const cx<double> *__restrict__ bb,
+                                                    const cx<double> *__restrict__ x,
+                                                    cx<double> *__restrict__ r, int64_t B,
+                                                    int64_t cps, ApplyMods<double> mods,
+                                                    ColState *st) {
+    COLUMN_PROLOGUE
+    const bool act = inb && st[b].active;
+    double nr = 0, nb = 0;
+    if (act) {
+        ROW_LOOP {
+            const int64_t n = row / v.d2;
+            const int e = (int)(row - n * v.d2);
+            const int64_t i = row * B + b;
+            cx<double> ax = apply_point(v, x, n, e, b, B, set, damping_of(v, n, set));
+            if (mods.shift) fma_to(ax, mods.shift[b], x[i]);
+            if (mods.aug != 0.0 && row == 0) {
+                cx<double> tr{0.0, 0.0};
+                for (int q = 0; q < v.d; ++q) tr = tr + x[(int64_t)(q * v.d + q) * B + b];
+                ax = ax + mods.aug * tr;
+            }
+            const cx<double> ri = bb[i] - ax;
+            r[i] = ri;
+            nr += norm2(ri);
+            nb += norm2(bb[i]);
+        }
+    }
+    double val[2] = {nr, nb};
+    double *const dst[2] = {act ? &st[b].acc_nr : nullptr, act ? &st[b].bnorm2 : nullptr};
+    reduce_add<2>(val, dst, act);
+}
+
+// r32 = r64 / ||r64|| per active column
+__global__ void k_scale_to32(int64_t rows, const cx<double> *__restrict__ r64,
+                             cx<float> *__restrict__ r32, int64_t B, const ColState *st) {
+    const int64_t b = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+    if (b >= B || !st[b].active) return;
+    const double inv = 1.0 / std::sqrt(st[b].acc_nr);
+    ROW_LOOP {
+        const int64_t i = row * B + b;
+        r32[i] = cx<float>{float(r64[i].re * inv), float(r64[i].im * inv)};
+    }
+}
+
+// x64 += ||r64|| d32 per active column
+__global__ void k_accum64(int64_t rows, cx<double> *__restrict__ x, const cx<float> *__restrict__ d32,
+                          int64_t B, const ColState *st) {
+    const int64_t b = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+    if (b >= B || !st[b].active) return;
+    const double s = std::sqrt(st[b].acc_nr);
+    ROW_LOOP {
+        const int64_t i = row * B + b;
+        x[i].re += s * (double)d32[i].re;
+        x[i].im += s * (double)d32[i].im;
+    }
+}
+
+// per column: |M x|^2 and |x|^2 (FP64, no shift, no augmentation) into out[2*b], out[2*b+1]
+__global__ void __launch_bounds__(256) k_apply_norms(DevView<double> v, const cx<double> *__restrict__ x,
+                                                     int64_t B, int64_t cps, double *out) {
+    COLUMN_PROLOGUE
+    double mx = 0, xx = 0;
+    if (inb) {
+        ROW_LOOP {
+            const int64_t n = row / v.d2;
+            const int e = (int)(row - n * v.d2);
+            const cx<double> y = apply_point(v, x, n, e, b, B, set, damping_of(v, n, set));
+            mx += norm2(y);
+            xx += norm2(x[row * B + b]);
+        }
+    }
+    double val[2] = {mx, xx};
+    double *const dst[2] = {inb ? out + 2 * b : nullptr, inb ? out + 2 * b + 1 : nullptr};
+    reduce_add<2>(val, dst, inb);
+}
+
+// steady-state right-hand side: e_(0,(0,0)) in every column
+template <class R>
+__global__ void k_set_e00(int64_t total, cx<R> *bvec, int64_t B) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x)
+        bvec[i] = cx<R>{i < B ? R(1) : R(0), R(0)};
+}
+
+// spectrum right-hand sides: columns [0, nw) get O_plus rho_n, columns [nw, 2nw) O_minus rho_n
+__global__ void k_dos_rhs(int64_t N, int d, const cx<double> *__restrict__ ss,
+                          const cx<double> *__restrict__ op_plus, const cx<double> *__restrict__ op_minus,
+                          cx<double> *__restrict__ bvec, int64_t nw) {
+    const int64_t B = 2 * nw;
+    const int64_t total = N * d * d * B;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = i % B, row = i / B;
+        const int64_t n = row / (d * d);
+        const int e = (int)(row - n * d * d), r = e / d, c = e - r * d;
+        const cx<double> *O = b < nw ? op_plus : op_minus;
+        cx<double> acc{0.0, 0.0};
+        for (int l = 0; l < d; ++l) fma_to(acc, O[r * d + l], ss[n * d * d + l * d + c]);
+        bvec[i] = acc;
+    }
+}
+
+template <class R>
+__global__ void k_scale_cols(int64_t total, cx<R> *x, int64_t B, const cx<double> *fac) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const cx<R> f = cast<R>(fac[i % B]);
+        x[i] = x[i] * f;
+    }
+}
+
+template <class R, class S>
+__global__ void k_convert(int64_t total, const cx<S> *__restrict__ in, cx<R> *__restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = cast<R>(in[i]);
+}
+
+// ------------------------------------------------------------------ host orchestration
+namespace {
+
+int flat_blocks(int64_t total) {
+    int64_t g = (total + 255) / 256;
+    return (int)std::min<int64_t>(std::max<int64_t>(g, 1), 152 * 16);
+}
+
+template <class R> DevView<R> view_of(const heom_hier *h);
+template <> DevView<double> view_of<double>(const heom_hier *h) { return h->view64(); }
+template <> DevView<float> view_of<float>(const heom_hier *h) { return h->view32(); }
+
+struct SolveOut {
+    std::vector<int> iters;
+    std::vector<int> status;
+    std::vector<double> res;  // final relative residual sqrt(acc_nr / bnorm2)
+};
+
+// Batched right-preconditioned BiCGStab on A x = b, A = M + diag(shift) (+ trace aug).
+// Columns with active[b] = 0 are left untouched. x holds the initial guess (x_zero: zero).
+template <class R>
+heom_status bicgstab(heom_hier *h, const cx<R> *bvec, cx<R> *x, int64_t B, const cx<R> *shift,
+                     R aug, bool x_zero, double tol, int max_iter, const std::vector<int> &active,
+                     cx<R> *work, ColState *st, int *d_flags, SolveOut &out, cudaStream_t s) {
+    const DevView<R> v = view_of<R>(h);
+    const int64_t rows = h->N * h->d2, L = rows * B;
+    cx<R> *r = work, *rh = work + L, *p = work + 2 * L, *ph = work + 3 * L, *vv = work + 4 * L,
+          *sh = work + 5 * L, *t = work + 6 * L;
+    const int64_t cps = B / h->n_sets;
+    const Geom gd = make_geom(rows, B, std::max<int64_t>(1, 2048 / ((B + 31) / 32)));
+    const Geom ga = gd;
+    ApplyMods<R> mods{shift, aug};
+    HEOM_CUDA(cudaMemcpyAsync(d_flags, active.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
+    k_state_init<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(st, B, d_flags);
+    k_bicg_init<R><<<gd.grid, gd.block, 0, s>>>(v, bvec, x, r, rh, p, vv, B, cps, mods, x_zero, st);
+    HEOM_CUDA(cudaGetLastError());
+    std::vector<ColState> hs(B);
+    std::vector<int> act = active;
+    out.iters.assign(B, 0);
+    out.status.assign(B, HEOM_OK);
+    out.res.assign(B, 0.0);
+    const double tol2 = tol * tol;
+    // columns whose initial residual already meets tol
+    HEOM_CUDA(cudaMemcpyAsync(hs.data(), st, B * sizeof(ColState), cudaMemcpyDeviceToHost, s));
+    HEOM_CUDA(cudaStreamSynchronize(s));
+    int n_act = 0;
+    for (int64_t b = 0; b < B; ++b) {
+        if (!act[b]) continue;
+        out.res[b] = hs[b].bnorm2 > 0 ? std::sqrt(hs[b].acc_nr / hs[b].bnorm2) : 0.0;
+        if (hs[b].acc_nr <= tol2 * hs[b].bnorm2) { act[b] = 0; hs[b].active = 0; }
+        else ++n_act;
+    }
+    int it = 0, check = 4;
+    while (n_act > 0 && it < max_iter) {
+        HEOM_CUDA(cudaMemcpyAsync(st, hs.data(), B * sizeof(ColState), cudaMemcpyHostToDevice, s));
+        const int steps = std::min(check, max_iter - it);
+        for (int k = 0; k < steps; ++k) {
+            k_bicg_p<R><<<gd.grid, gd.block, 0, s>>>(v, r, p, vv, ph, B, cps, shift, 1, st);
+            k_bicg_apply<R><<<ga.grid, ga.block, 0, s>>>(v, ph, vv, rh, B, cps, mods, 0, st);
+            k_bicg_s<R><<<gd.grid, gd.block, 0, s>>>(v, r, vv, sh, B, cps, shift, 1, st);
+            k_bicg_apply<R><<<ga.grid, ga.block, 0, s>>>(v, sh, t, r, B, cps, mods, 1, st);
+            k_bicg_x<R><<<gd.grid, gd.block, 0, s>>>(rows, x, ph, sh, r, t, rh, B, st);
+        }
+        HEOM_CUDA(cudaGetLastError());
+        it += steps;
+        HEOM_CUDA(cudaMemcpyAsync(hs.data(), st, B * sizeof(ColState), cudaMemcpyDeviceToHost, s));
+        HEOM_CUDA(cudaStreamSynchronize(s));
+        n_act = 0;
+        for (int64_t b = 0; b < B; ++b) {
+            if (!act[b]) continue;
+            out.iters[b] = it;
+            const double nr = hs[b].acc_nr;
+            out.res[b] = hs[b].bnorm2 > 0 ? std::sqrt(nr / hs[b].bnorm2) : 0.0;
+            if (!std::isfinite(nr) || hs[b].flag) {
+                out.status[b] = HEOM_EBREAKDOWN;
+                act[b] = 0; hs[b].active = 0;
+            } else if (nr <= tol2 * hs[b].bnorm2) {
+                act[b] = 0; hs[b].active = 0;
+            } else {
+                ++n_act;
+            }
+        }
+        check = std::min(check * 2, 32);
+    }
+    for (int64_t b = 0; b < B; ++b)
+        if (act[b]) out.status[b] = HEOM_ENOCONV;
+    return HEOM_OK;
+}
+
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Solve {
+    std::vector<int> iters, refine, status;
+    std::vector<double> res;
+};
+
+// Solve (M + diag(shift) + aug e00 tr) x = b for all columns, FP64 output.
+// prec HEOM_FP64: BiCGStab in FP64 to tol. prec HEOM_MIXED: FP64 residual, FP32 BiCGStab
+// correction to inner_tol, repeat.
+heom_status solve_system(heom_hier *h, const cx<double> *b64, cx<double> *x64, int64_t B,
+                         const cx<double> *shift64, double aug, bool x_zero, double tol,
+                         int max_iter, int prec, Solve &res, cudaStream_t s) {
+    const int64_t rows = h->N * h->d2, L = rows * B;
+    const bool mixed = prec == HEOM_MIXED;
+    size_t bytes = 0;
+    if (!mixed) bytes = align_up(7 * L * sizeof(cx<double>));
+    else bytes = align_up(L * sizeof(cx<double>)) + align_up(9 * L * sizeof(cx<float>)) +
+                 align_up(B * sizeof(cx<float>));
+    heom_status stt = ensure_ws(h->ws, bytes);
+    if (stt != HEOM_OK) return stt;
+    stt = ensure_ws(h->ws_small, align_up(2 * B * sizeof(ColState)) + align_up(B * sizeof(int)));
+    if (stt != HEOM_OK) return stt;
+    ColState *st = (ColState *)h->ws_small.p;
+    ColState *st_out = st + B;
+    int *d_flags = (int *)((char *)h->ws_small.p + align_up(2 * B * sizeof(ColState)));
+    res.iters.assign(B, 0);
+    res.refine.assign(B, 0);
+    res.status.assign(B, HEOM_OK);
+    res.res.assign(B, 0.0);
+    std::vector<int> active(B, 1);
+    if (!mixed) {
+        SolveOut o;
+        cx<double> *work = (cx<double> *)h->ws.p;
+        stt = bicgstab<double>(h, b64, x64, B, shift64, aug, x_zero, tol, max_iter, active, work,
+                               st, d_flags, o, s);
+        if (stt != HEOM_OK) return stt;
+        res.iters = o.iters;
+        res.status = o.status;
+        res.res = o.res;
+        return HEOM_OK;
+    }
+    char *base = (char *)h->ws.p;
+    cx<double> *r64 = (cx<double> *)base;
+    cx<float> *w32 = (cx<float> *)(base + align_up(L * sizeof(cx<double>)));
+    cx<float> *rhs32 = w32 + 7 * L, *d32 = w32 + 8 * L;
+    cx<float> *shift32 = (cx<float> *)((char *)w32 + align_up(9 * L * sizeof(cx<float>)));
+    if (shift64) k_convert<float, double><<<flat_blocks(B), 256, 0, s>>>(B, shift64, shift32);
+    const DevView<double> v64 = h->view64();
+    const int64_t cps = B / h->n_sets;
+    const Geom gd = make_geom(rows, B, std::max<int64_t>(1, 2048 / ((B + 31) / 32)));
+    ApplyMods<double> m64{shift64, aug};
+    std::vector<ColState> hs(B);
+    const double inner_tol = 1e-5;
+    const int max_sweeps = 12;
+    if (x_zero) HEOM_CUDA(cudaMemsetAsync(x64, 0, L * sizeof(cx<double>), s));
+    for (int sweep = 0; sweep <= max_sweeps; ++sweep) {
+        HEOM_CUDA(cudaMemcpyAsync(d_flags, active.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
+        k_state_init<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(st_out, B, d_flags);
+        k_residual64<<<gd.grid, gd.block, 0, s>>>(v64, b64, x64, r64, B, cps, m64, st_out);
+        HEOM_CUDA(cudaGetLastError());
+        HEOM_CUDA(cudaMemcpyAsync(hs.data(), st_out, B * sizeof(ColState), cudaMemcpyDeviceToHost, s));
+        HEOM_CUDA(cudaStreamSynchronize(s));
+        int n_act = 0;
+        for (int64_t b = 0; b < B; ++b) {
+            if (!active[b]) continue;
+            const double rel = hs[b].bnorm2 > 0 ? std::sqrt(hs[b].acc_nr / hs[b].bnorm2) : 0.0;
+            res.res[b] = rel;
+            if (!std::isfinite(rel)) { res.status[b] = HEOM_EBREAKDOWN; active[b] = 0; continue; }
+            if (rel <= tol || res.iters[b] >= max_iter || sweep == max_sweeps) {
+                if (rel > tol) res.status[b] = HEOM_ENOCONV;
+                active[b] = 0;
+                continue;
+            }
+            res.refine[b] = sweep + 1;
+            ++n_act;
+        }
+        if (n_act == 0) break;
+        // keep each residual norm (acc_nr) for the scaling kernels; retire converged columns
+        for (int64_t b = 0; b < B; ++b) hs[b].active = active[b];
+        HEOM_CUDA(cudaMemcpyAsync(st_out, hs.data(), B * sizeof(ColState), cudaMemcpyHostToDevice, s));
+        k_scale_to32<<<gd.grid, gd.block, 0, s>>>(rows, r64, rhs32, B, st_out);
+        HEOM_CUDA(cudaMemsetAsync(d32, 0, L * sizeof(cx<float>), s));
+        int inner_max = 0;
+        for (int64_t b = 0; b < B; ++b)
+            if (active[b]) inner_max = std::max(inner_max, max_iter - res.iters[b]);
+        SolveOut o;
+        stt = bicgstab<float>(h, rhs32, d32, B, shift64 ? shift32 : nullptr, (float)aug, true,
+                              inner_tol, inner_max, active, w32, st, d_flags, o, s);
+        if (stt != HEOM_OK) return stt;
+        for (int64_t b = 0; b < B; ++b)
+            if (active[b]) res.iters[b] += o.iters[b];
+        k_accum64<<<gd.grid, gd.block, 0, s>>>(rows, x64, d32, B, st_out);
+        HEOM_CUDA(cudaGetLastError());
+    }
+    return HEOM_OK;
+}
+
+template <class R>
+heom_status evolve_impl(heom_hier *h, cx<R> *y, int64_t B, double dt, int64_t n_steps,
+                        int64_t save_every, cx<R> *traj, cudaStream_t s) {
+    const DevView<R> v = view_of<R>(h);
+    const int64_t rows = h->N * h->d2, L = rows * B;
+    heom_status st = ensure_ws(h->ws, 3 * L * sizeof(cx<R>));
+    if (st != HEOM_OK) return st;
+    cx<R> *za = (cx<R> *)h->ws.p, *zb = za + L, *acc = za + 2 * L;
+    const Geom g = make_geom(rows, B, 1 << 30);
+    const int64_t cps = B / h->n_sets;
+    const size_t blk = (size_t)h->d2 * B * sizeof(cx<R>);
+    int64_t saved = 0;
+    if (traj) HEOM_CUDA(cudaMemcpyAsync(traj, y, blk, cudaMemcpyDeviceToDevice, s));
+    for (int64_t step = 1; step <= n_steps; ++step) {
+        k_rk4_stage<R><<<g.grid, g.block, 0, s>>>(v, y, za, y, acc, B, cps, (R)dt, 1);
+        k_rk4_stage<R><<<g.grid, g.block, 0, s>>>(v, za, zb, y, acc, B, cps, (R)dt, 2);
+        k_rk4_stage<R><<<g.grid, g.block, 0, s>>>(v, zb, za, y, acc, B, cps, (R)dt, 3);
+        k_rk4_stage<R><<<g.grid, g.block, 0, s>>>(v, za, zb, y, acc, B, cps, (R)dt, 4);
+        if (traj && step % save_every == 0) {
+            ++saved;
+            HEOM_CUDA(cudaMemcpyAsync((char *)traj + saved * blk, y, blk, cudaMemcpyDeviceToDevice, s));
+        }
+    }
+    HEOM_CUDA(cudaGetLastError());
+    HEOM_CUDA(cudaStreamSynchronize(s));
+    return HEOM_OK;
+}
+
+}  // namespace
+}  // namespace heom
+
+using namespace heom;
+
+extern "C" heom_status heom_evolve(heom_hier *h, void *ados, int64_t batch, double dt,
+                                   int64_t n_steps, int64_t save_every, void *rho_traj, int prec,
+                                   heom_stream s) {
+    if (!h || !ados || batch < 1 || batch % h->n_sets != 0 || !std::isfinite(dt) || n_steps < 0 ||
+        (rho_traj && save_every < 1) || (prec != HEOM_FP64 && prec != HEOM_FP32) ||
+        batch > 65535LL * 32) {
+        set_error("heom_evolve: need a hierarchy, ados, batch >= 1 (multiple of n_sets), finite dt, "
+                  "n_steps >= 0, save_every >= 1 with a trajectory, prec FP64 or FP32");
+        return HEOM_EINVAL;
+    }
+    HEOM_CUDA(cudaSetDevice(h->device));
+    if (prec == HEOM_FP64)
+        return evolve_impl<double>(h, (cx<double> *)ados, batch, dt, n_steps, save_every,
+                                   (cx<double> *)rho_traj, (cudaStream_t)s);
+    return evolve_impl<float>(h, (cx<float> *)ados, batch, dt, n_steps, save_every,
+                              (cx<float> *)rho_traj, (cudaStream_t)s);
+}
+
+static void fill_stats(heom_solve_stats *stats, const Solve &r, int64_t off, int64_t n) {
+    if (!stats) return;
+    for (int64_t b = 0; b < n; ++b) {
+        stats[b].iterations = r.iters[off + b];
+        stats[b].refinements = r.refine[off + b];
+        stats[b].residual = r.res[off + b];
+        stats[b].status = r.status[off + b];
+    }
+}
+
+extern "C" heom_status heom_steady(heom_hier *h, const void *x0, void *x_out, int64_t batch,
+                                   double tol, int max_iter, int prec, heom_solve_stats *stats,
+                                   heom_stream s) {
+    if (!h || !x_out || batch < 1 || batch % h->n_sets != 0 || !(tol > 0) || max_iter < 1 ||
+        (prec != HEOM_FP64 && prec != HEOM_MIXED) || batch > 65535LL * 32 || h->parity != 1) {
+        set_error("heom_steady: need an even-parity hierarchy, x_out, batch >= 1 (multiple of "
+                  "n_sets), tol > 0, max_iter >= 1, prec FP64 or MIXED");
+        return HEOM_EINVAL;
+    }
+    HEOM_CUDA(cudaSetDevice(h->device));
+    cudaStream_t st = (cudaStream_t)s;
+    const int64_t rows = h->N * h->d2, L = rows * batch;
+    // the right-hand side e_(0,(0,0)) lives behind the solver workspace in ws_small's sibling
+    DBuf bbuf;
+    heom_status stt = dalloc(bbuf, L * sizeof(cx<double>));
+    if (stt != HEOM_OK) return stt;
+    cx<double> *b64 = (cx<double> *)bbuf.p, *x = (cx<double> *)x_out;
+    k_set_e00<double><<<flat_blocks(L), 256, 0, st>>>(L, b64, batch);
+    if (x0) {
+        if (x0 != x_out) cudaMemcpyAsync(x, x0, L * sizeof(cx<double>), cudaMemcpyDeviceToDevice, st);
+    }
+    // drive ||b - A x|| below tol/10: then ||M x|| / ||x|| <= tol for ||x|| >= 0.2
+    Solve r;
+    stt = solve_system(h, b64, x, batch, nullptr, 1.0, x0 == nullptr, 0.1 * tol, max_iter, prec, r, st);
+    dfree(bbuf);
+    if (stt != HEOM_OK) return stt;
+    // normalise Tr rho_sys = 1 and measure r_ss = ||M x|| / ||x||
+    std::vector<cx<double>> top((size_t)h->d2 * batch);
+    HEOM_CUDA(cudaMemcpyAsync(top.data(), x, top.size() * sizeof(cx<double>), cudaMemcpyDeviceToHost, st));
+    HEOM_CUDA(cudaStreamSynchronize(st));
+    std::vector<cx<double>> fac(batch);
+    for (int64_t b = 0; b < batch; ++b) {
+        cx<double> tr{0.0, 0.0};
+        for (int i = 0; i < h->d; ++i) tr = tr + top[(size_t)(i * h->d + i) * batch + b];
+        fac[b] = (tr.re == 0.0 && tr.im == 0.0) ? cx<double>{1.0, 0.0} : cdiv(cx<double>{1.0, 0.0}, tr);
+    }
+    DBuf tmp;
+    stt = dalloc(tmp, batch * (sizeof(cx<double>) + 2 * sizeof(double)));
+    if (stt != HEOM_OK) return stt;
+    cx<double> *dfac = (cx<double> *)tmp.p;
+    double *norms = (double *)(dfac + batch);
+    HEOM_CUDA(cudaMemcpyAsync(dfac, fac.data(), batch * sizeof(cx<double>), cudaMemcpyHostToDevice, st));
+    k_scale_cols<double><<<flat_blocks(L), 256, 0, st>>>(L, x, batch, dfac);
+    HEOM_CUDA(cudaMemsetAsync(norms, 0, 2 * batch * sizeof(double), st));
+    const Geom gd = make_geom(rows, batch, std::max<int64_t>(1, 2048 / ((batch + 31) / 32)));
+    k_apply_norms<<<gd.grid, gd.block, 0, st>>>(h->view64(), x, batch, batch / h->n_sets, norms);
+    std::vector<double> hn(2 * batch);
+    HEOM_CUDA(cudaMemcpyAsync(hn.data(), norms, hn.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HEOM_CUDA(cudaStreamSynchronize(st));
+    dfree(tmp);
+    heom_status ret = HEOM_OK;
+    for (int64_t b = 0; b < batch; ++b) {
+        r.res[b] = std::sqrt(hn[2 * b] / hn[2 * b + 1]);
+        if (r.status[b] == HEOM_OK && !(r.res[b] <= tol)) r.status[b] = HEOM_ENOCONV;
+        if (r.status[b] != HEOM_OK && ret == HEOM_OK) ret = (heom_status)r.status[b];
+    }
+    fill_stats(stats, r, 0, batch);
+    if (ret != HEOM_OK) set_error("heom_steady: some columns did not converge (see stats)");
+    return ret;
+}
+
+extern "C" heom_status heom_spectrum(heom_hier *odd, const void *ss_ados, const heom_c64 *op_d,
+                                     const double *omega, int64_t n_omega, double tol,
+                                     int max_iter, double *A_out, int prec,
+                                     heom_solve_stats *stats, heom_stream s) {
+    if (!odd || !ss_ados || !op_d || !omega || n_omega < 1 || !(tol > 0) || max_iter < 1 ||
+        !A_out || (prec != HEOM_FP64 && prec != HEOM_MIXED) || odd->n_sets != 1 ||
+        2 * n_omega > 65535LL * 32) {
+        set_error("heom_spectrum: need an odd-parity hierarchy with one parameter set, ss_ados, "
+                  "op_d, omega[n_omega >= 1], A_out, tol > 0, max_iter >= 1, prec FP64 or MIXED");
+        return HEOM_EINVAL;
+    }
+    HEOM_CUDA(cudaSetDevice(odd->device));
+    cudaStream_t st = (cudaStream_t)s;
+    const int d = odd->d;
+    const int64_t B = 2 * n_omega, rows = odd->N * odd->d2, L = rows * B;
+    DBuf buf;
+    heom_status stt = dalloc(buf, L * 2 * sizeof(cx<double>) + B * sizeof(cx<double>) +
+                                      2 * d * d * sizeof(cx<double>));
+    if (stt != HEOM_OK) return stt;
+    cx<double> *b64 = (cx<double> *)buf.p, *x64 = b64 + L, *shift = x64 + L, *ops = shift + B;
+    std::vector<cx<double>> hops(2 * d * d), hshift(B);
+    for (int r = 0; r < d; ++r)
+        for (int c = 0; c < d; ++c) {
+            hops[r * d + c] = {op_d[c * d + r].re, -op_d[c * d + r].im};  // d^dagger
+            hops[d * d + r * d + c] = {op_d[r * d + c].re, op_d[r * d + c].im};
+        }
+    for (int64_t j = 0; j < n_omega; ++j) {
+        hshift[j] = {0.0, omega[j]};             // (M + i w) x_+ = d^dag rho
+        hshift[n_omega + j] = {0.0, -omega[j]};  // (M - i w) x_- = d rho
+    }
+    HEOM_CUDA(cudaMemcpyAsync(ops, hops.data(), hops.size() * sizeof(cx<double>), cudaMemcpyHostToDevice, st));
+    HEOM_CUDA(cudaMemcpyAsync(shift, hshift.data(), B * sizeof(cx<double>), cudaMemcpyHostToDevice, st));
+    k_dos_rhs<<<flat_blocks(L), 256, 0, st>>>(odd->N, d, (const cx<double> *)ss_ados, ops, ops + d * d, b64, n_omega);
+    Solve r;
+    stt = solve_system(odd, b64, x64, B, shift, 0.0, true, tol, max_iter, prec, r, st);
+    if (stt != HEOM_OK) { dfree(buf); return stt; }
+    std::vector<cx<double>> top((size_t)d * d * B);
+    HEOM_CUDA(cudaMemcpyAsync(top.data(), x64, top.size() * sizeof(cx<double>), cudaMemcpyDeviceToHost, st));
+    HEOM_CUDA(cudaStreamSynchronize(st));
+    dfree(buf);
+    heom_status ret = HEOM_OK;
+    for (int64_t j = 0; j < n_omega; ++j) {
+        // -Re{Tr[d x_+] + Tr[d^dag x_-]} / pi with Tr[O X] = sum_{i,l} O[i][l] X[l][i]
+        double acc = 0;
+        for (int i = 0; i < d; ++i)
+            for (int l = 0; l < d; ++l) {
+                const cx<double> xp = top[(size_t)(l * d + i) * B + j];
+                const cx<double> xm = top[(size_t)(l * d + i) * B + n_omega + j];
+                const cx<double> dd{op_d[i * d + l].re, op_d[i * d + l].im};
+                const cx<double> dh{op_d[l * d + i].re, -op_d[l * d + i].im};
+                acc += (dd * xp).re + (dh * xm).re;
+            }
+        A_out[j] = -acc / M_PI;
+    }
+    for (int64_t b = 0; b < B; ++b)
+        if (r.status[b] != HEOM_OK && ret == HEOM_OK) ret = (heom_status)r.status[b];
+    fill_stats(stats, r, 0, B);
+    if (ret != HEOM_OK) set_error("heom_spectrum: some frequencies did not converge (see stats)");
+    return ret;
+}

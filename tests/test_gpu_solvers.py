@@ -1,0 +1,156 @@
+"""Parity of the CUDA solvers (RK4, stationary state, density of states) with the oracle."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import hierarchy as hy
+from oracle import liouvillian as lv
+from oracle import solvers as so
+from tests.helpers import rel_err, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def heom():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    import paper_2306_07522_gb300 as heom
+    return heom
+
+
+def _oracle_rk4(prob, h, rho0, dt, n_steps, save_every):
+    M = lv.build_matrix(prob, h)
+    x0 = lv.to_liouville(so.initial_vector(h.n_ado, rho0))
+    d = rho0.shape[0]
+    _, snaps = so.rk4(lambda v: M @ v, x0, dt, n_steps, save_every,
+                      observe=lambda v: lv.from_liouville(v[: d * d], d)[0])
+    return np.array(snaps)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
+def test_evolve_spin_boson_matches_oracle_rk4(heom, prec, tol):
+    """Spin-boson, tier 4 (35 ADOs), dt = 0.01 to t = 10, snapshots every 0.5."""
+    import torch
+    m = W.spin_boson_model(tier=4)
+    prob = hy.model_to_problem(m)
+    h = hy.problem_hierarchy(prob)
+    ref = _oracle_rk4(prob, h, m.rho0, 0.01, 1000, 50)
+    g = heom.build_hierarchy(heom.problem_from_model(m))
+    x = to_dev(so.initial_vector(h.n_ado, m.rho0), torch.complex128 if prec == "fp64" else torch.complex64)
+    traj = heom.evolve(g, x, 0.01, 1000, 50)
+    got = traj.cpu().numpy().astype(np.complex128)
+    assert got.shape == ref.shape
+    assert rel_err(got, ref) < tol
+    tr = np.trace(got, axis1=1, axis2=2)
+    assert np.abs(tr - 1).max() < (1e-12 if prec == "fp64" else 1e-5)
+
+
+def test_evolve_batched_columns_are_independent(heom):
+    import torch
+    m = W.siam_model(tier=2)
+    prob = hy.model_to_problem(m)
+    h = hy.problem_hierarchy(prob)
+    rhos = [np.diag(v).astype(complex) for v in ([1, 0, 0, 0], [0, 0.5, 0.5, 0], [0, 0, 0, 1])]
+    X = np.stack([so.initial_vector(h.n_ado, r) for r in rhos], axis=-1)
+    g = heom.build_hierarchy(heom.problem_from_model(m))
+    x = to_dev(X, torch.complex128)
+    traj = heom.evolve(g, x, 0.005, 200, 100)
+    got = traj.cpu().numpy()
+    for j, r in enumerate(rhos):
+        ref = _oracle_rk4(prob, h, r, 0.005, 200, 100)
+        assert rel_err(got[..., j], ref) < 1e-10
+
+
+@pytest.mark.parametrize("prec", ["FP64", "MIXED"])
+@pytest.mark.parametrize("name,model", [
+    ("spin_boson_t4", lambda: W.spin_boson_model(tier=4)),
+    ("siam_t2", lambda: W.siam_model(tier=2)),
+    ("siam_t3", lambda: W.siam_model(tier=3)),
+])
+def test_steady_matches_oracle(heom, prec, name, model):
+    import torch
+    m = model()
+    prob = hy.model_to_problem(m)
+    h = hy.problem_hierarchy(prob)
+    M = lv.build_matrix(prob, h)
+    Xo = so.steady_state(M, m.d)
+    g = heom.build_hierarchy(heom.problem_from_model(m))
+    x = torch.zeros((h.n_ado, m.d, m.d), dtype=torch.complex128, device="cuda")
+    st, stats = heom.steady(g, x, tol=1e-10, max_iter=3000, prec=getattr(heom, prec))
+    X = x.cpu().numpy()
+    assert stats[0]["residual"] <= 1e-10
+    assert abs(np.trace(X[0]) - 1) < 1e-12
+    # the oracle's own residual of the GPU solution (independent check of r_ss)
+    assert so.steady_residual(M, X) <= 1.5e-10
+    assert rel_err(X[0], Xo[0]) < 1e-7
+
+
+def test_steady_batched_parameter_sets(heom):
+    """Three SIAM parameter sets (different U, bias) solved as one batch."""
+    import torch
+    models = [W.siam_model(tier=2, U=u, mu=mu) for u, mu in ((10.0, 1.0), (4.0, 0.3), (7.0, 2.0))]
+    g = heom.build_hierarchy(heom.problem_from_model(models[0]))
+    Hs, coefs, rates = [], [], []
+    for m in models:
+        p = heom.problem_from_model(m)
+        Hs.append(p["H"])
+        coefs.append(np.concatenate([b["coef"] for b in p["baths"]]))
+        rates.append(np.concatenate([b["rate"] for b in p["baths"]]))
+    heom.set_params(g, np.array(Hs), np.array(coefs), np.array(rates))
+    x = torch.zeros((g.n_ado, 4, 4, 3), dtype=torch.complex128, device="cuda")
+    st, stats = heom.steady(g, x, tol=1e-9, max_iter=3000, prec=heom.MIXED)
+    X = x.cpu().numpy()
+    for j, m in enumerate(models):
+        prob = hy.model_to_problem(m)
+        h = hy.problem_hierarchy(prob)
+        M = lv.build_matrix(prob, h)
+        assert stats[j]["residual"] <= 1e-9
+        assert rel_err(X[..., j][0], so.steady_state(M, 4)[0]) < 1e-6
+
+
+def test_steady_warm_start_from_solution_needs_no_iterations(heom):
+    import torch
+    m = W.siam_model(tier=2)
+    prob = hy.model_to_problem(m)
+    h = hy.problem_hierarchy(prob)
+    Xo = so.steady_state(lv.build_matrix(prob, h), 4)
+    g = heom.build_hierarchy(heom.problem_from_model(m))
+    x0 = to_dev(Xo, torch.complex128)
+    x = torch.zeros_like(x0)
+    st, stats = heom.steady(g, x, x0=x0, tol=1e-8, prec=heom.MIXED)
+    assert stats[0]["iterations"] == 0 and stats[0]["residual"] < 1e-8
+
+
+@pytest.mark.parametrize("prec", ["FP64", "MIXED"])
+def test_dos_noninteracting_level_closed_form(heom, prec):
+    """A(w) = -Im G^R(w) / pi for a noninteracting level (odd-parity HEOM, tier 2)."""
+    import torch
+    eps, G, Wd, kT, mus = 0.3, 1.0, 4.0, 0.5, (1.0, -0.5)
+    m = W.single_level_model(eps, G, Wd, kT, mus[0], mus[1], 4, 2)
+    even = heom.build_hierarchy(heom.problem_from_model(m, 1))
+    odd = heom.build_hierarchy(heom.problem_from_model(m, -1))
+    x = torch.zeros((even.n_ado, 2, 2), dtype=torch.complex128, device="cuda")
+    heom.steady(even, x, tol=1e-12, max_iter=4000, prec=heom.FP64)
+    om = np.linspace(-6, 6, 25)
+    A, st, stats = heom.spectrum(odd, x, m.fermion_baths[0][0], om, tol=1e-10, max_iter=4000,
+                                 prec=getattr(heom, prec))
+    GR = 1.0 / (om - eps - sum(0.5 * G * Wd / (om - mu + 1j * Wd) for mu in mus))
+    assert np.abs(A - (-GR.imag / np.pi)).max() < 1e-8
+    assert max(s["residual"] for s in stats) <= 1e-10
+
+
+def test_dos_siam_matches_oracle(heom):
+    import torch
+    m = W.siam_model(tier=2)
+    prob = hy.model_to_problem(m)
+    h = hy.problem_hierarchy(prob)
+    M = lv.build_matrix(prob, h)
+    Xo = so.steady_state(M, 4)
+    Mo = lv.build_matrix(hy.model_to_problem(m, -1), h)
+    om = np.array([-12.0, -5.0, -1.0, 0.0, 0.7, 3.0, 9.0])
+    Ao = so.dos(Mo, Xo, m.fermion_baths[0][0], om)
+    odd = heom.build_hierarchy(heom.problem_from_model(m, -1))
+    A, st, stats = heom.spectrum(odd, to_dev(Xo, torch.complex128), m.fermion_baths[0][0], om,
+                                 tol=1e-10, max_iter=4000, prec=heom.MIXED)
+    assert np.abs(A - Ao).max() < 1e-8 * np.abs(Ao).max()

@@ -261,3 +261,15 @@ def test_siam_dos_symmetry_and_hubbard_peaks():
     assert np.abs(A - A[::-1]).max() < 1e-10
     left = om[np.argmax(np.where(om < -2, A, 0))]
     assert -7.5 <= left <= -4.0
+
+
+@pytest.mark.parametrize("parity", [1, -1])
+def test_integer_tables_reproduce_the_apply(parity):
+    """oracle/tables.py (the integer tables the GPU must match) against the loop path."""
+    from oracle import tables as tb
+    prob = W.random_raw_problem(3, [("RI", 2), ("I", 1)], [4, 2], 2, 2, parity=parity, seed=21)
+    h = hy.problem_hierarchy(prob)
+    X = W.random_ado_vector(h.n_ado, 3, seed=22)
+    Y1 = lv.apply_loop(prob, X, h)
+    Y3 = tb.apply_from_tables(prob, X, h)
+    assert np.abs(Y1 - Y3).max() <= 1e-13 * np.abs(Y1).max()
