@@ -207,6 +207,36 @@ heom_status heom_spectrum(heom_hier *odd, const void *ss_ados, const heom_c64 *o
                           const double *omega, int64_t n_omega, double tol, int max_iter,
                           double *A_out, int prec, heom_solve_stats *stats, heom_stream s);
 
+/* ---------------------------------------------------------------- launch accounting */
+
+/* Measurement support for benchmarks; the paper has no counterpart. While enabled, every
+ * kernel the library launches is counted in one of these classes and bracketed by a pair of
+ * CUDA events on its stream. heom_profile_read waits for those events and returns, for one
+ * class, the number of launches, their summed device time in milliseconds, the work units
+ * they processed (ADO-applies -- one d x d output block of one batch column -- for the apply
+ * classes, vector elements for the others) and their algorithmic bytes: the compulsory
+ * reads and writes of the vectors each kernel streams, one pass per vector, with the
+ * neighbour re-reads of the apply counted as zero. heom_profile_enable(1) resets every
+ * counter; heom_profile_enable(0) stops recording. Not thread-safe; meant for one
+ * benchmarking thread. */
+typedef enum {
+    HEOM_KC_APPLY = 0,           /* heom_apply                                       */
+    HEOM_KC_RK4 = 1,             /* fused RK4 stages (one apply each)                */
+    HEOM_KC_KRYLOV_APPLY32 = 2,  /* apply + dot products inside FP32 BiCGStab         */
+    HEOM_KC_KRYLOV_APPLY64 = 3,  /* apply + dot products inside FP64 BiCGStab         */
+    HEOM_KC_KRYLOV_VECTOR = 4,   /* BiCGStab vector updates and start-up              */
+    HEOM_KC_RESIDUAL64 = 5,      /* FP64 residual applies (refinement, final norms)   */
+    HEOM_KC_OTHER = 6,           /* right-hand sides, scaling, normalisation          */
+    HEOM_KC_COUNT = 7
+} heom_kernel_class;
+
+heom_status heom_profile_enable(int on);
+heom_status heom_profile_read(int cls, int64_t *launches, double *device_ms, double *units,
+                              double *bytes);
+/* Bytes the library copied host -> device and device -> host while accounting was on
+ * (table and parameter uploads, right-hand sides, convergence flags, results). */
+heom_status heom_profile_copies(int64_t *h2d_bytes, int64_t *d2h_bytes);
+
 #ifdef __cplusplus
 }
 #endif

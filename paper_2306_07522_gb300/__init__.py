@@ -18,13 +18,16 @@ LIBRARY_PATH = os.path.join(_HERE, "libheom.so")
 
 if not os.path.exists(LIBRARY_PATH):
     raise ImportError(f"libheom.so is not built ({LIBRARY_PATH}); run "
-                      "`python -m paper_2306_07522_gb300.build` or __graft_entry__.build()")
+                      "`python paper_2306_07522_gb300/build.py` or __graft_entry__.build()")
 _lib = C.CDLL(LIBRARY_PATH)
 
 # ------------------------------------------------------------------------- ABI types
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EBREAKDOWN, ENOTSUP = range(7)
 BOSON_R, BOSON_I, BOSON_RI, FERMION = range(4)
 FP64, FP32, MIXED = range(3)
+KERNEL_CLASSES = ("apply", "rk4", "krylov_apply_fp32", "krylov_apply_fp64", "krylov_vector",
+                  "residual_fp64", "other")
+APPLY_CLASSES = ("apply", "rk4", "krylov_apply_fp32", "krylov_apply_fp64", "residual_fp64")
 KIND = {"R": BOSON_R, "I": BOSON_I, "RI": BOSON_RI, "F": FERMION}
 STATUS_NAMES = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA",
                 ENOCONV: "ENOCONV", EBREAKDOWN: "EBREAKDOWN", ENOTSUP: "ENOTSUP"}
@@ -69,6 +72,9 @@ _sig = {
     "heom_evolve": [_P, _P, C.c_int64, C.c_double, C.c_int64, C.c_int64, _P, C.c_int, _P],
     "heom_steady": [_P, _P, _P, C.c_int64, C.c_double, C.c_int, C.c_int, _P, _P],
     "heom_spectrum": [_P, _P, _P, _P, C.c_int64, C.c_double, C.c_int, _P, C.c_int, _P, _P],
+    "heom_profile_enable": [C.c_int],
+    "heom_profile_read": [C.c_int, _P, _P, _P, _P],
+    "heom_profile_copies": [_P, _P],
 }
 EXPORTED = sorted(list(_sig) + ["heom_destroy", "heom_last_error"])
 for _name, _args in _sig.items():
@@ -314,3 +320,26 @@ def spectrum(odd: Hierarchy, ss, op_d, omegas, tol: float = 1e-8, max_iter: int 
     if raise_on_error:
         _check(st, "heom_spectrum")
     return A, st, _stats_list(stats)
+
+
+# ------------------------------------------------------------------------- launch accounting
+def profile_enable(on: bool = True):
+    _check(_lib.heom_profile_enable(int(on)), "heom_profile_enable")
+
+
+def profile_read() -> dict:
+    """{class name: dict(launches, ms, units, bytes)} for every kernel class."""
+    out = {}
+    for i, name in enumerate(KERNEL_CLASSES):
+        n, ms, u, by = C.c_int64(), C.c_double(), C.c_double(), C.c_double()
+        _check(_lib.heom_profile_read(i, C.byref(n), C.byref(ms), C.byref(u), C.byref(by)),
+               "heom_profile_read")
+        out[name] = dict(launches=n.value, ms=ms.value, units=u.value, bytes=by.value)
+    return out
+
+
+def profile_copies():
+    """(host->device bytes, device->host bytes) copied by the library while accounting was on."""
+    a, b = C.c_int64(), C.c_int64()
+    _check(_lib.heom_profile_copies(C.byref(a), C.byref(b)), "heom_profile_copies")
+    return a.value, b.value

@@ -1,6 +1,8 @@
 """Compile libheom.so in-tree for sm_103a (nvcc for the kernels, g++ for the host code).
 
-Usage: ``python -m paper_2306_07522_gb300.build`` or ``__graft_entry__.build()``. The
+Usage: ``python paper_2306_07522_gb300/build.py`` or ``__graft_entry__.build()`` (this file is
+run by path, not imported as a submodule, because the package refuses to import before
+libheom.so exists). The
 translation units compile in parallel; objects go to ``_build/`` next to this file.
 """
 from __future__ import annotations

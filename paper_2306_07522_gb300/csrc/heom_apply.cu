@@ -56,6 +56,7 @@ template <class R>
 cudaError_t launch_apply(const DevView<R> &v, const cx<R> *x, cx<R> *y, int64_t B,
                          const ApplyMods<R> &mods, cudaStream_t s) {
     Geom g = make_geom(v.N * v.d2, B, 1 << 30);
+    Prof pr(HEOM_KC_APPLY, s, (double)v.N * B, 2.0 * v.N * B * v.d2 * sizeof(cx<R>));
     k_apply<R><<<g.grid, g.block, 0, s>>>(v, x, y, B, B / v.n_sets, mods);
     return cudaGetLastError();
 }

@@ -264,7 +264,10 @@ template <class T>
 heom_status upload(DBuf &b, const std::vector<T> &v) {
     heom_status st = heom::dalloc(b, v.size() * sizeof(T));
     if (st != HEOM_OK) return st;
-    if (!v.empty()) HEOM_CUDA(cudaMemcpy(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    if (!v.empty()) {
+        HEOM_CUDA(heom::memcpy_counted(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, 0));
+        HEOM_CUDA(cudaStreamSynchronize(0));
+    }
     return HEOM_OK;
 }
 
@@ -683,3 +686,108 @@ extern "C" void heom_destroy(heom_hier *h) {
 }
 
 extern "C" const char *heom_last_error(void) { return heom::g_err.c_str(); }
+
+// ======================================================================= launch accounting
+namespace {
+struct ProfRec {
+    int cls;
+    cudaEvent_t a, b;
+    double units;
+};
+struct ProfState {
+    bool on = false;
+    std::vector<ProfRec> pending;
+    std::vector<cudaEvent_t> pool;
+    int64_t launches[HEOM_KC_COUNT] = {};
+    double ms[HEOM_KC_COUNT] = {};
+    double units[HEOM_KC_COUNT] = {};
+    double bytes[HEOM_KC_COUNT] = {};
+    int64_t h2d = 0, d2h = 0;
+    cudaEvent_t open_ev = nullptr;
+};
+ProfState g_prof;
+
+cudaEvent_t prof_event() {
+    if (!g_prof.pool.empty()) {
+        cudaEvent_t e = g_prof.pool.back();
+        g_prof.pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void prof_drain() {
+    for (ProfRec &r : g_prof.pending) {
+        float t = 0.f;
+        if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess)
+            g_prof.ms[r.cls] += t;
+        g_prof.pool.push_back(r.a);
+        g_prof.pool.push_back(r.b);
+    }
+    g_prof.pending.clear();
+}
+}  // namespace
+
+namespace heom {
+bool prof_on() { return g_prof.on; }
+cudaError_t memcpy_counted(void *dst, const void *src, size_t bytes, cudaMemcpyKind kind,
+                           cudaStream_t s) {
+    if (g_prof.on) {
+        if (kind == cudaMemcpyHostToDevice) g_prof.h2d += (int64_t)bytes;
+        if (kind == cudaMemcpyDeviceToHost) g_prof.d2h += (int64_t)bytes;
+    }
+    return cudaMemcpyAsync(dst, src, bytes, kind, s);
+}
+void prof_begin(int cls, cudaStream_t s) {
+    (void)cls;
+    g_prof.open_ev = prof_event();
+    cudaEventRecord(g_prof.open_ev, s);
+}
+void prof_end(int cls, cudaStream_t s, double units, double bytes) {
+    cudaEvent_t e = prof_event();
+    cudaEventRecord(e, s);
+    g_prof.pending.push_back({cls, g_prof.open_ev, e, units});
+    g_prof.launches[cls] += 1;
+    g_prof.units[cls] += units;
+    g_prof.bytes[cls] += bytes;
+    if (g_prof.pending.size() > 4096) prof_drain();
+}
+}  // namespace heom
+
+extern "C" heom_status heom_profile_enable(int on) {
+    prof_drain();
+    if (on) {
+        for (int c = 0; c < HEOM_KC_COUNT; ++c) {
+            g_prof.launches[c] = 0;
+            g_prof.ms[c] = 0;
+            g_prof.units[c] = 0;
+            g_prof.bytes[c] = 0;
+        }
+        g_prof.h2d = 0;
+        g_prof.d2h = 0;
+    }
+    g_prof.on = on != 0;
+    return HEOM_OK;
+}
+
+extern "C" heom_status heom_profile_read(int cls, int64_t *launches, double *device_ms,
+                                         double *units, double *bytes) {
+    if (cls < 0 || cls >= HEOM_KC_COUNT) {
+        set_error("heom_profile_read: class out of range");
+        return HEOM_EINVAL;
+    }
+    prof_drain();
+    if (launches) *launches = g_prof.launches[cls];
+    if (device_ms) *device_ms = g_prof.ms[cls];
+    if (units) *units = g_prof.units[cls];
+    if (bytes) *bytes = g_prof.bytes[cls];
+    return HEOM_OK;
+}
+
+extern "C" heom_status heom_profile_copies(int64_t *h2d_bytes, int64_t *d2h_bytes) {
+    if (h2d_bytes) *h2d_bytes = g_prof.h2d;
+    if (d2h_bytes) *d2h_bytes = g_prof.d2h;
+    return HEOM_OK;
+}

@@ -163,6 +163,28 @@ struct Geom {
 };
 Geom make_geom(int64_t rows, int64_t B, int max_blocks_x = 0);
 
+// launch accounting: RAII bracket of one kernel launch (see heom_profile_enable)
+bool prof_on();
+void prof_begin(int cls, cudaStream_t s);
+void prof_end(int cls, cudaStream_t s, double units, double bytes);
+struct Prof {
+    int cls;
+    cudaStream_t s;
+    double units, bytes;
+    bool on;
+    Prof(int c, cudaStream_t st, double u, double by = 0.0)
+        : cls(c), s(st), units(u), bytes(by), on(prof_on()) {
+        if (on) prof_begin(cls, s);
+    }
+    ~Prof() {
+        if (on) prof_end(cls, s, units, bytes);
+    }
+};
+
+// cudaMemcpyAsync that adds host<->device bytes to the accounting when it is on
+cudaError_t memcpy_counted(void *dst, const void *src, size_t bytes, cudaMemcpyKind kind,
+                           cudaStream_t s);
+
 // kernels (heom_kernels.cu)
 template <class R>
 cudaError_t launch_apply(const DevView<R> &v, const cx<R> *x, cx<R> *y, int64_t B,

@@ -260,9 +260,15 @@ __global__ void __launch_bounds__(256) k_bicg_x(int64_t rows, cx<R> *x, const cx
     const bool act = b < B && st[b].active;
     double rr_re = 0, rr_im = 0, nr = 0;
     cx<double> omega{0.0, 0.0};
+    bool bad = false;
     if (act) {
         const ColState c = st[b];
         omega = c.acc_tt.re == 0.0 ? cx<double>{0.0, 0.0} : cdiv(c.acc_ts, c.acc_tt);
+        bad = !isfinite(omega.re) || !isfinite(omega.im) || !isfinite(c.alpha.re) ||
+              !isfinite(c.alpha.im);
+    }
+    if (act && !bad) {
+        const ColState c = st[b];
         const cx<R> al = cast<R>(c.alpha), om = cast<R>(omega);
         ROW_LOOP {
             const int64_t i = row * B + b;
@@ -278,8 +284,11 @@ __global__ void __launch_bounds__(256) k_bicg_x(int64_t rows, cx<R> *x, const cx
     double val[3] = {rr_re, rr_im, nr};
     double *const dst[3] = {act ? &st[b].acc_rr.re : nullptr, act ? &st[b].acc_rr.im : nullptr,
                             act ? &st[b].acc_nr : nullptr};
-    reduce_add<3>(val, dst, act);
-    if (act && designated()) st[b].omega = omega;
+    reduce_add<3>(val, dst, act && !bad);
+    if (act && designated()) {
+        st[b].omega = omega;
+        if (bad) st[b].flag = 1;
+    }
 }
 
 // ------------------------------------------------------------------ refinement helpers
@@ -315,28 +324,30 @@ __global__ void __launch_bounds__(256) k_residual64(DevView<double> v, const cx<
     reduce_add<2>(val, dst, act);
 }
 
-// r32 = r64 / ||r64|| per active column
-__global__ void k_scale_to32(int64_t rows, const cx<double> *__restrict__ r64,
-                             cx<float> *__restrict__ r32, int64_t B, const ColState *st) {
+// rin = r64 / ||r64|| per active column, in the inner solver's precision
+template <class RI>
+__global__ void k_scale_to(int64_t rows, const cx<double> *__restrict__ r64,
+                           cx<RI> *__restrict__ rin, int64_t B, const ColState *st) {
     const int64_t b = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
     if (b >= B || !st[b].active) return;
     const double inv = 1.0 / std::sqrt(st[b].acc_nr);
     ROW_LOOP {
         const int64_t i = row * B + b;
-        r32[i] = cx<float>{float(r64[i].re * inv), float(r64[i].im * inv)};
+        rin[i] = cx<RI>{RI(r64[i].re * inv), RI(r64[i].im * inv)};
     }
 }
 
-// x64 += ||r64|| d32 per active column
-__global__ void k_accum64(int64_t rows, cx<double> *__restrict__ x, const cx<float> *__restrict__ d32,
-                          int64_t B, const ColState *st) {
+// x64 += ||r64|| d per active column
+template <class RI>
+__global__ void k_accum(int64_t rows, cx<double> *__restrict__ x, const cx<RI> *__restrict__ dv,
+                        int64_t B, const ColState *st) {
     const int64_t b = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
     if (b >= B || !st[b].active) return;
     const double s = std::sqrt(st[b].acc_nr);
     ROW_LOOP {
         const int64_t i = row * B + b;
-        x[i].re += s * (double)d32[i].re;
-        x[i].im += s * (double)d32[i].im;
+        x[i].re += s * (double)dv[i].re;
+        x[i].im += s * (double)dv[i].im;
     }
 }
 
@@ -433,9 +444,17 @@ heom_status bicgstab(heom_hier *h, const cx<R> *bvec, cx<R> *x, int64_t B, const
     const Geom gd = make_geom(rows, B, std::max<int64_t>(1, 2048 / ((B + 31) / 32)));
     const Geom ga = gd;
     ApplyMods<R> mods{shift, aug};
-    HEOM_CUDA(cudaMemcpyAsync(d_flags, active.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
-    k_state_init<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(st, B, d_flags);
-    k_bicg_init<R><<<gd.grid, gd.block, 0, s>>>(v, bvec, x, r, rh, p, vv, B, cps, mods, x_zero, st);
+    HEOM_CUDA(memcpy_counted(d_flags, active.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
+    int n_act0 = 0;
+    for (int a : active) n_act0 += a != 0;
+    {
+        Prof pr(HEOM_KC_KRYLOV_VECTOR, s, (double)B);
+        k_state_init<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(st, B, d_flags);
+    }
+    {
+        Prof pr(HEOM_KC_KRYLOV_VECTOR, s, (double)rows * n_act0, (x_zero ? 5.0 : 6.0) * rows * n_act0 * sizeof(cx<R>));
+        k_bicg_init<R><<<gd.grid, gd.block, 0, s>>>(v, bvec, x, r, rh, p, vv, B, cps, mods, x_zero, st);
+    }
     HEOM_CUDA(cudaGetLastError());
     std::vector<ColState> hs(B);
     std::vector<int> act = active;
@@ -444,7 +463,7 @@ heom_status bicgstab(heom_hier *h, const cx<R> *bvec, cx<R> *x, int64_t B, const
     out.res.assign(B, 0.0);
     const double tol2 = tol * tol;
     // columns whose initial residual already meets tol
-    HEOM_CUDA(cudaMemcpyAsync(hs.data(), st, B * sizeof(ColState), cudaMemcpyDeviceToHost, s));
+    HEOM_CUDA(memcpy_counted(hs.data(), st, B * sizeof(ColState), cudaMemcpyDeviceToHost, s));
     HEOM_CUDA(cudaStreamSynchronize(s));
     int n_act = 0;
     for (int64_t b = 0; b < B; ++b) {
@@ -455,18 +474,26 @@ heom_status bicgstab(heom_hier *h, const cx<R> *bvec, cx<R> *x, int64_t B, const
     }
     int it = 0, check = 4;
     while (n_act > 0 && it < max_iter) {
-        HEOM_CUDA(cudaMemcpyAsync(st, hs.data(), B * sizeof(ColState), cudaMemcpyHostToDevice, s));
+        HEOM_CUDA(memcpy_counted(st, hs.data(), B * sizeof(ColState), cudaMemcpyHostToDevice, s));
         const int steps = std::min(check, max_iter - it);
+        const int kc_apply = sizeof(R) == 4 ? HEOM_KC_KRYLOV_APPLY32 : HEOM_KC_KRYLOV_APPLY64;
+        const double u_vec = (double)rows * n_act, u_app = (double)h->N * n_act;
+        const double sz = sizeof(cx<R>), e_vec = u_vec * sz;
         for (int k = 0; k < steps; ++k) {
-            k_bicg_p<R><<<gd.grid, gd.block, 0, s>>>(v, r, p, vv, ph, B, cps, shift, 1, st);
-            k_bicg_apply<R><<<ga.grid, ga.block, 0, s>>>(v, ph, vv, rh, B, cps, mods, 0, st);
-            k_bicg_s<R><<<gd.grid, gd.block, 0, s>>>(v, r, vv, sh, B, cps, shift, 1, st);
-            k_bicg_apply<R><<<ga.grid, ga.block, 0, s>>>(v, sh, t, r, B, cps, mods, 1, st);
-            k_bicg_x<R><<<gd.grid, gd.block, 0, s>>>(rows, x, ph, sh, r, t, rh, B, st);
+            { Prof pr(HEOM_KC_KRYLOV_VECTOR, s, u_vec, 5.0 * e_vec);
+              k_bicg_p<R><<<gd.grid, gd.block, 0, s>>>(v, r, p, vv, ph, B, cps, shift, 1, st); }
+            { Prof pr(kc_apply, s, u_app, 3.0 * e_vec);
+              k_bicg_apply<R><<<ga.grid, ga.block, 0, s>>>(v, ph, vv, rh, B, cps, mods, 0, st); }
+            { Prof pr(HEOM_KC_KRYLOV_VECTOR, s, u_vec, 4.0 * e_vec);
+              k_bicg_s<R><<<gd.grid, gd.block, 0, s>>>(v, r, vv, sh, B, cps, shift, 1, st); }
+            { Prof pr(kc_apply, s, u_app, 3.0 * e_vec);
+              k_bicg_apply<R><<<ga.grid, ga.block, 0, s>>>(v, sh, t, r, B, cps, mods, 1, st); }
+            { Prof pr(HEOM_KC_KRYLOV_VECTOR, s, u_vec, 8.0 * e_vec);
+              k_bicg_x<R><<<gd.grid, gd.block, 0, s>>>(rows, x, ph, sh, r, t, rh, B, st); }
         }
         HEOM_CUDA(cudaGetLastError());
         it += steps;
-        HEOM_CUDA(cudaMemcpyAsync(hs.data(), st, B * sizeof(ColState), cudaMemcpyDeviceToHost, s));
+        HEOM_CUDA(memcpy_counted(hs.data(), st, B * sizeof(ColState), cudaMemcpyDeviceToHost, s));
         HEOM_CUDA(cudaStreamSynchronize(s));
         n_act = 0;
         for (int64_t b = 0; b < B; ++b) {
@@ -497,18 +524,21 @@ struct Solve {
     std::vector<double> res;
 };
 
-// Solve (M + diag(shift) + aug e00 tr) x = b for all columns, FP64 output.
-// prec HEOM_FP64: BiCGStab in FP64 to tol. prec HEOM_MIXED: FP64 residual, FP32 BiCGStab
-// correction to inner_tol, repeat.
-heom_status solve_system(heom_hier *h, const cx<double> *b64, cx<double> *x64, int64_t B,
+// Solve (M + diag(shift) + aug e00 tr) x = b for all columns, FP64 output, by iterative
+// refinement: r = b - A x in FP64, then BiCGStab on A d = r / ||r|| in the inner precision RI,
+// x += ||r|| d, until the FP64 residual meets tol. RI = float is the mixed-precision path
+// (inner tolerance 1e-5); RI = double is the plain FP64 path, whose inner tolerance asks for
+// the whole remaining reduction at once and whose outer loop only guards against the drift
+// between BiCGStab's recursive residual and the true one.
+constexpr int kInnerCap = 400;
+
+template <class RI>
+heom_status refine_solve(heom_hier *h, const cx<double> *b64, cx<double> *x64, int64_t B,
                          const cx<double> *shift64, double aug, bool x_zero, double tol,
-                         int max_iter, int prec, Solve &res, cudaStream_t s) {
+                         int max_iter, Solve &res, cudaStream_t s) {
     const int64_t rows = h->N * h->d2, L = rows * B;
-    const bool mixed = prec == HEOM_MIXED;
-    size_t bytes = 0;
-    if (!mixed) bytes = align_up(7 * L * sizeof(cx<double>));
-    else bytes = align_up(L * sizeof(cx<double>)) + align_up(9 * L * sizeof(cx<float>)) +
-                 align_up(B * sizeof(cx<float>));
+    const size_t bytes = align_up(L * sizeof(cx<double>)) + align_up(9 * L * sizeof(cx<RI>)) +
+                         align_up(B * sizeof(cx<RI>));
     heom_status stt = ensure_ws(h->ws, bytes);
     if (stt != HEOM_OK) return stt;
     stt = ensure_ws(h->ws_small, align_up(2 * B * sizeof(ColState)) + align_up(B * sizeof(int)));
@@ -521,39 +551,37 @@ heom_status solve_system(heom_hier *h, const cx<double> *b64, cx<double> *x64, i
     res.status.assign(B, HEOM_OK);
     res.res.assign(B, 0.0);
     std::vector<int> active(B, 1);
-    if (!mixed) {
-        SolveOut o;
-        cx<double> *work = (cx<double> *)h->ws.p;
-        stt = bicgstab<double>(h, b64, x64, B, shift64, aug, x_zero, tol, max_iter, active, work,
-                               st, d_flags, o, s);
-        if (stt != HEOM_OK) return stt;
-        res.iters = o.iters;
-        res.status = o.status;
-        res.res = o.res;
-        return HEOM_OK;
-    }
     char *base = (char *)h->ws.p;
     cx<double> *r64 = (cx<double> *)base;
-    cx<float> *w32 = (cx<float> *)(base + align_up(L * sizeof(cx<double>)));
-    cx<float> *rhs32 = w32 + 7 * L, *d32 = w32 + 8 * L;
-    cx<float> *shift32 = (cx<float> *)((char *)w32 + align_up(9 * L * sizeof(cx<float>)));
-    if (shift64) k_convert<float, double><<<flat_blocks(B), 256, 0, s>>>(B, shift64, shift32);
+    cx<RI> *w = (cx<RI> *)(base + align_up(L * sizeof(cx<double>)));
+    cx<RI> *rhs = w + 7 * L, *dv = w + 8 * L;
+    cx<RI> *shift_in = (cx<RI> *)((char *)w + align_up(9 * L * sizeof(cx<RI>)));
+    if (shift64) {
+        Prof pr(HEOM_KC_OTHER, s, (double)B);
+        k_convert<RI, double><<<flat_blocks(B), 256, 0, s>>>(B, shift64, shift_in);
+    }
     const DevView<double> v64 = h->view64();
     const int64_t cps = B / h->n_sets;
     const Geom gd = make_geom(rows, B, std::max<int64_t>(1, 2048 / ((B + 31) / 32)));
     ApplyMods<double> m64{shift64, aug};
     std::vector<ColState> hs(B);
-    const double inner_tol = 1e-5;
-    const int max_sweeps = 12;
+    std::vector<int> breakdowns(B, 0);
+    const bool plain = sizeof(RI) == 8;
+    const int max_sweeps = plain ? 6 : 12;
     if (x_zero) HEOM_CUDA(cudaMemsetAsync(x64, 0, L * sizeof(cx<double>), s));
     for (int sweep = 0; sweep <= max_sweeps; ++sweep) {
-        HEOM_CUDA(cudaMemcpyAsync(d_flags, active.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
-        k_state_init<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(st_out, B, d_flags);
-        k_residual64<<<gd.grid, gd.block, 0, s>>>(v64, b64, x64, r64, B, cps, m64, st_out);
+        HEOM_CUDA(memcpy_counted(d_flags, active.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
+        int n_on = 0;
+        for (int a : active) n_on += a != 0;
+        { Prof pr(HEOM_KC_OTHER, s, (double)B);
+          k_state_init<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(st_out, B, d_flags); }
+        { Prof pr(HEOM_KC_RESIDUAL64, s, (double)h->N * n_on, 3.0 * rows * n_on * sizeof(cx<double>));
+          k_residual64<<<gd.grid, gd.block, 0, s>>>(v64, b64, x64, r64, B, cps, m64, st_out); }
         HEOM_CUDA(cudaGetLastError());
-        HEOM_CUDA(cudaMemcpyAsync(hs.data(), st_out, B * sizeof(ColState), cudaMemcpyDeviceToHost, s));
+        HEOM_CUDA(memcpy_counted(hs.data(), st_out, B * sizeof(ColState), cudaMemcpyDeviceToHost, s));
         HEOM_CUDA(cudaStreamSynchronize(s));
         int n_act = 0;
+        double worst = 0.0;
         for (int64_t b = 0; b < B; ++b) {
             if (!active[b]) continue;
             const double rel = hs[b].bnorm2 > 0 ? std::sqrt(hs[b].acc_nr / hs[b].bnorm2) : 0.0;
@@ -564,28 +592,53 @@ heom_status solve_system(heom_hier *h, const cx<double> *b64, cx<double> *x64, i
                 active[b] = 0;
                 continue;
             }
-            res.refine[b] = sweep + 1;
+            res.refine[b] = plain ? 0 : sweep + 1;
+            worst = std::max(worst, rel);
             ++n_act;
         }
         if (n_act == 0) break;
         // keep each residual norm (acc_nr) for the scaling kernels; retire converged columns
         for (int64_t b = 0; b < B; ++b) hs[b].active = active[b];
-        HEOM_CUDA(cudaMemcpyAsync(st_out, hs.data(), B * sizeof(ColState), cudaMemcpyHostToDevice, s));
-        k_scale_to32<<<gd.grid, gd.block, 0, s>>>(rows, r64, rhs32, B, st_out);
-        HEOM_CUDA(cudaMemsetAsync(d32, 0, L * sizeof(cx<float>), s));
+        HEOM_CUDA(memcpy_counted(st_out, hs.data(), B * sizeof(ColState), cudaMemcpyHostToDevice, s));
+        { Prof pr(HEOM_KC_OTHER, s, (double)rows * n_act, (16.0 + sizeof(cx<RI>)) * rows * n_act);
+          k_scale_to<RI><<<gd.grid, gd.block, 0, s>>>(rows, r64, rhs, B, st_out); }
+        HEOM_CUDA(cudaMemsetAsync(dv, 0, L * sizeof(cx<RI>), s));
         int inner_max = 0;
         for (int64_t b = 0; b < B; ++b)
             if (active[b]) inner_max = std::max(inner_max, max_iter - res.iters[b]);
+        // FP32 BiCGStab reaches about 1e-5 at best on these systems, so each mixed sweep asks
+        // for 1e-4 and at most kInnerCap iterations; refinement supplies the remaining digits.
+        const double inner_tol = plain ? std::max(0.5 * tol / worst, 1e-14) : 1e-4;
+        if (!plain) inner_max = std::min(inner_max, kInnerCap);
         SolveOut o;
-        stt = bicgstab<float>(h, rhs32, d32, B, shift64 ? shift32 : nullptr, (float)aug, true,
-                              inner_tol, inner_max, active, w32, st, d_flags, o, s);
+        stt = bicgstab<RI>(h, rhs, dv, B, shift64 ? shift_in : nullptr, (RI)aug, true, inner_tol,
+                           inner_max, active, w, st, d_flags, o, s);
         if (stt != HEOM_OK) return stt;
-        for (int64_t b = 0; b < B; ++b)
-            if (active[b]) res.iters[b] += o.iters[b];
-        k_accum64<<<gd.grid, gd.block, 0, s>>>(rows, x64, d32, B, st_out);
+        bool skip_any = false;
+        for (int64_t b = 0; b < B; ++b) {
+            if (!active[b]) continue;
+            res.iters[b] += o.iters[b];
+            if (o.status[b] == HEOM_EBREAKDOWN) {  // keep x64; retry from it next sweep
+                hs[b].active = 0;
+                skip_any = true;
+                if (++breakdowns[b] >= 2) { res.status[b] = HEOM_EBREAKDOWN; active[b] = 0; }
+            }
+        }
+        if (skip_any)
+            HEOM_CUDA(memcpy_counted(st_out, hs.data(), B * sizeof(ColState), cudaMemcpyHostToDevice, s));
+        { Prof pr(HEOM_KC_OTHER, s, (double)rows * n_act, (32.0 + sizeof(cx<RI>)) * rows * n_act);
+          k_accum<RI><<<gd.grid, gd.block, 0, s>>>(rows, x64, dv, B, st_out); }
         HEOM_CUDA(cudaGetLastError());
     }
     return HEOM_OK;
+}
+
+heom_status solve_system(heom_hier *h, const cx<double> *b64, cx<double> *x64, int64_t B,
+                         const cx<double> *shift64, double aug, bool x_zero, double tol,
+                         int max_iter, int prec, Solve &res, cudaStream_t s) {
+    if (prec == HEOM_MIXED)
+        return refine_solve<float>(h, b64, x64, B, shift64, aug, x_zero, tol, max_iter, res, s);
+    return refine_solve<double>(h, b64, x64, B, shift64, aug, x_zero, tol, max_iter, res, s);
 }
 
 template <class R>
@@ -600,15 +653,20 @@ heom_status evolve_impl(heom_hier *h, cx<R> *y, int64_t B, double dt, int64_t n_
     const int64_t cps = B / h->n_sets;
     const size_t blk = (size_t)h->d2 * B * sizeof(cx<R>);
     int64_t saved = 0;
-    if (traj) HEOM_CUDA(cudaMemcpyAsync(traj, y, blk, cudaMemcpyDeviceToDevice, s));
+    if (traj) HEOM_CUDA(memcpy_counted(traj, y, blk, cudaMemcpyDeviceToDevice, s));
+    const double u = (double)h->N * B, pass = (double)L * sizeof(cx<R>);
     for (int64_t step = 1; step <= n_steps; ++step) {
-        k_rk4_stage<R><<<g.grid, g.block, 0, s>>>(v, y, za, y, acc, B, cps, (R)dt, 1);
-        k_rk4_stage<R><<<g.grid, g.block, 0, s>>>(v, za, zb, y, acc, B, cps, (R)dt, 2);
-        k_rk4_stage<R><<<g.grid, g.block, 0, s>>>(v, zb, za, y, acc, B, cps, (R)dt, 3);
-        k_rk4_stage<R><<<g.grid, g.block, 0, s>>>(v, za, zb, y, acc, B, cps, (R)dt, 4);
+        { Prof pr(HEOM_KC_RK4, s, u, 3.0 * pass);
+          k_rk4_stage<R><<<g.grid, g.block, 0, s>>>(v, y, za, y, acc, B, cps, (R)dt, 1); }
+        { Prof pr(HEOM_KC_RK4, s, u, 5.0 * pass);
+          k_rk4_stage<R><<<g.grid, g.block, 0, s>>>(v, za, zb, y, acc, B, cps, (R)dt, 2); }
+        { Prof pr(HEOM_KC_RK4, s, u, 5.0 * pass);
+          k_rk4_stage<R><<<g.grid, g.block, 0, s>>>(v, zb, za, y, acc, B, cps, (R)dt, 3); }
+        { Prof pr(HEOM_KC_RK4, s, u, 4.0 * pass);
+          k_rk4_stage<R><<<g.grid, g.block, 0, s>>>(v, za, zb, y, acc, B, cps, (R)dt, 4); }
         if (traj && step % save_every == 0) {
             ++saved;
-            HEOM_CUDA(cudaMemcpyAsync((char *)traj + saved * blk, y, blk, cudaMemcpyDeviceToDevice, s));
+            HEOM_CUDA(memcpy_counted((char *)traj + saved * blk, y, blk, cudaMemcpyDeviceToDevice, s));
         }
     }
     HEOM_CUDA(cudaGetLastError());
@@ -666,9 +724,10 @@ extern "C" heom_status heom_steady(heom_hier *h, const void *x0, void *x_out, in
     heom_status stt = dalloc(bbuf, L * sizeof(cx<double>));
     if (stt != HEOM_OK) return stt;
     cx<double> *b64 = (cx<double> *)bbuf.p, *x = (cx<double> *)x_out;
-    k_set_e00<double><<<flat_blocks(L), 256, 0, st>>>(L, b64, batch);
+    { Prof pr(HEOM_KC_OTHER, st, (double)L);
+      k_set_e00<double><<<flat_blocks(L), 256, 0, st>>>(L, b64, batch); }
     if (x0) {
-        if (x0 != x_out) cudaMemcpyAsync(x, x0, L * sizeof(cx<double>), cudaMemcpyDeviceToDevice, st);
+        if (x0 != x_out) memcpy_counted(x, x0, L * sizeof(cx<double>), cudaMemcpyDeviceToDevice, st);
     }
     // drive ||b - A x|| below tol/10: then ||M x|| / ||x|| <= tol for ||x|| >= 0.2
     Solve r;
@@ -677,7 +736,7 @@ extern "C" heom_status heom_steady(heom_hier *h, const void *x0, void *x_out, in
     if (stt != HEOM_OK) return stt;
     // normalise Tr rho_sys = 1 and measure r_ss = ||M x|| / ||x||
     std::vector<cx<double>> top((size_t)h->d2 * batch);
-    HEOM_CUDA(cudaMemcpyAsync(top.data(), x, top.size() * sizeof(cx<double>), cudaMemcpyDeviceToHost, st));
+    HEOM_CUDA(memcpy_counted(top.data(), x, top.size() * sizeof(cx<double>), cudaMemcpyDeviceToHost, st));
     HEOM_CUDA(cudaStreamSynchronize(st));
     std::vector<cx<double>> fac(batch);
     for (int64_t b = 0; b < batch; ++b) {
@@ -690,13 +749,15 @@ extern "C" heom_status heom_steady(heom_hier *h, const void *x0, void *x_out, in
     if (stt != HEOM_OK) return stt;
     cx<double> *dfac = (cx<double> *)tmp.p;
     double *norms = (double *)(dfac + batch);
-    HEOM_CUDA(cudaMemcpyAsync(dfac, fac.data(), batch * sizeof(cx<double>), cudaMemcpyHostToDevice, st));
-    k_scale_cols<double><<<flat_blocks(L), 256, 0, st>>>(L, x, batch, dfac);
+    HEOM_CUDA(memcpy_counted(dfac, fac.data(), batch * sizeof(cx<double>), cudaMemcpyHostToDevice, st));
+    { Prof pr(HEOM_KC_OTHER, st, (double)L);
+      k_scale_cols<double><<<flat_blocks(L), 256, 0, st>>>(L, x, batch, dfac); }
     HEOM_CUDA(cudaMemsetAsync(norms, 0, 2 * batch * sizeof(double), st));
     const Geom gd = make_geom(rows, batch, std::max<int64_t>(1, 2048 / ((batch + 31) / 32)));
-    k_apply_norms<<<gd.grid, gd.block, 0, st>>>(h->view64(), x, batch, batch / h->n_sets, norms);
+    { Prof pr(HEOM_KC_RESIDUAL64, st, (double)h->N * batch, (double)L * sizeof(cx<double>));
+      k_apply_norms<<<gd.grid, gd.block, 0, st>>>(h->view64(), x, batch, batch / h->n_sets, norms); }
     std::vector<double> hn(2 * batch);
-    HEOM_CUDA(cudaMemcpyAsync(hn.data(), norms, hn.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HEOM_CUDA(memcpy_counted(hn.data(), norms, hn.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     HEOM_CUDA(cudaStreamSynchronize(st));
     dfree(tmp);
     heom_status ret = HEOM_OK;
@@ -740,14 +801,15 @@ extern "C" heom_status heom_spectrum(heom_hier *odd, const void *ss_ados, const 
         hshift[j] = {0.0, omega[j]};             // (M + i w) x_+ = d^dag rho
         hshift[n_omega + j] = {0.0, -omega[j]};  // (M - i w) x_- = d rho
     }
-    HEOM_CUDA(cudaMemcpyAsync(ops, hops.data(), hops.size() * sizeof(cx<double>), cudaMemcpyHostToDevice, st));
-    HEOM_CUDA(cudaMemcpyAsync(shift, hshift.data(), B * sizeof(cx<double>), cudaMemcpyHostToDevice, st));
-    k_dos_rhs<<<flat_blocks(L), 256, 0, st>>>(odd->N, d, (const cx<double> *)ss_ados, ops, ops + d * d, b64, n_omega);
+    HEOM_CUDA(memcpy_counted(ops, hops.data(), hops.size() * sizeof(cx<double>), cudaMemcpyHostToDevice, st));
+    HEOM_CUDA(memcpy_counted(shift, hshift.data(), B * sizeof(cx<double>), cudaMemcpyHostToDevice, st));
+    { Prof pr(HEOM_KC_OTHER, st, (double)L);
+      k_dos_rhs<<<flat_blocks(L), 256, 0, st>>>(odd->N, d, (const cx<double> *)ss_ados, ops, ops + d * d, b64, n_omega); }
     Solve r;
     stt = solve_system(odd, b64, x64, B, shift, 0.0, true, tol, max_iter, prec, r, st);
     if (stt != HEOM_OK) { dfree(buf); return stt; }
     std::vector<cx<double>> top((size_t)d * d * B);
-    HEOM_CUDA(cudaMemcpyAsync(top.data(), x64, top.size() * sizeof(cx<double>), cudaMemcpyDeviceToHost, st));
+    HEOM_CUDA(memcpy_counted(top.data(), x64, top.size() * sizeof(cx<double>), cudaMemcpyDeviceToHost, st));
     HEOM_CUDA(cudaStreamSynchronize(st));
     dfree(buf);
     heom_status ret = HEOM_OK;
