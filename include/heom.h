@@ -184,6 +184,22 @@ heom_status heom_apply(const heom_hier *h, const void *x, void *y, int64_t batch
 heom_status heom_evolve(heom_hier *h, void *ados, int64_t batch, double dt, int64_t n_steps,
                         int64_t save_every, void *rho_traj, int prec, heom_stream s);
 
+/* heom_evolve without any allocation. The paper has no counterpart: this serves callers
+ * that cannot let a library call cudaMalloc or cudaFree -- a process whose device memory is
+ * held by another allocator (a framework's caching pool, a fixed budget) can see cudaMalloc
+ * fail, and cudaFree waits for the whole device. Same arguments, layout and results as
+ * heom_evolve, but the three RK4 stage buffers come from one static 16 MiB device array of
+ * the library (held on every GPU that loads the library until the process exits), so
+ * 3 * N * d * d * batch * (16 bytes for HEOM_FP64, 8 for HEOM_FP32) must not exceed
+ * 16 MiB; larger requests return HEOM_EINVAL and allocate nothing. The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress, with that device
+ * current); make that first call before any stream capture. All calls share the one array:
+ * calls whose work overlaps on the GPU (other threads, other streams) race on it and must
+ * be serialised by the caller. Synchronises s. */
+heom_status heom_evolve_noalloc(heom_hier *h, void *ados, int64_t batch, double dt,
+                                int64_t n_steps, int64_t save_every, void *rho_traj, int prec,
+                                heom_stream s);
+
 /* Stationary state of every batch column: M x = 0 with Tr rho_sys = 1 (package
  * architecture: stationary states by a linear solve; the trace condition is added to the
  * (0,0) equation of the tier-0 ADO, which M leaves redundant because it preserves the

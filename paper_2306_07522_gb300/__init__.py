@@ -70,6 +70,8 @@ _sig = {
     "heom_export_tables": [_P, _P, _P, _P, _P, _P, _P],
     "heom_apply": [_P, _P, _P, C.c_int64, C.c_int, _P],
     "heom_evolve": [_P, _P, C.c_int64, C.c_double, C.c_int64, C.c_int64, _P, C.c_int, _P],
+    "heom_evolve_noalloc": [_P, _P, C.c_int64, C.c_double, C.c_int64, C.c_int64, _P, C.c_int,
+                            _P],
     "heom_steady": [_P, _P, _P, C.c_int64, C.c_double, C.c_int, C.c_int, _P, _P],
     "heom_spectrum": [_P, _P, _P, _P, C.c_int64, C.c_double, C.c_int, _P, C.c_int, _P, _P],
     "heom_profile_enable": [C.c_int],
@@ -288,6 +290,20 @@ def evolve(h: Hierarchy, ados, dt: float, n_steps: int, save_every: int = 0, str
     _check(_lib.heom_evolve(h.handle, _dptr(ados), B, dt, n_steps, max(save_every, 1),
                             _dptr(traj) if traj is not None else None, prec, _stream(stream)),
            "heom_evolve")
+    return traj
+
+
+def evolve_noalloc(h: Hierarchy, ados, dt: float, n_steps: int, save_every: int = 0,
+                   traj=None, stream=None):
+    """heom_evolve_noalloc: RK4 in place on ``ados`` with no allocation in the library; the
+    optional snapshot buffer ``traj`` is the caller's (this wrapper allocates nothing either)."""
+    prec = _prec_of(ados)
+    B = _batch_of(h, ados)
+    if save_every and traj is None:
+        raise ValueError("evolve_noalloc needs a caller-owned traj tensor when save_every > 0")
+    _check(_lib.heom_evolve_noalloc(h.handle, _dptr(ados), B, dt, n_steps, max(save_every, 1),
+                                    _dptr(traj) if save_every else None, prec, _stream(stream)),
+           "heom_evolve_noalloc")
     return traj
 
 

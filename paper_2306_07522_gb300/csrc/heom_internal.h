@@ -190,4 +190,9 @@ template <class R>
 cudaError_t launch_apply(const DevView<R> &v, const cx<R> *x, cx<R> *y, int64_t B,
                          const ApplyMods<R> &mods, cudaStream_t s);
 
+// one fused RK4 stage over all ADOs and columns (the launch heom_evolve uses)
+template <class R>
+cudaError_t launch_rk4_stage(const DevView<R> &v, const cx<R> *z_in, cx<R> *z_out, cx<R> *y,
+                             cx<R> *acc, int64_t B, R dt, int stage, cudaStream_t s);
+
 }  // namespace heom

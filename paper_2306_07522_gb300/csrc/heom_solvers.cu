@@ -83,6 +83,20 @@ __global__ void __launch_bounds__(256) k_rk4_stage(DevView<R> v, const cx<R> *__
     }
 }
 
+template <class R>
+cudaError_t launch_rk4_stage(const DevView<R> &v, const cx<R> *z_in, cx<R> *z_out, cx<R> *y,
+                             cx<R> *acc, int64_t B, R dt, int stage, cudaStream_t s) {
+    const Geom g = make_geom(v.N * v.d2, B, 1 << 30);
+    k_rk4_stage<R><<<g.grid, g.block, 0, s>>>(v, z_in, z_out, y, acc, B, B / v.n_sets, dt, stage);
+    return cudaGetLastError();
+}
+template cudaError_t launch_rk4_stage<double>(const DevView<double> &, const cx<double> *,
+                                              cx<double> *, cx<double> *, cx<double> *, int64_t,
+                                              double, int, cudaStream_t);
+template cudaError_t launch_rk4_stage<float>(const DevView<float> &, const cx<float> *,
+                                             cx<float> *, cx<float> *, cx<float> *, int64_t,
+                                             float, int, cudaStream_t);
+
 // ------------------------------------------------------------------ BiCGStab
 __global__ void k_state_init(ColState *st, int64_t B, const int *active) {
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
