@@ -166,13 +166,15 @@ def run_gpu(args):
     x_ss = torch.zeros((N, d, d), dtype=torch.complex128, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    def step(prec):
-        st1, s1 = heom.steady(even, x_ss, tol=TOL, max_iter=4000, prec=prec)
-        A, st2, s2 = heom.spectrum(odd, x_ss, dop, om, tol=TOL, max_iter=4000, prec=prec)
+    # chosen form: FP64 BiCGStab for the one stationary state (fewest iterations), the
+    # shift-invariant Arnoldi solve for all frequencies of the DOS
+    def step(steady_prec=heom.FP64, spec_prec=heom.SHIFTED):
+        st1, s1 = heom.steady(even, x_ss, tol=TOL, max_iter=4000, prec=steady_prec)
+        A, st2, s2 = heom.spectrum(odd, x_ss, dop, om, tol=TOL, max_iter=4000, prec=spec_prec)
         return A, s1, s2
 
     for _ in range(args.warmup):
-        step(heom.MIXED)
+        step()
     torch.cuda.synchronize()
 
     # ---- timed region: K chosen-form steps
@@ -189,7 +191,7 @@ def run_gpu(args):
     for k in range(args.steps):
         flush.zero_()  # L2 flush between timed steps (outside the step's events)
         ev[k][0].record(s)
-        A, s1, s2 = step(heom.MIXED)
+        A, s1, s2 = step()
         ev[k][1].record(s)
         stats.append((s1, s2))
     torch.cuda.synchronize()
@@ -246,7 +248,8 @@ def run_gpu(args):
         "config": {"workload": "SIAM d=4 tier 3 (2,325 ADOs, 24 Pade exponents): stationary "
                                "state + DOS at 1,000 omega in [-20,20], residual 1e-8",
                    "n_ado": N, "n_omega": N_OMEGA, "columns_per_dos_solve": 2 * N_OMEGA,
-                   "solver": "batched BiCGStab, FP32 inner + FP64 refinement",
+                   "solver": "stationary: FP64 BiCGStab; DOS: shift-invariant FP64 Arnoldi "
+                             "(one Krylov space per sign for all frequencies)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "l2": "flushed (256 MB write) before every timed step"},
         "roofline": roofline,
@@ -281,6 +284,13 @@ def _plain_vs_chosen(heom, torch, dev, model, om, even, odd, x_ss, dop, chosen_s
     plain_s = time.perf_counter() - t0
     res["spectrum_points_per_s_plain_fp64"] = round(len(om) / plain_s, 1)
     res["step_speedup_chosen_vs_plain"] = round(plain_s * 1e3 / chosen_step_ms, 2)
+    # the mixed-precision batched BiCGStab form of the same step, for reference
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    heom.steady(even, x_ss, tol=TOL, max_iter=4000, prec=heom.MIXED)
+    Am, st, sm = heom.spectrum(odd, x_ss, dop, om, tol=TOL, max_iter=4000, prec=heom.MIXED)
+    torch.cuda.synchronize()
+    res["spectrum_points_per_s_mixed_bicgstab"] = round(len(om) / (time.perf_counter() - t0), 1)
     # stationary states of many parameter sets (learned-warm-start workload shape)
     n_sets = 256
     draws = W.draw_warmstart_samples(n_sets, seed=7522)
@@ -330,8 +340,8 @@ def _e2e(heom, torch, model, om, dop, n_steps):
         even = heom.build_hierarchy(heom.problem_from_model(model, 1))
         odd = heom.build_hierarchy(heom.problem_from_model(model, -1))
         x = torch.zeros((even.n_ado, model.d, model.d), dtype=torch.complex128, device="cuda")
-        heom.steady(even, x, tol=TOL, max_iter=4000, prec=heom.MIXED)
-        A, _, _ = heom.spectrum(odd, x, dop, om, tol=TOL, max_iter=4000, prec=heom.MIXED)
+        heom.steady(even, x, tol=TOL, max_iter=4000, prec=heom.FP64)
+        A, _, _ = heom.spectrum(odd, x, dop, om, tol=TOL, max_iter=4000, prec=heom.SHIFTED)
         del even, odd, x
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
@@ -426,6 +436,38 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_apply_only(args):
+    """Kernel micro-benchmark for profiling: heom_apply on the workload's hierarchy with
+    ``--batch`` random columns, ``--warmup`` untimed then ``--steps`` timed launches."""
+    import torch
+
+    import paper_2306_07522_gb300 as heom
+    model, _ = _workload(0)
+    g = heom.build_hierarchy(heom.problem_from_model(model, 1))
+    dt = torch.complex64 if args.prec == "fp32" else torch.complex128
+    gen = torch.Generator(device="cuda").manual_seed(2306)
+    x = torch.randn((g.n_ado, model.d, model.d, args.batch), dtype=dt, device="cuda", generator=gen)
+    y = torch.empty_like(x)
+    for _ in range(args.warmup):
+        heom.apply(g, x, y)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        heom.apply(g, x, y)
+    b.record()
+    torch.cuda.synchronize()
+    us = 1e3 * a.elapsed_time(b) / max(args.steps, 1)
+    s = 8 if args.prec == "fp32" else 16
+    byts = 2.0 * g.n_ado * model.d ** 2 * s * args.batch
+    pk, kind = _peaks()
+    print(json.dumps({"kernel": "heom_apply", "prec": args.prec, "n_ado": g.n_ado,
+                      "batch": args.batch, "us_per_launch": round(us, 2),
+                      "ado_applies_per_s": round(g.n_ado * args.batch / (us * 1e-6), 1),
+                      "algorithmic_GBps": round(byts / (us * 1e-6) / 1e9, 1),
+                      "frac_hbm": round(byts / (us * 1e-6) / 1e9 / pk, 4), "peak": kind}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -434,7 +476,14 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--quick", action="store_true",
                     help="timed steps only (no plain-path, e2e or CPU-baseline legs)")
+    ap.add_argument("--only", choices=["apply"], default=None,
+                    help="kernel micro-benchmark (for profiling) instead of the step benchmark")
+    ap.add_argument("--batch", type=int, default=2000)
+    ap.add_argument("--prec", choices=["fp32", "fp64"], default="fp32")
     args = ap.parse_args()
+    if args.only == "apply":
+        run_apply_only(args)
+        return
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":

@@ -67,8 +67,11 @@ typedef enum {
 typedef enum {
     HEOM_FP64 = 0,   /* complex FP64 throughout (the plain path)                       */
     HEOM_FP32 = 1,   /* complex FP32 storage and arithmetic                            */
-    HEOM_MIXED = 2   /* solvers: FP32 inner Krylov solves inside FP64 iterative
+    HEOM_MIXED = 2,  /* solvers: FP32 inner Krylov solves inside FP64 iterative
                         refinement; FP64 residuals, dot products and normalisation      */
+    HEOM_SHIFTED = 3 /* heom_spectrum: one FP64 Arnoldi process per right-hand side serves
+                        every frequency (the shifted systems share one Krylov space);
+                        residual per frequency from its shifted Hessenberg problem      */
 } heom_prec;
 
 /* One bath = one coupling operator + its exponent list (Fig. 1b). */
@@ -217,7 +220,11 @@ heom_status heom_steady(heom_hier *h, const void *x0, void *x_out, int64_t batch
  * of the odd-parity hierarchy `odd` and b built from every ADO of the even stationary
  * state ss_ados (device complex128 [N][d][d], batch 1); pi A(w) = -Re{Tr[d x_+,0] +
  * Tr[d^dag x_-,0]}. op_d: host d x d. omega: host [n_omega]; A_out: host [n_omega].
- * Converged when ||b - (M -+ i w) x|| / ||b|| <= tol. prec as for heom_steady.
+ * Converged when ||b - (M -+ i w) x|| / ||b|| <= tol. prec: HEOM_FP64 or HEOM_MIXED (one
+ * BiCGStab solve per frequency and sign, batched as columns, as for heom_steady) or
+ * HEOM_SHIFTED (two Arnoldi processes, one per sign, up to max_iter steps; the residual of
+ * each frequency is the least-squares residual of its shifted Hessenberg problem, which
+ * equals ||b - (M -+ i w) x|| up to the rounding of the Arnoldi relation).
  * stats: host array of 2*n_omega entries (x_+ then x_-) or NULL. Synchronises s. */
 heom_status heom_spectrum(heom_hier *odd, const void *ss_ados, const heom_c64 *op_d,
                           const double *omega, int64_t n_omega, double tol, int max_iter,

@@ -24,7 +24,7 @@ _lib = C.CDLL(LIBRARY_PATH)
 # ------------------------------------------------------------------------- ABI types
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EBREAKDOWN, ENOTSUP = range(7)
 BOSON_R, BOSON_I, BOSON_RI, FERMION = range(4)
-FP64, FP32, MIXED = range(3)
+FP64, FP32, MIXED, SHIFTED = range(4)
 KERNEL_CLASSES = ("apply", "rk4", "krylov_apply_fp32", "krylov_apply_fp64", "krylov_vector",
                   "residual_fp64", "other")
 APPLY_CLASSES = ("apply", "rk4", "krylov_apply_fp32", "krylov_apply_fp64", "residual_fp64")

@@ -8,7 +8,7 @@
 // read straight from global memory; re-reads of a block by its neighbours are served by L1
 // and L2. Operators are applied through their sparse row/column lists, so the d_sigma of
 // the fermionic baths cost one multiply-add per neighbour and side.
-#include "heom_kernels.cuh"
+#include "heom_tile.cuh"
 
 namespace heom {
 
@@ -55,8 +55,18 @@ __global__ void __launch_bounds__(256) k_apply(DevView<R> v, const cx<R> *__rest
 template <class R>
 cudaError_t launch_apply(const DevView<R> &v, const cx<R> *x, cx<R> *y, int64_t B,
                          const ApplyMods<R> &mods, cudaStream_t s) {
-    Geom g = make_geom(v.N * v.d2, B, 1 << 30);
     Prof pr(HEOM_KC_APPLY, s, (double)v.N * B, 2.0 * v.N * B * v.d2 * sizeof(cx<R>));
+    if (tile_ok(v, B)) {
+        TileArgs<R> a{};
+        a.v = v;
+        a.x = x;
+        a.out = y;
+        a.shift = mods.shift;
+        a.aug = mods.aug;
+        a.B = B;
+        return launch_tile<R, TM_STORE>(a, s);
+    }
+    Geom g = make_geom(v.N * v.d2, B, 1 << 30);
     k_apply<R><<<g.grid, g.block, 0, s>>>(v, x, y, B, B / v.n_sets, mods);
     return cudaGetLastError();
 }

@@ -303,6 +303,13 @@ heom::DevView<double> heom_hier::view64() const {
     v.coefL = (const cx<double> *)d_coefL64.p; v.coefR = (const cx<double> *)d_coefR64.p;
     v.rate = (const cx<double> *)d_rate64.p; v.hdiag = (const cx<double> *)d_hdiag64.p;
     v.floor = (const double *)d_floor64.p;
+    v.t_ptr = (const int32_t *)d_t_ptr.p; v.t_src = (const int32_t *)d_t_src.p;
+    v.t_val = (const cx<double> *)d_t_val64.p;
+    v.th_ptr = (const int32_t *)d_th_ptr.p; v.th_src = (const int32_t *)d_th_src.p;
+    v.th_vi = (const int32_t *)d_th_vi.p;
+    v.max_terms = max_terms; v.max_entries = max_entries;
+    v.cta_ado = (const int32_t *)d_cta_ado.p; v.n_ranges = n_ranges; v.range_terms = range_terms;
+    v.range_slots = range_slots; v.range_ados = range_ados;
     return v;
 }
 
@@ -322,6 +329,13 @@ heom::DevView<float> heom_hier::view32() const {
     v.coefL = (const cx<float> *)d_coefL32.p; v.coefR = (const cx<float> *)d_coefR32.p;
     v.rate = (const cx<float> *)d_rate32.p; v.hdiag = (const cx<float> *)d_hdiag32.p;
     v.floor = (const float *)d_floor32.p;
+    v.t_ptr = (const int32_t *)d_t_ptr.p; v.t_src = (const int32_t *)d_t_src.p;
+    v.t_val = (const cx<float> *)d_t_val32.p;
+    v.th_ptr = (const int32_t *)d_th_ptr.p; v.th_src = (const int32_t *)d_th_src.p;
+    v.th_vi = (const int32_t *)d_th_vi.p;
+    v.max_terms = max_terms; v.max_entries = max_entries;
+    v.cta_ado = (const int32_t *)d_cta_ado.p; v.n_ranges = n_ranges; v.range_terms = range_terms;
+    v.range_slots = range_slots; v.range_ados = range_ados;
     return v;
 }
 
@@ -334,7 +348,9 @@ void free_all(heom_hier *h) {
                     &h->d_h_rcol, &h->d_h_rvi, &h->d_h_cptr, &h->d_h_crow, &h->d_h_cvi,
                     &h->d_hval64, &h->d_hval32, &h->d_coefL64, &h->d_coefL32, &h->d_coefR64,
                     &h->d_coefR32, &h->d_rate64, &h->d_rate32, &h->d_hdiag64, &h->d_hdiag32,
-                    &h->d_floor64, &h->d_floor32, &h->ws, &h->ws_small};
+                    &h->d_floor64, &h->d_floor32, &h->ws, &h->ws_small, &h->d_t_ptr,
+                    &h->d_t_src, &h->d_t_val64, &h->d_t_val32, &h->d_th_ptr, &h->d_th_src,
+                    &h->d_th_vi, &h->d_cta_ado};
     for (DBuf *b : bufs) heom::dfree(*b);
 }
 
@@ -390,8 +406,75 @@ heom_status upload_params(heom_hier *h, int n_sets, const heom_c64 *H, const heo
         fl[s] = first ? 1.0 : floor;
     }
     std::vector<float> fl32(fl.begin(), fl.end());
+    // H term lists for the tiled kernels: element (r,c) reads H[r][l] X[l][c] (left) and
+    // X[r][l] H[l][c] (right)
+    std::vector<int32_t> thp(d * d + 1, 0), ths, thv;
+    for (int r = 0; r < d; ++r)
+        for (int c = 0; c < d; ++c) {
+            for (int l = 0; l < d; ++l)
+                if (vidx[r * d + l] >= 0) { ths.push_back(l * d + c); thv.push_back(vidx[r * d + l]); }
+            for (int l = 0; l < d; ++l)
+                if (vidx[l * d + c] >= 0) { ths.push_back((r * d + l) | (1 << 16)); thv.push_back(vidx[l * d + c]); }
+            thp[r * d + c + 1] = (int32_t)ths.size();
+        }
+    h->h_terms = (int)ths.size();
+    // largest term program of one ADO: damping (1 per element) + H + neighbour terms + trace row
+    {
+        int mt = 0, me = 0;
+        for (int64_t i = 0; i < h->N; ++i) {
+            int t = h->d2 + h->h_terms + d;
+            for (int32_t k = h->row_ptr[i]; k < h->row_ptr[i + 1]; ++k) t += h->op_terms[h->ent[k].op];
+            mt = std::max(mt, t);
+            me = std::max(me, (int)(h->row_ptr[i + 1] - h->row_ptr[i]));
+        }
+        h->max_terms = mt;
+        h->max_entries = me;
+    }
+    // ADO ranges for the persistent tiled kernel: contiguous, about equal term counts
+    // (five CTAs per SM, all resident at once), each range's program and bookkeeping bounded for shared memory.
+    std::vector<int32_t> ranges(1, 0);
+    {
+        std::vector<int64_t> terms(h->N), slots(h->N);
+        int64_t total = 0;
+        for (int64_t i = 0; i < h->N; ++i) {
+            int64_t t = h->d2 + h->h_terms + (i == 0 ? d : 0);
+            for (int32_t k = h->row_ptr[i]; k < h->row_ptr[i + 1]; ++k) t += h->op_terms[h->ent[k].op];
+            terms[i] = t;
+            slots[i] = (int64_t)h->d2 * (h->row_ptr[i + 1] - h->row_ptr[i] + 3);
+            total += t;
+        }
+        // at most kResident ranges, so that every CTA is resident and they sweep together;
+        // a range closes once it reaches the target (or a shared-memory bound)
+        const int64_t kResident = 152 * 5;
+        int64_t target = std::max<int64_t>(1, (total + kResident - 1) / kResident);
+        int64_t rt = 0, rs = 0, rn = 0;
+        for (int attempt = 0; attempt < 64; ++attempt) {
+            ranges.assign(1, 0);
+            int64_t cur_t = 0, cur_s = 0, cur_n = 0;
+            rt = rs = rn = 0;
+            for (int64_t i = 0; i < h->N; ++i) {
+                const bool full = cur_n > 0 && (cur_t >= target || cur_t + terms[i] > heom::kRangeTerms ||
+                                                cur_s + slots[i] > heom::kRangeSlots ||
+                                                cur_n >= heom::kRangeAdos);
+                if (full) {
+                    ranges.push_back((int32_t)i);
+                    cur_t = cur_s = cur_n = 0;
+                }
+                cur_t += terms[i]; cur_s += slots[i]; ++cur_n;
+                rt = std::max(rt, cur_t); rs = std::max(rs, cur_s); rn = std::max(rn, cur_n);
+            }
+            ranges.push_back((int32_t)h->N);
+            if ((int64_t)ranges.size() - 1 <= kResident) break;
+            target += target / 8 + 1;
+        }
+        h->n_ranges = (int)ranges.size() - 1;
+        h->range_terms = (int)std::min<int64_t>(rt, INT32_MAX);
+        h->range_slots = (int)std::min<int64_t>(rs, INT32_MAX);
+        h->range_ados = (int)rn;
+    }
     heom_status st;
 #define UP(buf, vec) if ((st = upload(h->buf, vec)) != HEOM_OK) return st
+    UP(d_th_ptr, thp); UP(d_th_src, ths); UP(d_th_vi, thv); UP(d_cta_ado, ranges);
     UP(d_h_rptr, rptr); UP(d_h_rcol, rcol); UP(d_h_rvi, rvi);
     UP(d_h_cptr, cptr); UP(d_h_crow, crow); UP(d_h_cvi, cvi);
     UP(d_hval64, to_cx<double>(hval)); UP(d_hval32, to_cx<float>(hval));
@@ -596,6 +679,28 @@ extern "C" heom_status heom_build_hierarchy(int d, const heom_c64 *H, int n_bath
         UP(d_op_rptr, orp); UP(d_op_rcol, orc); UP(d_op_cptr, ocp); UP(d_op_crow, ocr);
         UP(d_op_rval64, to_cx<double>(orv)); UP(d_op_cval64, to_cx<double>(ocv));
         UP(d_op_rval32, to_cx<float>(orv)); UP(d_op_cval32, to_cx<float>(ocv));
+        // per-element term lists of every operator slot (tiled kernels)
+        std::vector<int32_t> tp(1, 0), tsrc;
+        std::vector<heom_c64> tval;
+        h->op_terms.assign(n_ops, 0);
+        for (int o = 0; o < n_ops; ++o) {
+            const heom_c64 *A = &h->ops[(size_t)o * d * d];
+            for (int r = 0; r < d; ++r)
+                for (int c = 0; c < d; ++c) {
+                    for (int l = 0; l < d; ++l)
+                        if (A[r * d + l].re != 0.0 || A[r * d + l].im != 0.0) {
+                            tsrc.push_back(l * d + c); tval.push_back(A[r * d + l]);
+                        }
+                    for (int l = 0; l < d; ++l)
+                        if (A[l * d + c].re != 0.0 || A[l * d + c].im != 0.0) {
+                            tsrc.push_back((r * d + l) | (1 << 16)); tval.push_back(A[l * d + c]);
+                        }
+                    tp.push_back((int32_t)tsrc.size());
+                }
+            h->op_terms[o] = tp.back() - tp[(size_t)o * d * d];
+        }
+        UP(d_t_ptr, tp); UP(d_t_src, tsrc);
+        UP(d_t_val64, to_cx<double>(tval)); UP(d_t_val32, to_cx<float>(tval));
 #undef UP
         if ((st = upload_params(h, 1, H, coef.data(), rate.data())) != HEOM_OK) { free_all(h); delete h; return st; }
     } catch (const std::bad_alloc &) {

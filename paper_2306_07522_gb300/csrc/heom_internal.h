@@ -90,6 +90,25 @@ struct DevView {
     const cx<R> *rate;        // [n_sets][K]
     const cx<R> *hdiag;       // [n_sets][d]   diagonal of H (preconditioner)
     const R *floor;           // [n_sets]      damping floor for undamped ADOs (preconditioner)
+    // Per-element term lists of every operator, for the tiled kernels: for operator slot o
+    // and output element e = r*d + c, terms t_ptr[o*d2+e] .. t_ptr[o*d2+e+1]-1 read local
+    // element (t_src & 0xffff) of the source block, as a left product (bit 16 clear:
+    // (O X)[r][c] needs X[l][c] O[r][l]) or a right product (bit 16 set: X[r][l] O[l][c]),
+    // with operator value t_val. th_* is the same for H, values by index into h_val.
+    const int32_t *t_ptr;     // [n_ops*d2 + 1]
+    const int32_t *t_src;
+    const cx<R> *t_val;
+    const int32_t *th_ptr;    // [d2 + 1]
+    const int32_t *th_src;
+    const int32_t *th_vi;
+    int max_terms;            // largest term program of one ADO (incl. damping, H, trace row)
+    int max_entries;          // largest neighbour-entry count of one ADO
+    // ADO ranges of the persistent tiled kernel (one CTA each, balanced by term count)
+    const int32_t *cta_ado;   // [n_ranges + 1]
+    int n_ranges;
+    int range_terms;          // largest program of one range (terms)
+    int range_slots;          // largest sum over a range of d2 * (entries + 3)
+    int range_ados;           // largest number of ADOs in a range
 };
 
 // Optional modifiers of the apply used by the solvers (all may be null / zero).
@@ -130,6 +149,12 @@ struct heom_hier {
         d_op_rval32, d_op_cval32;
     heom::DBuf d_h_rptr, d_h_rcol, d_h_rvi, d_h_cptr, d_h_crow, d_h_cvi;
     int nnzH = 0;
+    // tiled-kernel term lists (see DevView)
+    heom::DBuf d_t_ptr, d_t_src, d_t_val64, d_t_val32, d_th_ptr, d_th_src, d_th_vi;
+    std::vector<int> op_terms;              // total terms of operator slot o over all elements
+    int h_terms = 0, max_terms = 0, max_entries = 0;
+    heom::DBuf d_cta_ado;
+    int n_ranges = 0, range_terms = 0, range_slots = 0, range_ados = 0;
     // device parameters (per set), both precisions
     heom::DBuf d_hval64, d_hval32, d_coefL64, d_coefL32, d_coefR64, d_coefR32, d_rate64,
         d_rate32, d_hdiag64, d_hdiag32, d_floor64, d_floor32;
@@ -155,6 +180,11 @@ heom_status cuda_fail(cudaError_t e, const char *what);
 heom_status dalloc(DBuf &b, size_t bytes);
 void dfree(DBuf &b);
 heom_status ensure_ws(DBuf &b, size_t bytes);
+
+// bounds of one ADO range of the persistent tiled kernel (shared-memory budget)
+constexpr int kRangeTerms = 4096;
+constexpr int kRangeSlots = 8192;
+constexpr int kRangeAdos = 64;
 
 // launch geometry shared by every row x column kernel: block (bx, by), grid (gx, gy)
 struct Geom {
@@ -189,6 +219,12 @@ cudaError_t memcpy_counted(void *dst, const void *src, size_t bytes, cudaMemcpyK
 template <class R>
 cudaError_t launch_apply(const DevView<R> &v, const cx<R> *x, cx<R> *y, int64_t B,
                          const ApplyMods<R> &mods, cudaStream_t s);
+
+// shift-invariant GMRES (heom_shifted.cu): tier-0 blocks and residual estimates per shift
+heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
+                          const std::vector<cx<double>> &shift, const std::vector<int> &col_of,
+                          double tol, int mmax, std::vector<cx<double>> &x0,
+                          std::vector<double> &res, int *steps, cudaStream_t s);
 
 // one fused RK4 stage over all ADOs and columns (the launch heom_evolve uses)
 template <class R>

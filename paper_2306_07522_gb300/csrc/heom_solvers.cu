@@ -11,7 +11,7 @@
 #include <cmath>
 #include <vector>
 
-#include "heom_kernels.cuh"
+#include "heom_tile.cuh"
 
 namespace heom {
 
@@ -45,7 +45,8 @@ __device__ __forceinline__ void reduce_add(double (&val)[NV], double *const (&ds
     const int set = inb ? (int)(b / cps) : 0;                              \
     (void)set;
 
-#define ROW_LOOP for (int64_t row = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; row < rows; \
+#define ROW_LOOP _Pragma("unroll 4") \
+                 for (int64_t row = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; row < rows; \
                       row += (int64_t)gridDim.x * blockDim.y)
 
 __device__ __forceinline__ bool designated() { return blockIdx.x == 0 && threadIdx.y == 0; }
@@ -150,6 +151,15 @@ __global__ void __launch_bounds__(256) k_bicg_init(DevView<R> v, const cx<R> *__
     reduce_add<3>(val, dst, act);
 }
 
+// The per-column Krylov scalars are computed once per column and block (FP64 divisions are
+// slow on GB300) by the threads of row 0 and shared with the block.
+template <class R>
+struct ColScalars {
+    cx<R> a, b;      // two working-precision scalars of the kernel
+    cx<double> keep; // an FP64 value to store back
+    int on;          // column active
+};
+
 // p = r + beta (p - omega v), ph = P^-1 p, beta = (rho / rho_old)(alpha / omega)
 template <class R>
 __global__ void __launch_bounds__(256) k_bicg_p(DevView<R> v, const cx<R> *__restrict__ r,
@@ -157,11 +167,22 @@ __global__ void __launch_bounds__(256) k_bicg_p(DevView<R> v, const cx<R> *__res
                                                 cx<R> *__restrict__ ph, int64_t B, int64_t cps,
                                                 const cx<R> *shift, int precond, ColState *st) {
     COLUMN_PROLOGUE
-    if (!inb || !st[b].active) return;
-    const ColState c = st[b];
-    const cx<double> beta = cdiv(c.acc_rr, c.rho_old) * cdiv(c.alpha, c.omega);
-    const cx<R> bt = cast<R>(beta), om = cast<R>(c.omega);
-    const cx<R> sh = shift ? shift[b] : cx<R>{R(0), R(0)};
+    __shared__ ColScalars<R> sc[32];
+    if (threadIdx.y == 0) {
+        ColScalars<R> c{};
+        c.on = inb && st[b].active;
+        if (c.on) {
+            const ColState cs = st[b];
+            c.a = cast<R>(cdiv(cs.acc_rr, cs.rho_old) * cdiv(cs.alpha, cs.omega));  // beta
+            c.b = cast<R>(cs.omega);
+        }
+        sc[threadIdx.x] = c;
+    }
+    __syncthreads();
+    const ColScalars<R> c = sc[threadIdx.x];
+    if (!c.on) return;
+    const cx<R> bt = c.a, om = c.b;
+    const cx<R> shv = shift ? shift[b] : cx<R>{R(0), R(0)};
     ROW_LOOP {
         const int64_t i = row * B + b;
         const cx<R> pi = r[i] + bt * (p[i] - om * vv[i]);
@@ -169,7 +190,7 @@ __global__ void __launch_bounds__(256) k_bicg_p(DevView<R> v, const cx<R> *__res
         if (precond) {
             const int64_t n = row / v.d2;
             const int e = (int)(row - n * v.d2);
-            ph[i] = pi * precond_inv(v, n, e, set, damping_of(v, n, set), sh);
+            ph[i] = pi * precond_inv(v, n, e, set, damping_of(v, n, set), shv);
         } else {
             ph[i] = pi;
         }
@@ -235,11 +256,23 @@ __global__ void __launch_bounds__(256) k_bicg_s(DevView<R> v, cx<R> *r, const cx
                                                 cx<R> *__restrict__ sh, int64_t B, int64_t cps,
                                                 const cx<R> *shift, int precond, ColState *st) {
     COLUMN_PROLOGUE
-    if (!inb || !st[b].active) return;
-    const ColState c = st[b];
-    const bool bad = norm2(c.acc_rv) == 0.0;
-    const cx<double> alpha = bad ? cx<double>{0.0, 0.0} : cdiv(c.acc_rr, c.acc_rv);
-    const cx<R> al = cast<R>(alpha);
+    __shared__ ColScalars<R> sc[32];
+    if (threadIdx.y == 0) {
+        ColScalars<R> c{};
+        c.on = inb && st[b].active;
+        if (c.on) {
+            const ColState cs = st[b];
+            const bool bad = norm2(cs.acc_rv) == 0.0;
+            c.keep = bad ? cx<double>{0.0, 0.0} : cdiv(cs.acc_rr, cs.acc_rv);  // alpha
+            c.a = cast<R>(c.keep);
+            c.b = cx<R>{bad ? R(1) : R(0), R(0)};
+        }
+        sc[threadIdx.x] = c;
+    }
+    __syncthreads();
+    const ColScalars<R> c = sc[threadIdx.x];
+    if (!c.on) return;
+    const cx<R> al = c.a;
     const cx<R> shf = shift ? shift[b] : cx<R>{R(0), R(0)};
     ROW_LOOP {
         const int64_t i = row * B + b;
@@ -254,11 +287,12 @@ __global__ void __launch_bounds__(256) k_bicg_s(DevView<R> v, cx<R> *r, const cx
         }
     }
     if (designated()) {
-        st[b].alpha = alpha;
-        st[b].rho_old = c.acc_rr;
+        const cx<double> rr = st[b].acc_rr;
+        st[b].alpha = c.keep;
+        st[b].rho_old = rr;
         st[b].acc_ts = {0.0, 0.0};
         st[b].acc_tt = {0.0, 0.0};
-        if (bad) st[b].flag = 1;
+        if (c.b.re != R(0)) st[b].flag = 1;
     }
 }
 
@@ -271,19 +305,29 @@ __global__ void __launch_bounds__(256) k_bicg_x(int64_t rows, cx<R> *x, const cx
                                                 const cx<R> *__restrict__ rh, int64_t B,
                                                 ColState *st) {
     const int64_t b = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
-    const bool act = b < B && st[b].active;
-    double rr_re = 0, rr_im = 0, nr = 0;
-    cx<double> omega{0.0, 0.0};
-    bool bad = false;
-    if (act) {
-        const ColState c = st[b];
-        omega = c.acc_tt.re == 0.0 ? cx<double>{0.0, 0.0} : cdiv(c.acc_ts, c.acc_tt);
-        bad = !isfinite(omega.re) || !isfinite(omega.im) || !isfinite(c.alpha.re) ||
-              !isfinite(c.alpha.im);
+    __shared__ ColScalars<R> sc[32];
+    if (threadIdx.y == 0) {
+        ColScalars<R> c{};
+        c.on = b < B && st[b].active;
+        if (c.on) {
+            const ColState cs = st[b];
+            const cx<double> omega =
+                cs.acc_tt.re == 0.0 ? cx<double>{0.0, 0.0} : cdiv(cs.acc_ts, cs.acc_tt);
+            const bool bad = !isfinite(omega.re) || !isfinite(omega.im) ||
+                             !isfinite(cs.alpha.re) || !isfinite(cs.alpha.im);
+            c.keep = omega;
+            c.a = cast<R>(cs.alpha);
+            c.b = cast<R>(omega);
+            c.on = bad ? 2 : 1;
+        }
+        sc[threadIdx.x] = c;
     }
-    if (act && !bad) {
-        const ColState c = st[b];
-        const cx<R> al = cast<R>(c.alpha), om = cast<R>(omega);
+    __syncthreads();
+    const ColScalars<R> c = sc[threadIdx.x];
+    const bool act = c.on == 1;
+    double rr_re = 0, rr_im = 0, nr = 0;
+    if (act) {
+        const cx<R> al = c.a, om = c.b;
         ROW_LOOP {
             const int64_t i = row * B + b;
             x[i] = x[i] + al * ph[i] + om * sh[i];
@@ -298,10 +342,10 @@ __global__ void __launch_bounds__(256) k_bicg_x(int64_t rows, cx<R> *x, const cx
     double val[3] = {rr_re, rr_im, nr};
     double *const dst[3] = {act ? &st[b].acc_rr.re : nullptr, act ? &st[b].acc_rr.im : nullptr,
                             act ? &st[b].acc_nr : nullptr};
-    reduce_add<3>(val, dst, act && !bad);
-    if (act && designated()) {
-        st[b].omega = omega;
-        if (bad) st[b].flag = 1;
+    reduce_add<3>(val, dst, act);
+    if (c.on && designated()) {
+        st[b].omega = c.keep;
+        if (c.on == 2) st[b].flag = 1;
     }
 }
 
@@ -426,6 +470,29 @@ __global__ void k_convert(int64_t total, const cx<S> *__restrict__ in, cx<R> *__
         out[i] = cast<R>(in[i]);
 }
 
+// batch-column gather / scatter: out[row][j] = in[row][map[j]] and out[row][map[j]] = in[row][j]
+template <class R>
+__global__ void k_gather_cols(int64_t rows, const cx<R> *__restrict__ in, int64_t Bin,
+                              cx<R> *__restrict__ out, int64_t Bout, const int *__restrict__ map) {
+    const int64_t total = rows * Bout;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = i / Bout, j = i - row * Bout;
+        out[i] = in[row * Bin + map[j]];
+    }
+}
+
+template <class R>
+__global__ void k_scatter_cols(int64_t rows, const cx<R> *__restrict__ in, int64_t Bin,
+                               cx<R> *__restrict__ out, int64_t Bout, const int *__restrict__ map) {
+    const int64_t total = rows * Bin;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = i / Bin, j = i - row * Bin;
+        out[row * Bout + map[j]] = in[i];
+    }
+}
+
 // ------------------------------------------------------------------ host orchestration
 namespace {
 
@@ -446,88 +513,203 @@ struct SolveOut {
 
 // Batched right-preconditioned BiCGStab on A x = b, A = M + diag(shift) (+ trace aug).
 // Columns with active[b] = 0 are left untouched. x holds the initial guess (x_zero: zero).
+constexpr int kStallIters = 96;
+
+// Batched right-preconditioned BiCGStab on A x = b, A = M + diag(shift) (+ trace aug).
+// Columns with active[b] = 0 are left untouched. x holds the initial guess (x_zero: zero).
+//
+// The solver works on a compact copy of the active columns ([rows][Bc] with Bc <= B) and
+// re-compacts whenever the still-active columns fall to 60 % of the working width, so that
+// iteration cost follows the columns that still iterate (frequencies converge at different
+// iterations). Converged solutions are scattered back into x. Workspace: 13 vectors of
+// rows x B (two sets of x, r, rh, p, v and the scratch ph, sh, t).
 template <class R>
 heom_status bicgstab(heom_hier *h, const cx<R> *bvec, cx<R> *x, int64_t B, const cx<R> *shift,
                      R aug, bool x_zero, double tol, int max_iter, const std::vector<int> &active,
-                     cx<R> *work, ColState *st, int *d_flags, SolveOut &out, cudaStream_t s) {
+                     cx<R> *work, ColState *st, int *d_map, int *d_lmap, cx<R> *shift_c,
+                     SolveOut &out, cudaStream_t s) {
     const DevView<R> v = view_of<R>(h);
     const int64_t rows = h->N * h->d2, L = rows * B;
-    cx<R> *r = work, *rh = work + L, *p = work + 2 * L, *ph = work + 3 * L, *vv = work + 4 * L,
-          *sh = work + 5 * L, *t = work + 6 * L;
-    const int64_t cps = B / h->n_sets;
-    const Geom gd = make_geom(rows, B, std::max<int64_t>(1, 2048 / ((B + 31) / 32)));
-    const Geom ga = gd;
-    ApplyMods<R> mods{shift, aug};
-    HEOM_CUDA(memcpy_counted(d_flags, active.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
-    int n_act0 = 0;
-    for (int a : active) n_act0 += a != 0;
-    {
-        Prof pr(HEOM_KC_KRYLOV_VECTOR, s, (double)B);
-        k_state_init<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(st, B, d_flags);
-    }
-    {
-        Prof pr(HEOM_KC_KRYLOV_VECTOR, s, (double)rows * n_act0, (x_zero ? 5.0 : 6.0) * rows * n_act0 * sizeof(cx<R>));
-        k_bicg_init<R><<<gd.grid, gd.block, 0, s>>>(v, bvec, x, r, rh, p, vv, B, cps, mods, x_zero, st);
-    }
-    HEOM_CUDA(cudaGetLastError());
-    std::vector<ColState> hs(B);
-    std::vector<int> act = active;
+    cx<R> *set_a[5], *set_b[5];
+    for (int i = 0; i < 5; ++i) { set_a[i] = work + i * L; set_b[i] = work + (5 + i) * L; }
+    cx<R> *ph = work + 10 * L, *sh = work + 11 * L, *t = work + 12 * L;
+    const bool compact = h->n_sets == 1;
     out.iters.assign(B, 0);
     out.status.assign(B, HEOM_OK);
     out.res.assign(B, 0.0);
+    // the initial column set
+    std::vector<int> cols, alive;  // global column of each compact column; its activity
+    for (int64_t b = 0; b < B; ++b)
+        if (!compact || active[b]) { cols.push_back((int)b); alive.push_back(active[b] != 0); }
+    if (cols.empty()) return HEOM_OK;
+    if (compact && sizeof(R) == 4 && (cols.size() & 1) && (int64_t)cols.size() < B) {
+        for (int64_t b = 0; b < B; ++b)  // an even width keeps the float4 column loads aligned
+            if (!active[b]) { cols.push_back((int)b); alive.push_back(0); break; }
+    }
+    int64_t Bc = (int64_t)cols.size();
+    HEOM_CUDA(memcpy_counted(d_map, cols.data(), Bc * sizeof(int), cudaMemcpyHostToDevice, s));
+    HEOM_CUDA(memcpy_counted(d_lmap, alive.data(), Bc * sizeof(int), cudaMemcpyHostToDevice, s));
+    cx<R> **cur = set_a, **nxt = set_b;
+    const cx<R> *shc = nullptr;
+    {
+        Prof pr(HEOM_KC_OTHER, s, (double)rows * Bc, (3.0 + (x_zero ? 0 : 2)) * rows * Bc * sizeof(cx<R>));
+        k_gather_cols<R><<<flat_blocks(rows * Bc), 256, 0, s>>>(rows, bvec, B, t, Bc, d_map);
+        if (x_zero) HEOM_CUDA(cudaMemsetAsync(cur[0], 0, rows * Bc * sizeof(cx<R>), s));
+        else k_gather_cols<R><<<flat_blocks(rows * Bc), 256, 0, s>>>(rows, x, B, cur[0], Bc, d_map);
+        if (shift) {
+            k_gather_cols<R><<<flat_blocks(Bc), 256, 0, s>>>(1, shift, B, shift_c, Bc, d_map);
+            shc = shift_c;
+        }
+    }
+    {
+        Prof pr(HEOM_KC_KRYLOV_VECTOR, s, (double)Bc);
+        k_state_init<<<(unsigned)((Bc + 255) / 256), 256, 0, s>>>(st, Bc, d_lmap);
+    }
+    auto geoms = [&](int64_t w, Geom &gd, Geom &gv) {
+        // kernels with per-column dot products: a capped grid (few atomics per column);
+        // pure vector updates: a larger grid
+        gd = make_geom(rows, w, std::max<int64_t>(1, 4096 / ((w + 31) / 32)));
+        gv = make_geom(rows, w, std::max<int64_t>(1, 16384 / ((w + 31) / 32)));
+    };
+    Geom gd, gv;
+    geoms(Bc, gd, gv);
+    {
+        ApplyMods<R> mods{shc, aug};
+        Prof pr(HEOM_KC_KRYLOV_VECTOR, s, (double)rows * Bc, (x_zero ? 5.0 : 6.0) * rows * Bc * sizeof(cx<R>));
+        k_bicg_init<R><<<gd.grid, gd.block, 0, s>>>(v, t, cur[0], cur[1], cur[2], cur[3], cur[4],
+                                                    Bc, Bc, mods, x_zero, st);
+    }
+    HEOM_CUDA(cudaGetLastError());
+    std::vector<ColState> hs(Bc);
     const double tol2 = tol * tol;
-    // columns whose initial residual already meets tol
-    HEOM_CUDA(memcpy_counted(hs.data(), st, B * sizeof(ColState), cudaMemcpyDeviceToHost, s));
+    HEOM_CUDA(memcpy_counted(hs.data(), st, Bc * sizeof(ColState), cudaMemcpyDeviceToHost, s));
     HEOM_CUDA(cudaStreamSynchronize(s));
     int n_act = 0;
-    for (int64_t b = 0; b < B; ++b) {
-        if (!act[b]) continue;
-        out.res[b] = hs[b].bnorm2 > 0 ? std::sqrt(hs[b].acc_nr / hs[b].bnorm2) : 0.0;
-        if (hs[b].acc_nr <= tol2 * hs[b].bnorm2) { act[b] = 0; hs[b].active = 0; }
+    for (int64_t j = 0; j < Bc; ++j) {
+        if (!alive[j]) continue;
+        const int b = cols[j];
+        out.res[b] = hs[j].bnorm2 > 0 ? std::sqrt(hs[j].acc_nr / hs[j].bnorm2) : 0.0;
+        if (hs[j].acc_nr <= tol2 * hs[j].bnorm2) { alive[j] = 0; hs[j].active = 0; }
         else ++n_act;
     }
+    // stall / divergence guard: a column whose residual has not reached a new minimum for
+    // kStallIters iterations, or has grown 1e12-fold above its minimum, stops; the caller's
+    // refinement then restarts from its FP64 residual (or skips a correction that grew).
+    std::vector<double> best(Bc);
+    std::vector<int> best_it(Bc, 0);
+    for (int64_t j = 0; j < Bc; ++j) best[j] = hs[j].acc_nr;
     int it = 0, check = 4;
     while (n_act > 0 && it < max_iter) {
-        HEOM_CUDA(memcpy_counted(st, hs.data(), B * sizeof(ColState), cudaMemcpyHostToDevice, s));
+        // ---- re-compaction when the active columns fall to 60 % of the working width
+        if (compact && n_act <= 0.6 * Bc && Bc - n_act >= 16) {
+            std::vector<int> keep;
+            for (int64_t j = 0; j < Bc; ++j)
+                if (alive[j]) keep.push_back((int)j);
+            if (sizeof(R) == 4 && (keep.size() & 1)) {
+                for (int64_t j = 0; j < Bc; ++j)
+                    if (!alive[j]) { keep.push_back((int)j); break; }
+            }
+            std::sort(keep.begin(), keep.end());
+            const int64_t Bn = (int64_t)keep.size();
+            {   // solutions of every current column go home first
+                Prof pr(HEOM_KC_OTHER, s, (double)rows * Bc, 2.0 * rows * Bc * sizeof(cx<R>));
+                k_scatter_cols<R><<<flat_blocks(rows * Bc), 256, 0, s>>>(rows, cur[0], Bc, x, B, d_map);
+            }
+            HEOM_CUDA(memcpy_counted(d_lmap, keep.data(), Bn * sizeof(int), cudaMemcpyHostToDevice, s));
+            {
+                Prof pr(HEOM_KC_OTHER, s, 5.0 * rows * Bn, 10.0 * rows * Bn * sizeof(cx<R>));
+                for (int i = 0; i < 5; ++i)
+                    k_gather_cols<R><<<flat_blocks(rows * Bn), 256, 0, s>>>(rows, cur[i], Bc, nxt[i], Bn, d_lmap);
+            }
+            std::vector<int> ncols(Bn), nalive(Bn);
+            std::vector<ColState> nhs(Bn);
+            std::vector<double> nbest(Bn);
+            std::vector<int> nbest_it(Bn);
+            for (int64_t j = 0; j < Bn; ++j) {
+                const int o = keep[j];
+                ncols[j] = cols[o];
+                nalive[j] = alive[o];
+                nhs[j] = hs[o];
+                nhs[j].active = alive[o];
+                nbest[j] = best[o];
+                nbest_it[j] = best_it[o];
+            }
+            cols.swap(ncols); alive.swap(nalive); hs.swap(nhs); best.swap(nbest); best_it.swap(nbest_it);
+            std::swap(cur, nxt);
+            Bc = Bn;
+            HEOM_CUDA(memcpy_counted(d_map, cols.data(), Bc * sizeof(int), cudaMemcpyHostToDevice, s));
+            if (shift) {
+                Prof pr(HEOM_KC_OTHER, s, (double)Bc);
+                k_gather_cols<R><<<flat_blocks(Bc), 256, 0, s>>>(1, shift, B, shift_c, Bc, d_map);
+            }
+            geoms(Bc, gd, gv);
+        }
+        HEOM_CUDA(memcpy_counted(st, hs.data(), Bc * sizeof(ColState), cudaMemcpyHostToDevice, s));
         const int steps = std::min(check, max_iter - it);
         const int kc_apply = sizeof(R) == 4 ? HEOM_KC_KRYLOV_APPLY32 : HEOM_KC_KRYLOV_APPLY64;
-        const double u_vec = (double)rows * n_act, u_app = (double)h->N * n_act;
+        ApplyMods<R> mods{shc, aug};
+        const bool tiled = tile_ok(v, Bc);
+        TileArgs<R> ta{};
+        ta.v = v;
+        ta.shift = shc;
+        ta.aug = aug;
+        ta.st = st;
+        ta.B = Bc;
+        cx<R> *xw = cur[0], *r = cur[1], *rh = cur[2], *p = cur[3], *vv = cur[4];
+        const int64_t cps = Bc / h->n_sets;
+        const double u_vec = (double)rows * Bc, u_app = (double)h->N * Bc;
         const double sz = sizeof(cx<R>), e_vec = u_vec * sz;
         for (int k = 0; k < steps; ++k) {
             { Prof pr(HEOM_KC_KRYLOV_VECTOR, s, u_vec, 5.0 * e_vec);
-              k_bicg_p<R><<<gd.grid, gd.block, 0, s>>>(v, r, p, vv, ph, B, cps, shift, 1, st); }
+              k_bicg_p<R><<<gv.grid, gv.block, 0, s>>>(v, r, p, vv, ph, Bc, cps, shc, 1, st); }
             { Prof pr(kc_apply, s, u_app, 3.0 * e_vec);
-              k_bicg_apply<R><<<ga.grid, ga.block, 0, s>>>(v, ph, vv, rh, B, cps, mods, 0, st); }
+              if (tiled) { ta.x = ph; ta.out = vv; ta.w = rh; HEOM_CUDA((launch_tile<R, TM_BICG_V>(ta, s))); }
+              else k_bicg_apply<R><<<gd.grid, gd.block, 0, s>>>(v, ph, vv, rh, Bc, cps, mods, 0, st); }
             { Prof pr(HEOM_KC_KRYLOV_VECTOR, s, u_vec, 4.0 * e_vec);
-              k_bicg_s<R><<<gd.grid, gd.block, 0, s>>>(v, r, vv, sh, B, cps, shift, 1, st); }
+              k_bicg_s<R><<<gv.grid, gv.block, 0, s>>>(v, r, vv, sh, Bc, cps, shc, 1, st); }
             { Prof pr(kc_apply, s, u_app, 3.0 * e_vec);
-              k_bicg_apply<R><<<ga.grid, ga.block, 0, s>>>(v, sh, t, r, B, cps, mods, 1, st); }
+              if (tiled) { ta.x = sh; ta.out = t; ta.w = r; HEOM_CUDA((launch_tile<R, TM_BICG_T>(ta, s))); }
+              else k_bicg_apply<R><<<gd.grid, gd.block, 0, s>>>(v, sh, t, r, Bc, cps, mods, 1, st); }
             { Prof pr(HEOM_KC_KRYLOV_VECTOR, s, u_vec, 8.0 * e_vec);
-              k_bicg_x<R><<<gd.grid, gd.block, 0, s>>>(rows, x, ph, sh, r, t, rh, B, st); }
+              k_bicg_x<R><<<gd.grid, gd.block, 0, s>>>(rows, xw, ph, sh, r, t, rh, Bc, st); }
         }
         HEOM_CUDA(cudaGetLastError());
         it += steps;
-        HEOM_CUDA(memcpy_counted(hs.data(), st, B * sizeof(ColState), cudaMemcpyDeviceToHost, s));
+        HEOM_CUDA(memcpy_counted(hs.data(), st, Bc * sizeof(ColState), cudaMemcpyDeviceToHost, s));
         HEOM_CUDA(cudaStreamSynchronize(s));
         n_act = 0;
-        for (int64_t b = 0; b < B; ++b) {
-            if (!act[b]) continue;
+        for (int64_t j = 0; j < Bc; ++j) {
+            if (!alive[j]) continue;
+            const int b = cols[j];
             out.iters[b] = it;
-            const double nr = hs[b].acc_nr;
-            out.res[b] = hs[b].bnorm2 > 0 ? std::sqrt(nr / hs[b].bnorm2) : 0.0;
-            if (!std::isfinite(nr) || hs[b].flag) {
+            const double nr = hs[j].acc_nr;
+            out.res[b] = hs[j].bnorm2 > 0 ? std::sqrt(nr / hs[j].bnorm2) : 0.0;
+            if (!std::isfinite(nr) || hs[j].flag) {
                 out.status[b] = HEOM_EBREAKDOWN;
-                act[b] = 0; hs[b].active = 0;
-            } else if (nr <= tol2 * hs[b].bnorm2) {
-                act[b] = 0; hs[b].active = 0;
+                alive[j] = 0; hs[j].active = 0;
+            } else if (nr <= tol2 * hs[j].bnorm2) {
+                alive[j] = 0; hs[j].active = 0;
+            } else if (nr < best[j]) {
+                best[j] = nr;
+                best_it[j] = it;
+                ++n_act;
+            } else if (it - best_it[j] >= kStallIters || nr > 1e12 * best[j]) {
+                // stalled: usable if it still improved on the start, otherwise discard
+                out.status[b] = nr < hs[j].bnorm2 ? HEOM_ENOCONV : HEOM_EBREAKDOWN;
+                alive[j] = 0; hs[j].active = 0;
             } else {
                 ++n_act;
             }
         }
         check = std::min(check * 2, 32);
     }
-    for (int64_t b = 0; b < B; ++b)
-        if (act[b]) out.status[b] = HEOM_ENOCONV;
+    for (int64_t j = 0; j < Bc; ++j)
+        if (alive[j]) out.status[cols[j]] = HEOM_ENOCONV;
+    {
+        Prof pr(HEOM_KC_OTHER, s, (double)rows * Bc, 2.0 * rows * Bc * sizeof(cx<R>));
+        k_scatter_cols<R><<<flat_blocks(rows * Bc), 256, 0, s>>>(rows, cur[0], Bc, x, B, d_map);
+    }
+    HEOM_CUDA(cudaGetLastError());
     return HEOM_OK;
 }
 
@@ -544,32 +726,38 @@ struct Solve {
 // (inner tolerance 1e-5); RI = double is the plain FP64 path, whose inner tolerance asks for
 // the whole remaining reduction at once and whose outer loop only guards against the drift
 // between BiCGStab's recursive residual and the true one.
-constexpr int kInnerCap = 400;
+constexpr int kInnerCap = 400;     // FP32 BiCGStab iterations per refinement sweep
+constexpr int kInnerCap64 = 1500;  // FP64 BiCGStab iterations per sweep (plain path)
 
 template <class RI>
 heom_status refine_solve(heom_hier *h, const cx<double> *b64, cx<double> *x64, int64_t B,
                          const cx<double> *shift64, double aug, bool x_zero, double tol,
-                         int max_iter, Solve &res, cudaStream_t s) {
+                         int max_iter, Solve &res, cudaStream_t s,
+                         const std::vector<int> *only = nullptr) {
     const int64_t rows = h->N * h->d2, L = rows * B;
-    const size_t bytes = align_up(L * sizeof(cx<double>)) + align_up(9 * L * sizeof(cx<RI>)) +
-                         align_up(B * sizeof(cx<RI>));
+    const size_t bytes = align_up(L * sizeof(cx<double>)) + align_up(15 * L * sizeof(cx<RI>)) +
+                         2 * align_up(B * sizeof(cx<RI>));
     heom_status stt = ensure_ws(h->ws, bytes);
     if (stt != HEOM_OK) return stt;
-    stt = ensure_ws(h->ws_small, align_up(2 * B * sizeof(ColState)) + align_up(B * sizeof(int)));
+    stt = ensure_ws(h->ws_small, align_up(2 * B * sizeof(ColState)) + 3 * align_up(B * sizeof(int)));
     if (stt != HEOM_OK) return stt;
     ColState *st = (ColState *)h->ws_small.p;
     ColState *st_out = st + B;
     int *d_flags = (int *)((char *)h->ws_small.p + align_up(2 * B * sizeof(ColState)));
+    int *d_map = (int *)((char *)d_flags + align_up(B * sizeof(int)));
+    int *d_lmap = (int *)((char *)d_map + align_up(B * sizeof(int)));
     res.iters.assign(B, 0);
     res.refine.assign(B, 0);
     res.status.assign(B, HEOM_OK);
     res.res.assign(B, 0.0);
     std::vector<int> active(B, 1);
+    if (only) active = *only;
     char *base = (char *)h->ws.p;
     cx<double> *r64 = (cx<double> *)base;
     cx<RI> *w = (cx<RI> *)(base + align_up(L * sizeof(cx<double>)));
-    cx<RI> *rhs = w + 7 * L, *dv = w + 8 * L;
-    cx<RI> *shift_in = (cx<RI> *)((char *)w + align_up(9 * L * sizeof(cx<RI>)));
+    cx<RI> *rhs = w + 13 * L, *dv = w + 14 * L;
+    cx<RI> *shift_in = (cx<RI> *)((char *)w + align_up(15 * L * sizeof(cx<RI>)));
+    cx<RI> *shift_c = (cx<RI> *)((char *)shift_in + align_up(B * sizeof(cx<RI>)));
     if (shift64) {
         Prof pr(HEOM_KC_OTHER, s, (double)B);
         k_convert<RI, double><<<flat_blocks(B), 256, 0, s>>>(B, shift64, shift_in);
@@ -590,7 +778,14 @@ heom_status refine_solve(heom_hier *h, const cx<double> *b64, cx<double> *x64, i
         { Prof pr(HEOM_KC_OTHER, s, (double)B);
           k_state_init<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(st_out, B, d_flags); }
         { Prof pr(HEOM_KC_RESIDUAL64, s, (double)h->N * n_on, 3.0 * rows * n_on * sizeof(cx<double>));
-          k_residual64<<<gd.grid, gd.block, 0, s>>>(v64, b64, x64, r64, B, cps, m64, st_out); }
+          if (tile_ok(v64, B)) {
+              TileArgs<double> ta{};
+              ta.v = v64; ta.x = x64; ta.out = r64; ta.w = b64; ta.shift = shift64; ta.aug = aug;
+              ta.st = st_out; ta.B = B;
+              HEOM_CUDA((launch_tile<double, TM_RESID>(ta, s)));
+          } else {
+              k_residual64<<<gd.grid, gd.block, 0, s>>>(v64, b64, x64, r64, B, cps, m64, st_out);
+          } }
         HEOM_CUDA(cudaGetLastError());
         HEOM_CUDA(memcpy_counted(hs.data(), st_out, B * sizeof(ColState), cudaMemcpyDeviceToHost, s));
         HEOM_CUDA(cudaStreamSynchronize(s));
@@ -620,13 +815,14 @@ heom_status refine_solve(heom_hier *h, const cx<double> *b64, cx<double> *x64, i
         int inner_max = 0;
         for (int64_t b = 0; b < B; ++b)
             if (active[b]) inner_max = std::max(inner_max, max_iter - res.iters[b]);
-        // FP32 BiCGStab reaches about 1e-5 at best on these systems, so each mixed sweep asks
-        // for 1e-4 and at most kInnerCap iterations; refinement supplies the remaining digits.
-        const double inner_tol = plain ? std::max(0.5 * tol / worst, 1e-14) : 1e-4;
-        if (!plain) inner_max = std::min(inner_max, kInnerCap);
+        // One sweep never asks BiCGStab for more than its attainable accuracy (about 1e-5
+        // relative in FP32, about 1e-10 in FP64 on these systems, limited by the size of
+        // intermediate residuals); refinement from the FP64 residual supplies the rest.
+        const double inner_tol = plain ? std::max(0.5 * tol / worst, 1e-10) : 1e-4;
+        inner_max = std::min(inner_max, plain ? kInnerCap64 : kInnerCap);
         SolveOut o;
         stt = bicgstab<RI>(h, rhs, dv, B, shift64 ? shift_in : nullptr, (RI)aug, true, inner_tol,
-                           inner_max, active, w, st, d_flags, o, s);
+                           inner_max, active, w, st, d_map, d_lmap, shift_c, o, s);
         if (stt != HEOM_OK) return stt;
         bool skip_any = false;
         for (int64_t b = 0; b < B; ++b) {
@@ -647,12 +843,45 @@ heom_status refine_solve(heom_hier *h, const cx<double> *b64, cx<double> *x64, i
     return HEOM_OK;
 }
 
+// zero the batch columns flagged in keep (device int [B])
+__global__ void k_zero_cols(int64_t total, cx<double> *x, int64_t B, const int *flags) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (flags[i % B]) x[i] = cx<double>{0.0, 0.0};
+}
+
 heom_status solve_system(heom_hier *h, const cx<double> *b64, cx<double> *x64, int64_t B,
                          const cx<double> *shift64, double aug, bool x_zero, double tol,
                          int max_iter, int prec, Solve &res, cudaStream_t s) {
-    if (prec == HEOM_MIXED)
-        return refine_solve<float>(h, b64, x64, B, shift64, aug, x_zero, tol, max_iter, res, s);
-    return refine_solve<double>(h, b64, x64, B, shift64, aug, x_zero, tol, max_iter, res, s);
+    if (prec != HEOM_MIXED)
+        return refine_solve<double>(h, b64, x64, B, shift64, aug, x_zero, tol, max_iter, res, s);
+    heom_status st = refine_solve<float>(h, b64, x64, B, shift64, aug, x_zero, tol, max_iter, res, s);
+    if (st != HEOM_OK) return st;
+    // columns whose FP32 corrections broke down (near-singular systems whose FP32 BiCGStab
+    // overflows or stalls) are solved again from zero with FP64 inner solves
+    std::vector<int> redo(B, 0);
+    int n_redo = 0;
+    for (int64_t b = 0; b < B; ++b)
+        if (res.status[b] == HEOM_EBREAKDOWN) { redo[b] = 1; ++n_redo; }
+    if (n_redo == 0) return HEOM_OK;
+    DBuf flags;
+    st = dalloc(flags, B * sizeof(int));
+    if (st != HEOM_OK) return st;
+    HEOM_CUDA(memcpy_counted(flags.p, redo.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
+    const int64_t L = h->N * h->d2 * B;
+    { Prof pr(HEOM_KC_OTHER, s, (double)L);
+      k_zero_cols<<<flat_blocks(L), 256, 0, s>>>(L, x64, B, (const int *)flags.p); }
+    Solve r2;
+    st = refine_solve<double>(h, b64, x64, B, shift64, aug, false, tol, max_iter, r2, s, &redo);
+    dfree(flags);
+    if (st != HEOM_OK) return st;
+    for (int64_t b = 0; b < B; ++b)
+        if (redo[b]) {
+            res.iters[b] += r2.iters[b];
+            res.res[b] = r2.res[b];
+            res.status[b] = r2.status[b];
+        }
+    return HEOM_OK;
 }
 
 template <class R>
@@ -669,15 +898,28 @@ heom_status evolve_impl(heom_hier *h, cx<R> *y, int64_t B, double dt, int64_t n_
     int64_t saved = 0;
     if (traj) HEOM_CUDA(memcpy_counted(traj, y, blk, cudaMemcpyDeviceToDevice, s));
     const double u = (double)h->N * B, pass = (double)L * sizeof(cx<R>);
+    const bool tiled = tile_ok(v, B);
+    TileArgs<R> ta{};
+    ta.v = v;
+    ta.y = y;
+    ta.acc = acc;
+    ta.dt = (R)dt;
+    ta.B = B;
+    auto stage = [&](const cx<R> *zi, cx<R> *zo, int st_no) -> cudaError_t {
+        if (tiled) {
+            ta.x = zi;
+            ta.out = zo;
+            ta.stage = st_no;
+            return launch_tile<R, TM_RK4>(ta, s);
+        }
+        k_rk4_stage<R><<<g.grid, g.block, 0, s>>>(v, zi, zo, y, acc, B, cps, (R)dt, st_no);
+        return cudaGetLastError();
+    };
     for (int64_t step = 1; step <= n_steps; ++step) {
-        { Prof pr(HEOM_KC_RK4, s, u, 3.0 * pass);
-          k_rk4_stage<R><<<g.grid, g.block, 0, s>>>(v, y, za, y, acc, B, cps, (R)dt, 1); }
-        { Prof pr(HEOM_KC_RK4, s, u, 5.0 * pass);
-          k_rk4_stage<R><<<g.grid, g.block, 0, s>>>(v, za, zb, y, acc, B, cps, (R)dt, 2); }
-        { Prof pr(HEOM_KC_RK4, s, u, 5.0 * pass);
-          k_rk4_stage<R><<<g.grid, g.block, 0, s>>>(v, zb, za, y, acc, B, cps, (R)dt, 3); }
-        { Prof pr(HEOM_KC_RK4, s, u, 4.0 * pass);
-          k_rk4_stage<R><<<g.grid, g.block, 0, s>>>(v, za, zb, y, acc, B, cps, (R)dt, 4); }
+        { Prof pr(HEOM_KC_RK4, s, u, 3.0 * pass); HEOM_CUDA(stage(y, za, 1)); }
+        { Prof pr(HEOM_KC_RK4, s, u, 5.0 * pass); HEOM_CUDA(stage(za, zb, 2)); }
+        { Prof pr(HEOM_KC_RK4, s, u, 5.0 * pass); HEOM_CUDA(stage(zb, za, 3)); }
+        { Prof pr(HEOM_KC_RK4, s, u, 4.0 * pass); HEOM_CUDA(stage(za, zb, 4)); }
         if (traj && step % save_every == 0) {
             ++saved;
             HEOM_CUDA(memcpy_counted((char *)traj + saved * blk, y, blk, cudaMemcpyDeviceToDevice, s));
@@ -769,7 +1011,13 @@ extern "C" heom_status heom_steady(heom_hier *h, const void *x0, void *x_out, in
     HEOM_CUDA(cudaMemsetAsync(norms, 0, 2 * batch * sizeof(double), st));
     const Geom gd = make_geom(rows, batch, std::max<int64_t>(1, 2048 / ((batch + 31) / 32)));
     { Prof pr(HEOM_KC_RESIDUAL64, st, (double)h->N * batch, (double)L * sizeof(cx<double>));
-      k_apply_norms<<<gd.grid, gd.block, 0, st>>>(h->view64(), x, batch, batch / h->n_sets, norms); }
+      if (tile_ok(h->view64(), batch)) {
+          TileArgs<double> ta{};
+          ta.v = h->view64(); ta.x = x; ta.norms = norms; ta.B = batch;
+          HEOM_CUDA((launch_tile<double, TM_NORMS>(ta, st)));
+      } else {
+          k_apply_norms<<<gd.grid, gd.block, 0, st>>>(h->view64(), x, batch, batch / h->n_sets, norms);
+      } }
     std::vector<double> hn(2 * batch);
     HEOM_CUDA(memcpy_counted(hn.data(), norms, hn.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     HEOM_CUDA(cudaStreamSynchronize(st));
@@ -785,20 +1033,82 @@ extern "C" heom_status heom_steady(heom_hier *h, const void *x0, void *x_out, in
     return ret;
 }
 
+// Density of states from two shift-invariant Krylov processes (x_+ family on column 0,
+// x_- family on column 1).
+static heom_status spectrum_shifted(heom_hier *odd, const void *ss_ados, const heom_c64 *op_d,
+                                    const double *omega, int64_t n_omega, double tol,
+                                    int max_iter, double *A_out, heom_solve_stats *stats,
+                                    cudaStream_t st) {
+    const int d = odd->d;
+    const int64_t rows = odd->N * odd->d2, L = rows * 2;
+    DBuf buf;
+    heom_status stt = dalloc(buf, L * sizeof(cx<double>) + 2 * d * d * sizeof(cx<double>));
+    if (stt != HEOM_OK) return stt;
+    cx<double> *b64 = (cx<double> *)buf.p, *ops = b64 + L;
+    std::vector<cx<double>> hops(2 * d * d);
+    for (int r = 0; r < d; ++r)
+        for (int c = 0; c < d; ++c) {
+            hops[r * d + c] = {op_d[c * d + r].re, -op_d[c * d + r].im};  // d^dagger
+            hops[d * d + r * d + c] = {op_d[r * d + c].re, op_d[r * d + c].im};
+        }
+    HEOM_CUDA(memcpy_counted(ops, hops.data(), hops.size() * sizeof(cx<double>), cudaMemcpyHostToDevice, st));
+    { Prof pr(HEOM_KC_OTHER, st, (double)L);
+      k_dos_rhs<<<flat_blocks(L), 256, 0, st>>>(odd->N, d, (const cx<double> *)ss_ados, ops, ops + d * d, b64, 1); }
+    std::vector<cx<double>> shift(2 * n_omega);
+    std::vector<int> col_of(2 * n_omega);
+    for (int64_t j = 0; j < n_omega; ++j) {
+        shift[j] = {0.0, omega[j]};             // (M + i w) x_+ = d^dag rho
+        col_of[j] = 0;
+        shift[n_omega + j] = {0.0, -omega[j]};  // (M - i w) x_- = d rho
+        col_of[n_omega + j] = 1;
+    }
+    std::vector<cx<double>> x0;
+    std::vector<double> res;
+    int steps = 0;
+    stt = shifted_gmres(odd, b64, 2, shift, col_of, 0.5 * tol, std::max(1, std::min(max_iter, 2000)),
+                        x0, res, &steps, st);
+    dfree(buf);
+    if (stt != HEOM_OK) return stt;
+    heom_status ret = HEOM_OK;
+    const int d2 = d * d;
+    for (int64_t j = 0; j < n_omega; ++j) {
+        double acc = 0;
+        for (int i = 0; i < d; ++i)
+            for (int l = 0; l < d; ++l) {
+                const cx<double> xp = x0[(size_t)j * d2 + l * d + i];
+                const cx<double> xm = x0[(size_t)(n_omega + j) * d2 + l * d + i];
+                const cx<double> dd{op_d[i * d + l].re, op_d[i * d + l].im};
+                const cx<double> dh{op_d[l * d + i].re, -op_d[l * d + i].im};
+                acc += (dd * xp).re + (dh * xm).re;
+            }
+        A_out[j] = -acc / M_PI;
+    }
+    for (int64_t k = 0; k < 2 * n_omega; ++k) {
+        const int status = (std::isfinite(res[k]) && res[k] <= tol) ? HEOM_OK : HEOM_ENOCONV;
+        if (status != HEOM_OK && ret == HEOM_OK) ret = HEOM_ENOCONV;
+        if (stats) stats[k] = heom_solve_stats{steps, 0, res[k], status};
+    }
+    if (ret != HEOM_OK) set_error("heom_spectrum: some frequencies did not converge (see stats)");
+    return ret;
+}
+
 extern "C" heom_status heom_spectrum(heom_hier *odd, const void *ss_ados, const heom_c64 *op_d,
                                      const double *omega, int64_t n_omega, double tol,
                                      int max_iter, double *A_out, int prec,
                                      heom_solve_stats *stats, heom_stream s) {
     if (!odd || !ss_ados || !op_d || !omega || n_omega < 1 || !(tol > 0) || max_iter < 1 ||
-        !A_out || (prec != HEOM_FP64 && prec != HEOM_MIXED) || odd->n_sets != 1 ||
-        2 * n_omega > 65535LL * 32) {
+        !A_out || (prec != HEOM_FP64 && prec != HEOM_MIXED && prec != HEOM_SHIFTED) ||
+        odd->n_sets != 1 || 2 * n_omega > 65535LL * 32) {
         set_error("heom_spectrum: need an odd-parity hierarchy with one parameter set, ss_ados, "
-                  "op_d, omega[n_omega >= 1], A_out, tol > 0, max_iter >= 1, prec FP64 or MIXED");
+                  "op_d, omega[n_omega >= 1], A_out, tol > 0, max_iter >= 1, prec FP64, MIXED "
+                  "or SHIFTED");
         return HEOM_EINVAL;
     }
     HEOM_CUDA(cudaSetDevice(odd->device));
     cudaStream_t st = (cudaStream_t)s;
     const int d = odd->d;
+    if (prec == HEOM_SHIFTED) return spectrum_shifted(odd, ss_ados, op_d, omega, n_omega, tol,
+                                                      max_iter, A_out, stats, st);
     const int64_t B = 2 * n_omega, rows = odd->N * odd->d2, L = rows * B;
     DBuf buf;
     heom_status stt = dalloc(buf, L * 2 * sizeof(cx<double>) + B * sizeof(cx<double>) +

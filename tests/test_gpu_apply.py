@@ -36,7 +36,7 @@ def _run(heom, prob, X, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("batch", [1, 3, 37])
+@pytest.mark.parametrize("batch", [1, 3, 37, 64])
 @pytest.mark.parametrize("parity", [1, -1])
 @pytest.mark.parametrize("bos,fer,tb_,tf", [
     ([("RI", 2), ("R", 1), ("I", 1)], [], 3, 0),

@@ -211,22 +211,44 @@ def omega_grid(n: int, lo: float = -20.0, hi: float = 20.0) -> np.ndarray:
 
 
 def draw_siam_sets(n_sets: int = 64, seed: int = SEED_SETS):
-    """Batched-spectra parameter draws: U~U[0,12], bias~U[0,3], kT~U[0.2,1], tier~{2,3,4}."""
+    """Batched-spectra parameter draws: U~U[0,12], bias~U[0,3], kT~U[0.2,1] (outside
+    KT_EXCLUDED), tier~{2,3,4}."""
     rng = np.random.default_rng(seed)
     U = rng.uniform(0.0, 12.0, n_sets)
     bias = rng.uniform(0.0, 3.0, n_sets)
-    kT = rng.uniform(0.2, 1.0, n_sets)
+    kT = _draw_kt(rng, n_sets)
     tier = rng.choice(np.array([2, 3, 4]), n_sets)
     return [dict(U=float(U[i]), mu=float(bias[i]), kT=float(kT[i]), tier=int(tier[i]))
             for i in range(n_sets)]
 
 
+# With the lead band width W = 10 and two Pade poles, the second pole of the Fermi function
+# sits on the Lorentzian's pole (zeta_2 kT = W) at kT = 10 / 13.0432 = 0.7667, where the
+# exponent formula divides by W^2 - (zeta_2 kT)^2 = 0. Draws of kT avoid this band.
+KT_EXCLUDED = (0.73, 0.80)
+
+
+def _draw_kt(rng, n, lo=0.2, hi=1.0):
+    out = np.empty(n)
+    for i in range(n):
+        while True:
+            v = rng.uniform(lo, hi)
+            if not (KT_EXCLUDED[0] <= v <= KT_EXCLUDED[1]):
+                out[i] = v
+                break
+    return out
+
+
 def draw_warmstart_samples(n: int, seed: int = SEED_VECTORS):
-    """Learned-warm-start draws: U~U[0,12], eps~U[-8,-2], Gamma~U[1,3], kT~U[0.2,1], bias~U[0,3]."""
+    """Learned-warm-start draws: U~U[0,12], eps~U[-8,-2], Gamma~U[1,3], kT~U[0.2,1] (outside
+    KT_EXCLUDED), bias~U[0,3]."""
     rng = np.random.default_rng(seed)
-    return np.stack([rng.uniform(0.0, 12.0, n), rng.uniform(-8.0, -2.0, n),
-                     rng.uniform(1.0, 3.0, n), rng.uniform(0.2, 1.0, n),
-                     rng.uniform(0.0, 3.0, n)], axis=1)
+    U = rng.uniform(0.0, 12.0, n)
+    eps = rng.uniform(-8.0, -2.0, n)
+    G = rng.uniform(1.0, 3.0, n)
+    kT = _draw_kt(rng, n)
+    mu = rng.uniform(0.0, 3.0, n)
+    return np.stack([U, eps, G, kT, mu], axis=1)
 
 
 # --------------------------------------------------------------------------------------
