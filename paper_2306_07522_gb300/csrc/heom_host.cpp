@@ -310,6 +310,8 @@ heom::DevView<double> heom_hier::view64() const {
     v.max_terms = max_terms; v.max_entries = max_entries;
     v.cta_ado = (const int32_t *)d_cta_ado.p; v.n_ranges = n_ranges; v.range_terms = range_terms;
     v.range_slots = range_slots; v.range_ados = range_ados;
+    v.pers_ado = (const int32_t *)d_pers_ado.p; v.pers_ranges = pers_ranges;
+    v.pers_terms = pers_terms; v.pers_slots = pers_slots; v.pers_ados = pers_ados;
     return v;
 }
 
@@ -336,6 +338,8 @@ heom::DevView<float> heom_hier::view32() const {
     v.max_terms = max_terms; v.max_entries = max_entries;
     v.cta_ado = (const int32_t *)d_cta_ado.p; v.n_ranges = n_ranges; v.range_terms = range_terms;
     v.range_slots = range_slots; v.range_ados = range_ados;
+    v.pers_ado = (const int32_t *)d_pers_ado.p; v.pers_ranges = pers_ranges;
+    v.pers_terms = pers_terms; v.pers_slots = pers_slots; v.pers_ados = pers_ados;
     return v;
 }
 
@@ -350,7 +354,7 @@ void free_all(heom_hier *h) {
                     &h->d_coefR32, &h->d_rate64, &h->d_rate32, &h->d_hdiag64, &h->d_hdiag32,
                     &h->d_floor64, &h->d_floor32, &h->ws, &h->ws_small, &h->d_t_ptr,
                     &h->d_t_src, &h->d_t_val64, &h->d_t_val32, &h->d_th_ptr, &h->d_th_src,
-                    &h->d_th_vi, &h->d_cta_ado};
+                    &h->d_th_vi, &h->d_cta_ado, &h->d_pers_ado, &h->ws_pers};
     for (DBuf *b : bufs) heom::dfree(*b);
 }
 
@@ -430,9 +434,10 @@ heom_status upload_params(heom_hier *h, int n_sets, const heom_c64 *H, const heo
         h->max_terms = mt;
         h->max_entries = me;
     }
-    // ADO ranges for the persistent tiled kernel: contiguous, about equal term counts
-    // (five CTAs per SM, all resident at once), each range's program and bookkeeping bounded for shared memory.
-    std::vector<int32_t> ranges(1, 0);
+    // ADO ranges: contiguous, about equal term counts, each range's program and bookkeeping
+    // bounded for shared memory. Tiled kernel: five CTAs per SM, all resident at once.
+    // Cooperative persistent solvers: one range per SM.
+    std::vector<int32_t> ranges, pranges;
     {
         std::vector<int64_t> terms(h->N), slots(h->N);
         int64_t total = 0;
@@ -443,38 +448,49 @@ heom_status upload_params(heom_hier *h, int n_sets, const heom_c64 *H, const heo
             slots[i] = (int64_t)h->d2 * (h->row_ptr[i + 1] - h->row_ptr[i] + 3);
             total += t;
         }
-        // at most kResident ranges, so that every CTA is resident and they sweep together;
-        // a range closes once it reaches the target (or a shared-memory bound)
-        const int64_t kResident = 152 * 5;
-        int64_t target = std::max<int64_t>(1, (total + kResident - 1) / kResident);
-        int64_t rt = 0, rs = 0, rn = 0;
-        for (int attempt = 0; attempt < 64; ++attempt) {
-            ranges.assign(1, 0);
-            int64_t cur_t = 0, cur_s = 0, cur_n = 0;
-            rt = rs = rn = 0;
-            for (int64_t i = 0; i < h->N; ++i) {
-                const bool full = cur_n > 0 && (cur_t >= target || cur_t + terms[i] > heom::kRangeTerms ||
-                                                cur_s + slots[i] > heom::kRangeSlots ||
-                                                cur_n >= heom::kRangeAdos);
-                if (full) {
-                    ranges.push_back((int32_t)i);
-                    cur_t = cur_s = cur_n = 0;
+        // at most `resident` ranges; a range closes once it reaches the target term count (or
+        // a shared-memory bound). Returns whether every range fits within the bounds.
+        auto partition = [&](int64_t resident, int64_t cap_terms, std::vector<int32_t> &rg, int64_t &rt,
+                             int64_t &rs, int64_t &rn) {
+            int64_t target = std::max<int64_t>(1, (total + resident - 1) / resident);
+            for (int attempt = 0; attempt < 64; ++attempt) {
+                rg.assign(1, 0);
+                int64_t cur_t = 0, cur_s = 0, cur_n = 0;
+                rt = rs = rn = 0;
+                for (int64_t i = 0; i < h->N; ++i) {
+                    const bool full = cur_n > 0 && (cur_t >= target || cur_t + terms[i] > cap_terms ||
+                                                    cur_s + slots[i] > heom::kRangeSlots ||
+                                                    cur_n >= heom::kRangeAdos);
+                    if (full) {
+                        rg.push_back((int32_t)i);
+                        cur_t = cur_s = cur_n = 0;
+                    }
+                    cur_t += terms[i]; cur_s += slots[i]; ++cur_n;
+                    rt = std::max(rt, cur_t); rs = std::max(rs, cur_s); rn = std::max(rn, cur_n);
                 }
-                cur_t += terms[i]; cur_s += slots[i]; ++cur_n;
-                rt = std::max(rt, cur_t); rs = std::max(rs, cur_s); rn = std::max(rn, cur_n);
+                rg.push_back((int32_t)h->N);
+                if ((int64_t)rg.size() - 1 <= resident) return true;
+                target += target / 8 + 1;
             }
-            ranges.push_back((int32_t)h->N);
-            if ((int64_t)ranges.size() - 1 <= kResident) break;
-            target += target / 8 + 1;
-        }
+            return false;
+        };
+        int n_sm = 152;
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, h->device);
+        int64_t rt, rs, rn;
+        partition(152 * 5, heom::kRangeTerms, ranges, rt, rs, rn);
         h->n_ranges = (int)ranges.size() - 1;
         h->range_terms = (int)std::min<int64_t>(rt, INT32_MAX);
         h->range_slots = (int)std::min<int64_t>(rs, INT32_MAX);
         h->range_ados = (int)rn;
+        const bool pfit = partition(n_sm, heom::kPersistTerms, pranges, rt, rs, rn);
+        h->pers_ranges = (pfit && rt <= heom::kPersistTerms && rs <= heom::kRangeSlots) ? (int)pranges.size() - 1 : 0;
+        h->pers_terms = (int)std::min<int64_t>(rt, INT32_MAX);
+        h->pers_slots = (int)std::min<int64_t>(rs, INT32_MAX);
+        h->pers_ados = (int)rn;
     }
     heom_status st;
 #define UP(buf, vec) if ((st = upload(h->buf, vec)) != HEOM_OK) return st
-    UP(d_th_ptr, thp); UP(d_th_src, ths); UP(d_th_vi, thv); UP(d_cta_ado, ranges);
+    UP(d_th_ptr, thp); UP(d_th_src, ths); UP(d_th_vi, thv); UP(d_cta_ado, ranges); UP(d_pers_ado, pranges);
     UP(d_h_rptr, rptr); UP(d_h_rcol, rcol); UP(d_h_rvi, rvi);
     UP(d_h_cptr, cptr); UP(d_h_crow, crow); UP(d_h_cvi, cvi);
     UP(d_hval64, to_cx<double>(hval)); UP(d_hval32, to_cx<float>(hval));
@@ -858,6 +874,11 @@ void prof_end(int cls, cudaStream_t s, double units, double bytes) {
     g_prof.units[cls] += units;
     g_prof.bytes[cls] += bytes;
     if (g_prof.pending.size() > 4096) prof_drain();
+}
+void prof_add(int cls, double units, double bytes) {
+    if (!g_prof.on) return;
+    g_prof.units[cls] += units;
+    g_prof.bytes[cls] += bytes;
 }
 }  // namespace heom
 

@@ -109,6 +109,10 @@ struct DevView {
     int range_terms;          // largest program of one range (terms)
     int range_slots;          // largest sum over a range of d2 * (entries + 3)
     int range_ados;           // largest number of ADOs in a range
+    // ADO ranges of the cooperative persistent solvers: one range per SM, programs of the
+    // whole hierarchy resident in shared memory (pers_ranges = 0 when they do not fit)
+    const int32_t *pers_ado;  // [pers_ranges + 1]
+    int pers_ranges, pers_terms, pers_slots, pers_ados;
 };
 
 // Optional modifiers of the apply used by the solvers (all may be null / zero).
@@ -153,14 +157,16 @@ struct heom_hier {
     heom::DBuf d_t_ptr, d_t_src, d_t_val64, d_t_val32, d_th_ptr, d_th_src, d_th_vi;
     std::vector<int> op_terms;              // total terms of operator slot o over all elements
     int h_terms = 0, max_terms = 0, max_entries = 0;
-    heom::DBuf d_cta_ado;
+    heom::DBuf d_cta_ado, d_pers_ado;
     int n_ranges = 0, range_terms = 0, range_slots = 0, range_ados = 0;
+    int pers_ranges = 0, pers_terms = 0, pers_slots = 0, pers_ados = 0;
     // device parameters (per set), both precisions
     heom::DBuf d_hval64, d_hval32, d_coefL64, d_coefL32, d_coefR64, d_coefR32, d_rate64,
         d_rate32, d_hdiag64, d_hdiag32, d_floor64, d_floor32;
     // solver workspace (grown on demand)
     heom::DBuf ws;
     heom::DBuf ws_small;
+    heom::DBuf ws_pers;  // cooperative persistent solver (vectors, block partials)
     heom::DevView<double> view64() const;
     heom::DevView<float> view32() const;
 };
@@ -185,6 +191,7 @@ heom_status ensure_ws(DBuf &b, size_t bytes);
 constexpr int kRangeTerms = 4096;
 constexpr int kRangeSlots = 8192;
 constexpr int kRangeAdos = 64;
+constexpr int kPersistTerms = 6144;  // terms of one persistent range (FP64: 20 B each)
 
 // launch geometry shared by every row x column kernel: block (bx, by), grid (gx, gy)
 struct Geom {
@@ -197,6 +204,7 @@ Geom make_geom(int64_t rows, int64_t B, int max_blocks_x = 0);
 bool prof_on();
 void prof_begin(int cls, cudaStream_t s);
 void prof_end(int cls, cudaStream_t s, double units, double bytes);
+void prof_add(int cls, double units, double bytes);  // work known only after a launch
 struct Prof {
     int cls;
     cudaStream_t s;
@@ -225,6 +233,15 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
                           const std::vector<cx<double>> &shift, const std::vector<int> &col_of,
                           double tol, int mmax, std::vector<cx<double>> &x0,
                           std::vector<double> &res, int *steps, cudaStream_t s);
+
+// cooperative persistent BiCGStab for one column (heom_persist.cu)
+template <class R>
+bool persist_ok(const heom_hier *h);
+template <class R>
+heom_status bicgstab_persistent(heom_hier *h, const cx<R> *b, cx<R> *x, bool x_zero,
+                                const cx<R> *shift, R aug, double tol, int max_iter,
+                                int stall_iters, int *iters, int *status, double *rel_res,
+                                cudaStream_t s);
 
 // one fused RK4 stage over all ADOs and columns (the launch heom_evolve uses)
 template <class R>

@@ -6,14 +6,24 @@
 
 namespace heom {
 
+// BiCGStab restart rule: when |(rh, r)| < tau ||rh|| ||r|| the shadow residual rh has lost
+// its grip on the Krylov space (the Lanczos biorthogonality behind the method has broken
+// down in all but name); the iteration restarts with rh = r, p = r. tau = 1e-10. A sparse
+// right-hand side such as the trace row of the stationary-state system makes the initial
+// rh = b a poor shadow vector, and without the restart the recursion can stagnate.
+constexpr double kRestartTau2 = 1e-20;
+
 // Per-column solver state; every field is FP64 (Krylov scalars, dots, residuals).
 struct ColState {
     cx<double> rho_old, alpha, omega;      // BiCGStab scalars
     cx<double> acc_rv, acc_ts, acc_tt, acc_rr;  // dot-product accumulators
     double acc_nr;                          // ||r||^2 accumulator
     double bnorm2;                          // ||b||^2
+    double rhn;                             // ||rh||^2 of the current shadow residual
     int active;                             // 1 while the column iterates
     int flag;                               // breakdown marker
+    int restart;                            // this iteration restarts (rh = r, p = r)
+    int pad_;
 };
 
 template <class R>

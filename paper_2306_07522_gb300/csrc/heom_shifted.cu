@@ -23,21 +23,26 @@ namespace {
 
 constexpr int kDotThreads = 256;
 
-// h[i][b] = sum_rows conj(V_i[row][b]) w[row][b] for i = 0..nv-1 (one block per i)
-__global__ void __launch_bounds__(kDotThreads) k_multidot(int64_t rows, int64_t B,
+// Partial dot products over a chunk of rows: part[c][i][b] = sum_{rows of chunk c}
+// conj(V_i[row][b]) w[row][b]; grid (i, chunk). Deterministic (no atomics).
+__global__ void __launch_bounds__(kDotThreads) k_multidot(int64_t rows, int64_t B, int nv,
                                                           const cx<double> *__restrict__ V,
                                                           int64_t vstride,
                                                           const cx<double> *__restrict__ w,
-                                                          cx<double> *__restrict__ h) {
-    const int i = blockIdx.x;
+                                                          cx<double> *__restrict__ part) {
+    const int i = blockIdx.x, c = blockIdx.y, nc = gridDim.y;
+    const int64_t L = rows * B;
+    const int64_t t0 = L * c / nc, t1 = L * (c + 1) / nc;
     const cx<double> *Vi = V + (int64_t)i * vstride;
     __shared__ double sre[kDotThreads], sim[kDotThreads];
     for (int64_t b = 0; b < B; ++b) {
         double re = 0.0, im = 0.0;
-        for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) {
-            const cx<double> a = Vi[r * B + b], c = w[r * B + b];
-            re += a.re * c.re + a.im * c.im;
-            im += a.re * c.im - a.im * c.re;
+        // elements t of column b inside [t0, t1): t = row * B + b
+        int64_t tb = t0 + ((b - t0 % B) + B) % B;
+        for (int64_t t = tb + (int64_t)threadIdx.x * B; t < t1; t += (int64_t)blockDim.x * B) {
+            const cx<double> a = Vi[t], x = w[t];
+            re += a.re * x.re + a.im * x.im;
+            im += a.re * x.im - a.im * x.re;
         }
         sre[threadIdx.x] = re;
         sim[threadIdx.x] = im;
@@ -49,8 +54,23 @@ __global__ void __launch_bounds__(kDotThreads) k_multidot(int64_t rows, int64_t 
             }
             __syncthreads();
         }
-        if (threadIdx.x == 0) h[(int64_t)i * B + b] = cx<double>{sre[0], sim[0]};
+        if (threadIdx.x == 0) part[((int64_t)c * nv + i) * B + b] = cx<double>{sre[0], sim[0]};
         __syncthreads();
+    }
+}
+
+// h[i][b] = sum_c part[c][i][b]; Hb[i][j][b] += h[i][b] (column j of the Hessenberg matrix
+// accumulates both Gram-Schmidt passes)
+__global__ void k_reduce_h(int nc, int nv, int64_t B, const cx<double> *__restrict__ part,
+                           cx<double> *__restrict__ h, cx<double> *__restrict__ Hb, int j, int mmax) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)nv * B;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        cx<double> acc{0.0, 0.0};
+        for (int c = 0; c < nc; ++c) acc = acc + part[(int64_t)c * nv * B + t];
+        h[t] = acc;
+        const int64_t i = t / B, b = t - i * B;
+        cx<double> &e = Hb[(i * mmax + j) * B + b];
+        e = e + acc;
     }
 }
 
@@ -70,17 +90,6 @@ __global__ void k_gs_update(int64_t rows, int64_t B, int nv, const cx<double> *_
             acc.im -= vi.re * hi.im + vi.im * hi.re;
         }
         w[t] = acc;
-    }
-}
-
-// Hb[i][j][b] += h[i][b] for i < nv (column j of the Hessenberg matrix, both CGS passes)
-__global__ void k_acc_col(cx<double> *__restrict__ Hb, int j, int mmax, int64_t B, int nv,
-                          const cx<double> *__restrict__ h) {
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)nv * B;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = t / B, b = t - i * B;
-        cx<double> &e = Hb[(i * mmax + j) * B + b];
-        e = e + h[t];
     }
 }
 
@@ -243,6 +252,9 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
                  oy = take((size_t)S * mmax * 16), ocb = take((size_t)S * (mmax + 1) * 16),
                  ox0 = take((size_t)S * d2 * 16), ores = take((size_t)S * 8),
                  osh = take((size_t)S * 16), oco = take((size_t)S * 4);
+    // row chunks of the partial dot products: enough blocks to fill the GPU at small j
+    const int nchunk = (int)std::max<int64_t>(1, std::min<int64_t>(64, L / 4096));
+    const size_t opart = take((size_t)nchunk * (mmax + 1) * B * 16);
     heom_status st = ensure_ws(h->ws, off);
     if (st != HEOM_OK) return st;
     char *base = (char *)h->ws.p;
@@ -256,6 +268,7 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
                *dsh = (cx<double> *)(base + osh);
     double *dres = (double *)(base + ores);
     int *dco = (int *)(base + oco);
+    cx<double> *part = (cx<double> *)(base + opart);
     HEOM_CUDA(memcpy_counted(dsh, shift.data(), S * 16, cudaMemcpyHostToDevice, s));
     HEOM_CUDA(memcpy_counted(dco, col_of.data(), S * 4, cudaMemcpyHostToDevice, s));
     HEOM_CUDA(cudaMemsetAsync(Hb, 0, (size_t)(mmax + 1) * mmax * B * 16, s));
@@ -297,10 +310,10 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
         {   // classical Gram-Schmidt, twice; Hb[:, j] accumulates both passes
             Prof pr(HEOM_KC_KRYLOV_VECTOR, s, (double)(j + 1) * L, 2.0 * (2.0 * (j + 1) + 2.0) * L * 16);
             for (int pass = 0; pass < 2; ++pass) {
-                k_multidot<<<(unsigned)(j + 1), kDotThreads, 0, s>>>(rows, B, V, L, w, ht);
-                // column j of Hb is rows 0..j at stride mmax*B: accumulate via a strided view
+                k_multidot<<<dim3((unsigned)(j + 1), (unsigned)nchunk), kDotThreads, 0, s>>>(
+                    rows, B, j + 1, V, L, w, part);
+                k_reduce_h<<<blocks_for((int64_t)(j + 1) * B), 256, 0, s>>>(nchunk, j + 1, B, part, ht, Hb, j, mmax);
                 k_gs_update<<<blocks_for(L), 256, 0, s>>>(rows, B, j + 1, V, L, ht, w);
-                k_acc_col<<<blocks_for((int64_t)(j + 1) * B), 256, 0, s>>>(Hb, j, mmax, B, j + 1, ht);
             }
         }
         {   // h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j}

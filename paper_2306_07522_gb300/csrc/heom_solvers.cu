@@ -158,14 +158,19 @@ struct ColScalars {
     cx<R> a, b;      // two working-precision scalars of the kernel
     cx<double> keep; // an FP64 value to store back
     int on;          // column active
+    int rs;          // restart this iteration (rh = r, p = r)
 };
 
-// p = r + beta (p - omega v), ph = P^-1 p, beta = (rho / rho_old)(alpha / omega)
+// p = r + beta (p - omega v), ph = P^-1 p, beta = (rho / rho_old)(alpha / omega); or, when
+// the restart rule fires (rho small against ||rh|| ||r||), rh = r and p = r. The decision is
+// taken from fields no kernel writes between here and k_bicg_s, which reads it back from
+// st.restart.
 template <class R>
 __global__ void __launch_bounds__(256) k_bicg_p(DevView<R> v, const cx<R> *__restrict__ r,
                                                 cx<R> *p, const cx<R> *__restrict__ vv,
-                                                cx<R> *__restrict__ ph, int64_t B, int64_t cps,
-                                                const cx<R> *shift, int precond, ColState *st) {
+                                                cx<R> *__restrict__ ph, cx<R> *rh, int64_t B,
+                                                int64_t cps, const cx<R> *shift, int precond,
+                                                ColState *st) {
     COLUMN_PROLOGUE
     __shared__ ColScalars<R> sc[32];
     if (threadIdx.y == 0) {
@@ -173,6 +178,7 @@ __global__ void __launch_bounds__(256) k_bicg_p(DevView<R> v, const cx<R> *__res
         c.on = inb && st[b].active;
         if (c.on) {
             const ColState cs = st[b];
+            c.rs = norm2(cs.acc_rr) < kRestartTau2 * cs.rhn * cs.acc_nr;
             c.a = cast<R>(cdiv(cs.acc_rr, cs.rho_old) * cdiv(cs.alpha, cs.omega));  // beta
             c.b = cast<R>(cs.omega);
         }
@@ -182,10 +188,13 @@ __global__ void __launch_bounds__(256) k_bicg_p(DevView<R> v, const cx<R> *__res
     const ColScalars<R> c = sc[threadIdx.x];
     if (!c.on) return;
     const cx<R> bt = c.a, om = c.b;
+    const bool rs = c.rs != 0;
     const cx<R> shv = shift ? shift[b] : cx<R>{R(0), R(0)};
     ROW_LOOP {
         const int64_t i = row * B + b;
-        const cx<R> pi = r[i] + bt * (p[i] - om * vv[i]);
+        const cx<R> ri = r[i];
+        const cx<R> pi = rs ? ri : ri + bt * (p[i] - om * vv[i]);
+        if (rs) rh[i] = ri;
         p[i] = pi;
         if (precond) {
             const int64_t n = row / v.d2;
@@ -195,7 +204,10 @@ __global__ void __launch_bounds__(256) k_bicg_p(DevView<R> v, const cx<R> *__res
             ph[i] = pi;
         }
     }
-    if (designated()) st[b].acc_rv = {0.0, 0.0};
+    if (designated()) {
+        st[b].acc_rv = {0.0, 0.0};
+        st[b].restart = rs;
+    }
 }
 
 // out = A in (apply with shift / trace augmentation), plus FP64 dots against two vectors:
@@ -263,7 +275,9 @@ __global__ void __launch_bounds__(256) k_bicg_s(DevView<R> v, cx<R> *r, const cx
         if (c.on) {
             const ColState cs = st[b];
             const bool bad = norm2(cs.acc_rv) == 0.0;
-            c.keep = bad ? cx<double>{0.0, 0.0} : cdiv(cs.acc_rr, cs.acc_rv);  // alpha
+            const cx<double> rho = cs.restart ? cx<double>{cs.acc_nr, 0.0} : cs.acc_rr;
+            c.keep = bad ? cx<double>{0.0, 0.0} : cdiv(rho, cs.acc_rv);  // alpha
+            c.rs = cs.restart;
             c.a = cast<R>(c.keep);
             c.b = cx<R>{bad ? R(1) : R(0), R(0)};
         }
@@ -287,7 +301,8 @@ __global__ void __launch_bounds__(256) k_bicg_s(DevView<R> v, cx<R> *r, const cx
         }
     }
     if (designated()) {
-        const cx<double> rr = st[b].acc_rr;
+        const cx<double> rr = c.rs ? cx<double>{st[b].acc_nr, 0.0} : st[b].acc_rr;
+        if (c.rs) st[b].rhn = st[b].acc_nr;
         st[b].alpha = c.keep;
         st[b].rho_old = rr;
         st[b].acc_ts = {0.0, 0.0};
@@ -586,6 +601,7 @@ heom_status bicgstab(heom_hier *h, const cx<R> *bvec, cx<R> *x, int64_t B, const
     HEOM_CUDA(cudaStreamSynchronize(s));
     int n_act = 0;
     for (int64_t j = 0; j < Bc; ++j) {
+        hs[j].rhn = hs[j].acc_nr;  // rh = r0
         if (!alive[j]) continue;
         const int b = cols[j];
         out.res[b] = hs[j].bnorm2 > 0 ? std::sqrt(hs[j].acc_nr / hs[j].bnorm2) : 0.0;
@@ -661,7 +677,7 @@ heom_status bicgstab(heom_hier *h, const cx<R> *bvec, cx<R> *x, int64_t B, const
         const double sz = sizeof(cx<R>), e_vec = u_vec * sz;
         for (int k = 0; k < steps; ++k) {
             { Prof pr(HEOM_KC_KRYLOV_VECTOR, s, u_vec, 5.0 * e_vec);
-              k_bicg_p<R><<<gv.grid, gv.block, 0, s>>>(v, r, p, vv, ph, Bc, cps, shc, 1, st); }
+              k_bicg_p<R><<<gv.grid, gv.block, 0, s>>>(v, r, p, vv, ph, rh, Bc, cps, shc, 1, st); }
             { Prof pr(kc_apply, s, u_app, 3.0 * e_vec);
               if (tiled) { ta.x = ph; ta.out = vv; ta.w = rh; HEOM_CUDA((launch_tile<R, TM_BICG_V>(ta, s))); }
               else k_bicg_apply<R><<<gd.grid, gd.block, 0, s>>>(v, ph, vv, rh, Bc, cps, mods, 0, st); }
@@ -821,8 +837,18 @@ heom_status refine_solve(heom_hier *h, const cx<double> *b64, cx<double> *x64, i
         const double inner_tol = plain ? std::max(0.5 * tol / worst, 1e-10) : 1e-4;
         inner_max = std::min(inner_max, plain ? kInnerCap64 : kInnerCap);
         SolveOut o;
-        stt = bicgstab<RI>(h, rhs, dv, B, shift64 ? shift_in : nullptr, (RI)aug, true, inner_tol,
-                           inner_max, active, w, st, d_map, d_lmap, shift_c, o, s);
+        if (B == 1 && persist_ok<RI>(h)) {
+            // one column: the whole BiCGStab solve is one cooperative launch
+            o.iters.assign(1, 0);
+            o.status.assign(1, HEOM_OK);
+            o.res.assign(1, 0.0);
+            stt = bicgstab_persistent<RI>(h, rhs, dv, true, shift64 ? shift_in : nullptr, (RI)aug,
+                                          inner_tol, inner_max, kStallIters, &o.iters[0],
+                                          &o.status[0], &o.res[0], s);
+        } else {
+            stt = bicgstab<RI>(h, rhs, dv, B, shift64 ? shift_in : nullptr, (RI)aug, true, inner_tol,
+                               inner_max, active, w, st, d_map, d_lmap, shift_c, o, s);
+        }
         if (stt != HEOM_OK) return stt;
         bool skip_any = false;
         for (int64_t b = 0; b < B; ++b) {

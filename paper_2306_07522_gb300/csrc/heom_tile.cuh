@@ -59,54 +59,56 @@ struct TileArgs {
     int set;             // parameter set (every column of this launch uses it)
 };
 
-// Shared-memory footprint of one CTA (one ADO range) for a hierarchy view.
+// Shared-memory layout of the term programs of one ADO range (see build_programs).
 template <class R>
-__host__ __device__ inline size_t tile_smem_bytes(const DevView<R> &v) {
-    const size_t pairs = (size_t)v.range_slots / (size_t)v.d2 + 1;   // (ADO, entry) pairs
-    const size_t items = (size_t)v.range_ados * v.d2 + 1;            // (ADO, element) items
-    const size_t cw = 32 * VecT<R>::VC;
-    return ((size_t)v.range_terms + 2 * pairs) * sizeof(cx<R>) +      // coefficients, cl, cr
-           kTileWarps * cw * 3 * sizeof(double) +                     // per-warp dot partials
-           ((size_t)v.range_terms + (size_t)v.range_slots + items + 2 * pairs +
-            (size_t)v.range_ados + 2 + kTileWarps * 32) * sizeof(int32_t) + 64;
+struct ProgSmem {
+    cx<R> *coef, *cl, *cr;
+    int32_t *src, *off, *item, *nb, *op, *pb, *scan;
+};
+
+template <class R>
+__host__ __device__ inline size_t prog_smem_bytes(int terms, int slots, int ados, int d2) {
+    const size_t pairs = (size_t)slots / (size_t)d2 + 1, items = (size_t)ados * d2 + 1;
+    return ((size_t)terms + 2 * pairs) * sizeof(cx<R>) +
+           ((size_t)terms + (size_t)slots + items + 2 * pairs + (size_t)ados + 2 + 1024) *
+               sizeof(int32_t) + 32;
 }
 
-// One CTA per ADO range (persistent: all ranges resident at once). The CTA builds the term
-// programs of its ADOs in shared memory once per launch, then sweeps the batch columns in
-// chunks of 32 x VC; every CTA sweeps the chunks in the same order, so the data in use at
-// any moment is one column chunk of every ADO (about 19 MB per vector for 2,325 ADOs of
-// 4 x 4 FP32 blocks), which L2 holds while the neighbours re-read it.
-//
-// Program layout: triples (ADO p, element e, entry t) in that order, entry t = 0 damping,
-// t = 1 system commutator, t = 2 .. E_p + 1 neighbour entries, t = E_p + 2 trace row (ADO 0
-// of the steady-state system only); an exclusive scan of their term counts gives every
-// term's slot, so each (p, e) item's terms are contiguous and in the apply_point order.
-template <class R, int MODE>
-__global__ void __launch_bounds__(kTileWarps * 32, 5) k_tile(TileArgs<R> a) {
-    constexpr int VC = VecT<R>::VC;
-    constexpr int CW = 32 * VC;
-    const DevView<R> &v = a.v;
-    const int d = v.d, d2 = v.d2, set = a.set;
+template <class R>
+__device__ inline ProgSmem<R> prog_layout(int terms, int slots, int ados, int d2,
+                                          unsigned char *base) {
+    ProgSmem<R> s;
+    const int pairs = slots / d2 + 1, items = ados * d2 + 1;
+    s.coef = reinterpret_cast<cx<R> *>(base);  // [terms]
+    s.cl = s.coef + terms;                       // [pairs]
+    s.cr = s.cl + pairs;                         // [pairs]
+    s.src = reinterpret_cast<int32_t *>(s.cr + pairs);  // [terms]
+    s.off = s.src + terms;                       // [triples]
+    s.item = s.off + slots;                      // [items] program start of (p, e)
+    s.nb = s.item + items;                       // [pairs]
+    s.op = s.nb + pairs;                         // [pairs] op slot / -1 H / -2 trace / -3 damping
+    s.pb = s.op + pairs;                         // [ados + 2] first pair of ADO p
+    s.scan = s.pb + ados + 2;                    // [<= 1024 threads] scan scratch
+    return s;
+}
+
+// Build, in shared memory, the term programs of ADOs n0 .. n1-1 (all threads of the block
+// take part; blockDim.x a multiple of 32, at most 1024). Program layout: triples (ADO p,
+// element e, entry t) in that order, entry t = 0 damping, t = 1 system commutator,
+// t = 2 .. E_p + 1 neighbour entries, t = E_p + 2 trace row (ADO 0 of the steady-state
+// system only); an exclusive scan of their term counts gives every term's slot, so each
+// (p, e) item's terms are contiguous and in the apply_point order. Item i = p * d2 + e
+// holds terms item[i] .. item[i+1]-1 as (source element src, coefficient coef).
+template <class R>
+__device__ void build_programs(const DevView<R> &v, ProgSmem<R> &ps, int n0, int n1, R aug,
+                               int set) {
+    const int d = v.d, d2 = v.d2;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tid = threadIdx.x;
-    const int64_t B = a.B;
-    const int n0 = __ldg(v.cta_ado + blockIdx.x), n1 = __ldg(v.cta_ado + blockIdx.x + 1);
+    const int nwarps = blockDim.x >> 5;
     const int P = n1 - n0;
-
-    const int pairs_max = v.range_slots / d2 + 1;
-    const int items_max = v.range_ados * d2 + 1;
-    extern __shared__ __align__(16) unsigned char smem[];
-    cx<R> *s_coef = reinterpret_cast<cx<R> *>(smem);      // [range_terms]
-    cx<R> *s_cl = s_coef + v.range_terms;                  // [pairs]
-    cx<R> *s_cr = s_cl + pairs_max;                        // [pairs]
-    double *s_red = reinterpret_cast<double *>(s_cr + pairs_max);  // [warps][CW][3]
-    int32_t *s_src = reinterpret_cast<int32_t *>(s_red + kTileWarps * CW * 3);
-    int32_t *s_off = s_src + v.range_terms;                // [triples]
-    int32_t *s_item = s_off + v.range_slots;               // [items + 1] program start of (p, e)
-    int32_t *s_nb = s_item + items_max;                    // [pairs]
-    int32_t *s_op = s_nb + pairs_max;                      // [pairs] op slot / -1 H / -2 trace / -3 damping
-    int32_t *s_pb = s_op + pairs_max;                      // [P + 1] first pair of ADO p
-    int32_t *s_scan = s_pb + v.range_ados + 2;             // [threads] scan scratch
-
+    cx<R> *s_coef = ps.coef, *s_cl = ps.cl, *s_cr = ps.cr;
+    int32_t *s_src = ps.src, *s_off = ps.off, *s_item = ps.item, *s_nb = ps.nb, *s_op = ps.op,
+            *s_pb = ps.pb, *s_scan = ps.scan;
     // ---------------- pair bases (entries + 3 per ADO): warp 0 scans the ranges' ADOs
     if (warp == 0) {
         int carry = 0;
@@ -166,7 +168,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, 5) k_tile(TileArgs<R> a) {
         } else {
             op = -2;  // trace row of the steady-state system
             nb = 0;
-            cl = cx<R>{a.aug, R(0)};
+            cl = cx<R>{aug, R(0)};
         }
         s_nb[q] = nb;
         s_op[q] = op;
@@ -185,7 +187,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, 5) k_tile(TileArgs<R> a) {
         if (op >= 0) len = __ldg(v.t_ptr + op * d2 + e + 1) - __ldg(v.t_ptr + op * d2 + e);
         else if (op == -1) len = __ldg(v.th_ptr + e + 1) - __ldg(v.th_ptr + e);
         else if (op == -3) len = 1;
-        else len = (e == 0 && n0 + p == 0 && a.aug != R(0)) ? d : 0;
+        else len = (e == 0 && n0 + p == 0 && aug != R(0)) ? d : 0;
         s_off[z] = len;
     }
     __syncthreads();
@@ -206,7 +208,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, 5) k_tile(TileArgs<R> a) {
         __syncthreads();
         if (tid == 0) {
             int run = 0;
-            for (int w = 0; w < kTileWarps; ++w) {
+            for (int w = 0; w < nwarps; ++w) {
                 const int tmp = s_scan[w];
                 s_scan[w] = run;
                 run += tmp;
@@ -254,7 +256,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, 5) k_tile(TileArgs<R> a) {
             const cx<R> dmp = damping_of(v, (int64_t)(n0 + p), set);
             s_src[pos] = (n0 + p) * d2 + e;
             s_coef[pos] = cx<R>{-dmp.re, -dmp.im};
-        } else if (e == 0 && n0 + p == 0 && a.aug != R(0)) {
+        } else if (e == 0 && n0 + p == 0 && aug != R(0)) {
             for (int i = 0; i < d; ++i, ++pos) {
                 s_src[pos] = i * d + i;
                 s_coef[pos] = s_cl[q];
@@ -262,6 +264,47 @@ __global__ void __launch_bounds__(kTileWarps * 32, 5) k_tile(TileArgs<R> a) {
         }
     }
     __syncthreads();
+
+}
+
+// Shared-memory footprint of one CTA (one ADO range) for a hierarchy view.
+template <class R>
+__host__ __device__ inline size_t tile_smem_bytes(const DevView<R> &v) {
+    const size_t cw = 32 * VecT<R>::VC;
+    return kTileWarps * cw * 3 * sizeof(double) +  // per-warp dot partials
+           prog_smem_bytes<R>(v.range_terms, v.range_slots, v.range_ados, v.d2);
+}
+
+// One CTA per ADO range (persistent: all ranges resident at once). The CTA builds the term
+// programs of its ADOs in shared memory once per launch, then sweeps the batch columns in
+// chunks of 32 x VC; every CTA sweeps the chunks in the same order, so the data in use at
+// any moment is one column chunk of every ADO (about 19 MB per vector for 2,325 ADOs of
+// 4 x 4 FP32 blocks), which L2 holds while the neighbours re-read it.
+//
+// Program layout: triples (ADO p, element e, entry t) in that order, entry t = 0 damping,
+// t = 1 system commutator, t = 2 .. E_p + 1 neighbour entries, t = E_p + 2 trace row (ADO 0
+// of the steady-state system only); an exclusive scan of their term counts gives every
+// term's slot, so each (p, e) item's terms are contiguous and in the apply_point order.
+template <class R, int MODE>
+__global__ void __launch_bounds__(kTileWarps * 32, 5) k_tile(TileArgs<R> a) {
+    constexpr int VC = VecT<R>::VC;
+    constexpr int CW = 32 * VC;
+    const DevView<R> &v = a.v;
+    const int d = v.d, d2 = v.d2, set = a.set;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tid = threadIdx.x;
+    const int64_t B = a.B;
+    const int n0 = __ldg(v.cta_ado + blockIdx.x), n1 = __ldg(v.cta_ado + blockIdx.x + 1);
+    const int P = n1 - n0;
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    double *s_red = reinterpret_cast<double *>(smem);  // [warps][CW][3] per-warp dot partials
+    ProgSmem<R> ps = prog_layout<R>(v.range_terms, v.range_slots, v.range_ados, d2,
+                                    smem + (size_t)kTileWarps * CW * 3 * sizeof(double));
+    build_programs<R>(v, ps, n0, n1, a.aug, set);
+    const int32_t *s_item = ps.item;
+    const int32_t *s_src = ps.src;
+    const cx<R> *s_coef = ps.coef;
+    (void)lane;
 
     // ---------------- sweep the column chunks
     const cx<R> *__restrict__ X = a.x;
