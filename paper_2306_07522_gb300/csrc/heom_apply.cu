@@ -55,7 +55,6 @@ __global__ void __launch_bounds__(256) k_apply(DevView<R> v, const cx<R> *__rest
 template <class R>
 cudaError_t launch_apply(const DevView<R> &v, const cx<R> *x, cx<R> *y, int64_t B,
                          const ApplyMods<R> &mods, cudaStream_t s) {
-    Prof pr(HEOM_KC_APPLY, s, (double)v.N * B, 2.0 * v.N * B * v.d2 * sizeof(cx<R>));
     if (tile_ok(v, B)) {
         TileArgs<R> a{};
         a.v = v;
@@ -100,6 +99,9 @@ extern "C" heom_status heom_apply(const heom_hier *h, const void *x, void *y, in
     }
     HEOM_CUDA(cudaSetDevice(h->device));
     cudaError_t e;
+    // accounted here, not in launch_apply: the solvers that call launch_apply account the
+    // launch under their own kernel class
+    heom::Prof pr(HEOM_KC_APPLY, (cudaStream_t)s, (double)h->N * batch, 2.0 * bytes);
     if (prec == HEOM_FP64) {
         heom::ApplyMods<double> m{nullptr, 0.0};
         e = heom::launch_apply(h->view64(), (const heom::cx<double> *)x, (heom::cx<double> *)y,

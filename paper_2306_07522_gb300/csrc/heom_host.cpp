@@ -866,11 +866,11 @@ void prof_begin(int cls, cudaStream_t s) {
     g_prof.open_ev = prof_event();
     cudaEventRecord(g_prof.open_ev, s);
 }
-void prof_end(int cls, cudaStream_t s, double units, double bytes) {
+void prof_end(int cls, cudaStream_t s, double units, double bytes, int kernels) {
     cudaEvent_t e = prof_event();
     cudaEventRecord(e, s);
     g_prof.pending.push_back({cls, g_prof.open_ev, e, units});
-    g_prof.launches[cls] += 1;
+    g_prof.launches[cls] += kernels;
     g_prof.units[cls] += units;
     g_prof.bytes[cls] += bytes;
     if (g_prof.pending.size() > 4096) prof_drain();

@@ -203,19 +203,22 @@ Geom make_geom(int64_t rows, int64_t B, int max_blocks_x = 0);
 // launch accounting: RAII bracket of one kernel launch (see heom_profile_enable)
 bool prof_on();
 void prof_begin(int cls, cudaStream_t s);
-void prof_end(int cls, cudaStream_t s, double units, double bytes);
+void prof_end(int cls, cudaStream_t s, double units, double bytes, int kernels);
 void prof_add(int cls, double units, double bytes);  // work known only after a launch
+// The bracket covers `kernels` kernel launches of the library (default one); the device
+// time between its two events is charged to class cls.
 struct Prof {
     int cls;
     cudaStream_t s;
     double units, bytes;
     bool on;
+    int kernels = 1;
     Prof(int c, cudaStream_t st, double u, double by = 0.0)
         : cls(c), s(st), units(u), bytes(by), on(prof_on()) {
         if (on) prof_begin(cls, s);
     }
     ~Prof() {
-        if (on) prof_end(cls, s, units, bytes);
+        if (on) prof_end(cls, s, units, bytes, kernels);
     }
 };
 

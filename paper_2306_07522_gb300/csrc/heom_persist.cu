@@ -80,8 +80,9 @@ __device__ __forceinline__ cx<R> prog_apply(const ProgSmem<R> &ps, int it, const
     return acc;
 }
 
-// Grid-wide sum of NV doubles: block sums to part[slot][block], grid barrier, then every
-// block adds the per-block values in block order into s_tot.
+// Grid-wide sum of NV doubles: block sums to part[slot][block], grid barrier, then in every
+// block warp k adds value k over all blocks (lane-strided loads through L2, then a fixed
+// shuffle tree; lane 0's result is used), so every block derives bit-identical totals.
 template <int NV>
 __device__ __forceinline__ void grid_sum(double (&val)[NV], double *part, int slot, double *s_red,
                                          double *s_tot, cg::grid_group &grid) {
@@ -100,12 +101,15 @@ __device__ __forceinline__ void grid_sum(double (&val)[NV], double *part, int sl
         part[((size_t)slot * gridDim.x + blockIdx.x) * 4 + threadIdx.x] = x;
     }
     grid.sync();
-    if (threadIdx.x < NV) {
-        double x = 0.0;
+    if (warp < NV) {
         // written by the other CTAs since this CTA last read the slot: through L2, so that
-        // no line of the previous iteration cached in L1 is reused
-        for (unsigned g = 0; g < gridDim.x; ++g) x += __ldcg(part + ((size_t)slot * gridDim.x + g) * 4 + threadIdx.x);
-        s_tot[threadIdx.x] = x;
+        // no line of an earlier iteration cached in L1 is reused
+        double x = 0.0;
+        for (unsigned g = lane; g < gridDim.x; g += 32)
+            x += __ldcg(part + ((size_t)slot * gridDim.x + g) * 4 + warp);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) s_tot[warp] = x;
     }
     __syncthreads();
 #pragma unroll

@@ -1,7 +1,7 @@
 // Shift-invariant Krylov solves for spectra (Methods, numerical computation of the
 // spectrum): every frequency w of a density of states solves (M -+ i w) x = b with the same
 // M and the same b, so all of them live in one Krylov space K_m(M, b). One FP64 Arnoldi
-// process (classical Gram-Schmidt, reorthogonalised once) builds an orthonormal basis V and
+// process (classical Gram-Schmidt, reorthogonalised when one pass loses too much) builds an orthonormal basis V and
 // the Hessenberg matrix Hb with M V_m = V_{m+1} Hb_m; for each shift s the least-squares
 // problem min || beta e_1 - (Hb_m + s I~) y || gives x_s = V_m y_s and its residual norm
 // (GMRES on the shifted system; the shift leaves the basis unchanged). Only the tier-0 block
@@ -24,17 +24,44 @@ namespace {
 constexpr int kDotThreads = 256;
 
 // Partial dot products over a chunk of rows: part[c][i][b] = sum_{rows of chunk c}
-// conj(V_i[row][b]) w[row][b]; grid (i, chunk). Deterministic (no atomics).
+// conj(V_i[row][b]) w[row][b]; grid (i, chunk). Deterministic (no atomics). When B is a
+// power of two dividing the block size every thread keeps one column and the chunk is read
+// once for all columns; otherwise one sweep per column.
 __global__ void __launch_bounds__(kDotThreads) k_multidot(int64_t rows, int64_t B, int nv,
                                                           const cx<double> *__restrict__ V,
                                                           int64_t vstride,
                                                           const cx<double> *__restrict__ w,
-                                                          cx<double> *__restrict__ part) {
+                                                          cx<double> *__restrict__ part,
+                                                          const int *__restrict__ skip) {
+    if (skip && *skip) return;
     const int i = blockIdx.x, c = blockIdx.y, nc = gridDim.y;
     const int64_t L = rows * B;
     const int64_t t0 = L * c / nc, t1 = L * (c + 1) / nc;
     const cx<double> *Vi = V + (int64_t)i * vstride;
     __shared__ double sre[kDotThreads], sim[kDotThreads];
+    if (B <= kDotThreads && (kDotThreads % B) == 0) {
+        // t0 rounded down to a multiple of B keeps column b = threadIdx.x % B for every t
+        const int64_t tb = t0 - t0 % B;
+        double re = 0.0, im = 0.0;
+        for (int64_t t = tb + threadIdx.x; t < t1; t += kDotThreads) {
+            if (t < t0) continue;
+            const cx<double> a = Vi[t], x = w[t];
+            re += a.re * x.re + a.im * x.im;
+            im += a.re * x.im - a.im * x.re;
+        }
+        sre[threadIdx.x] = re;
+        sim[threadIdx.x] = im;
+        __syncthreads();
+        for (int s = kDotThreads >> 1; s >= B; s >>= 1) {
+            if (threadIdx.x < s) {
+                sre[threadIdx.x] += sre[threadIdx.x + s];
+                sim[threadIdx.x] += sim[threadIdx.x + s];
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x < B) part[((int64_t)c * nv + i) * B + threadIdx.x] = cx<double>{sre[threadIdx.x], sim[threadIdx.x]};
+        return;
+    }
     for (int64_t b = 0; b < B; ++b) {
         double re = 0.0, im = 0.0;
         // elements t of column b inside [t0, t1): t = row * B + b
@@ -59,25 +86,190 @@ __global__ void __launch_bounds__(kDotThreads) k_multidot(int64_t rows, int64_t 
     }
 }
 
-// h[i][b] = sum_c part[c][i][b]; Hb[i][j][b] += h[i][b] (column j of the Hessenberg matrix
-// accumulates both Gram-Schmidt passes)
-__global__ void k_reduce_h(int nc, int nv, int64_t B, const cx<double> *__restrict__ part,
-                           cx<double> *__restrict__ h, cx<double> *__restrict__ Hb, int j, int mmax) {
+// ---------------------------------------------------------------- float-float arithmetic
+// GB300 issues FP64 at 1/64 of its FP32 rate, and the Gram-Schmidt loops are nothing but
+// complex multiply-adds. They run in float-float instead: a value is an unevaluated sum
+// hi + lo of two FP32 numbers (about 48 significant bits, unit roundoff 2^-48 ~ 3.6e-15),
+// products by the FMA-based exact product of Dekker/Kahan (p = a*b, e = fma(a, b, -p)),
+// sums by Knuth's two-sum. A complex value is a float4 {hi.re, hi.im, lo.re, lo.im}.
+// Per-thread results are turned back into FP64 before any block or grid reduction.
+__device__ __forceinline__ float4 ff_split(cx<double> a) {
+    const float hr = __double2float_rn(a.re), hi = __double2float_rn(a.im);
+    return make_float4(hr, hi, __double2float_rn(a.re - (double)hr), __double2float_rn(a.im - (double)hi));
+}
+__device__ __forceinline__ cx<double> ff_join(float4 f) {
+    return cx<double>{(double)f.x + (double)f.z, (double)f.y + (double)f.w};
+}
+// (sh, sl) += (ah + al)(bh + bl), dropping al*bl (2^-48 relative)
+__device__ __forceinline__ void ff_mac(float &sh, float &sl, float ah, float al, float bh, float bl) {
+    const float p = ah * bh;
+    float e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, e);
+    e = fmaf(al, bh, e);
+    const float s = sh + p;
+    const float bb = s - sh;
+    const float t = (sh - (s - bb)) + (p - bb);
+    sh = s;
+    sl += t + e;
+}
+// normalise (sh, sl) so that |sl| <= ulp(sh) / 2
+__device__ __forceinline__ void ff_norm(float &sh, float &sl) {
+    const float s = sh + sl;
+    sl = sl - (s - sh);
+    sh = s;
+}
+
+// wf[t] = split(w[t])
+__global__ void k_split(int64_t total, const cx<double> *__restrict__ w, float4 *__restrict__ wf) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x)
+        wf[t] = ff_split(w[t]);
+}
+
+// Float-float partial dot products over a chunk of rows: part[c][i][b] = sum_{rows of chunk
+// c} conj(V_i[row][b]) w[row][b] (FP64 result); grid (i, chunk). B must be a power of two
+// dividing the block (checked by the caller), so every thread keeps one column.
+__global__ void __launch_bounds__(kDotThreads) k_multidot_ff(int64_t rows, int64_t B, int nv,
+                                                             const float4 *__restrict__ Vf,
+                                                             int64_t vstride,
+                                                             const float4 *__restrict__ wf,
+                                                             cx<double> *__restrict__ part,
+                                                             const int *__restrict__ skip) {
+    if (skip && *skip) return;
+    const int i = blockIdx.x, c = blockIdx.y, nc = gridDim.y;
+    const int64_t L = rows * B;
+    const int64_t t0 = L * c / nc, t1 = L * (c + 1) / nc;
+    const float4 *Vi = Vf + (int64_t)i * vstride;
+    __shared__ double sre[kDotThreads], sim[kDotThreads];
+    const int64_t tb = t0 - t0 % B;
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    for (int64_t t = tb + threadIdx.x; t < t1; t += kDotThreads) {
+        if (t < t0) continue;
+        const float4 a = Vi[t], x = wf[t];
+        // conj(a) x: re = a.re x.re + a.im x.im, im = a.re x.im - a.im x.re
+        ff_mac(rh, rl, a.x, a.z, x.x, x.z);
+        ff_mac(rh, rl, a.y, a.w, x.y, x.w);
+        ff_mac(ih, il, a.x, a.z, x.y, x.w);
+        ff_mac(ih, il, -a.y, -a.w, x.x, x.z);
+    }
+    sre[threadIdx.x] = (double)rh + (double)rl;
+    sim[threadIdx.x] = (double)ih + (double)il;
+    __syncthreads();
+    for (int s = kDotThreads >> 1; s >= B; s >>= 1) {
+        if (threadIdx.x < s) {
+            sre[threadIdx.x] += sre[threadIdx.x + s];
+            sim[threadIdx.x] += sim[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < B) part[((int64_t)c * nv + i) * B + threadIdx.x] = cx<double>{sre[threadIdx.x], sim[threadIdx.x]};
+}
+
+// wf[row][b] -= sum_i V_i[row][b] h_i[b] in float-float (hf = split h)
+__global__ void k_gs_update_ff(int64_t rows, int64_t B, int nv, const float4 *__restrict__ Vf,
+                               int64_t vstride, const float4 *__restrict__ hf,
+                               float4 *__restrict__ wf, const int *__restrict__ skip) {
+    if (skip && *skip) return;
+    const int64_t total = rows * B;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = t % B;
+        const float4 w0 = wf[t];
+        float rh = w0.x, rl = w0.z, ih = w0.y, il = w0.w;
+        for (int i = 0; i < nv; ++i) {
+            const float4 h = hf[(int64_t)i * B + b];
+            const float4 v = Vf[(int64_t)i * vstride + t];
+            // -= v h: re -= v.re h.re - v.im h.im, im -= v.re h.im + v.im h.re
+            ff_mac(rh, rl, -v.x, -v.z, h.x, h.z);
+            ff_mac(rh, rl, v.y, v.w, h.y, h.w);
+            ff_mac(ih, il, -v.x, -v.z, h.y, h.w);
+            ff_mac(ih, il, -v.y, -v.w, h.x, h.z);
+        }
+        ff_norm(rh, rl);
+        ff_norm(ih, il);
+        wf[t] = make_float4(rh, ih, rl, il);
+    }
+}
+
+// Partial squared column norms (FP64) of a float-float vector over a chunk of rows.
+__global__ void __launch_bounds__(kDotThreads) k_colnorm_part_ff(int64_t rows, int64_t B,
+                                                                 const float4 *__restrict__ wf,
+                                                                 double *__restrict__ part) {
+    const int c = blockIdx.x, nc = gridDim.x;
+    const int64_t b = blockIdx.y;
+    const int64_t r0 = rows * c / nc, r1 = rows * (c + 1) / nc;
+    __shared__ double sh[kDotThreads];
+    double acc = 0.0;
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) acc += norm2(ff_join(wf[r * B + b]));
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int k = blockDim.x >> 1; k > 0; k >>= 1) {
+        if (threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[(int64_t)c * B + b] = sh[0];
+}
+
+// v = w / nrm[b] in FP64 (for the apply) and its float-float split (for Gram-Schmidt); in
+// place on wf. nrm = 0 leaves zeros (exact invariant subspace).
+__global__ void k_scale_ff(int64_t total, int64_t B, float4 *__restrict__ wf,
+                           const double *__restrict__ nrm, cx<double> *__restrict__ v) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const double n = nrm[t % B];
+        const cx<double> x = n > 0.0 ? (1.0 / n) * ff_join(wf[t]) : cx<double>{0.0, 0.0};
+        v[t] = x;
+        wf[t] = ff_split(x);
+    }
+}
+
+// h[i][b] = sum_c part[c][i][b] for i < nv (and its float-float split hf when hf is not
+// null); Hb[i][j][b] += h[i][b] for i < nh (column j of
+// the Hessenberg matrix accumulates both Gram-Schmidt passes; entry nh, when nv > nh, is the
+// squared norm of the vector itself). With a non-null skip flag the kernel does nothing when
+// the flag is set.
+__global__ void k_reduce_h(int nc, int nv, int nh, int64_t B, const cx<double> *__restrict__ part,
+                           cx<double> *__restrict__ h, float4 *__restrict__ hf, cx<double> *__restrict__ Hb,
+                           int j, int mmax, const int *__restrict__ skip) {
+    if (skip && *skip) return;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)nv * B;
          t += (int64_t)gridDim.x * blockDim.x) {
         cx<double> acc{0.0, 0.0};
         for (int c = 0; c < nc; ++c) acc = acc + part[(int64_t)c * nv * B + t];
         h[t] = acc;
+        if (hf) hf[t] = ff_split(acc);
         const int64_t i = t / B, b = t - i * B;
-        cx<double> &e = Hb[(i * mmax + j) * B + b];
-        e = e + acc;
+        if (i < nh) {
+            cx<double> &e = Hb[(i * mmax + j) * B + b];
+            e = e + acc;
+        }
     }
+}
+
+// Whether the second Gram-Schmidt pass can be skipped: after one classical pass the vector
+// keeps norm^2 = |w|^2 - sum_i |h_i|^2 (V orthonormal); when that is at least kKeep^2 |w|^2
+// for every column, the orthogonality lost in the pass is at most about eps / kKeep per step
+// and a second pass would change nothing measurable. skip = 1 in that case.
+constexpr double kKeep2 = 0.05 * 0.05;
+__global__ void k_reorth_flag(int nh, int64_t B, const cx<double> *__restrict__ h, int *__restrict__ skip) {
+    __shared__ int need;
+    if (threadIdx.x == 0) need = 0;
+    __syncthreads();
+    for (int64_t b = threadIdx.x; b < B; b += blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i < nh; ++i) s += norm2(h[(int64_t)i * B + b]);
+        const double w2 = h[(int64_t)nh * B + b].re;
+        if (!(w2 - s >= kKeep2 * w2)) need = 1;  // also when not finite
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *skip = need ? 0 : 1;
 }
 
 // w[row][b] -= sum_i V_i[row][b] h[i][b]
 __global__ void k_gs_update(int64_t rows, int64_t B, int nv, const cx<double> *__restrict__ V,
                             int64_t vstride, const cx<double> *__restrict__ h,
-                            cx<double> *__restrict__ w) {
+                            cx<double> *__restrict__ w, const int *__restrict__ skip) {
+    if (skip && *skip) return;
     const int64_t total = rows * B;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -93,28 +285,36 @@ __global__ void k_gs_update(int64_t rows, int64_t B, int nv, const cx<double> *_
     }
 }
 
-// Hb[j+1][j][b] = nrm[b]
-__global__ void k_set_sub(cx<double> *__restrict__ Hb, int j, int mmax, int64_t B,
-                          const double *__restrict__ nrm) {
-    for (int64_t b = threadIdx.x; b < B; b += blockDim.x)
-        Hb[((int64_t)(j + 1) * mmax + j) * B + b] = cx<double>{nrm[b], 0.0};
-}
-
-// nrm[b] = ||w[:, b]|| (one block per column)
-__global__ void __launch_bounds__(kDotThreads) k_colnorm(int64_t rows, int64_t B,
-                                                         const cx<double> *__restrict__ w,
-                                                         double *__restrict__ nrm) {
-    const int64_t b = blockIdx.x;
-    __shared__ double s[kDotThreads];
+// Partial squared column norms over a chunk of rows: part[c][b]; grid (chunk, b).
+__global__ void __launch_bounds__(kDotThreads) k_colnorm_part(int64_t rows, int64_t B,
+                                                              const cx<double> *__restrict__ w,
+                                                              double *__restrict__ part) {
+    const int c = blockIdx.x, nc = gridDim.x;
+    const int64_t b = blockIdx.y;
+    const int64_t r0 = rows * c / nc, r1 = rows * (c + 1) / nc;
+    __shared__ double sh[kDotThreads];
     double acc = 0.0;
-    for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) acc += norm2(w[r * B + b]);
-    s[threadIdx.x] = acc;
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) acc += norm2(w[r * B + b]);
+    sh[threadIdx.x] = acc;
     __syncthreads();
     for (int k = blockDim.x >> 1; k > 0; k >>= 1) {
-        if (threadIdx.x < k) s[threadIdx.x] += s[threadIdx.x + k];
+        if (threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
         __syncthreads();
     }
-    if (threadIdx.x == 0) nrm[b] = std::sqrt(s[0]);
+    if (threadIdx.x == 0) part[(int64_t)c * B + b] = sh[0];
+}
+
+// nrm[b] = sqrt(sum_c part[c][b]); with Hb, also Hb[j+1][j][b] = nrm[b]
+__global__ void k_colnorm_fin(int nc, int64_t B, const double *__restrict__ part,
+                              double *__restrict__ nrm, cx<double> *__restrict__ Hb, int j, int mmax) {
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < B;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int c = 0; c < nc; ++c) acc += part[(int64_t)c * B + b];
+        const double n = std::sqrt(acc);
+        nrm[b] = n;
+        if (Hb) Hb[((int64_t)(j + 1) * mmax + j) * B + b] = cx<double>{n, 0.0};
+    }
 }
 
 // out[row][b] = w[row][b] / nrm[b] (nrm = 0 leaves zeros: exact invariant subspace)
@@ -141,27 +341,27 @@ __device__ inline void givens(cx<double> a, cx<double> b, double &c, cx<double> 
 
 // Per (column b, shift k): apply the stored rotations to Hessenberg column j of the shifted
 // matrix, make the new rotation, update g and the residual estimate |g_{j+1}| / beta.
-// Hb: [mmax+1][mmax][B] (row i, column j, batch b). rot_c [S][mmax], rot_s [S][mmax],
-// g [S][mmax+1], shift [S], col_of [S] (the batch column of shift k), res [S].
+// Hb: [mmax+1][mmax][B] (row i, column j, batch b). Per-shift arrays are stored [i][S] so that
+// neighbouring threads (shifts) read neighbouring words: rot_c, rot_s, rdiag [mmax][S],
+// g [mmax+1][S]; shift [S], col_of [S] (the batch column of shift k), res [S]. rdiag keeps
+// the diagonal entry R_jj of the triangular factor for the back substitution.
 __global__ void k_shift_step(int j, int mmax, int64_t B, int64_t S, const cx<double> *__restrict__ Hb,
                              const cx<double> *__restrict__ shift, const int *__restrict__ col_of,
                              double *__restrict__ rot_c, cx<double> *__restrict__ rot_s,
-                             cx<double> *__restrict__ g, const double *__restrict__ beta,
-                             double *__restrict__ res) {
+                             cx<double> *__restrict__ rdiag, cx<double> *__restrict__ g,
+                             const double *__restrict__ beta, double *__restrict__ res) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= S) return;
     const int64_t b = col_of[k];
-    double *rc = rot_c + k * mmax;
-    cx<double> *rs = rot_s + k * mmax;
-    cx<double> *gk = g + k * (mmax + 1);
+    const cx<double> shk = shift[k];
     // column j of Hb + shift * I~ ; apply rotations 0..j-1 on the fly
     cx<double> hj = Hb[((int64_t)0 * mmax + j) * B + b];
-    if (j == 0) hj = hj + shift[k];
+    if (j == 0) hj = hj + shk;
     for (int i = 0; i < j; ++i) {
         cx<double> hi1 = Hb[((int64_t)(i + 1) * mmax + j) * B + b];
-        if (i + 1 == j) hi1 = hi1 + shift[k];
-        const double c = rc[i];
-        const cx<double> s = rs[i];
+        if (i + 1 == j) hi1 = hi1 + shk;
+        const double c = rot_c[(int64_t)i * S + k];
+        const cx<double> s = rot_s[(int64_t)i * S + k];
         // (hj, hi1) <- (c hj + s hi1, -conj(s) hj + c hi1): row i is final, row i+1 carries on
         hj = c * hi1 - conj(s) * hj;
     }
@@ -169,59 +369,53 @@ __global__ void k_shift_step(int j, int mmax, int64_t B, int64_t S, const cx<dou
     double c;
     cx<double> s, r;
     givens(hj, hsub, c, s, r);
-    rc[j] = c;
-    rs[j] = s;
-    const cx<double> gj = gk[j];
-    gk[j] = c * gj;
-    gk[j + 1] = cx<double>{0.0, 0.0} - conj(s) * gj;
-    res[k] = std::sqrt(norm2(gk[j + 1])) / beta[b];
+    rot_c[(int64_t)j * S + k] = c;
+    rot_s[(int64_t)j * S + k] = s;
+    rdiag[(int64_t)j * S + k] = r;
+    const cx<double> gj = g[(int64_t)j * S + k];
+    g[(int64_t)j * S + k] = c * gj;
+    const cx<double> gn = cx<double>{0.0, 0.0} - conj(s) * gj;
+    g[(int64_t)(j + 1) * S + k] = gn;
+    res[k] = std::sqrt(norm2(gn)) / beta[b];
 }
 
-// Per shift: solve R y = g (column-oriented back substitution, columns of R regenerated
-// from the rotations) for the first m Hessenberg columns and form the tier-0 block
-// x0[e] = sum_l V_l[e][b] y_l, e < d2. Work arrays y [S][mmax] (scratch), x0 [S][d2].
+// Per shift: solve R y = g for the first m Hessenberg columns (column-oriented back
+// substitution: y_l = g_l / R_ll, then g_i -= R_il y_l for i < l, the entries R_il of column l
+// regenerated in registers from Hb and the stored rotations) and form the tier-0 block
+// x0[e] = sum_l V_l[e][b] y_l, e < d2. g is copied into the work array gw ([mmax+1][S]);
+// y [mmax][S]; x0 [S][d2].
 __global__ void k_shift_solve(int m, int mmax, int64_t B, int64_t S, int d2,
                               const cx<double> *__restrict__ Hb, const cx<double> *__restrict__ shift,
                               const int *__restrict__ col_of, const double *__restrict__ rot_c,
-                              const cx<double> *__restrict__ rot_s, const cx<double> *__restrict__ g,
-                              cx<double> *__restrict__ gw, cx<double> *__restrict__ y,
-                              cx<double> *__restrict__ colbuf, const cx<double> *__restrict__ V,
+                              const cx<double> *__restrict__ rot_s, const cx<double> *__restrict__ rdiag,
+                              const cx<double> *__restrict__ g, cx<double> *__restrict__ gw,
+                              cx<double> *__restrict__ y, const cx<double> *__restrict__ V,
                               int64_t vstride, cx<double> *__restrict__ x0) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= S) return;
     const int64_t b = col_of[k];
-    const double *rc = rot_c + k * mmax;
-    const cx<double> *rs = rot_s + k * mmax;
-    cx<double> *gk = gw + k * (mmax + 1);
-    cx<double> *yk = y + k * mmax;
-    cx<double> *col = colbuf + k * (mmax + 1);
-    for (int i = 0; i <= m; ++i) gk[i] = g[k * (mmax + 1) + i];
+    const cx<double> shk = shift[k];
+    for (int i = 0; i < m; ++i) gw[(int64_t)i * S + k] = g[(int64_t)i * S + k];
     for (int l = m - 1; l >= 0; --l) {
-        // column l of R: rotations 0..l-1 applied to column l of Hb + shift I~
-        for (int i = 0; i <= l + 1; ++i) {
-            cx<double> v = Hb[((int64_t)i * mmax + l) * B + b];
-            if (i == l) v = v + shift[k];
-            col[i] = v;
-        }
+        const cx<double> yl = cdiv(gw[(int64_t)l * S + k], rdiag[(int64_t)l * S + k]);
+        y[(int64_t)l * S + k] = yl;
+        // rows 0..l-1 of column l of R: rotation i fixes row i and carries row i+1 on
+        cx<double> carry = Hb[((int64_t)0 * mmax + l) * B + b];
+        if (l == 0) carry = carry + shk;
         for (int i = 0; i < l; ++i) {
-            const double c = rc[i];
-            const cx<double> s = rs[i];
-            const cx<double> a0 = col[i], a1 = col[i + 1];
-            col[i] = c * a0 + s * a1;
-            col[i + 1] = c * a1 - conj(s) * a0;
+            cx<double> a1 = Hb[((int64_t)(i + 1) * mmax + l) * B + b];
+            if (i + 1 == l) a1 = a1 + shk;
+            const double c = rot_c[(int64_t)i * S + k];
+            const cx<double> s = rot_s[(int64_t)i * S + k];
+            const cx<double> ril = c * carry + s * a1;
+            carry = c * a1 - conj(s) * carry;
+            cx<double> &gi = gw[(int64_t)i * S + k];
+            gi = gi - ril * yl;
         }
-        {   // the diagonal entry after rotation l
-            const double c = rc[l];
-            const cx<double> s = rs[l];
-            col[l] = c * col[l] + s * col[l + 1];
-        }
-        const cx<double> yl = cdiv(gk[l], col[l]);
-        yk[l] = yl;
-        for (int i = 0; i < l; ++i) gk[i] = gk[i] - col[i] * yl;
     }
     for (int e = 0; e < d2; ++e) {
         cx<double> acc{0.0, 0.0};
-        for (int l = 0; l < m; ++l) fma_to(acc, V[(int64_t)l * vstride + (int64_t)e * B + b], yk[l]);
+        for (int l = 0; l < m; ++l) fma_to(acc, V[(int64_t)l * vstride + (int64_t)e * B + b], y[(int64_t)l * S + k]);
         x0[k * d2 + e] = acc;
     }
 }
@@ -240,50 +434,64 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
                           std::vector<double> &res, int *steps, cudaStream_t s) {
     const int64_t rows = h->N * h->d2, L = rows * B, S = (int64_t)shift.size();
     const int d2 = h->d2;
-    // device memory: basis V [mmax+1][L], w [L], Hb [mmax+1][mmax][B], h tmp [mmax+1][B],
-    // norms [B], beta [B], per shift: rot_c, rot_s, g, gw, y, colbuf, x0, res, shift, col_of
+    // device memory: basis V [mmax+1][L] (the new vector is formed in its slot), Hb
+    // [mmax+1][mmax][B], h tmp [mmax+2][B], norms [B], beta [B], per shift: rot_c, rot_s,
+    // g, gw, y, rdiag, x0, res, shift, col_of
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~size_t(255); return o; };
-    const size_t oV = take((size_t)(mmax + 1) * L * 16), ow = take((size_t)L * 16),
-                 oH = take((size_t)(mmax + 1) * mmax * B * 16), oh = take((size_t)(mmax + 1) * B * 16),
+    const size_t oV = take((size_t)(mmax + 1) * L * 16),
+                 oH = take((size_t)(mmax + 1) * mmax * B * 16), oh = take((size_t)(mmax + 2) * B * 16),
                  on = take((size_t)B * 8), obeta = take((size_t)B * 8),
                  orc = take((size_t)S * mmax * 8), ors = take((size_t)S * mmax * 16),
                  og = take((size_t)S * (mmax + 1) * 16), ogw = take((size_t)S * (mmax + 1) * 16),
-                 oy = take((size_t)S * mmax * 16), ocb = take((size_t)S * (mmax + 1) * 16),
+                 oy = take((size_t)S * mmax * 16), ocb = take((size_t)S * mmax * 16),
                  ox0 = take((size_t)S * d2 * 16), ores = take((size_t)S * 8),
                  osh = take((size_t)S * 16), oco = take((size_t)S * 4);
     // row chunks of the partial dot products: enough blocks to fill the GPU at small j
     const int nchunk = (int)std::max<int64_t>(1, std::min<int64_t>(64, L / 4096));
-    const size_t opart = take((size_t)nchunk * (mmax + 1) * B * 16);
+    const size_t opart = take((size_t)nchunk * (mmax + 2) * B * 16), oskip = take(sizeof(int));
+    const size_t onp = take((size_t)nchunk * B * 8);
+    // float-float Gram-Schmidt (B a power of two up to the block size): a split copy of the
+    // basis and of h
+    const bool ffgs = B <= kDotThreads && (kDotThreads % B) == 0;
+    const size_t oVf = ffgs ? take((size_t)(mmax + 1) * L * 16) : 0,
+                 ohf = ffgs ? take((size_t)(mmax + 2) * B * 16) : 0;
     heom_status st = ensure_ws(h->ws, off);
     if (st != HEOM_OK) return st;
     char *base = (char *)h->ws.p;
-    cx<double> *V = (cx<double> *)(base + oV), *w = (cx<double> *)(base + ow),
-               *Hb = (cx<double> *)(base + oH), *ht = (cx<double> *)(base + oh);
+    cx<double> *V = (cx<double> *)(base + oV), *Hb = (cx<double> *)(base + oH),
+               *ht = (cx<double> *)(base + oh);
     double *nrm = (double *)(base + on), *beta = (double *)(base + obeta);
     double *rot_c = (double *)(base + orc);
     cx<double> *rot_s = (cx<double> *)(base + ors), *g = (cx<double> *)(base + og),
                *gw = (cx<double> *)(base + ogw), *y = (cx<double> *)(base + oy),
-               *cb = (cx<double> *)(base + ocb), *dx0 = (cx<double> *)(base + ox0),
+               *rdiag = (cx<double> *)(base + ocb), *dx0 = (cx<double> *)(base + ox0),
                *dsh = (cx<double> *)(base + osh);
     double *dres = (double *)(base + ores);
     int *dco = (int *)(base + oco);
     cx<double> *part = (cx<double> *)(base + opart);
+    double *npart = (double *)(base + onp);
+    int *dskip = (int *)(base + oskip);
+    float4 *Vf = ffgs ? (float4 *)(base + oVf) : nullptr;
+    float4 *hft = ffgs ? (float4 *)(base + ohf) : nullptr;
     HEOM_CUDA(memcpy_counted(dsh, shift.data(), S * 16, cudaMemcpyHostToDevice, s));
     HEOM_CUDA(memcpy_counted(dco, col_of.data(), S * 4, cudaMemcpyHostToDevice, s));
     HEOM_CUDA(cudaMemsetAsync(Hb, 0, (size_t)(mmax + 1) * mmax * B * 16, s));
     // v_0 = b / ||b||, g = (beta, 0, ...)
     {
         Prof pr(HEOM_KC_OTHER, s, (double)L, 2.0 * L * 16);
-        k_colnorm<<<(unsigned)B, kDotThreads, 0, s>>>(rows, B, bvec, beta);
+        k_colnorm_part<<<dim3((unsigned)nchunk, (unsigned)B), kDotThreads, 0, s>>>(rows, B, bvec, npart);
+        k_colnorm_fin<<<blocks_for(B), 256, 0, s>>>(nchunk, B, npart, beta, nullptr, 0, mmax);
         k_scale_by<<<blocks_for(L), 256, 0, s>>>(L, B, bvec, beta, V);
+        if (ffgs) k_split<<<blocks_for(L), 256, 0, s>>>(L, V, Vf);
+        pr.kernels = ffgs ? 4 : 3;
     }
     std::vector<double> hbeta(B);
     HEOM_CUDA(memcpy_counted(hbeta.data(), beta, B * 8, cudaMemcpyDeviceToHost, s));
     HEOM_CUDA(cudaStreamSynchronize(s));
     {
         std::vector<cx<double>> g0((size_t)S * (mmax + 1), cx<double>{0.0, 0.0});
-        for (int64_t k = 0; k < S; ++k) g0[(size_t)k * (mmax + 1)] = cx<double>{hbeta[col_of[k]], 0.0};
+        for (int64_t k = 0; k < S; ++k) g0[(size_t)k] = cx<double>{hbeta[col_of[k]], 0.0};  // row 0 of [mmax+1][S]
         HEOM_CUDA(memcpy_counted(g, g0.data(), g0.size() * 16, cudaMemcpyHostToDevice, s));
     }
     const DevView<double> v = h->view64();
@@ -291,11 +499,11 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
     TileArgs<double> ta{};
     ta.v = v;
     ta.B = B;
-    const Geom gapply = make_geom(rows, B, 1 << 30);
     std::vector<double> hres(S, 1.0);
     int m = 0, check = 5;
     for (int j = 0; j < mmax; ++j) {
         const cx<double> *vj = V + (int64_t)j * L;
+        cx<double> *w = V + (int64_t)(j + 1) * L;  // the new vector is built in place
         {   // w = M v_j
             Prof pr(HEOM_KC_KRYLOV_APPLY64, s, (double)h->N * B, 2.0 * L * 16);
             if (tiled) {
@@ -307,22 +515,67 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
                 HEOM_CUDA(launch_apply(v, vj, w, B, mods, s));
             }
         }
-        {   // classical Gram-Schmidt, twice; Hb[:, j] accumulates both passes
-            Prof pr(HEOM_KC_KRYLOV_VECTOR, s, (double)(j + 1) * L, 2.0 * (2.0 * (j + 1) + 2.0) * L * 16);
-            for (int pass = 0; pass < 2; ++pass) {
-                k_multidot<<<dim3((unsigned)(j + 1), (unsigned)nchunk), kDotThreads, 0, s>>>(
-                    rows, B, j + 1, V, L, w, part);
-                k_reduce_h<<<blocks_for((int64_t)(j + 1) * B), 256, 0, s>>>(nchunk, j + 1, B, part, ht, Hb, j, mmax);
-                k_gs_update<<<blocks_for(L), 256, 0, s>>>(rows, B, j + 1, V, L, ht, w);
+        if (ffgs) {
+            float4 *wf = Vf + (int64_t)(j + 1) * L;
+            {   // classical Gram-Schmidt in float-float; pass 1 also yields |w|^2 (w's dot with
+                // itself), from which k_reorth_flag decides on the device whether pass 2 runs
+                Prof pr(HEOM_KC_KRYLOV_VECTOR, s, (double)(j + 1) * L, (2.0 * (j + 1) + 5.0) * L * 16);
+                pr.kernels = 5;
+                k_split<<<blocks_for(L), 256, 0, s>>>(L, w, wf);
+                k_multidot_ff<<<dim3((unsigned)(j + 2), (unsigned)nchunk), kDotThreads, 0, s>>>(
+                    rows, B, j + 2, Vf, L, wf, part, nullptr);
+                k_reduce_h<<<blocks_for((int64_t)(j + 2) * B), 256, 0, s>>>(nchunk, j + 2, j + 1, B, part, ht,
+                                                                           hft, Hb, j, mmax, nullptr);
+                k_reorth_flag<<<1, 128, 0, s>>>(j + 1, B, ht, dskip);
+                k_gs_update_ff<<<blocks_for(L), 256, 0, s>>>(rows, B, j + 1, Vf, L, hft, wf, nullptr);
             }
-        }
-        {   // h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j}
-            Prof pr(HEOM_KC_KRYLOV_VECTOR, s, (double)L, 3.0 * L * 16);
-            k_colnorm<<<(unsigned)B, kDotThreads, 0, s>>>(rows, B, w, nrm);
-            k_scale_by<<<blocks_for(L), 256, 0, s>>>(L, B, w, nrm, V + (int64_t)(j + 1) * L);
-            k_set_sub<<<1, 32, 0, s>>>(Hb, j, mmax, B, nrm);
-            k_shift_step<<<(unsigned)((S + 127) / 128), 128, 0, s>>>(j, mmax, B, S, Hb, dsh, dco, rot_c,
-                                                                   rot_s, g, beta, dres);
+            {   // pass 2 (skipped on the device when pass 1 kept enough of w)
+                Prof pr(HEOM_KC_KRYLOV_VECTOR, s, 0.0, 0.0);
+                pr.kernels = 3;
+                k_multidot_ff<<<dim3((unsigned)(j + 1), (unsigned)nchunk), kDotThreads, 0, s>>>(
+                    rows, B, j + 1, Vf, L, wf, part, dskip);
+                k_reduce_h<<<blocks_for((int64_t)(j + 1) * B), 256, 0, s>>>(nchunk, j + 1, j + 1, B, part, ht,
+                                                                           hft, Hb, j, mmax, dskip);
+                k_gs_update_ff<<<blocks_for(L), 256, 0, s>>>(rows, B, j + 1, Vf, L, hft, wf, dskip);
+            }
+            {   // h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j} (FP64 and split), shifted rotations
+                Prof pr(HEOM_KC_KRYLOV_VECTOR, s, (double)L, 4.0 * L * 16);
+                pr.kernels = 4;
+                k_colnorm_part_ff<<<dim3((unsigned)nchunk, (unsigned)B), kDotThreads, 0, s>>>(rows, B, wf, npart);
+                k_colnorm_fin<<<blocks_for(B), 256, 0, s>>>(nchunk, B, npart, nrm, Hb, j, mmax);
+                k_scale_ff<<<blocks_for(L), 256, 0, s>>>(L, B, wf, nrm, w);
+                k_shift_step<<<(unsigned)((S + 63) / 64), 64, 0, s>>>(j, mmax, B, S, Hb, dsh, dco, rot_c,
+                                                                     rot_s, rdiag, g, beta, dres);
+            }
+        } else {
+            {   // classical Gram-Schmidt in FP64, as above
+                Prof pr(HEOM_KC_KRYLOV_VECTOR, s, (double)(j + 1) * L, (2.0 * (j + 1) + 3.0) * L * 16);
+                pr.kernels = 4;
+                k_multidot<<<dim3((unsigned)(j + 2), (unsigned)nchunk), kDotThreads, 0, s>>>(
+                    rows, B, j + 2, V, L, w, part, nullptr);
+                k_reduce_h<<<blocks_for((int64_t)(j + 2) * B), 256, 0, s>>>(nchunk, j + 2, j + 1, B, part, ht,
+                                                                           nullptr, Hb, j, mmax, nullptr);
+                k_reorth_flag<<<1, 128, 0, s>>>(j + 1, B, ht, dskip);
+                k_gs_update<<<blocks_for(L), 256, 0, s>>>(rows, B, j + 1, V, L, ht, w, nullptr);
+            }
+            {
+                Prof pr(HEOM_KC_KRYLOV_VECTOR, s, 0.0, 0.0);
+                pr.kernels = 3;
+                k_multidot<<<dim3((unsigned)(j + 1), (unsigned)nchunk), kDotThreads, 0, s>>>(
+                    rows, B, j + 1, V, L, w, part, dskip);
+                k_reduce_h<<<blocks_for((int64_t)(j + 1) * B), 256, 0, s>>>(nchunk, j + 1, j + 1, B, part, ht,
+                                                                           nullptr, Hb, j, mmax, dskip);
+                k_gs_update<<<blocks_for(L), 256, 0, s>>>(rows, B, j + 1, V, L, ht, w, dskip);
+            }
+            {
+                Prof pr(HEOM_KC_KRYLOV_VECTOR, s, (double)L, 3.0 * L * 16);
+                pr.kernels = 4;
+                k_colnorm_part<<<dim3((unsigned)nchunk, (unsigned)B), kDotThreads, 0, s>>>(rows, B, w, npart);
+                k_colnorm_fin<<<blocks_for(B), 256, 0, s>>>(nchunk, B, npart, nrm, Hb, j, mmax);
+                k_scale_by<<<blocks_for(L), 256, 0, s>>>(L, B, w, nrm, w);
+                k_shift_step<<<(unsigned)((S + 63) / 64), 64, 0, s>>>(j, mmax, B, S, Hb, dsh, dco, rot_c,
+                                                                     rot_s, rdiag, g, beta, dres);
+            }
         }
         HEOM_CUDA(cudaGetLastError());
         m = j + 1;
@@ -338,7 +591,7 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
     {
         Prof pr(HEOM_KC_OTHER, s, (double)S, (double)S * m * 16);
         k_shift_solve<<<(unsigned)((S + 63) / 64), 64, 0, s>>>(m, mmax, B, S, d2, Hb, dsh, dco, rot_c, rot_s,
-                                                               g, gw, y, cb, V, L, dx0);
+                                                               rdiag, g, gw, y, V, L, dx0);
     }
     HEOM_CUDA(cudaGetLastError());
     x0.resize((size_t)S * d2);

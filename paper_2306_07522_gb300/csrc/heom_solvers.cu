@@ -568,6 +568,7 @@ heom_status bicgstab(heom_hier *h, const cx<R> *bvec, cx<R> *x, int64_t B, const
     const cx<R> *shc = nullptr;
     {
         Prof pr(HEOM_KC_OTHER, s, (double)rows * Bc, (3.0 + (x_zero ? 0 : 2)) * rows * Bc * sizeof(cx<R>));
+        pr.kernels = 1 + (x_zero ? 0 : 1) + (shift ? 1 : 0);
         k_gather_cols<R><<<flat_blocks(rows * Bc), 256, 0, s>>>(rows, bvec, B, t, Bc, d_map);
         if (x_zero) HEOM_CUDA(cudaMemsetAsync(cur[0], 0, rows * Bc * sizeof(cx<R>), s));
         else k_gather_cols<R><<<flat_blocks(rows * Bc), 256, 0, s>>>(rows, x, B, cur[0], Bc, d_map);
@@ -634,6 +635,7 @@ heom_status bicgstab(heom_hier *h, const cx<R> *bvec, cx<R> *x, int64_t B, const
             HEOM_CUDA(memcpy_counted(d_lmap, keep.data(), Bn * sizeof(int), cudaMemcpyHostToDevice, s));
             {
                 Prof pr(HEOM_KC_OTHER, s, 5.0 * rows * Bn, 10.0 * rows * Bn * sizeof(cx<R>));
+                pr.kernels = 5;
                 for (int i = 0; i < 5; ++i)
                     k_gather_cols<R><<<flat_blocks(rows * Bn), 256, 0, s>>>(rows, cur[i], Bc, nxt[i], Bn, d_lmap);
             }
