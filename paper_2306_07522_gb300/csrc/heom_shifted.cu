@@ -1,8 +1,8 @@
 // Shift-invariant Krylov solves for spectra (Methods, numerical computation of the
 // spectrum): every frequency w of a density of states solves (M -+ i w) x = b with the same
 // M and the same b, so all of them live in one Krylov space K_m(M, b). One FP64 Arnoldi
-// process (classical Gram-Schmidt, reorthogonalised when one pass loses too much) builds an orthonormal basis V and
-// the Hessenberg matrix Hb with M V_m = V_{m+1} Hb_m; for each shift s the least-squares
+// process (classical Gram-Schmidt, reorthogonalised when one pass loses too much) builds an
+// orthonormal basis V and the Hessenberg matrix Hb with M V_m = V_{m+1} Hb_m; for each shift s the least-squares
 // problem min || beta e_1 - (Hb_m + s I~) y || gives x_s = V_m y_s and its residual norm
 // (GMRES on the shifted system; the shift leaves the basis unchanged). Only the tier-0 block
 // of every x_s is formed, because the spectrum is a trace over it.
@@ -22,6 +22,12 @@ namespace heom {
 namespace {
 
 constexpr int kDotThreads = 256;
+
+// Hessenberg matrices of all columns, column-major: entry (i, j) of column b's matrix at
+// Hb[(j (mmax + 1) + i) B + b], so that one Hessenberg column is contiguous.
+__device__ __forceinline__ int64_t hb_at(int i, int j, int mmax, int64_t B, int64_t b) {
+    return ((int64_t)j * (mmax + 1) + i) * B + b;
+}
 
 // Partial dot products over a chunk of rows: part[c][i][b] = sum_{rows of chunk c}
 // conj(V_i[row][b]) w[row][b]; grid (i, chunk). Deterministic (no atomics). When B is a
@@ -224,7 +230,7 @@ __global__ void k_scale_ff(int64_t total, int64_t B, float4 *__restrict__ wf,
 }
 
 // h[i][b] = sum_c part[c][i][b] for i < nv (and its float-float split hf when hf is not
-// null); Hb[i][j][b] += h[i][b] for i < nh (column j of
+// null); Hb(i, j)[b] += h[i][b] for i < nh (column j of
 // the Hessenberg matrix accumulates both Gram-Schmidt passes; entry nh, when nv > nh, is the
 // squared norm of the vector itself). With a non-null skip flag the kernel does nothing when
 // the flag is set.
@@ -240,7 +246,7 @@ __global__ void k_reduce_h(int nc, int nv, int nh, int64_t B, const cx<double> *
         if (hf) hf[t] = ff_split(acc);
         const int64_t i = t / B, b = t - i * B;
         if (i < nh) {
-            cx<double> &e = Hb[(i * mmax + j) * B + b];
+            cx<double> &e = Hb[hb_at((int)i, j, mmax, B, b)];
             e = e + acc;
         }
     }
@@ -255,11 +261,14 @@ __global__ void k_reorth_flag(int nh, int64_t B, const cx<double> *__restrict__ 
     __shared__ int need;
     if (threadIdx.x == 0) need = 0;
     __syncthreads();
-    for (int64_t b = threadIdx.x; b < B; b += blockDim.x) {
-        double s = 0.0;
-        for (int i = 0; i < nh; ++i) s += norm2(h[(int64_t)i * B + b]);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t b = warp; b < B; b += nw) {  // one warp per column
+        double sacc = 0.0;
+        for (int i = lane; i < nh; i += 32) sacc += norm2(h[(int64_t)i * B + b]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
         const double w2 = h[(int64_t)nh * B + b].re;
-        if (!(w2 - s >= kKeep2 * w2)) need = 1;  // also when not finite
+        if (lane == 0 && !(w2 - sacc >= kKeep2 * w2)) need = 1;  // also when not finite
     }
     __syncthreads();
     if (threadIdx.x == 0) *skip = need ? 0 : 1;
@@ -285,6 +294,7 @@ __global__ void k_gs_update(int64_t rows, int64_t B, int nv, const cx<double> *_
     }
 }
 
+
 // Partial squared column norms over a chunk of rows: part[c][b]; grid (chunk, b).
 __global__ void __launch_bounds__(kDotThreads) k_colnorm_part(int64_t rows, int64_t B,
                                                               const cx<double> *__restrict__ w,
@@ -304,7 +314,7 @@ __global__ void __launch_bounds__(kDotThreads) k_colnorm_part(int64_t rows, int6
     if (threadIdx.x == 0) part[(int64_t)c * B + b] = sh[0];
 }
 
-// nrm[b] = sqrt(sum_c part[c][b]); with Hb, also Hb[j+1][j][b] = nrm[b]
+// nrm[b] = sqrt(sum_c part[c][b]); with Hb, also Hb(j+1, j)[b] = nrm[b]
 __global__ void k_colnorm_fin(int nc, int64_t B, const double *__restrict__ part,
                               double *__restrict__ nrm, cx<double> *__restrict__ Hb, int j, int mmax) {
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < B;
@@ -313,7 +323,7 @@ __global__ void k_colnorm_fin(int nc, int64_t B, const double *__restrict__ part
         for (int c = 0; c < nc; ++c) acc += part[(int64_t)c * B + b];
         const double n = std::sqrt(acc);
         nrm[b] = n;
-        if (Hb) Hb[((int64_t)(j + 1) * mmax + j) * B + b] = cx<double>{n, 0.0};
+        if (Hb) Hb[hb_at(j + 1, j, mmax, B, b)] = cx<double>{n, 0.0};
     }
 }
 
@@ -339,85 +349,235 @@ __device__ inline void givens(cx<double> a, cx<double> b, double &c, cx<double> 
     r = ph * cx<double>{nr, 0.0};
 }
 
-// Per (column b, shift k): apply the stored rotations to Hessenberg column j of the shifted
-// matrix, make the new rotation, update g and the residual estimate |g_{j+1}| / beta.
-// Hb: [mmax+1][mmax][B] (row i, column j, batch b). Per-shift arrays are stored [i][S] so that
-// neighbouring threads (shifts) read neighbouring words: rot_c, rot_s, rdiag [mmax][S],
-// g [mmax+1][S]; shift [S], col_of [S] (the batch column of shift k), res [S]. rdiag keeps
-// the diagonal entry R_jj of the triangular factor for the back substitution.
-__global__ void k_shift_step(int j, int mmax, int64_t B, int64_t S, const cx<double> *__restrict__ Hb,
-                             const cx<double> *__restrict__ shift, const int *__restrict__ col_of,
-                             double *__restrict__ rot_c, cx<double> *__restrict__ rot_s,
-                             cx<double> *__restrict__ rdiag, cx<double> *__restrict__ g,
-                             const double *__restrict__ beta, double *__restrict__ res) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= S) return;
+// ---------------------------------------------------------------- per-shift Givens QR
+// Applying the stored rotations 0..i to a Hessenberg column is a chain: with carry_{-1} =
+// H(0, l) and a_i = H(i+1, l) (+ shift on the diagonal), rotation i gives the final entry
+// R(i, l) = c_i carry_{i-1} + s_i a_i and carries carry_i = -conj(s_i) carry_{i-1} + c_i a_i
+// on. The carries are therefore the partial compositions of the affine maps
+// x -> -conj(s_i) x + c_i a_i, which a warp combines by shuffles (a reduction for the last
+// carry, a scan for all of them) instead of walking the chain one rotation at a time.
+struct Aff {
+    cx<double> a, b;  // x -> a x + b
+};
+__device__ __forceinline__ Aff aff_then(const Aff &f, const Aff &g) {  // f first, then g
+    return Aff{g.a * f.a, g.a * f.b + g.b};
+}
+__device__ __forceinline__ Aff aff_shfl_down(const Aff &f, int off) {
+    Aff r;
+    r.a.re = __shfl_down_sync(0xffffffffu, f.a.re, off);
+    r.a.im = __shfl_down_sync(0xffffffffu, f.a.im, off);
+    r.b.re = __shfl_down_sync(0xffffffffu, f.b.re, off);
+    r.b.im = __shfl_down_sync(0xffffffffu, f.b.im, off);
+    return r;
+}
+__device__ __forceinline__ Aff aff_shfl_up(const Aff &f, int off) {
+    Aff r;
+    r.a.re = __shfl_up_sync(0xffffffffu, f.a.re, off);
+    r.a.im = __shfl_up_sync(0xffffffffu, f.a.im, off);
+    r.b.re = __shfl_up_sync(0xffffffffu, f.b.re, off);
+    r.b.im = __shfl_up_sync(0xffffffffu, f.b.im, off);
+    return r;
+}
+__device__ __forceinline__ Aff aff_shfl(const Aff &f, int src) {
+    Aff r;
+    r.a.re = __shfl_sync(0xffffffffu, f.a.re, src);
+    r.a.im = __shfl_sync(0xffffffffu, f.a.im, src);
+    r.b.re = __shfl_sync(0xffffffffu, f.b.re, src);
+    r.b.im = __shfl_sync(0xffffffffu, f.b.im, src);
+    return r;
+}
+__device__ __forceinline__ cx<double> cx_shfl(cx<double> v, int src) {
+    return cx<double>{__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src)};
+}
+constexpr Aff kAffId{{1.0, 0.0}, {0.0, 0.0}};
+
+// One warp per shift k: apply the stored rotations to Hessenberg column j of the shifted
+// matrix (Hb + shift I~), make rotation j, update g and the residual estimate |g_{j+1}| /
+// beta. Per-shift arrays are [S][mmax] (rot_c, rot_s, rdiag: the diagonal R(j, j) for the
+// back substitution) and [S][mmax+1] (g); shift [S], col_of [S] (the batch column of shift
+// k), res [S].
+__global__ void __launch_bounds__(128) k_shift_step(int j, int mmax, int64_t B, int64_t S,
+                                                    const cx<double> *__restrict__ Hb,
+                                                    const cx<double> *__restrict__ shift,
+                                                    const int *__restrict__ col_of,
+                                                    double *__restrict__ rot_c, cx<double> *__restrict__ rot_s,
+                                                    cx<double> *__restrict__ rdiag, cx<double> *__restrict__ g,
+                                                    const double *__restrict__ beta, double *__restrict__ res) {
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (k >= S) return;  // whole warp
     const int64_t b = col_of[k];
     const cx<double> shk = shift[k];
-    // column j of Hb + shift * I~ ; apply rotations 0..j-1 on the fly
-    cx<double> hj = Hb[((int64_t)0 * mmax + j) * B + b];
-    if (j == 0) hj = hj + shk;
-    for (int i = 0; i < j; ++i) {
-        cx<double> hi1 = Hb[((int64_t)(i + 1) * mmax + j) * B + b];
-        if (i + 1 == j) hi1 = hi1 + shk;
-        const double c = rot_c[(int64_t)i * S + k];
-        const cx<double> s = rot_s[(int64_t)i * S + k];
-        // (hj, hi1) <- (c hj + s hi1, -conj(s) hj + c hi1): row i is final, row i+1 carries on
-        hj = c * hi1 - conj(s) * hj;
+    Aff run = kAffId;
+    for (int base = 0; base < j; base += 32) {
+        const int i = base + lane;
+        Aff f = kAffId;
+        if (i < j) {
+            cx<double> a1 = Hb[hb_at(i + 1, j, mmax, B, b)];
+            if (i + 1 == j) a1 = a1 + shk;
+            const double c = rot_c[k * mmax + i];
+            const cx<double> s = rot_s[k * mmax + i];
+            f = Aff{cx<double>{0.0, 0.0} - conj(s), c * a1};
+        }
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {  // ordered tree: lane 0 ends with maps base..base+31
+            const Aff o = aff_shfl_down(f, off);
+            if ((lane & (2 * off - 1)) == 0) f = aff_then(f, o);
+        }
+        run = aff_then(run, aff_shfl(f, 0));
     }
-    const cx<double> hsub = Hb[((int64_t)(j + 1) * mmax + j) * B + b];
+    if (lane != 0) return;
+    cx<double> a0 = Hb[hb_at(0, j, mmax, B, b)];
+    if (j == 0) a0 = a0 + shk;
+    const cx<double> hj = run.a * a0 + run.b;
+    const cx<double> hsub = Hb[hb_at(j + 1, j, mmax, B, b)];
     double c;
     cx<double> s, r;
     givens(hj, hsub, c, s, r);
-    rot_c[(int64_t)j * S + k] = c;
-    rot_s[(int64_t)j * S + k] = s;
-    rdiag[(int64_t)j * S + k] = r;
-    const cx<double> gj = g[(int64_t)j * S + k];
-    g[(int64_t)j * S + k] = c * gj;
+    rot_c[k * mmax + j] = c;
+    rot_s[k * mmax + j] = s;
+    rdiag[k * mmax + j] = r;
+    const cx<double> gj = g[k * (mmax + 1) + j];
+    g[k * (mmax + 1) + j] = c * gj;
     const cx<double> gn = cx<double>{0.0, 0.0} - conj(s) * gj;
-    g[(int64_t)(j + 1) * S + k] = gn;
+    g[k * (mmax + 1) + j + 1] = gn;
     res[k] = std::sqrt(norm2(gn)) / beta[b];
 }
 
-// Per shift: solve R y = g for the first m Hessenberg columns (column-oriented back
-// substitution: y_l = g_l / R_ll, then g_i -= R_il y_l for i < l, the entries R_il of column l
-// regenerated in registers from Hb and the stored rotations) and form the tier-0 block
-// x0[e] = sum_l V_l[e][b] y_l, e < d2. g is copied into the work array gw ([mmax+1][S]);
-// y [mmax][S]; x0 [S][d2].
-__global__ void k_shift_solve(int m, int mmax, int64_t B, int64_t S, int d2,
-                              const cx<double> *__restrict__ Hb, const cx<double> *__restrict__ shift,
-                              const int *__restrict__ col_of, const double *__restrict__ rot_c,
-                              const cx<double> *__restrict__ rot_s, const cx<double> *__restrict__ rdiag,
-                              const cx<double> *__restrict__ g, cx<double> *__restrict__ gw,
-                              cx<double> *__restrict__ y, const cx<double> *__restrict__ V,
-                              int64_t vstride, cx<double> *__restrict__ x0) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= S) return;
+// One warp per shift: solve R y = g for the first m <= 32 NQ Hessenberg columns and form the
+// tier-0 block x0[e] = sum_l V_l[e][b] y_l (e < d2). Lane q holds rows i = 32 t + q (t < NQ)
+// of g, the rotations and y in registers. Column-oriented back substitution: y_l = g_l /
+// R(l, l), then g_i -= R(i, l) y_l for i < l, the entries R(i, l) regenerated by a warp scan
+// of the rotation chain of column l.
+template <int NQ>
+__global__ void __launch_bounds__(128) k_shift_solve(int m, int mmax, int64_t B, int64_t S, int d2,
+                                                     const cx<double> *__restrict__ Hb,
+                                                     const cx<double> *__restrict__ shift,
+                                                     const int *__restrict__ col_of,
+                                                     const double *__restrict__ rot_c,
+                                                     const cx<double> *__restrict__ rot_s,
+                                                     const cx<double> *__restrict__ rdiag,
+                                                     const cx<double> *__restrict__ g,
+                                                     const cx<double> *__restrict__ V, int64_t vstride,
+                                                     cx<double> *__restrict__ x0) {
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (k >= S) return;  // whole warp
     const int64_t b = col_of[k];
     const cx<double> shk = shift[k];
-    for (int i = 0; i < m; ++i) gw[(int64_t)i * S + k] = g[(int64_t)i * S + k];
+    double c[NQ];
+    cx<double> sr[NQ], gw[NQ], y[NQ];
+#pragma unroll
+    for (int t = 0; t < NQ; ++t) {
+        const int i = 32 * t + lane;
+        const bool ok = i < m;
+        c[t] = ok ? rot_c[k * mmax + i] : 1.0;
+        sr[t] = ok ? rot_s[k * mmax + i] : cx<double>{0.0, 0.0};
+        gw[t] = ok ? g[k * (mmax + 1) + i] : cx<double>{0.0, 0.0};
+        y[t] = cx<double>{0.0, 0.0};
+    }
     for (int l = m - 1; l >= 0; --l) {
-        const cx<double> yl = cdiv(gw[(int64_t)l * S + k], rdiag[(int64_t)l * S + k]);
-        y[(int64_t)l * S + k] = yl;
-        // rows 0..l-1 of column l of R: rotation i fixes row i and carries row i+1 on
-        cx<double> carry = Hb[((int64_t)0 * mmax + l) * B + b];
-        if (l == 0) carry = carry + shk;
-        for (int i = 0; i < l; ++i) {
-            cx<double> a1 = Hb[((int64_t)(i + 1) * mmax + l) * B + b];
-            if (i + 1 == l) a1 = a1 + shk;
-            const double c = rot_c[(int64_t)i * S + k];
-            const cx<double> s = rot_s[(int64_t)i * S + k];
-            const cx<double> ril = c * carry + s * a1;
-            carry = c * a1 - conj(s) * carry;
-            cx<double> &gi = gw[(int64_t)i * S + k];
-            gi = gi - ril * yl;
+        const int tl = l >> 5, ql = l & 31;
+        cx<double> gl{0.0, 0.0};
+#pragma unroll
+        for (int t = 0; t < NQ; ++t)
+            if (t == tl) gl = gw[t];
+        gl = cx_shfl(gl, ql);
+        const cx<double> yl = cdiv(gl, rdiag[k * mmax + l]);
+#pragma unroll
+        for (int t = 0; t < NQ; ++t)
+            if (t == tl && lane == ql) y[t] = yl;
+        cx<double> a0 = Hb[hb_at(0, l, mmax, B, b)];
+        if (l == 0) a0 = a0 + shk;
+        Aff run = kAffId;  // maps 0 .. 32 t - 1
+#pragma unroll
+        for (int t = 0; t < NQ; ++t) {
+            if (32 * t >= l) break;
+            const int i = 32 * t + lane;
+            const bool ok = i < l;
+            cx<double> a1{0.0, 0.0};
+            if (ok) {
+                a1 = Hb[hb_at(i + 1, l, mmax, B, b)];
+                if (i + 1 == l) a1 = a1 + shk;
+            }
+            const Aff f = ok ? Aff{cx<double>{0.0, 0.0} - conj(sr[t]), c[t] * a1} : kAffId;
+            Aff incl = f;  // maps 32 t .. i, in order
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const Aff o = aff_shfl_up(incl, off);
+                if (lane >= off) incl = aff_then(o, incl);
+            }
+            Aff excl = aff_shfl_up(incl, 1);  // maps 32 t .. i - 1
+            if (lane == 0) excl = kAffId;
+            const Aff pre = aff_then(run, excl);
+            const cx<double> carry = pre.a * a0 + pre.b;  // carry_{i-1}
+            if (ok) {
+                const cx<double> ril = c[t] * carry + sr[t] * a1;
+                gw[t] = gw[t] - ril * yl;
+            }
+            run = aff_then(run, aff_shfl(incl, 31));
         }
     }
     for (int e = 0; e < d2; ++e) {
         cx<double> acc{0.0, 0.0};
-        for (int l = 0; l < m; ++l) fma_to(acc, V[(int64_t)l * vstride + (int64_t)e * B + b], y[(int64_t)l * S + k]);
+#pragma unroll
+        for (int t = 0; t < NQ; ++t) {
+            const int l = 32 * t + lane;
+            if (l < m) fma_to(acc, V[(int64_t)l * vstride + (int64_t)e * B + b], y[t]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            acc.re += __shfl_xor_sync(0xffffffffu, acc.re, o);
+            acc.im += __shfl_xor_sync(0xffffffffu, acc.im, o);
+        }
+        if (lane == 0) x0[k * d2 + e] = acc;
+    }
+}
+
+// The same solve for any m, one thread per shift walking the rotation chains (used when m
+// exceeds the register budget of k_shift_solve). Work arrays gw [S][mmax+1], y [S][mmax].
+__global__ void k_shift_solve_long(int m, int mmax, int64_t B, int64_t S, int d2,
+                                   const cx<double> *__restrict__ Hb, const cx<double> *__restrict__ shift,
+                                   const int *__restrict__ col_of, const double *__restrict__ rot_c,
+                                   const cx<double> *__restrict__ rot_s, const cx<double> *__restrict__ rdiag,
+                                   const cx<double> *__restrict__ g, cx<double> *__restrict__ gw,
+                                   cx<double> *__restrict__ y, const cx<double> *__restrict__ V,
+                                   int64_t vstride, cx<double> *__restrict__ x0) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= S) return;
+    const int64_t b = col_of[k];
+    const cx<double> shk = shift[k];
+    cx<double> *gk = gw + k * (mmax + 1);
+    cx<double> *yk = y + k * mmax;
+    for (int i = 0; i < m; ++i) gk[i] = g[k * (mmax + 1) + i];
+    for (int l = m - 1; l >= 0; --l) {
+        const cx<double> yl = cdiv(gk[l], rdiag[k * mmax + l]);
+        yk[l] = yl;
+        cx<double> carry = Hb[hb_at(0, l, mmax, B, b)];
+        if (l == 0) carry = carry + shk;
+        for (int i = 0; i < l; ++i) {
+            cx<double> a1 = Hb[hb_at(i + 1, l, mmax, B, b)];
+            if (i + 1 == l) a1 = a1 + shk;
+            const double c = rot_c[k * mmax + i];
+            const cx<double> s = rot_s[k * mmax + i];
+            const cx<double> ril = c * carry + s * a1;
+            carry = c * a1 - conj(s) * carry;
+            gk[i] = gk[i] - ril * yl;
+        }
+    }
+    for (int e = 0; e < d2; ++e) {
+        cx<double> acc{0.0, 0.0};
+        for (int l = 0; l < m; ++l) fma_to(acc, V[(int64_t)l * vstride + (int64_t)e * B + b], yk[l]);
         x0[k * d2 + e] = acc;
     }
+}
+
+// g[k][0] = beta of shift k's column
+__global__ void k_init_g(int64_t S, int mmax, const int *__restrict__ col_of,
+                         const double *__restrict__ beta, cx<double> *__restrict__ g) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < S;
+         k += (int64_t)gridDim.x * blockDim.x)
+        g[k * (mmax + 1)] = cx<double>{beta[col_of[k]], 0.0};
 }
 
 int blocks_for(int64_t n) { return (int)std::min<int64_t>(std::max<int64_t>((n + 255) / 256, 1), 152 * 16); }
@@ -435,8 +595,8 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
     const int64_t rows = h->N * h->d2, L = rows * B, S = (int64_t)shift.size();
     const int d2 = h->d2;
     // device memory: basis V [mmax+1][L] (the new vector is formed in its slot), Hb
-    // [mmax+1][mmax][B], h tmp [mmax+2][B], norms [B], beta [B], per shift: rot_c, rot_s,
-    // g, gw, y, rdiag, x0, res, shift, col_of
+    // (column-major, see hb_at), h tmp [mmax+2][B], norms [B], beta [B], per shift: rot_c,
+    // rot_s, g, gw, y, rdiag, x0, res, shift, col_of
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~size_t(255); return o; };
     const size_t oV = take((size_t)(mmax + 1) * L * 16),
@@ -486,13 +646,11 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
         if (ffgs) k_split<<<blocks_for(L), 256, 0, s>>>(L, V, Vf);
         pr.kernels = ffgs ? 4 : 3;
     }
-    std::vector<double> hbeta(B);
-    HEOM_CUDA(memcpy_counted(hbeta.data(), beta, B * 8, cudaMemcpyDeviceToHost, s));
-    HEOM_CUDA(cudaStreamSynchronize(s));
+    // g = (beta_b, 0, ...) per shift
+    HEOM_CUDA(cudaMemsetAsync(g, 0, (size_t)S * (mmax + 1) * 16, s));
     {
-        std::vector<cx<double>> g0((size_t)S * (mmax + 1), cx<double>{0.0, 0.0});
-        for (int64_t k = 0; k < S; ++k) g0[(size_t)k] = cx<double>{hbeta[col_of[k]], 0.0};  // row 0 of [mmax+1][S]
-        HEOM_CUDA(memcpy_counted(g, g0.data(), g0.size() * 16, cudaMemcpyHostToDevice, s));
+        Prof pr(HEOM_KC_OTHER, s, (double)S, (double)S * 16);
+        k_init_g<<<blocks_for(S), 256, 0, s>>>(S, mmax, dco, beta, g);
     }
     const DevView<double> v = h->view64();
     const bool tiled = tile_ok(v, B);
@@ -544,7 +702,7 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
                 k_colnorm_part_ff<<<dim3((unsigned)nchunk, (unsigned)B), kDotThreads, 0, s>>>(rows, B, wf, npart);
                 k_colnorm_fin<<<blocks_for(B), 256, 0, s>>>(nchunk, B, npart, nrm, Hb, j, mmax);
                 k_scale_ff<<<blocks_for(L), 256, 0, s>>>(L, B, wf, nrm, w);
-                k_shift_step<<<(unsigned)((S + 63) / 64), 64, 0, s>>>(j, mmax, B, S, Hb, dsh, dco, rot_c,
+                k_shift_step<<<(unsigned)((S + 3) / 4), 128, 0, s>>>(j, mmax, B, S, Hb, dsh, dco, rot_c,
                                                                      rot_s, rdiag, g, beta, dres);
             }
         } else {
@@ -573,7 +731,7 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
                 k_colnorm_part<<<dim3((unsigned)nchunk, (unsigned)B), kDotThreads, 0, s>>>(rows, B, w, npart);
                 k_colnorm_fin<<<blocks_for(B), 256, 0, s>>>(nchunk, B, npart, nrm, Hb, j, mmax);
                 k_scale_by<<<blocks_for(L), 256, 0, s>>>(L, B, w, nrm, w);
-                k_shift_step<<<(unsigned)((S + 63) / 64), 64, 0, s>>>(j, mmax, B, S, Hb, dsh, dco, rot_c,
+                k_shift_step<<<(unsigned)((S + 3) / 4), 128, 0, s>>>(j, mmax, B, S, Hb, dsh, dco, rot_c,
                                                                      rot_s, rdiag, g, beta, dres);
             }
         }
@@ -590,8 +748,18 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
     }
     {
         Prof pr(HEOM_KC_OTHER, s, (double)S, (double)S * m * 16);
-        k_shift_solve<<<(unsigned)((S + 63) / 64), 64, 0, s>>>(m, mmax, B, S, d2, Hb, dsh, dco, rot_c, rot_s,
-                                                               rdiag, g, gw, y, V, L, dx0);
+        const unsigned wb = (unsigned)((S + 3) / 4);  // one warp per shift, four per block
+        if (m <= 32)
+            k_shift_solve<1><<<wb, 128, 0, s>>>(m, mmax, B, S, d2, Hb, dsh, dco, rot_c, rot_s, rdiag, g, V, L, dx0);
+        else if (m <= 64)
+            k_shift_solve<2><<<wb, 128, 0, s>>>(m, mmax, B, S, d2, Hb, dsh, dco, rot_c, rot_s, rdiag, g, V, L, dx0);
+        else if (m <= 96)
+            k_shift_solve<3><<<wb, 128, 0, s>>>(m, mmax, B, S, d2, Hb, dsh, dco, rot_c, rot_s, rdiag, g, V, L, dx0);
+        else if (m <= 128)
+            k_shift_solve<4><<<wb, 128, 0, s>>>(m, mmax, B, S, d2, Hb, dsh, dco, rot_c, rot_s, rdiag, g, V, L, dx0);
+        else
+            k_shift_solve_long<<<(unsigned)((S + 63) / 64), 64, 0, s>>>(m, mmax, B, S, d2, Hb, dsh, dco, rot_c,
+                                                                        rot_s, rdiag, g, gw, y, V, L, dx0);
     }
     HEOM_CUDA(cudaGetLastError());
     x0.resize((size_t)S * d2);
