@@ -206,7 +206,8 @@ heom_status heom_evolve_noalloc(heom_hier *h, void *ados, int64_t batch, double 
 /* Stationary state of every batch column: M x = 0 with Tr rho_sys = 1 (package
  * architecture: stationary states by a linear solve; the trace condition is added to the
  * (0,0) equation of the tier-0 ADO, which M leaves redundant because it preserves the
- * trace). x0: optional device warm start (complex128, NULL for a cold start). x_out:
+ * trace). x0: optional device warm start (complex128, NULL for a cold start); a column whose
+ * x0 has a residual ||b - A x0|| above ||b|| starts from zero instead. x_out:
  * device complex128 [N][d][d][batch]. Converged when ||M x||_2 / ||x||_2 <= tol for x
  * normalised to Tr rho_sys = 1. prec: HEOM_FP64 (plain FP64 BiCGStab) or HEOM_MIXED
  * (FP32 BiCGStab corrections inside FP64 iterative refinement). stats: host array of
@@ -229,6 +230,56 @@ heom_status heom_steady(heom_hier *h, const void *x0, void *x_out, int64_t batch
 heom_status heom_spectrum(heom_hier *odd, const void *ss_ados, const heom_c64 *op_d,
                           const double *omega, int64_t n_omega, double tol, int max_iter,
                           double *A_out, int prec, heom_solve_stats *stats, heom_stream s);
+
+/* ---------------------------------------------------------------- learned warm start */
+
+/* A multilayer perceptron trained on stationary states the library computes, predicting the
+ * reduced density matrix and the first-tier ADOs of a model from its physical parameters;
+ * the prediction seeds heom_steady (x0). The paper has no counterpart: it solves every
+ * stationary state from scratch. Layers: width[0] inputs -> ... -> width[n_layers] outputs,
+ * tanh on hidden layers, linear output. Every matrix product rounds both operands to BF16
+ * and accumulates in FP32 (tensor cores); parameters, activations, gradients and the Adam
+ * state are FP32. Inputs and targets are standardised ((v - mean) / sd) inside the network;
+ * the loss is the mean squared error of the standardised targets. Parameters are one flat
+ * FP32 array: for each layer W ([in][out], row-major) then b ([out]). The network lives on
+ * the device that is current at creation; all pointers below are device pointers unless
+ * marked host. Not thread-safe per network. */
+typedef struct heom_mlp heom_mlp;
+
+/* widths: host [n_layers + 1], each 1..65536; 1 <= n_layers <= 16. Weights Glorot-uniform
+ * from a splitmix64 stream started at seed, biases zero, identity standardisation. */
+heom_status heom_mlp_create(int n_layers, const int *widths, uint64_t seed, heom_mlp **out);
+void heom_mlp_destroy(heom_mlp *net);
+heom_status heom_mlp_info(const heom_mlp *net, int64_t *n_params, int *n_in, int *n_out);
+/* host arrays: in_mean/in_sd [n_in], out_mean/out_sd [n_out]; deviations > 0 */
+heom_status heom_mlp_set_standardisation(heom_mlp *net, const float *in_mean, const float *in_sd,
+                                         const float *out_mean, const float *out_sd);
+/* flat FP32 parameters, host [n_params] */
+heom_status heom_mlp_get_params(const heom_mlp *net, float *host_out);
+heom_status heom_mlp_set_params(heom_mlp *net, const float *host_in);
+/* y [batch][n_out] = net(x [batch][n_in]) in raw (de-standardised) units */
+heom_status heom_mlp_forward(heom_mlp *net, const float *x, float *y, int64_t batch, heom_stream s);
+/* Gradient of the loss with respect to the flat parameters for inputs x [batch][n_in] and
+ * raw targets t [batch][n_out]: grad_out (device [n_params], or NULL) and the loss (host,
+ * or NULL; synchronises s when given). */
+heom_status heom_mlp_gradients(heom_mlp *net, const float *x, const float *t, int64_t batch,
+                               float *grad_out, double *loss, heom_stream s);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) at learning rate lr on
+ * the gradient of (x, t); loss as in heom_mlp_gradients, before the step. */
+heom_status heom_mlp_train_step(heom_mlp *net, const float *x, const float *t, int64_t batch,
+                                float lr, double *loss, heom_stream s);
+/* Warm-start features of n_sets states x (device complex128 [N][d][d][n_sets], columns =
+ * parameter sets) into f (device FP32 [n_sets][n_features]): rho_sys as d diagonal reals,
+ * then Re and Im of rho[i][j] for i < j in row-major order (d^2 reals), then every tier-1
+ * ADO of h in hierarchy order, its d^2 elements row-major with Re and Im interleaved.
+ * n_features must equal d^2 (1 + 2 x number of tier-1 ADOs). Synchronises s. */
+heom_status heom_warm_start_features(const heom_hier *h, const void *x, int64_t n_sets, float *f,
+                                     int n_features, heom_stream s);
+/* x_out (device complex128 [N][d][d][n_sets]) = the ADO vector the network predicts for
+ * the parameter rows params (device FP32 [n_sets][n_in]): rho_sys (Hermitian) and the
+ * tier-1 ADOs from the features above, every other ADO zero. Synchronises s. */
+heom_status heom_warm_start(const heom_hier *h, heom_mlp *net, const float *params, int64_t n_sets,
+                            void *x_out, heom_stream s);
 
 /* ---------------------------------------------------------------- launch accounting */
 

@@ -74,17 +74,29 @@ _sig = {
                             _P],
     "heom_steady": [_P, _P, _P, C.c_int64, C.c_double, C.c_int, C.c_int, _P, _P],
     "heom_spectrum": [_P, _P, _P, _P, C.c_int64, C.c_double, C.c_int, _P, C.c_int, _P, _P],
+    "heom_mlp_create": [C.c_int, _P, C.c_uint64, C.POINTER(_P)],
+    "heom_mlp_info": [_P, _P, _P, _P],
+    "heom_mlp_set_standardisation": [_P, _P, _P, _P, _P],
+    "heom_mlp_get_params": [_P, _P],
+    "heom_mlp_set_params": [_P, _P],
+    "heom_mlp_forward": [_P, _P, _P, C.c_int64, _P],
+    "heom_mlp_gradients": [_P, _P, _P, C.c_int64, _P, _P, _P],
+    "heom_mlp_train_step": [_P, _P, _P, C.c_int64, C.c_float, _P, _P],
+    "heom_warm_start_features": [_P, _P, C.c_int64, _P, C.c_int, _P],
+    "heom_warm_start": [_P, _P, _P, C.c_int64, _P, _P],
     "heom_profile_enable": [C.c_int],
     "heom_profile_read": [C.c_int, _P, _P, _P, _P],
     "heom_profile_copies": [_P, _P],
 }
-EXPORTED = sorted(list(_sig) + ["heom_destroy", "heom_last_error"])
+EXPORTED = sorted(list(_sig) + ["heom_destroy", "heom_last_error", "heom_mlp_destroy"])
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
     _f.argtypes = _args
     _f.restype = C.c_int
 _lib.heom_destroy.argtypes = [_P]
 _lib.heom_destroy.restype = None
+_lib.heom_mlp_destroy.argtypes = [_P]
+_lib.heom_mlp_destroy.restype = None
 _lib.heom_last_error.argtypes = []
 _lib.heom_last_error.restype = C.c_char_p
 
@@ -359,3 +371,90 @@ def profile_copies():
     a, b = C.c_int64(), C.c_int64()
     _check(_lib.heom_profile_copies(C.byref(a), C.byref(b)), "heom_profile_copies")
     return a.value, b.value
+
+
+# ------------------------------------------------------------------------- learned warm start
+def _f32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+class Mlp:
+    """heom_mlp_*: a network that predicts warm-start features from model parameters."""
+
+    def __init__(self, widths, seed: int = 0):
+        w = np.ascontiguousarray(np.asarray(widths, dtype=np.int32))
+        h = C.c_void_p()
+        _check(_lib.heom_mlp_create(len(w) - 1, _ptr(w), seed, C.byref(h)), "heom_mlp_create")
+        self._h = h
+        n, i, o = C.c_int64(), C.c_int(), C.c_int()
+        _check(_lib.heom_mlp_info(self._h, C.byref(n), C.byref(i), C.byref(o)), "heom_mlp_info")
+        self.widths = [int(x) for x in w]
+        self.n_params, self.n_in, self.n_out = n.value, i.value, o.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _lib.heom_mlp_destroy(self._h)
+            self._h = None
+
+    def set_standardisation(self, in_mean, in_sd, out_mean, out_sd):
+        arrs = [_f32(a) for a in (in_mean, in_sd, out_mean, out_sd)]
+        _check(_lib.heom_mlp_set_standardisation(self._h, *[_ptr(a) for a in arrs]),
+               "heom_mlp_set_standardisation")
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.n_params, np.float32)
+        _check(_lib.heom_mlp_get_params(self._h, _ptr(out)), "heom_mlp_get_params")
+        return out
+
+    def set_params(self, p):
+        p = _f32(p)
+        if p.size != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters")
+        _check(_lib.heom_mlp_set_params(self._h, _ptr(p)), "heom_mlp_set_params")
+
+    def forward(self, x, y=None, stream=None):
+        import torch
+        if y is None:
+            y = torch.empty((x.shape[0], self.n_out), dtype=torch.float32, device=x.device)
+        _check(_lib.heom_mlp_forward(self._h, _dptr(x), _dptr(y), x.shape[0], _stream(stream)),
+               "heom_mlp_forward")
+        return y
+
+    def gradients(self, x, t, stream=None):
+        import torch
+        g = torch.empty(self.n_params, dtype=torch.float32, device=x.device)
+        loss = C.c_double()
+        _check(_lib.heom_mlp_gradients(self._h, _dptr(x), _dptr(t), x.shape[0], _dptr(g),
+                                       C.byref(loss), _stream(stream)), "heom_mlp_gradients")
+        return g, loss.value
+
+    def train_step(self, x, t, lr: float, want_loss: bool = False, stream=None):
+        loss = C.c_double()
+        _check(_lib.heom_mlp_train_step(self._h, _dptr(x), _dptr(t), x.shape[0], lr,
+                                        C.byref(loss) if want_loss else None, _stream(stream)),
+               "heom_mlp_train_step")
+        return loss.value if want_loss else None
+
+
+def warm_start_features(h: "Hierarchy", x, n_features: int, stream=None):
+    """Features (torch float32 [n_sets][n_features]) of states x (N, d, d[, n_sets])."""
+    import torch
+    n_sets = x.shape[3] if x.dim() == 4 else 1
+    f = torch.empty((n_sets, n_features), dtype=torch.float32, device=x.device)
+    _check(_lib.heom_warm_start_features(h.handle, _dptr(x), n_sets, _dptr(f), n_features,
+                                         _stream(stream)), "heom_warm_start_features")
+    return f
+
+
+def warm_start(h: "Hierarchy", net: Mlp, params, x_out, stream=None):
+    """x_out (N, d, d[, n_sets], complex128) = the ADO vector net predicts for params."""
+    n_sets = x_out.shape[3] if x_out.dim() == 4 else 1
+    if params.shape[0] != n_sets:
+        raise ValueError("params must have one row per column of x_out")
+    _check(_lib.heom_warm_start(h.handle, net.handle, _dptr(params), n_sets, _dptr(x_out),
+                                _stream(stream)), "heom_warm_start")
+    return x_out

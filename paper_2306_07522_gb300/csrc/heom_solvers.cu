@@ -747,6 +747,17 @@ struct Solve {
 constexpr int kInnerCap = 400;     // FP32 BiCGStab iterations per refinement sweep
 constexpr int kInnerCap64 = 1500;  // FP64 BiCGStab iterations per sweep (plain path)
 
+// flagged columns: x = 0, r = b
+__global__ void k_reset_cols(int64_t total, int64_t B, const int *flags, const cx<double> *b,
+                             cx<double> *x, cx<double> *r) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (flags[i % B]) {
+            x[i] = cx<double>{0.0, 0.0};
+            r[i] = b[i];
+        }
+}
+
 template <class RI>
 heom_status refine_solve(heom_hier *h, const cx<double> *b64, cx<double> *x64, int64_t B,
                          const cx<double> *shift64, double aug, bool x_zero, double tol,
@@ -807,6 +818,19 @@ heom_status refine_solve(heom_hier *h, const cx<double> *b64, cx<double> *x64, i
         HEOM_CUDA(cudaGetLastError());
         HEOM_CUDA(memcpy_counted(hs.data(), st_out, B * sizeof(ColState), cudaMemcpyDeviceToHost, s));
         HEOM_CUDA(cudaStreamSynchronize(s));
+        if (sweep == 0 && !x_zero) {
+            // a starting guess whose residual exceeds ||b|| is worse than the zero vector:
+            // those columns start cold (x = 0, r = b)
+            std::vector<int> reset(B, 0);
+            int n_reset = 0;
+            for (int64_t b = 0; b < B; ++b)
+                if (active[b] && !(hs[b].acc_nr <= hs[b].bnorm2)) { reset[b] = 1; ++n_reset; hs[b].acc_nr = hs[b].bnorm2; }
+            if (n_reset) {
+                HEOM_CUDA(memcpy_counted(d_flags, reset.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
+                Prof pr(HEOM_KC_OTHER, s, (double)L, 3.0 * L * sizeof(cx<double>));
+                k_reset_cols<<<flat_blocks(L), 256, 0, s>>>(L, B, d_flags, b64, x64, r64);
+            }
+        }
         int n_act = 0;
         double worst = 0.0;
         for (int64_t b = 0; b < B; ++b) {
