@@ -225,8 +225,13 @@ heom_status heom_steady(heom_hier *h, const void *x0, void *x_out, int64_t batch
  * BiCGStab solve per frequency and sign, batched as columns, as for heom_steady) or
  * HEOM_SHIFTED (two Arnoldi processes, one per sign, up to max_iter steps; the residual of
  * each frequency is the least-squares residual of its shifted Hessenberg problem, which
- * equals ||b - (M -+ i w) x|| up to the rounding of the Arnoldi relation).
- * stats: host array of 2*n_omega entries (x_+ then x_-) or NULL. Synchronises s. */
+ * equals ||b - (M -+ i w) x|| up to the rounding of the Arnoldi relation; the basis is kept
+ * within 60 % of the free device memory, which may lower max_iter).
+ * Parameter sets (HEOM_SHIFTED only): when `odd` holds n_sets > 1 sets (heom_set_params),
+ * ss_ados is [N][d][d][n_sets] (set s's stationary state in column s), every set gets its own
+ * pair of Arnoldi processes, A_out is [n_sets][n_omega] and stats run set by set.
+ * stats: host array of 2*n_omega*n_sets entries (per set: x_+ then x_-) or NULL.
+ * Synchronises s. */
 heom_status heom_spectrum(heom_hier *odd, const void *ss_ados, const heom_c64 *op_d,
                           const double *omega, int64_t n_omega, double tol, int max_iter,
                           double *A_out, int prec, heom_solve_stats *stats, heom_stream s);

@@ -338,11 +338,13 @@ def steady(h: Hierarchy, x_out, x0=None, tol: float = 1e-8, max_iter: int = 2000
 
 def spectrum(odd: Hierarchy, ss, op_d, omegas, tol: float = 1e-8, max_iter: int = 2000,
              prec: int = MIXED, stream=None, raise_on_error: bool = True):
-    """Density of states A(w) of mode op_d; returns (A, status, stats of x_+ then x_-)."""
+    """Density of states A(w) of mode op_d; returns (A, status, stats of x_+ then x_-).
+    With a hierarchy holding several parameter sets (SHIFTED only), ss is (N, d, d, n_sets),
+    A is (n_sets, n_omega) and the stats run set by set."""
     op = _c64(op_d)
     om = np.ascontiguousarray(omegas, np.float64)
-    A = np.zeros(len(om))
-    stats = (SolveStats * (2 * len(om)))()
+    A = np.zeros(len(om)) if odd.n_sets == 1 else np.zeros((odd.n_sets, len(om)))
+    stats = (SolveStats * (2 * len(om) * odd.n_sets))()
     st = _lib.heom_spectrum(odd.handle, _dptr(ss), _ptr(op), _ptr(om), len(om), tol, max_iter,
                             _ptr(A), prec, C.cast(stats, C.c_void_p), _stream(stream))
     if raise_on_error:

@@ -7,14 +7,10 @@
 // barrier, so every CTA derives the same Krylov scalars and the same convergence decision
 // without any host round trip. Five grid barriers per iteration; the host reads the result
 // once, at the end.
-#include <cooperative_groups.h>
-
 #include <algorithm>
 #include <cmath>
 
 #include "heom_tile.cuh"
-
-namespace cg = cooperative_groups;
 
 namespace heom {
 
@@ -23,6 +19,14 @@ struct PersistOut {
     int status;
     double nr;   // ||r||^2 at exit
     double bn;   // ||b||^2
+};
+
+// state of the grid barrier below (zeroed before every launch)
+struct GridBar {
+    unsigned count;  // arrivals in the current generation
+    unsigned gen;    // completed barriers
+    int err;         // a wait ran out
+    int pad;
 };
 
 template <class R>
@@ -36,6 +40,7 @@ struct PersistArgs {
     int precond;
     cx<R> *r, *rh, *p, *vv, *ph, *sh, *t;
     double *part;  // [kSlots][G][4]
+    GridBar *bar;
     double tol;
     int max_iter, stall_iters;
     PersistOut *out;
@@ -80,12 +85,54 @@ __device__ __forceinline__ cx<R> prog_apply(const ProgSmem<R> &ps, int it, const
     return acc;
 }
 
+// Grid barrier of the cooperative launch (every CTA resident). Generation counting: each
+// CTA adds one arrival; the last arrival resets the count and publishes the next generation;
+// the others wait for it with a bounded spin (about 2 s of SM clock). A wait that runs out
+// raises the shared error flag; every CTA that sees the flag leaves its wait too, so no CTA
+// waits for one that has gone. Returns false in every thread of a CTA that must stop.
+constexpr long long kBarrierCycles = 4000000000LL;
+
+__device__ __forceinline__ bool grid_barrier(GridBar *bar, unsigned &gen) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned target = gen + 1;
+        __threadfence();  // this CTA's writes are visible before its arrival
+        const unsigned prev = atomicAdd(&bar->count, 1u);
+        if (prev == gridDim.x - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            atomicExch(&bar->gen, target);
+        } else {
+            const long long t0 = clock64();
+            for (;;) {
+                unsigned g;
+                asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(g) : "l"(&bar->gen) : "memory");
+                if (g == target) break;
+                if (*(volatile int *)&bar->err) { ok = 0; break; }
+                if (clock64() - t0 > kBarrierCycles) {
+                    atomicExch(&bar->err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        gen = target;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
 // Grid-wide sum of NV doubles: block sums to part[slot][block], grid barrier, then in every
 // block warp k adds value k over all blocks (lane-strided loads through L2, then a fixed
 // shuffle tree; lane 0's result is used), so every block derives bit-identical totals.
 template <int NV>
-__device__ __forceinline__ void grid_sum(double (&val)[NV], double *part, int slot, double *s_red,
-                                         double *s_tot, cg::grid_group &grid) {
+__device__ __forceinline__ bool grid_sum(double (&val)[NV], double *part, int slot, double *s_red,
+                                         double *s_tot, GridBar *bar, unsigned &gen) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
@@ -100,7 +147,7 @@ __device__ __forceinline__ void grid_sum(double (&val)[NV], double *part, int sl
         for (int w = 0; w < nw; ++w) x += s_red[w * 4 + threadIdx.x];
         part[((size_t)slot * gridDim.x + blockIdx.x) * 4 + threadIdx.x] = x;
     }
-    grid.sync();
+    if (!grid_barrier(bar, gen)) return false;
     if (warp < NV) {
         // written by the other CTAs since this CTA last read the slot: through L2, so that
         // no line of an earlier iteration cached in L1 is reused
@@ -115,6 +162,7 @@ __device__ __forceinline__ void grid_sum(double (&val)[NV], double *part, int sl
 #pragma unroll
     for (int k = 0; k < NV; ++k) val[k] = s_tot[k];
     __syncthreads();
+    return true;
 }
 
 __device__ __forceinline__ cx<double> cplx_div(cx<double> a, cx<double> b) { return cdiv(a, b); }
@@ -122,7 +170,7 @@ __device__ __forceinline__ bool finite_c(cx<double> a) { return isfinite(a.re) &
 
 template <class R>
 __global__ void __launch_bounds__(kPersThreads) k_persist_bicg(PersistArgs<R> a) {
-    cg::grid_group grid = cg::this_grid();
+    unsigned gen = 0;  // barriers this block has passed (the barrier starts zeroed)
     const DevView<R> &v = a.v;
     const int d2 = v.d2;
     const int n0 = __ldg(v.pers_ado + blockIdx.x), n1 = __ldg(v.pers_ado + blockIdx.x + 1);
@@ -159,11 +207,11 @@ __global__ void __launch_bounds__(kPersThreads) k_persist_bicg(PersistArgs<R> a)
         val2[0] += (double)norm2(ri);
         val2[1] += (double)norm2(bi);
     }
-    grid_sum<2>(val2, a.part, 0, s_red, s_tot, grid);
+    const bool started = grid_sum<2>(val2, a.part, 0, s_red, s_tot, a.bar, gen);
     double nr = val2[0];
     const double bn = val2[1], tol2 = a.tol * a.tol;
     cx<double> rho{nr, 0.0}, rho_old{1.0, 0.0}, alpha{1.0, 0.0}, omega{1.0, 0.0};
-    int status = (nr <= tol2 * bn) ? 0 : -1, it_done = 0;
+    int status = !started ? HEOM_ECUDA : (nr <= tol2 * bn) ? 0 : -1, it_done = 0;
     double best = nr, rhn = nr;  // rhn = ||rh||^2
     int best_it = 0;
     for (int iter = 1; status < 0 && iter <= a.max_iter; ++iter) {
@@ -184,7 +232,7 @@ __global__ void __launch_bounds__(kPersThreads) k_persist_bicg(PersistArgs<R> a)
             a.p[i] = pi;
             a.ph[i] = pi * s_pinv[it];
         }
-        grid.sync();
+        if (!grid_barrier(a.bar, gen)) { status = HEOM_ECUDA; break; }
         // ---- v = A ph, (rh, v)
         double d1[2] = {0.0, 0.0};
         for (int it = threadIdx.x; it < items; it += blockDim.x) {
@@ -195,7 +243,7 @@ __global__ void __launch_bounds__(kPersThreads) k_persist_bicg(PersistArgs<R> a)
             d1[0] += wd.re * yd.re + wd.im * yd.im;
             d1[1] += wd.re * yd.im - wd.im * yd.re;
         }
-        grid_sum<2>(d1, a.part, 1, s_red, s_tot, grid);
+        if (!grid_sum<2>(d1, a.part, 1, s_red, s_tot, a.bar, gen)) { status = HEOM_ECUDA; break; }
         const cx<double> rv{d1[0], d1[1]};
         if (norm2(rv) == 0.0) { status = HEOM_EBREAKDOWN; it_done = iter; break; }
         alpha = cplx_div(rho, rv);
@@ -207,7 +255,7 @@ __global__ void __launch_bounds__(kPersThreads) k_persist_bicg(PersistArgs<R> a)
             a.r[i] = si;
             a.sh[i] = si * s_pinv[it];
         }
-        grid.sync();
+        if (!grid_barrier(a.bar, gen)) { status = HEOM_ECUDA; break; }
         // ---- t = A sh, (t, s), (t, t)
         double d2v[3] = {0.0, 0.0, 0.0};
         for (int it = threadIdx.x; it < items; it += blockDim.x) {
@@ -219,7 +267,7 @@ __global__ void __launch_bounds__(kPersThreads) k_persist_bicg(PersistArgs<R> a)
             d2v[1] += yd.re * wd.im - yd.im * wd.re;
             d2v[2] += yd.re * yd.re + yd.im * yd.im;
         }
-        grid_sum<3>(d2v, a.part, 2, s_red, s_tot, grid);
+        if (!grid_sum<3>(d2v, a.part, 2, s_red, s_tot, a.bar, gen)) { status = HEOM_ECUDA; break; }
         omega = d2v[2] == 0.0 ? cx<double>{0.0, 0.0} : cplx_div(cx<double>{d2v[0], d2v[1]}, cx<double>{d2v[2], 0.0});
         if (!finite_c(omega) || !finite_c(alpha)) { status = HEOM_EBREAKDOWN; it_done = iter; break; }
         // ---- x += alpha ph + omega sh, r = s - omega t, (rh, r), ||r||^2
@@ -235,7 +283,7 @@ __global__ void __launch_bounds__(kPersThreads) k_persist_bicg(PersistArgs<R> a)
             d3[1] += hd.re * rd.im - hd.im * rd.re;
             d3[2] += rd.re * rd.re + rd.im * rd.im;
         }
-        grid_sum<3>(d3, a.part, 3, s_red, s_tot, grid);
+        if (!grid_sum<3>(d3, a.part, 3, s_red, s_tot, a.bar, gen)) { status = HEOM_ECUDA; break; }
         rho_old = rho;
         rho = cx<double>{d3[0], d3[1]};
         nr = d3[2];
@@ -286,7 +334,7 @@ heom_status bicgstab_persistent(heom_hier *h, const cx<R> *b, cx<R> *x, bool x_z
     const int64_t rows = h->N * h->d2;
     const int G = h->pers_ranges;
     const size_t vec = ((size_t)rows * sizeof(cx<R>) + 255) & ~size_t(255);
-    const size_t bytes = 7 * vec + (size_t)kSlots * G * 4 * sizeof(double) + 256;
+    const size_t bytes = 7 * vec + (size_t)kSlots * G * 4 * sizeof(double) + 512;
     heom_status st = ensure_ws(h->ws_pers, bytes);
     if (st != HEOM_OK) return st;
     char *base = (char *)h->ws_pers.p;
@@ -302,6 +350,8 @@ heom_status bicgstab_persistent(heom_hier *h, const cx<R> *b, cx<R> *x, bool x_z
     for (int i = 0; i < 7; ++i) *vecs[i] = (cx<R> *)(base + i * vec);
     a.part = (double *)(base + 7 * vec);
     a.out = (PersistOut *)(base + 7 * vec + (size_t)kSlots * G * 4 * sizeof(double));
+    a.bar = (GridBar *)((char *)a.out + 128);
+    HEOM_CUDA(cudaMemsetAsync(a.bar, 0, sizeof(GridBar), s));
     a.tol = tol;
     a.max_iter = max_iter;
     a.stall_iters = stall_iters;
@@ -317,6 +367,10 @@ heom_status bicgstab_persistent(heom_hier *h, const cx<R> *b, cx<R> *x, bool x_z
     PersistOut o{};
     HEOM_CUDA(memcpy_counted(&o, a.out, sizeof(o), cudaMemcpyDeviceToHost, s));
     HEOM_CUDA(cudaStreamSynchronize(s));
+    if (o.status == HEOM_ECUDA) {
+        set_error("persistent BiCGStab: a grid barrier wait ran out (CTAs not co-resident?)");
+        return HEOM_ECUDA;
+    }
     *iters = o.iterations;
     *status = o.status;
     *rel_res = o.bn > 0 ? std::sqrt(o.nr / o.bn) : 0.0;

@@ -594,6 +594,22 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
                           std::vector<double> &res, int *steps, cudaStream_t s) {
     const int64_t rows = h->N * h->d2, L = rows * B, S = (int64_t)shift.size();
     const int d2 = h->d2;
+    {   // the basis (FP64 + float-float split) and the per-shift arrays grow with mmax: keep
+        // them within 60 % of the free device memory
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+            const double per_step = 32.0 * (double)L + 88.0 * (double)S + 64.0 * (double)B;
+            const double fixed = 64.0 * (double)L + 48.0 * (double)S + (double)(64 * 2 + 2) * B * 16.0;
+            const double avail = 0.6 * (double)free_b - fixed;
+            const int fit = avail > per_step ? (int)std::min(2.0e9, avail / per_step) - 1 : 0;
+            if (fit < 1) {
+                set_error("shift-invariant solver: not enough device memory for %lld columns and %lld shifts",
+                          (long long)B, (long long)S);
+                return HEOM_ENOMEM;
+            }
+            mmax = std::min(mmax, fit);
+        }
+    }
     // device memory: basis V [mmax+1][L] (the new vector is formed in its slot), Hb
     // (column-major, see hb_at), h tmp [mmax+2][B], norms [B], beta [B], per shift: rot_c,
     // rot_s, g, gw, y, rdiag, x0, res, shift, col_of

@@ -469,6 +469,25 @@ __global__ void k_dos_rhs(int64_t N, int d, const cx<double> *__restrict__ ss,
     }
 }
 
+// b[row][2s] = (op_plus rho_s)[row], b[row][2s+1] = (op_minus rho_s)[row] for the stationary
+// states of ns parameter sets (ss [N][d][d][ns])
+__global__ void k_dos_rhs_sets(int64_t N, int d, const cx<double> *__restrict__ ss,
+                               const cx<double> *__restrict__ op_plus, const cx<double> *__restrict__ op_minus,
+                               cx<double> *__restrict__ bvec, int64_t ns) {
+    const int64_t B = 2 * ns;
+    const int64_t total = N * d * d * B;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = i % B, row = i / B, set = b >> 1;
+        const int64_t n = row / (d * d);
+        const int e = (int)(row - n * d * d), r = e / d, c = e - r * d;
+        const cx<double> *O = (b & 1) ? op_minus : op_plus;
+        cx<double> acc{0.0, 0.0};
+        for (int l = 0; l < d; ++l) fma_to(acc, O[r * d + l], ss[(n * d * d + l * d + c) * ns + set]);
+        bvec[i] = acc;
+    }
+}
+
 template <class R>
 __global__ void k_scale_cols(int64_t total, cx<R> *x, int64_t B, const cx<double> *fac) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
@@ -1085,14 +1104,17 @@ extern "C" heom_status heom_steady(heom_hier *h, const void *x0, void *x_out, in
     return ret;
 }
 
-// Density of states from two shift-invariant Krylov processes (x_+ family on column 0,
-// x_- family on column 1).
+// Density of states from shift-invariant Krylov processes: for parameter set s of the
+// hierarchy, column 2s carries the x_+ family (right-hand side d^dag rho_s, shifts +i w) and
+// column 2s+1 the x_- family (d rho_s, shifts -i w). A_out [n_sets][n_omega]; stats
+// [n_sets][x_+ then x_-][n_omega].
 static heom_status spectrum_shifted(heom_hier *odd, const void *ss_ados, const heom_c64 *op_d,
                                     const double *omega, int64_t n_omega, double tol,
                                     int max_iter, double *A_out, heom_solve_stats *stats,
                                     cudaStream_t st) {
     const int d = odd->d;
-    const int64_t rows = odd->N * odd->d2, L = rows * 2;
+    const int64_t ns = odd->n_sets, B = 2 * ns;
+    const int64_t rows = odd->N * odd->d2, L = rows * B;
     DBuf buf;
     heom_status stt = dalloc(buf, L * sizeof(cx<double>) + 2 * d * d * sizeof(cx<double>));
     if (stt != HEOM_OK) return stt;
@@ -1105,37 +1127,42 @@ static heom_status spectrum_shifted(heom_hier *odd, const void *ss_ados, const h
         }
     HEOM_CUDA(memcpy_counted(ops, hops.data(), hops.size() * sizeof(cx<double>), cudaMemcpyHostToDevice, st));
     { Prof pr(HEOM_KC_OTHER, st, (double)L);
-      k_dos_rhs<<<flat_blocks(L), 256, 0, st>>>(odd->N, d, (const cx<double> *)ss_ados, ops, ops + d * d, b64, 1); }
-    std::vector<cx<double>> shift(2 * n_omega);
-    std::vector<int> col_of(2 * n_omega);
-    for (int64_t j = 0; j < n_omega; ++j) {
-        shift[j] = {0.0, omega[j]};             // (M + i w) x_+ = d^dag rho
-        col_of[j] = 0;
-        shift[n_omega + j] = {0.0, -omega[j]};  // (M - i w) x_- = d rho
-        col_of[n_omega + j] = 1;
-    }
+      k_dos_rhs_sets<<<flat_blocks(L), 256, 0, st>>>(odd->N, d, (const cx<double> *)ss_ados, ops, ops + d * d, b64, ns); }
+    const int64_t S = 2 * n_omega * ns;
+    std::vector<cx<double>> shift(S);
+    std::vector<int> col_of(S);
+    for (int64_t set = 0; set < ns; ++set)
+        for (int64_t j = 0; j < n_omega; ++j) {
+            const int64_t kp = set * 2 * n_omega + j, km = kp + n_omega;
+            shift[kp] = {0.0, omega[j]};   // (M + i w) x_+ = d^dag rho
+            col_of[kp] = (int)(2 * set);
+            shift[km] = {0.0, -omega[j]};  // (M - i w) x_- = d rho
+            col_of[km] = (int)(2 * set + 1);
+        }
     std::vector<cx<double>> x0;
     std::vector<double> res;
     int steps = 0;
-    stt = shifted_gmres(odd, b64, 2, shift, col_of, 0.5 * tol, std::max(1, std::min(max_iter, 2000)),
+    stt = shifted_gmres(odd, b64, B, shift, col_of, 0.5 * tol, std::max(1, std::min(max_iter, 2000)),
                         x0, res, &steps, st);
     dfree(buf);
     if (stt != HEOM_OK) return stt;
     heom_status ret = HEOM_OK;
     const int d2 = d * d;
-    for (int64_t j = 0; j < n_omega; ++j) {
-        double acc = 0;
-        for (int i = 0; i < d; ++i)
-            for (int l = 0; l < d; ++l) {
-                const cx<double> xp = x0[(size_t)j * d2 + l * d + i];
-                const cx<double> xm = x0[(size_t)(n_omega + j) * d2 + l * d + i];
-                const cx<double> dd{op_d[i * d + l].re, op_d[i * d + l].im};
-                const cx<double> dh{op_d[l * d + i].re, -op_d[l * d + i].im};
-                acc += (dd * xp).re + (dh * xm).re;
-            }
-        A_out[j] = -acc / M_PI;
-    }
-    for (int64_t k = 0; k < 2 * n_omega; ++k) {
+    for (int64_t set = 0; set < ns; ++set)
+        for (int64_t j = 0; j < n_omega; ++j) {
+            const int64_t kp = set * 2 * n_omega + j, km = kp + n_omega;
+            double acc = 0;
+            for (int i = 0; i < d; ++i)
+                for (int l = 0; l < d; ++l) {
+                    const cx<double> xp = x0[(size_t)kp * d2 + l * d + i];
+                    const cx<double> xm = x0[(size_t)km * d2 + l * d + i];
+                    const cx<double> dd{op_d[i * d + l].re, op_d[i * d + l].im};
+                    const cx<double> dh{op_d[l * d + i].re, -op_d[l * d + i].im};
+                    acc += (dd * xp).re + (dh * xm).re;
+                }
+            A_out[set * n_omega + j] = -acc / M_PI;
+        }
+    for (int64_t k = 0; k < S; ++k) {
         const int status = (std::isfinite(res[k]) && res[k] <= tol) ? HEOM_OK : HEOM_ENOCONV;
         if (status != HEOM_OK && ret == HEOM_OK) ret = HEOM_ENOCONV;
         if (stats) stats[k] = heom_solve_stats{steps, 0, res[k], status};
@@ -1150,10 +1177,11 @@ extern "C" heom_status heom_spectrum(heom_hier *odd, const void *ss_ados, const 
                                      heom_solve_stats *stats, heom_stream s) {
     if (!odd || !ss_ados || !op_d || !omega || n_omega < 1 || !(tol > 0) || max_iter < 1 ||
         !A_out || (prec != HEOM_FP64 && prec != HEOM_MIXED && prec != HEOM_SHIFTED) ||
-        odd->n_sets != 1 || 2 * n_omega > 65535LL * 32) {
-        set_error("heom_spectrum: need an odd-parity hierarchy with one parameter set, ss_ados, "
-                  "op_d, omega[n_omega >= 1], A_out, tol > 0, max_iter >= 1, prec FP64, MIXED "
-                  "or SHIFTED");
+        (odd->n_sets != 1 && prec != HEOM_SHIFTED) || 2 * n_omega > 65535LL * 32 ||
+        2LL * odd->n_sets > 65535LL * 32) {
+        set_error("heom_spectrum: need an odd-parity hierarchy (several parameter sets only with "
+                  "SHIFTED), ss_ados, op_d, omega[n_omega >= 1], A_out, tol > 0, max_iter >= 1, "
+                  "prec FP64, MIXED or SHIFTED");
         return HEOM_EINVAL;
     }
     HEOM_CUDA(cudaSetDevice(odd->device));

@@ -195,3 +195,40 @@ def test_dos_siam_tier3_many_frequencies_shifted(heom):
     Mo = lv.build_matrix(hy.model_to_problem(m, -1), h)
     Ao = so.dos(Mo, Xo, m.fermion_baths[0][0], om[idx])
     assert np.abs(A[idx] - Ao).max() < 1e-7 * np.abs(Ao).max()
+
+
+def _set_params_of(heom, g, models, parity):
+    Hs, coefs, rates = [], [], []
+    for m in models:
+        p = heom.problem_from_model(m, parity)
+        Hs.append(p["H"])
+        coefs.append(np.concatenate([b["coef"] for b in p["baths"]]))
+        rates.append(np.concatenate([b["rate"] for b in p["baths"]]))
+    heom.set_params(g, np.array(Hs), np.array(coefs), np.array(rates))
+
+
+def test_dos_parameter_sets_shifted(heom):
+    """Three SIAM parameter sets in one shift-invariant solve (two Krylov processes per set):
+    every set's A(w) against the oracle's sparse-LU DOS of that set."""
+    import torch
+    models = [W.siam_model(tier=2, U=u, mu=mu, eps=e) for u, mu, e in
+              ((10.0, 1.0, -5.0), (4.0, 0.3, -2.0), (7.0, 2.0, -3.5))]
+    even = heom.build_hierarchy(heom.problem_from_model(models[0], 1))
+    _set_params_of(heom, even, models, 1)
+    odd = heom.build_hierarchy(heom.problem_from_model(models[0], -1))
+    _set_params_of(heom, odd, models, -1)
+    x = torch.zeros((even.n_ado, 4, 4, 3), dtype=torch.complex128, device="cuda")
+    heom.steady(even, x, tol=1e-10, max_iter=3000, prec=heom.FP64)
+    om = np.linspace(-15, 15, 61)
+    A, st, stats = heom.spectrum(odd, x, models[0].fermion_baths[0][0], om, tol=1e-9,
+                                 max_iter=1500, prec=heom.SHIFTED)
+    assert A.shape == (3, 61) and len(stats) == 3 * 2 * 61
+    assert st == heom.OK and max(s_["residual"] for s_ in stats) <= 1e-9
+    idx = np.array([0, 13, 30, 31, 47, 60])
+    for j, m in enumerate(models):
+        prob = hy.model_to_problem(m)
+        h = hy.problem_hierarchy(prob)
+        Xo = so.steady_state(lv.build_matrix(prob, h), 4)
+        Mo = lv.build_matrix(hy.model_to_problem(m, -1), h)
+        Ao = so.dos(Mo, Xo, m.fermion_baths[0][0], om[idx])
+        assert np.abs(A[j, idx] - Ao).max() < 1e-7 * np.abs(Ao).max(), j
