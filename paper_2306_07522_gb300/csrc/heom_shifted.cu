@@ -9,9 +9,10 @@
 //
 // Batch columns are independent Arnoldi processes (different right-hand sides, and
 // different parameter sets when the hierarchy holds several); each has its own list of
-// shifts. Everything per shift runs on the device: Givens rotations are applied one new
-// Hessenberg column at a time (residual estimates every step) and the final triangular
-// solve regenerates the columns of R from the rotations, so memory per shift is O(m).
+// shifts. Everything per shift runs on the device: at every convergence check each shift's
+// Givens QR takes in the Hessenberg columns added since the last one (residual estimates at
+// the check), and the final triangular solve regenerates the columns of R from the
+// rotations, so memory per shift is O(m).
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -350,189 +351,103 @@ __device__ inline void givens(cx<double> a, cx<double> b, double &c, cx<double> 
 }
 
 // ---------------------------------------------------------------- per-shift Givens QR
-// Applying the stored rotations 0..i to a Hessenberg column is a chain: with carry_{-1} =
-// H(0, l) and a_i = H(i+1, l) (+ shift on the diagonal), rotation i gives the final entry
-// R(i, l) = c_i carry_{i-1} + s_i a_i and carries carry_i = -conj(s_i) carry_{i-1} + c_i a_i
-// on. The carries are therefore the partial compositions of the affine maps
-// x -> -conj(s_i) x + c_i a_i, which a warp combines by shuffles (a reduction for the last
-// carry, a scan for all of them) instead of walking the chain one rotation at a time.
-struct Aff {
-    cx<double> a, b;  // x -> a x + b
-};
-__device__ __forceinline__ Aff aff_then(const Aff &f, const Aff &g) {  // f first, then g
-    return Aff{g.a * f.a, g.a * f.b + g.b};
-}
-__device__ __forceinline__ Aff aff_shfl_down(const Aff &f, int off) {
-    Aff r;
-    r.a.re = __shfl_down_sync(0xffffffffu, f.a.re, off);
-    r.a.im = __shfl_down_sync(0xffffffffu, f.a.im, off);
-    r.b.re = __shfl_down_sync(0xffffffffu, f.b.re, off);
-    r.b.im = __shfl_down_sync(0xffffffffu, f.b.im, off);
-    return r;
-}
-__device__ __forceinline__ Aff aff_shfl_up(const Aff &f, int off) {
-    Aff r;
-    r.a.re = __shfl_up_sync(0xffffffffu, f.a.re, off);
-    r.a.im = __shfl_up_sync(0xffffffffu, f.a.im, off);
-    r.b.re = __shfl_up_sync(0xffffffffu, f.b.re, off);
-    r.b.im = __shfl_up_sync(0xffffffffu, f.b.im, off);
-    return r;
-}
-__device__ __forceinline__ Aff aff_shfl(const Aff &f, int src) {
-    Aff r;
-    r.a.re = __shfl_sync(0xffffffffu, f.a.re, src);
-    r.a.im = __shfl_sync(0xffffffffu, f.a.im, src);
-    r.b.re = __shfl_sync(0xffffffffu, f.b.re, src);
-    r.b.im = __shfl_sync(0xffffffffu, f.b.im, src);
-    return r;
-}
-__device__ __forceinline__ cx<double> cx_shfl(cx<double> v, int src) {
-    return cx<double>{__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src)};
-}
-constexpr Aff kAffId{{1.0, 0.0}, {0.0, 0.0}};
+// One thread per shift. Applying the stored rotations to a Hessenberg column is a chain:
+// with carry = H(0, l) and a_i = H(i+1, l) (+ shift on the diagonal), rotation i fixes row i
+// as R(i, l) = c_i carry + s_i a_i and carries carry <- -conj(s_i) carry + c_i a_i on. GB300
+// issues FP64 at 1/64 of its FP32 rate, so the chains are walked once, serially, by their
+// own thread (a warp-parallel scan of the chain would repeat each complex product on every
+// lane); the many shifts supply the parallelism.
 
-// One warp per shift k: apply the stored rotations to Hessenberg column j of the shifted
-// matrix (Hb + shift I~), make rotation j, update g and the residual estimate |g_{j+1}| /
-// beta. Per-shift arrays are [S][mmax] (rot_c, rot_s, rdiag: the diagonal R(j, j) for the
-// back substitution) and [S][mmax+1] (g); shift [S], col_of [S] (the batch column of shift
-// k), res [S].
-__global__ void __launch_bounds__(128) k_shift_step(int j, int mmax, int64_t B, int64_t S,
+// Shifts' Givens QR of the new Hessenberg columns j0 .. j1-1 of (Hb + shift I~): apply the
+// stored rotations, make rotation j, update g; then the residual estimate |g_{j1}| / beta.
+// Per-shift arrays are [S][mmax] (rot_c, rot_s, rdiag: the diagonal R(j, j) for the back
+// substitution) and [S][mmax+1] (g); shift [S], col_of [S] (the batch column of shift k),
+// res [S].
+__global__ void __launch_bounds__(64) k_shift_steps(int j0, int j1, int mmax, int64_t B, int64_t S,
                                                     const cx<double> *__restrict__ Hb,
                                                     const cx<double> *__restrict__ shift,
                                                     const int *__restrict__ col_of,
                                                     double *__restrict__ rot_c, cx<double> *__restrict__ rot_s,
                                                     cx<double> *__restrict__ rdiag, cx<double> *__restrict__ g,
                                                     const double *__restrict__ beta, double *__restrict__ res) {
-    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (k >= S) return;  // whole warp
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= S) return;
     const int64_t b = col_of[k];
     const cx<double> shk = shift[k];
-    Aff run = kAffId;
-    for (int base = 0; base < j; base += 32) {
-        const int i = base + lane;
-        Aff f = kAffId;
-        if (i < j) {
-            cx<double> a1 = Hb[hb_at(i + 1, j, mmax, B, b)];
-            if (i + 1 == j) a1 = a1 + shk;
-            const double c = rot_c[k * mmax + i];
-            const cx<double> s = rot_s[k * mmax + i];
-            f = Aff{cx<double>{0.0, 0.0} - conj(s), c * a1};
+    double *rc = rot_c + k * mmax;
+    cx<double> *rs = rot_s + k * mmax;
+    cx<double> *gk = g + k * (mmax + 1);
+    for (int j = j0; j < j1; ++j) {
+        cx<double> hj = Hb[hb_at(0, j, mmax, B, b)];
+        if (j == 0) hj = hj + shk;
+        for (int i = 0; i < j; ++i) {
+            cx<double> hi1 = Hb[hb_at(i + 1, j, mmax, B, b)];
+            if (i + 1 == j) hi1 = hi1 + shk;
+            hj = rc[i] * hi1 - conj(rs[i]) * hj;
         }
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {  // ordered tree: lane 0 ends with maps base..base+31
-            const Aff o = aff_shfl_down(f, off);
-            if ((lane & (2 * off - 1)) == 0) f = aff_then(f, o);
-        }
-        run = aff_then(run, aff_shfl(f, 0));
+        double c;
+        cx<double> sn, r;
+        givens(hj, Hb[hb_at(j + 1, j, mmax, B, b)], c, sn, r);
+        rc[j] = c;
+        rs[j] = sn;
+        rdiag[k * mmax + j] = r;
+        const cx<double> gj = gk[j];
+        gk[j] = c * gj;
+        gk[j + 1] = cx<double>{0.0, 0.0} - conj(sn) * gj;
     }
-    if (lane != 0) return;
-    cx<double> a0 = Hb[hb_at(0, j, mmax, B, b)];
-    if (j == 0) a0 = a0 + shk;
-    const cx<double> hj = run.a * a0 + run.b;
-    const cx<double> hsub = Hb[hb_at(j + 1, j, mmax, B, b)];
-    double c;
-    cx<double> s, r;
-    givens(hj, hsub, c, s, r);
-    rot_c[k * mmax + j] = c;
-    rot_s[k * mmax + j] = s;
-    rdiag[k * mmax + j] = r;
-    const cx<double> gj = g[k * (mmax + 1) + j];
-    g[k * (mmax + 1) + j] = c * gj;
-    const cx<double> gn = cx<double>{0.0, 0.0} - conj(s) * gj;
-    g[k * (mmax + 1) + j + 1] = gn;
-    res[k] = std::sqrt(norm2(gn)) / beta[b];
+    res[k] = std::sqrt(norm2(gk[j1])) / beta[b];
 }
 
-// One warp per shift: solve R y = g for the first m <= 32 NQ Hessenberg columns and form the
-// tier-0 block x0[e] = sum_l V_l[e][b] y_l (e < d2). Lane q holds rows i = 32 t + q (t < NQ)
-// of g, the rotations and y in registers. Column-oriented back substitution: y_l = g_l /
-// R(l, l), then g_i -= R(i, l) y_l for i < l, the entries R(i, l) regenerated by a warp scan
-// of the rotation chain of column l.
-template <int NQ>
-__global__ void __launch_bounds__(128) k_shift_solve(int m, int mmax, int64_t B, int64_t S, int d2,
-                                                     const cx<double> *__restrict__ Hb,
-                                                     const cx<double> *__restrict__ shift,
-                                                     const int *__restrict__ col_of,
-                                                     const double *__restrict__ rot_c,
-                                                     const cx<double> *__restrict__ rot_s,
-                                                     const cx<double> *__restrict__ rdiag,
-                                                     const cx<double> *__restrict__ g,
-                                                     const cx<double> *__restrict__ V, int64_t vstride,
-                                                     cx<double> *__restrict__ x0) {
-    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (k >= S) return;  // whole warp
+// Solve R y = g for the first m Hessenberg columns of every shift (column-oriented back
+// substitution: y_l = g_l / R(l, l), then g_i -= R(i, l) y_l for i < l, the entries R(i, l)
+// regenerated from Hb and the stored rotations) and form the tier-0 block
+// x0[e] = sum_l V_l[e][b] y_l, e < d2. g and y of the block's shifts live in shared memory,
+// interleaved by thread ([i][thread]) so that a warp's accesses fall in distinct banks.
+constexpr int kSolveThreads = 32;
+__global__ void __launch_bounds__(kSolveThreads) k_shift_solve(int m, int mmax, int64_t B, int64_t S, int d2,
+                                                               const cx<double> *__restrict__ Hb,
+                                                               const cx<double> *__restrict__ shift,
+                                                               const int *__restrict__ col_of,
+                                                               const double *__restrict__ rot_c,
+                                                               const cx<double> *__restrict__ rot_s,
+                                                               const cx<double> *__restrict__ rdiag,
+                                                               const cx<double> *__restrict__ g,
+                                                               const cx<double> *__restrict__ V, int64_t vstride,
+                                                               cx<double> *__restrict__ x0) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<double> *sm = reinterpret_cast<cx<double> *>(smem_raw);
+    const int t = threadIdx.x, bd = blockDim.x;
+    const int64_t k = (int64_t)blockIdx.x * bd + t;
+    if (k >= S) return;
+    cx<double> *gw = sm + t, *y = sm + (int64_t)m * bd + t;  // element i at [i * bd]
     const int64_t b = col_of[k];
     const cx<double> shk = shift[k];
-    double c[NQ];
-    cx<double> sr[NQ], gw[NQ], y[NQ];
-#pragma unroll
-    for (int t = 0; t < NQ; ++t) {
-        const int i = 32 * t + lane;
-        const bool ok = i < m;
-        c[t] = ok ? rot_c[k * mmax + i] : 1.0;
-        sr[t] = ok ? rot_s[k * mmax + i] : cx<double>{0.0, 0.0};
-        gw[t] = ok ? g[k * (mmax + 1) + i] : cx<double>{0.0, 0.0};
-        y[t] = cx<double>{0.0, 0.0};
-    }
+    const double *rc = rot_c + k * mmax;
+    const cx<double> *rs = rot_s + k * mmax;
+    for (int i = 0; i < m; ++i) gw[(int64_t)i * bd] = g[k * (mmax + 1) + i];
     for (int l = m - 1; l >= 0; --l) {
-        const int tl = l >> 5, ql = l & 31;
-        cx<double> gl{0.0, 0.0};
-#pragma unroll
-        for (int t = 0; t < NQ; ++t)
-            if (t == tl) gl = gw[t];
-        gl = cx_shfl(gl, ql);
-        const cx<double> yl = cdiv(gl, rdiag[k * mmax + l]);
-#pragma unroll
-        for (int t = 0; t < NQ; ++t)
-            if (t == tl && lane == ql) y[t] = yl;
-        cx<double> a0 = Hb[hb_at(0, l, mmax, B, b)];
-        if (l == 0) a0 = a0 + shk;
-        Aff run = kAffId;  // maps 0 .. 32 t - 1
-#pragma unroll
-        for (int t = 0; t < NQ; ++t) {
-            if (32 * t >= l) break;
-            const int i = 32 * t + lane;
-            const bool ok = i < l;
-            cx<double> a1{0.0, 0.0};
-            if (ok) {
-                a1 = Hb[hb_at(i + 1, l, mmax, B, b)];
-                if (i + 1 == l) a1 = a1 + shk;
-            }
-            const Aff f = ok ? Aff{cx<double>{0.0, 0.0} - conj(sr[t]), c[t] * a1} : kAffId;
-            Aff incl = f;  // maps 32 t .. i, in order
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const Aff o = aff_shfl_up(incl, off);
-                if (lane >= off) incl = aff_then(o, incl);
-            }
-            Aff excl = aff_shfl_up(incl, 1);  // maps 32 t .. i - 1
-            if (lane == 0) excl = kAffId;
-            const Aff pre = aff_then(run, excl);
-            const cx<double> carry = pre.a * a0 + pre.b;  // carry_{i-1}
-            if (ok) {
-                const cx<double> ril = c[t] * carry + sr[t] * a1;
-                gw[t] = gw[t] - ril * yl;
-            }
-            run = aff_then(run, aff_shfl(incl, 31));
+        const cx<double> yl = cdiv(gw[(int64_t)l * bd], rdiag[k * mmax + l]);
+        y[(int64_t)l * bd] = yl;
+        cx<double> carry = Hb[hb_at(0, l, mmax, B, b)];
+        if (l == 0) carry = carry + shk;
+        for (int i = 0; i < l; ++i) {
+            cx<double> a1 = Hb[hb_at(i + 1, l, mmax, B, b)];
+            if (i + 1 == l) a1 = a1 + shk;
+            const double c = rc[i];
+            const cx<double> sn = rs[i];
+            const cx<double> ril = c * carry + sn * a1;
+            carry = c * a1 - conj(sn) * carry;
+            cx<double> &gi = gw[(int64_t)i * bd];
+            gi = gi - ril * yl;
         }
     }
     for (int e = 0; e < d2; ++e) {
         cx<double> acc{0.0, 0.0};
-#pragma unroll
-        for (int t = 0; t < NQ; ++t) {
-            const int l = 32 * t + lane;
-            if (l < m) fma_to(acc, V[(int64_t)l * vstride + (int64_t)e * B + b], y[t]);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            acc.re += __shfl_xor_sync(0xffffffffu, acc.re, o);
-            acc.im += __shfl_xor_sync(0xffffffffu, acc.im, o);
-        }
-        if (lane == 0) x0[k * d2 + e] = acc;
+        for (int l = 0; l < m; ++l) fma_to(acc, V[(int64_t)l * vstride + (int64_t)e * B + b], y[(int64_t)l * bd]);
+        x0[k * d2 + e] = acc;
     }
 }
+constexpr int kSolveSmemMax = 200 * 1024;
 
 // The same solve for any m, one thread per shift walking the rotation chains (used when m
 // exceeds the register budget of k_shift_solve). Work arrays gw [S][mmax+1], y [S][mmax].
@@ -674,7 +589,7 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
     ta.v = v;
     ta.B = B;
     std::vector<double> hres(S, 1.0);
-    int m = 0, check = 5;
+    int m = 0, check = 5, j_done = 0;
     for (int j = 0; j < mmax; ++j) {
         const cx<double> *vj = V + (int64_t)j * L;
         cx<double> *w = V + (int64_t)(j + 1) * L;  // the new vector is built in place
@@ -712,14 +627,12 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
                                                                            hft, Hb, j, mmax, dskip);
                 k_gs_update_ff<<<blocks_for(L), 256, 0, s>>>(rows, B, j + 1, Vf, L, hft, wf, dskip);
             }
-            {   // h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j} (FP64 and split), shifted rotations
+            {   // h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j} (FP64 and split)
                 Prof pr(HEOM_KC_KRYLOV_VECTOR, s, (double)L, 4.0 * L * 16);
-                pr.kernels = 4;
+                pr.kernels = 3;
                 k_colnorm_part_ff<<<dim3((unsigned)nchunk, (unsigned)B), kDotThreads, 0, s>>>(rows, B, wf, npart);
                 k_colnorm_fin<<<blocks_for(B), 256, 0, s>>>(nchunk, B, npart, nrm, Hb, j, mmax);
                 k_scale_ff<<<blocks_for(L), 256, 0, s>>>(L, B, wf, nrm, w);
-                k_shift_step<<<(unsigned)((S + 3) / 4), 128, 0, s>>>(j, mmax, B, S, Hb, dsh, dco, rot_c,
-                                                                     rot_s, rdiag, g, beta, dres);
             }
         } else {
             {   // classical Gram-Schmidt in FP64, as above
@@ -743,17 +656,21 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
             }
             {
                 Prof pr(HEOM_KC_KRYLOV_VECTOR, s, (double)L, 3.0 * L * 16);
-                pr.kernels = 4;
+                pr.kernels = 3;
                 k_colnorm_part<<<dim3((unsigned)nchunk, (unsigned)B), kDotThreads, 0, s>>>(rows, B, w, npart);
                 k_colnorm_fin<<<blocks_for(B), 256, 0, s>>>(nchunk, B, npart, nrm, Hb, j, mmax);
                 k_scale_by<<<blocks_for(L), 256, 0, s>>>(L, B, w, nrm, w);
-                k_shift_step<<<(unsigned)((S + 3) / 4), 128, 0, s>>>(j, mmax, B, S, Hb, dsh, dco, rot_c,
-                                                                     rot_s, rdiag, g, beta, dres);
             }
         }
         HEOM_CUDA(cudaGetLastError());
         m = j + 1;
         if (m % check == 0 || m == mmax) {
+            {   // every shift's Givens QR catches up with the new Hessenberg columns
+                Prof pr(HEOM_KC_OTHER, s, (double)S * (m - j_done), 0.0);
+                k_shift_steps<<<(unsigned)((S + 63) / 64), 64, 0, s>>>(j_done, m, mmax, B, S, Hb, dsh, dco,
+                                                                      rot_c, rot_s, rdiag, g, beta, dres);
+            }
+            j_done = m;
             HEOM_CUDA(memcpy_counted(hres.data(), dres, S * 8, cudaMemcpyDeviceToHost, s));
             HEOM_CUDA(cudaStreamSynchronize(s));
             double worst = 0.0;
@@ -764,18 +681,16 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
     }
     {
         Prof pr(HEOM_KC_OTHER, s, (double)S, (double)S * m * 16);
-        const unsigned wb = (unsigned)((S + 3) / 4);  // one warp per shift, four per block
-        if (m <= 32)
-            k_shift_solve<1><<<wb, 128, 0, s>>>(m, mmax, B, S, d2, Hb, dsh, dco, rot_c, rot_s, rdiag, g, V, L, dx0);
-        else if (m <= 64)
-            k_shift_solve<2><<<wb, 128, 0, s>>>(m, mmax, B, S, d2, Hb, dsh, dco, rot_c, rot_s, rdiag, g, V, L, dx0);
-        else if (m <= 96)
-            k_shift_solve<3><<<wb, 128, 0, s>>>(m, mmax, B, S, d2, Hb, dsh, dco, rot_c, rot_s, rdiag, g, V, L, dx0);
-        else if (m <= 128)
-            k_shift_solve<4><<<wb, 128, 0, s>>>(m, mmax, B, S, d2, Hb, dsh, dco, rot_c, rot_s, rdiag, g, V, L, dx0);
-        else
+        const size_t smb = (size_t)2 * m * kSolveThreads * sizeof(cx<double>);
+        if (smb <= (size_t)kSolveSmemMax) {
+            if (smb > 48 * 1024)
+                HEOM_CUDA(cudaFuncSetAttribute(k_shift_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
+            k_shift_solve<<<(unsigned)((S + kSolveThreads - 1) / kSolveThreads), kSolveThreads, smb, s>>>(
+                m, mmax, B, S, d2, Hb, dsh, dco, rot_c, rot_s, rdiag, g, V, L, dx0);
+        } else {
             k_shift_solve_long<<<(unsigned)((S + 63) / 64), 64, 0, s>>>(m, mmax, B, S, d2, Hb, dsh, dco, rot_c,
                                                                         rot_s, rdiag, g, gw, y, V, L, dx0);
+        }
     }
     HEOM_CUDA(cudaGetLastError());
     x0.resize((size_t)S * d2);
