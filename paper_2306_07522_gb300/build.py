@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 CU_SOURCES = ["heom_apply.cu", "heom_solvers.cu", "heom_noalloc.cu", "heom_shifted.cu",
-              "heom_persist.cu", "heom_mlp.cu"]
+              "heom_persist.cu", "heom_mlp.cu", "heom_arnoldi.cu"]
 CPP_SOURCES = ["heom_host.cpp"]
 
 

@@ -246,6 +246,15 @@ heom_status bicgstab_persistent(heom_hier *h, const cx<R> *b, cx<R> *x, bool x_z
                                 int stall_iters, int *iters, int *status, double *rel_res,
                                 cudaStream_t s);
 
+// persistent shift-invariant Arnoldi (heom_arnoldi.cu)
+bool arnoldi_persistent_ok(const heom_hier *h, int64_t B, int max_steps);
+int arnoldi_max_steps();
+heom_status arnoldi_persistent(heom_hier *h, int64_t B, int mmax, int max_steps, float4 *Vf, cx<double> *V,
+                               cx<double> *Hb, int64_t S, const cx<double> *shift, const int *col_of,
+                               double *rot_c, cx<double> *rot_s, cx<double> *rdiag, cx<double> *g,
+                               const double *beta, double *res, double tol, int *steps, bool *converged,
+                               cudaStream_t s);
+
 // one fused RK4 stage over all ADOs and columns (the launch heom_evolve uses)
 template <class R>
 cudaError_t launch_rk4_stage(const DevView<R> &v, const cx<R> *z_in, cx<R> *z_out, cx<R> *y,

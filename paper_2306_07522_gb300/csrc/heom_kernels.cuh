@@ -108,6 +108,27 @@ __device__ __forceinline__ cx<R> precond_inv(const DevView<R> &v, int64_t n, int
     return cdiv(cx<R>{R(1), R(0)}, loc);
 }
 
+// Complex Givens rotation zeroing b in (a, b): G = [c s; -conj(s) c] with c real, so that
+// G (a, b) = (r, 0). Built from two reciprocal square roots: an FP64 division or square root
+// is a long instruction sequence on GB300's narrow FP64 pipe. With ia = 1/|a| and
+// inr = 1/sqrt(|a|^2 + |b|^2): c = |a| inr, s = (a / |a|) conj(b) inr, r = (a / |a|) nr.
+__device__ __forceinline__ void givens_rot(cx<double> a, cx<double> b, double &c, cx<double> &s,
+                                           cx<double> &r) {
+    const double a2 = norm2(a), b2 = norm2(b);
+    if (b2 == 0.0) { c = 1.0; s = cx<double>{0.0, 0.0}; r = a; return; }
+    if (a2 == 0.0) {
+        const double ib = rsqrt(b2);
+        c = 0.0;
+        s = ib * conj(b);
+        r = cx<double>{b2 * ib, 0.0};
+        return;
+    }
+    const double ia = rsqrt(a2), inr = rsqrt(a2 + b2);
+    c = a2 * ia * inr;
+    s = (ia * inr) * (a * conj(b));
+    r = ((a2 + b2) * inr * ia) * a;
+}
+
 // Sum a per-thread FP64 complex value over threadIdx.y and atomically add it to acc[col].
 // Block is (bx, by) with by a power of two; every thread of the block must call this.
 __device__ __forceinline__ void block_add(double re, double im, double *acc_re, double *acc_im,

@@ -17,6 +17,7 @@
 #include <cmath>
 #include <vector>
 
+#include "heom_ff.cuh"
 #include "heom_tile.cuh"
 
 namespace heom {
@@ -91,39 +92,6 @@ __global__ void __launch_bounds__(kDotThreads) k_multidot(int64_t rows, int64_t 
         if (threadIdx.x == 0) part[((int64_t)c * nv + i) * B + b] = cx<double>{sre[0], sim[0]};
         __syncthreads();
     }
-}
-
-// ---------------------------------------------------------------- float-float arithmetic
-// GB300 issues FP64 at 1/64 of its FP32 rate, and the Gram-Schmidt loops are nothing but
-// complex multiply-adds. They run in float-float instead: a value is an unevaluated sum
-// hi + lo of two FP32 numbers (about 48 significant bits, unit roundoff 2^-48 ~ 3.6e-15),
-// products by the FMA-based exact product of Dekker/Kahan (p = a*b, e = fma(a, b, -p)),
-// sums by Knuth's two-sum. A complex value is a float4 {hi.re, hi.im, lo.re, lo.im}.
-// Per-thread results are turned back into FP64 before any block or grid reduction.
-__device__ __forceinline__ float4 ff_split(cx<double> a) {
-    const float hr = __double2float_rn(a.re), hi = __double2float_rn(a.im);
-    return make_float4(hr, hi, __double2float_rn(a.re - (double)hr), __double2float_rn(a.im - (double)hi));
-}
-__device__ __forceinline__ cx<double> ff_join(float4 f) {
-    return cx<double>{(double)f.x + (double)f.z, (double)f.y + (double)f.w};
-}
-// (sh, sl) += (ah + al)(bh + bl), dropping al*bl (2^-48 relative)
-__device__ __forceinline__ void ff_mac(float &sh, float &sl, float ah, float al, float bh, float bl) {
-    const float p = ah * bh;
-    float e = fmaf(ah, bh, -p);
-    e = fmaf(ah, bl, e);
-    e = fmaf(al, bh, e);
-    const float s = sh + p;
-    const float bb = s - sh;
-    const float t = (sh - (s - bb)) + (p - bb);
-    sh = s;
-    sl += t + e;
-}
-// normalise (sh, sl) so that |sl| <= ulp(sh) / 2
-__device__ __forceinline__ void ff_norm(float &sh, float &sl) {
-    const float s = sh + sl;
-    sl = sl - (s - sh);
-    sh = s;
 }
 
 // wf[t] = split(w[t])
@@ -338,18 +306,6 @@ __global__ void k_scale_by(int64_t total, int64_t B, const cx<double> *__restric
     }
 }
 
-// Complex Givens rotation zeroing b in (a, b): [c s; -conj(s) c] with c real.
-__device__ inline void givens(cx<double> a, cx<double> b, double &c, cx<double> &s, cx<double> &r) {
-    const double na = std::sqrt(norm2(a)), nb = std::sqrt(norm2(b));
-    if (nb == 0.0) { c = 1.0; s = {0.0, 0.0}; r = a; return; }
-    if (na == 0.0) { c = 0.0; s = (1.0 / nb) * conj(b); r = cx<double>{nb, 0.0}; return; }
-    const double nr = std::sqrt(na * na + nb * nb);
-    const cx<double> ph = (1.0 / na) * a;  // a / |a|
-    c = na / nr;
-    s = (1.0 / nr) * (ph * conj(b));
-    r = ph * cx<double>{nr, 0.0};
-}
-
 // ---------------------------------------------------------------- per-shift Givens QR
 // One thread per shift. Applying the stored rotations to a Hessenberg column is a chain:
 // with carry = H(0, l) and a_i = H(i+1, l) (+ shift on the diagonal), rotation i fixes row i
@@ -378,6 +334,7 @@ __global__ void __launch_bounds__(64) k_shift_steps(int j0, int j1, int mmax, in
     cx<double> *rs = rot_s + k * mmax;
     cx<double> *gk = g + k * (mmax + 1);
     for (int j = j0; j < j1; ++j) {
+        // (the chain is walked from the stored rotations; see the comment above)
         cx<double> hj = Hb[hb_at(0, j, mmax, B, b)];
         if (j == 0) hj = hj + shk;
         for (int i = 0; i < j; ++i) {
@@ -387,7 +344,7 @@ __global__ void __launch_bounds__(64) k_shift_steps(int j0, int j1, int mmax, in
         }
         double c;
         cx<double> sn, r;
-        givens(hj, Hb[hb_at(j + 1, j, mmax, B, b)], c, sn, r);
+        givens_rot(hj, Hb[hb_at(j + 1, j, mmax, B, b)], c, sn, r);
         rc[j] = c;
         rs[j] = sn;
         rdiag[k * mmax + j] = r;
@@ -590,7 +547,16 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
     ta.B = B;
     std::vector<double> hres(S, 1.0);
     int m = 0, check = 5, j_done = 0;
-    for (int j = 0; j < mmax; ++j) {
+    bool done = false;
+    if (ffgs && arnoldi_persistent_ok(h, B, mmax)) {
+        // the whole solve (up to its shared-memory limit of steps) in one cooperative launch
+        int steps = 0;
+        heom_status pst = arnoldi_persistent(h, B, mmax, std::min(mmax, arnoldi_max_steps()), Vf, V, Hb, S, dsh,
+                                             dco, rot_c, rot_s, rdiag, g, beta, dres, tol, &steps, &done, s);
+        if (pst != HEOM_OK) return pst;
+        m = j_done = steps;
+    }
+    for (int j = m; j < mmax && !done; ++j) {
         const cx<double> *vj = V + (int64_t)j * L;
         cx<double> *w = V + (int64_t)(j + 1) * L;  // the new vector is built in place
         {   // w = M v_j
