@@ -358,8 +358,9 @@ __global__ void __launch_bounds__(64) k_shift_steps(int j0, int j1, int mmax, in
 // Solve R y = g for the first m Hessenberg columns of every shift (column-oriented back
 // substitution: y_l = g_l / R(l, l), then g_i -= R(i, l) y_l for i < l, the entries R(i, l)
 // regenerated from Hb and the stored rotations) and form the tier-0 block
-// x0[e] = sum_l V_l[e][b] y_l, e < d2. g and y of the block's shifts live in shared memory,
-// interleaved by thread ([i][thread]) so that a warp's accesses fall in distinct banks.
+// x0[e] = sum_l V_l[e][b] y_l, e < d2. The block's rotations, g and y are staged in shared
+// memory, interleaved by thread ([i][thread]) so that a warp's accesses fall in distinct
+// banks: the chains then read on-chip memory instead of 32 scattered L2 sectors per step.
 constexpr int kSolveThreads = 32;
 __global__ void __launch_bounds__(kSolveThreads) k_shift_solve(int m, int mmax, int64_t B, int64_t S, int d2,
                                                                const cx<double> *__restrict__ Hb,
@@ -372,16 +373,19 @@ __global__ void __launch_bounds__(kSolveThreads) k_shift_solve(int m, int mmax, 
                                                                const cx<double> *__restrict__ V, int64_t vstride,
                                                                cx<double> *__restrict__ x0) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cx<double> *sm = reinterpret_cast<cx<double> *>(smem_raw);
     const int t = threadIdx.x, bd = blockDim.x;
+    cx<double> *sm = reinterpret_cast<cx<double> *>(smem_raw);
+    cx<double> *gw = sm + t, *y = sm + (int64_t)m * bd + t, *ss = sm + 2 * (int64_t)m * bd + t;
+    double *sc = reinterpret_cast<double *>(sm + 3 * (int64_t)m * bd) + t;  // element i at [i * bd]
     const int64_t k = (int64_t)blockIdx.x * bd + t;
     if (k >= S) return;
-    cx<double> *gw = sm + t, *y = sm + (int64_t)m * bd + t;  // element i at [i * bd]
     const int64_t b = col_of[k];
     const cx<double> shk = shift[k];
-    const double *rc = rot_c + k * mmax;
-    const cx<double> *rs = rot_s + k * mmax;
-    for (int i = 0; i < m; ++i) gw[(int64_t)i * bd] = g[k * (mmax + 1) + i];
+    for (int i = 0; i < m; ++i) {
+        gw[(int64_t)i * bd] = g[k * (mmax + 1) + i];
+        sc[(int64_t)i * bd] = rot_c[k * mmax + i];
+        ss[(int64_t)i * bd] = rot_s[k * mmax + i];
+    }
     for (int l = m - 1; l >= 0; --l) {
         const cx<double> yl = cdiv(gw[(int64_t)l * bd], rdiag[k * mmax + l]);
         y[(int64_t)l * bd] = yl;
@@ -390,18 +394,25 @@ __global__ void __launch_bounds__(kSolveThreads) k_shift_solve(int m, int mmax, 
         for (int i = 0; i < l; ++i) {
             cx<double> a1 = Hb[hb_at(i + 1, l, mmax, B, b)];
             if (i + 1 == l) a1 = a1 + shk;
-            const double c = rc[i];
-            const cx<double> sn = rs[i];
+            const double c = sc[(int64_t)i * bd];
+            const cx<double> sn = ss[(int64_t)i * bd];
             const cx<double> ril = c * carry + sn * a1;
             carry = c * a1 - conj(sn) * carry;
             cx<double> &gi = gw[(int64_t)i * bd];
             gi = gi - ril * yl;
         }
     }
-    for (int e = 0; e < d2; ++e) {
-        cx<double> acc{0.0, 0.0};
-        for (int l = 0; l < m; ++l) fma_to(acc, V[(int64_t)l * vstride + (int64_t)e * B + b], y[(int64_t)l * bd]);
-        x0[k * d2 + e] = acc;
+    for (int e0 = 0; e0 < d2; e0 += 4) {  // four independent accumulations
+        cx<double> acc[4] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
+        for (int l = 0; l < m; ++l) {
+            const cx<double> yl = y[(int64_t)l * bd];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (e0 + u < d2) fma_to(acc[u], V[(int64_t)l * vstride + (int64_t)(e0 + u) * B + b], yl);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (e0 + u < d2) x0[k * d2 + e0 + u] = acc[u];
     }
 }
 constexpr int kSolveSmemMax = 200 * 1024;
@@ -647,7 +658,7 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
     }
     {
         Prof pr(HEOM_KC_OTHER, s, (double)S, (double)S * m * 16);
-        const size_t smb = (size_t)2 * m * kSolveThreads * sizeof(cx<double>);
+        const size_t smb = (size_t)m * kSolveThreads * (3 * sizeof(cx<double>) + sizeof(double));
         if (smb <= (size_t)kSolveSmemMax) {
             if (smb > 48 * 1024)
                 HEOM_CUDA(cudaFuncSetAttribute(k_shift_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
