@@ -236,6 +236,18 @@ heom_status heom_spectrum(heom_hier *odd, const void *ss_ados, const heom_c64 *o
                           const double *omega, int64_t n_omega, double tol, int max_iter,
                           double *A_out, int prec, heom_solve_stats *stats, heom_stream s);
 
+/* Electronic current into lead alpha (Methods, electronic current; e = 1):
+ * <I_alpha> = Re( i sum_q s_q Tr[d^{-nu_q} rho_q] ) over the fermionic exponents q of the
+ * baths that form the lead, rho_q the tier-1 ADO with S = {q} (bosonic occupations zero),
+ * s_q = +1 for nu = +1 and -1 for nu = -1 ((-1)^{delta_{nu,-}}). x: device complex128
+ * [N][d][d][batch] stationary states of the even-parity hierarchy h (columns = parameter
+ * sets or repeats); baths: host [n_baths] indices of the lead's baths in the order given
+ * to heom_build_hierarchy; I_out: host [batch]. A conductance is the difference quotient of
+ * currents at neighbouring biases (a batched stationary solve over the biases, then this
+ * call). Synchronises s. */
+heom_status heom_current(const heom_hier *h, const void *x, int64_t batch, const int *baths,
+                         int n_baths, double *I_out, heom_stream s);
+
 /* ---------------------------------------------------------------- learned warm start */
 
 /* A multilayer perceptron trained on stationary states the library computes, predicting the

@@ -74,6 +74,7 @@ _sig = {
                             _P],
     "heom_steady": [_P, _P, _P, C.c_int64, C.c_double, C.c_int, C.c_int, _P, _P],
     "heom_spectrum": [_P, _P, _P, _P, C.c_int64, C.c_double, C.c_int, _P, C.c_int, _P, _P],
+    "heom_current": [_P, _P, C.c_int64, _P, C.c_int, _P, _P],
     "heom_mlp_create": [C.c_int, _P, C.c_uint64, C.POINTER(_P)],
     "heom_mlp_info": [_P, _P, _P, _P],
     "heom_mlp_set_standardisation": [_P, _P, _P, _P, _P],
@@ -350,6 +351,17 @@ def spectrum(odd: Hierarchy, ss, op_d, omegas, tol: float = 1e-8, max_iter: int 
     if raise_on_error:
         _check(st, "heom_spectrum")
     return A, st, _stats_list(stats)
+
+
+def current(h: Hierarchy, x, baths, stream=None) -> np.ndarray:
+    """Electronic current into the lead made of ``baths`` for stationary states x
+    (N, d, d[, batch], complex128); one value per batch column."""
+    B = _batch_of(h, x)
+    idx = np.ascontiguousarray(baths, np.int32)
+    out = np.zeros(B)
+    _check(_lib.heom_current(h.handle, _dptr(x), B, _ptr(idx), len(idx), _ptr(out), _stream(stream)),
+           "heom_current")
+    return out
 
 
 # ------------------------------------------------------------------------- launch accounting

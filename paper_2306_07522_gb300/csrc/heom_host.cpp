@@ -582,6 +582,7 @@ extern "C" heom_status heom_build_hierarchy(int d, const heom_c64 *H, int n_bath
     }
     h->K = h->K_b + h->K_f;
     h->n_ops = n_ops;
+    h->bath_slot = op_slot_of_bath;
     if (h->K_f > 64) { set_error("heom_build_hierarchy: at most 64 fermionic exponents"); delete h; return HEOM_EINVAL; }
     if (h->K_b == 0) h->tier_b = 0;
     if (h->K_f < h->tier_f) h->tier_f = h->K_f;

@@ -145,6 +145,7 @@ struct heom_hier {
     std::vector<int> exp_bath;              // bath per global exponent
     std::vector<int> exp_nu;                // fermionic nu per global exponent (0 for bosons)
     std::vector<int> exp_partner;           // global index of the partner (fermions)
+    std::vector<int> bath_slot;             // first operator slot of each bath (fermions: d, then d^dagger)
     std::vector<heom_c64> ops;              // [n_ops][d][d]
     std::vector<heom_c64> H0;               // [n_sets][d][d]
     // device tables

@@ -1236,3 +1236,100 @@ extern "C" heom_status heom_spectrum(heom_hier *odd, const void *ss_ados, const 
     if (ret != HEOM_OK) set_error("heom_spectrum: some frequencies did not converge (see stats)");
     return ret;
 }
+
+// ------------------------------------------------------------------ electronic current
+namespace heom {
+namespace {
+
+// I[b] = Re(i sum_t sign_t Tr[O_t rho_{ado_t}]) for batch column b: one block per column,
+// threads over (term, row, column) triples, a fixed-order block reduction.
+__global__ void __launch_bounds__(128) k_current(int n_terms, int d, const int *__restrict__ ado,
+                                                 const int *__restrict__ sign, const cx<double> *__restrict__ O,
+                                                 const cx<double> *__restrict__ x, int64_t B, double *__restrict__ out) {
+    const int64_t b = blockIdx.x;
+    const int d2 = d * d;
+    __shared__ double s_im[128];
+    double acc = 0.0;  // Im of the signed trace sum
+    for (int w = threadIdx.x; w < n_terms * d2; w += blockDim.x) {
+        const int t = w / d2, e = w - t * d2, r = e / d, l = e - r * d;
+        // Tr[O rho] = sum_{r,l} O[r][l] rho[l][r]
+        const cx<double> o = O[(int64_t)t * d2 + r * d + l];
+        const cx<double> rho = x[((int64_t)ado[t] * d2 + l * d + r) * B + b];
+        acc += sign[t] * (o.re * rho.im + o.im * rho.re);
+    }
+    s_im[threadIdx.x] = acc;
+    __syncthreads();
+    for (int k = 64; k > 0; k >>= 1) {
+        if (threadIdx.x < k) s_im[threadIdx.x] += s_im[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[b] = -s_im[0];  // Re(i z) = -Im z
+}
+
+}  // namespace
+}  // namespace heom
+
+extern "C" heom_status heom_current(const heom_hier *h, const void *x, int64_t batch, const int *baths,
+                                    int n_baths, double *I_out, heom_stream s) {
+    using namespace heom;
+    if (!h || !x || !I_out || batch < 1 || n_baths < 1 || !baths || h->parity != 1 || h->tier_f < 1) {
+        set_error("heom_current: need an even-parity hierarchy with fermionic tier >= 1, x, batch >= 1, "
+                  "baths[n_baths >= 1] and I_out");
+        return HEOM_EINVAL;
+    }
+    std::vector<char> in_lead(h->bath_slot.size(), 0);
+    for (int i = 0; i < n_baths; ++i) {
+        if (baths[i] < 0 || baths[i] >= (int)h->bath_slot.size()) {
+            set_error("heom_current: bath index %d out of range", baths[i]);
+            return HEOM_EINVAL;
+        }
+        in_lead[baths[i]] = 1;
+    }
+    // tier-1 fermionic ADO {q} (bosonic part 0) of every exponent of the lead, with
+    // O = d^{-nu} (slot of d for nu = +1, of d^dagger for nu = -1) and sign nu
+    const int d = h->d, d2 = h->d2;
+    std::vector<int> ado, sign;
+    std::vector<heom_c64> O;
+    for (int q = 0; q < h->K_f; ++q) {
+        const int g = h->K_b + q, bath = h->exp_bath[g];
+        if (h->exp_kind[g] != HEOM_FERMION || !in_lead[bath]) continue;
+        int64_t idx = -1;
+        for (int64_t f = 0; f < h->N_f; ++f)
+            if (h->fer[f] == (1ULL << q)) { idx = f; break; }
+        if (idx < 0) continue;
+        const int nu = h->exp_nu[g];
+        const int slot = h->bath_slot[bath] + (nu == 1 ? 0 : 1);
+        ado.push_back((int)idx);  // bosonic index 0: ADO index = fermionic index
+        sign.push_back(nu);
+        O.insert(O.end(), h->ops.begin() + (size_t)slot * d2, h->ops.begin() + (size_t)(slot + 1) * d2);
+    }
+    if (ado.empty()) {
+        set_error("heom_current: the baths hold no fermionic exponents");
+        return HEOM_EINVAL;
+    }
+    HEOM_CUDA(cudaSetDevice(h->device));
+    cudaStream_t st = (cudaStream_t)s;
+    const int nt = (int)ado.size();
+    const size_t obytes = O.size() * sizeof(cx<double>), ooff = (obytes + (size_t)nt * 8 + 15) & ~size_t(15);
+    DBuf buf;
+    heom_status r = dalloc(buf, ooff + batch * sizeof(double));
+    if (r != HEOM_OK) return r;
+    char *base = (char *)buf.p;
+    cx<double> *dO = (cx<double> *)base;
+    int *dado = (int *)(base + obytes);
+    int *dsign = dado + nt;
+    double *dout = (double *)(base + ooff);
+    HEOM_CUDA(memcpy_counted(dO, O.data(), obytes, cudaMemcpyHostToDevice, st));
+    HEOM_CUDA(memcpy_counted(dado, ado.data(), nt * 4, cudaMemcpyHostToDevice, st));
+    HEOM_CUDA(memcpy_counted(dsign, sign.data(), nt * 4, cudaMemcpyHostToDevice, st));
+    {
+        Prof pr(HEOM_KC_OTHER, st, (double)batch * nt * d2);
+        k_current<<<(unsigned)batch, 128, 0, st>>>(nt, d, dado, dsign, dO, (const cx<double> *)x, batch, dout);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = memcpy_counted(I_out, dout, batch * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    dfree(buf);
+    if (e != cudaSuccess) return cuda_fail(e, "heom_current");
+    return HEOM_OK;
+}

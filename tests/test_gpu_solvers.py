@@ -232,3 +232,32 @@ def test_dos_parameter_sets_shifted(heom):
         Mo = lv.build_matrix(hy.model_to_problem(m, -1), h)
         Ao = so.dos(Mo, Xo, m.fermion_baths[0][0], om[idx])
         assert np.abs(A[j, idx] - Ao).max() < 1e-7 * np.abs(Ao).max(), j
+
+
+def test_current_matches_oracle(heom):
+    """Lead currents from the tier-1 ADOs of GPU stationary states (one parameter set, then
+    three biases batched as parameter sets) against the oracle's current of its own sparse-LU
+    stationary states; I_L + I_R = 0."""
+    import torch
+    biases = (1.0, 0.4, 2.2)
+    models = [W.siam_model(tier=2, mu=mu) for mu in biases]
+    g = heom.build_hierarchy(heom.problem_from_model(models[0]))
+    x = torch.zeros((g.n_ado, 4, 4), dtype=torch.complex128, device="cuda")
+    heom.steady(g, x, tol=1e-10, max_iter=3000, prec=heom.FP64)
+    IL1 = heom.current(g, x, [0, 1])[0]
+    IR1 = heom.current(g, x, [2, 3])[0]
+    gb = heom.build_hierarchy(heom.problem_from_model(models[0]))
+    _set_params_of(heom, gb, models, 1)
+    xb = torch.zeros((gb.n_ado, 4, 4, 3), dtype=torch.complex128, device="cuda")
+    heom.steady(gb, xb, tol=1e-10, max_iter=3000, prec=heom.FP64)
+    IL = heom.current(gb, xb, [0, 1])
+    IR = heom.current(gb, xb, [2, 3])
+    for j, m in enumerate(models):
+        prob = hy.model_to_problem(m)
+        h = hy.problem_hierarchy(prob)
+        X = so.steady_state(lv.build_matrix(prob, h), 4)
+        il, ir = so.current(prob, h, X, [0, 1]), so.current(prob, h, X, [2, 3])
+        assert abs(IL[j] - il) <= 1e-7 * abs(il), (j, IL[j], il)
+        assert abs(IR[j] - ir) <= 1e-7 * abs(ir), (j, IR[j], ir)
+        assert abs(IL[j] + IR[j]) <= 1e-7 * abs(il)
+    assert abs(IL1 - IL[0]) <= 1e-8 * abs(IL[0]) and abs(IR1 - IR[0]) <= 1e-8 * abs(IR[0])
