@@ -236,6 +236,19 @@ heom_status heom_spectrum(heom_hier *odd, const void *ss_ados, const heom_c64 *o
                           const double *omega, int64_t n_omega, double tol, int max_iter,
                           double *A_out, int prec, heom_solve_stats *stats, heom_stream s);
 
+/* Autotuner of the apply for one batch width (measurement of this GPU; the paper has no
+ * counterpart). Times heom_apply on a library-allocated test vector of `batch` columns in
+ * precision prec with the per-element kernel and with the tiled kernel at 1..5 ADO ranges
+ * per SM, and keeps the fastest in h: the tiled granularity for every later batched apply
+ * and solve, or, when the per-element kernel wins, the per-element kernel for batches up to
+ * `batch` columns. candidates_us: host [6] or NULL (index 0 per-element, p = 1..5 tiled with
+ * p ranges per SM, -1 where not applicable); tiled, ctas_per_sm, best_us: host or NULL.
+ * Results of the apply do not depend on the choice (the same terms, summed in the same
+ * order). Allocates two vectors of N d^2 batch elements for the duration of the call.
+ * Synchronises s. */
+heom_status heom_autotune(heom_hier *h, int64_t batch, int prec, double *candidates_us,
+                          int *tiled, int *ctas_per_sm, double *best_us, heom_stream s);
+
 /* Electronic current into lead alpha (Methods, electronic current; e = 1):
  * <I_alpha> = Re( i sum_q s_q Tr[d^{-nu_q} rho_q] ) over the fermionic exponents q of the
  * baths that form the lead, rho_q the tier-1 ADO with S = {q} (bosonic occupations zero),

@@ -75,6 +75,7 @@ _sig = {
     "heom_steady": [_P, _P, _P, C.c_int64, C.c_double, C.c_int, C.c_int, _P, _P],
     "heom_spectrum": [_P, _P, _P, _P, C.c_int64, C.c_double, C.c_int, _P, C.c_int, _P, _P],
     "heom_current": [_P, _P, C.c_int64, _P, C.c_int, _P, _P],
+    "heom_autotune": [_P, C.c_int64, C.c_int, _P, _P, _P, _P, _P],
     "heom_mlp_create": [C.c_int, _P, C.c_uint64, C.POINTER(_P)],
     "heom_mlp_info": [_P, _P, _P, _P],
     "heom_mlp_set_standardisation": [_P, _P, _P, _P, _P],
@@ -351,6 +352,16 @@ def spectrum(odd: Hierarchy, ss, op_d, omegas, tol: float = 1e-8, max_iter: int 
     if raise_on_error:
         _check(st, "heom_spectrum")
     return A, st, _stats_list(stats)
+
+
+def autotune(h: Hierarchy, batch: int, prec: int = FP32, stream=None) -> dict:
+    """heom_autotune: time the apply's kernel choices for `batch` columns, keep the fastest."""
+    cand = np.zeros(6)
+    t, p, best = C.c_int(), C.c_int(), C.c_double()
+    _check(_lib.heom_autotune(h.handle, batch, prec, _ptr(cand), C.byref(t), C.byref(p),
+                              C.byref(best), _stream(stream)), "heom_autotune")
+    return {"tiled": bool(t.value), "ctas_per_sm": p.value, "best_us": best.value,
+            "candidates_us": cand.tolist()}
 
 
 def current(h: Hierarchy, x, baths, stream=None) -> np.ndarray:

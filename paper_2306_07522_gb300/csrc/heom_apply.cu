@@ -8,6 +8,9 @@
 // read straight from global memory; re-reads of a block by its neighbours are served by L1
 // and L2. Operators are applied through their sparse row/column lists, so the d_sigma of
 // the fermionic baths cost one multiply-add per neighbour and side.
+#include <algorithm>
+#include <cstdint>
+
 #include "heom_tile.cuh"
 
 namespace heom {
@@ -112,5 +115,129 @@ extern "C" heom_status heom_apply(const heom_hier *h, const void *x, void *y, in
                                batch, m, (cudaStream_t)s);
     }
     if (e != cudaSuccess) return heom::cuda_fail(e, "heom_apply launch");
+    return HEOM_OK;
+}
+
+// ------------------------------------------------------------------ autotuner
+namespace heom {
+namespace {
+
+// deterministic bounded input: re, im of x[i] from a 64-bit mix of i, in [-1, 1)
+template <class R>
+__global__ void k_tune_fill(int64_t total, cx<R> *x) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t z = (uint64_t)i * 0x9e3779b97f4a7c15ULL;
+        z = (z ^ (z >> 31)) * 0xbf58476d1ce4e5b9ULL;
+        z ^= z >> 29;
+        const double a = (double)(z >> 40) * (1.0 / 8388608.0) - 1.0;
+        const double b = (double)((z >> 16) & 0xffffffULL) * (1.0 / 8388608.0) - 1.0;
+        x[i] = cx<R>{R(a), R(b)};
+    }
+}
+
+// average device time of `reps` applies of the hierarchy's current configuration
+template <class R>
+heom_status tune_time(heom_hier *h, const cx<R> *x, cx<R> *y, int64_t B, cudaStream_t s, double *us) {
+    const ApplyMods<R> m{nullptr, R(0)};
+    auto view = [&]() {
+        if constexpr (sizeof(R) == 8) return h->view64();
+        else return h->view32();
+    };
+    const DevView<R> cur = view();
+    cudaEvent_t e0, e1;
+    HEOM_CUDA(cudaEventCreate(&e0));
+    HEOM_CUDA(cudaEventCreate(&e1));
+    const int reps = 5;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = launch_apply(cur, x, y, B, m, s);  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    for (int k = 0; k < reps && e == cudaSuccess; ++k) e = launch_apply(cur, x, y, B, m, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "heom_autotune");
+    *us = 1e3 * ms / reps;
+    return HEOM_OK;
+}
+
+template <class R>
+heom_status autotune(heom_hier *h, int64_t B, double *cand, int *tiled, int *per_sm, double *best,
+                     cudaStream_t s) {
+    const int64_t total = h->N * h->d2 * B;
+    DBuf buf;
+    heom_status st = dalloc(buf, 2 * total * sizeof(cx<R>));
+    if (st != HEOM_OK) return st;
+    cx<R> *x = (cx<R> *)buf.p, *y = x + total;
+    k_tune_fill<R><<<(unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16), 256, 0, s>>>(total, x);
+    const int per_sm0 = h->tile_per_sm;
+    const int64_t min_b0 = h->tile_min_b;
+    // candidate 0: the per-element kernel (tiled kernel switched off)
+    h->tile_min_b = INT64_MAX;
+    double t0 = 0.0;
+    st = tune_time<R>(h, x, y, B, s, &t0);
+    cand[0] = t0;
+    int best_p = 0;
+    double best_t = t0;
+    // candidates 1..5: the tiled kernel with 1..5 ADO ranges per SM
+    const bool tile_possible = B >= 16 && h->n_sets == 1 && !(sizeof(R) == 4 && (B & 1));
+    for (int p = 1; p <= 5 && st == HEOM_OK; ++p) {
+        cand[p] = -1.0;
+        if (!tile_possible) continue;
+        if ((st = set_tile_partition(h, p)) != HEOM_OK) break;
+        h->tile_min_b = 16;
+        bool ok;
+        if constexpr (sizeof(R) == 8) ok = tile_ok(h->view64(), B);
+        else ok = tile_ok(h->view32(), B);
+        if (!ok) continue;  // ranges exceed the shared-memory budget
+        double t = 0.0;
+        if ((st = tune_time<R>(h, x, y, B, s, &t)) != HEOM_OK) break;
+        cand[p] = t;
+        if (t < best_t) { best_t = t; best_p = p; }
+    }
+    dfree(buf);
+    if (st != HEOM_OK) {  // leave the configuration as it was
+        set_tile_partition(h, per_sm0);
+        h->tile_min_b = min_b0;
+        return st;
+    }
+    // keep the winner: tiled with best_p ranges per SM, or the per-element kernel for batches
+    // up to this width (wider batches keep the tiled kernel at its default granularity)
+    if (best_p > 0) {
+        st = set_tile_partition(h, best_p);
+        h->tile_min_b = 16;
+    } else {
+        st = set_tile_partition(h, per_sm0 > 0 ? per_sm0 : 5);
+        h->tile_min_b = B + 1;
+    }
+    *tiled = best_p > 0;
+    *per_sm = best_p;
+    *best = best_t;
+    return st;
+}
+
+}  // namespace
+}  // namespace heom
+
+extern "C" heom_status heom_autotune(heom_hier *h, int64_t batch, int prec, double *candidates_us,
+                                     int *tiled, int *ctas_per_sm, double *best_us, heom_stream s) {
+    if (!h || batch < 1 || batch > 65535LL * 32 || (prec != HEOM_FP64 && prec != HEOM_FP32)) {
+        heom::set_error("heom_autotune: need a hierarchy, 1 <= batch <= 2097120, prec FP64 or FP32");
+        return HEOM_EINVAL;
+    }
+    HEOM_CUDA(cudaSetDevice(h->device));
+    double cand[6], best = 0.0;
+    int t = 0, p = 0;
+    const heom_status st = prec == HEOM_FP64
+                               ? heom::autotune<double>(h, batch, cand, &t, &p, &best, (cudaStream_t)s)
+                               : heom::autotune<float>(h, batch, cand, &t, &p, &best, (cudaStream_t)s);
+    if (st != HEOM_OK) return st;
+    if (candidates_us) for (int i = 0; i < 6; ++i) candidates_us[i] = cand[i];
+    if (tiled) *tiled = t;
+    if (ctas_per_sm) *ctas_per_sm = p;
+    if (best_us) *best_us = best;
     return HEOM_OK;
 }

@@ -309,7 +309,7 @@ heom::DevView<double> heom_hier::view64() const {
     v.th_vi = (const int32_t *)d_th_vi.p;
     v.max_terms = max_terms; v.max_entries = max_entries;
     v.cta_ado = (const int32_t *)d_cta_ado.p; v.n_ranges = n_ranges; v.range_terms = range_terms;
-    v.range_slots = range_slots; v.range_ados = range_ados;
+    v.range_slots = range_slots; v.range_ados = range_ados; v.tile_min_b = tile_min_b;
     v.pers_ado = (const int32_t *)d_pers_ado.p; v.pers_ranges = pers_ranges;
     v.pers_terms = pers_terms; v.pers_slots = pers_slots; v.pers_ados = pers_ados;
     return v;
@@ -337,7 +337,7 @@ heom::DevView<float> heom_hier::view32() const {
     v.th_vi = (const int32_t *)d_th_vi.p;
     v.max_terms = max_terms; v.max_entries = max_entries;
     v.cta_ado = (const int32_t *)d_cta_ado.p; v.n_ranges = n_ranges; v.range_terms = range_terms;
-    v.range_slots = range_slots; v.range_ados = range_ados;
+    v.range_slots = range_slots; v.range_ados = range_ados; v.tile_min_b = tile_min_b;
     v.pers_ado = (const int32_t *)d_pers_ado.p; v.pers_ranges = pers_ranges;
     v.pers_terms = pers_terms; v.pers_slots = pers_slots; v.pers_ados = pers_ados;
     return v;
@@ -360,6 +360,53 @@ void free_all(heom_hier *h) {
 
 // Upload the parameter-dependent arrays: H values on the shared pattern, (a, b) pairs,
 // rates, H diagonal and the damping floor, for n_sets sets.
+// Term count and shared-memory slots of every ADO's program (damping 1 per element, H, the
+// neighbour terms, the trace row of ADO 0).
+struct RangeCosts {
+    std::vector<int64_t> terms, slots;
+    int64_t total = 0;
+};
+RangeCosts range_costs(const heom_hier *h) {
+    RangeCosts rc;
+    rc.terms.resize(h->N);
+    rc.slots.resize(h->N);
+    for (int64_t i = 0; i < h->N; ++i) {
+        int64_t t = h->d2 + h->h_terms + (i == 0 ? h->d : 0);
+        for (int32_t k = h->row_ptr[i]; k < h->row_ptr[i + 1]; ++k) t += h->op_terms[h->ent[k].op];
+        rc.terms[i] = t;
+        rc.slots[i] = (int64_t)h->d2 * (h->row_ptr[i + 1] - h->row_ptr[i] + 3);
+        rc.total += t;
+    }
+    return rc;
+}
+
+// At most `resident` contiguous ranges; a range closes once it reaches the target term count
+// (or a shared-memory bound). Returns whether every range fits within the bounds.
+bool partition_ranges(const heom_hier *h, const RangeCosts &rc, int64_t resident, int64_t cap_terms,
+                      std::vector<int32_t> &rg, int64_t &rt, int64_t &rs, int64_t &rn) {
+    int64_t target = std::max<int64_t>(1, (rc.total + resident - 1) / resident);
+    for (int attempt = 0; attempt < 64; ++attempt) {
+        rg.assign(1, 0);
+        int64_t cur_t = 0, cur_s = 0, cur_n = 0;
+        rt = rs = rn = 0;
+        for (int64_t i = 0; i < h->N; ++i) {
+            const bool full = cur_n > 0 && (cur_t >= target || cur_t + rc.terms[i] > cap_terms ||
+                                            cur_s + rc.slots[i] > heom::kRangeSlots ||
+                                            cur_n >= heom::kRangeAdos);
+            if (full) {
+                rg.push_back((int32_t)i);
+                cur_t = cur_s = cur_n = 0;
+            }
+            cur_t += rc.terms[i]; cur_s += rc.slots[i]; ++cur_n;
+            rt = std::max(rt, cur_t); rs = std::max(rs, cur_s); rn = std::max(rn, cur_n);
+        }
+        rg.push_back((int32_t)h->N);
+        if ((int64_t)rg.size() - 1 <= resident) return true;
+        target += target / 8 + 1;
+    }
+    return false;
+}
+
 heom_status upload_params(heom_hier *h, int n_sets, const heom_c64 *H, const heom_c64 *coef,
                           const heom_c64 *rate) {
     const int d = h->d, K = h->K;
@@ -435,54 +482,21 @@ heom_status upload_params(heom_hier *h, int n_sets, const heom_c64 *H, const heo
         h->max_entries = me;
     }
     // ADO ranges: contiguous, about equal term counts, each range's program and bookkeeping
-    // bounded for shared memory. Tiled kernel: five CTAs per SM, all resident at once.
-    // Cooperative persistent solvers: one range per SM.
+    // bounded for shared memory. Tiled kernel: tile_per_sm CTAs per SM (five unless the
+    // autotuner chose otherwise), all resident at once. Cooperative persistent solvers: one
+    // range per SM.
     std::vector<int32_t> ranges, pranges;
     {
-        std::vector<int64_t> terms(h->N), slots(h->N);
-        int64_t total = 0;
-        for (int64_t i = 0; i < h->N; ++i) {
-            int64_t t = h->d2 + h->h_terms + (i == 0 ? d : 0);
-            for (int32_t k = h->row_ptr[i]; k < h->row_ptr[i + 1]; ++k) t += h->op_terms[h->ent[k].op];
-            terms[i] = t;
-            slots[i] = (int64_t)h->d2 * (h->row_ptr[i + 1] - h->row_ptr[i] + 3);
-            total += t;
-        }
-        // at most `resident` ranges; a range closes once it reaches the target term count (or
-        // a shared-memory bound). Returns whether every range fits within the bounds.
-        auto partition = [&](int64_t resident, int64_t cap_terms, std::vector<int32_t> &rg, int64_t &rt,
-                             int64_t &rs, int64_t &rn) {
-            int64_t target = std::max<int64_t>(1, (total + resident - 1) / resident);
-            for (int attempt = 0; attempt < 64; ++attempt) {
-                rg.assign(1, 0);
-                int64_t cur_t = 0, cur_s = 0, cur_n = 0;
-                rt = rs = rn = 0;
-                for (int64_t i = 0; i < h->N; ++i) {
-                    const bool full = cur_n > 0 && (cur_t >= target || cur_t + terms[i] > cap_terms ||
-                                                    cur_s + slots[i] > heom::kRangeSlots ||
-                                                    cur_n >= heom::kRangeAdos);
-                    if (full) {
-                        rg.push_back((int32_t)i);
-                        cur_t = cur_s = cur_n = 0;
-                    }
-                    cur_t += terms[i]; cur_s += slots[i]; ++cur_n;
-                    rt = std::max(rt, cur_t); rs = std::max(rs, cur_s); rn = std::max(rn, cur_n);
-                }
-                rg.push_back((int32_t)h->N);
-                if ((int64_t)rg.size() - 1 <= resident) return true;
-                target += target / 8 + 1;
-            }
-            return false;
-        };
+        RangeCosts rc = range_costs(h);
         int n_sm = 152;
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, h->device);
         int64_t rt, rs, rn;
-        partition(152 * 5, heom::kRangeTerms, ranges, rt, rs, rn);
+        partition_ranges(h, rc, (int64_t)n_sm * h->tile_per_sm, heom::kRangeTerms, ranges, rt, rs, rn);
         h->n_ranges = (int)ranges.size() - 1;
         h->range_terms = (int)std::min<int64_t>(rt, INT32_MAX);
         h->range_slots = (int)std::min<int64_t>(rs, INT32_MAX);
         h->range_ados = (int)rn;
-        const bool pfit = partition(n_sm, heom::kPersistTerms, pranges, rt, rs, rn);
+        const bool pfit = partition_ranges(h, rc, n_sm, heom::kPersistTerms, pranges, rt, rs, rn);
         h->pers_ranges = (pfit && rt <= heom::kPersistTerms && rs <= heom::kRangeSlots) ? (int)pranges.size() - 1 : 0;
         h->pers_terms = (int)std::min<int64_t>(rt, INT32_MAX);
         h->pers_slots = (int)std::min<int64_t>(rs, INT32_MAX);
@@ -880,6 +894,31 @@ void prof_add(int cls, double units, double bytes) {
     if (!g_prof.on) return;
     g_prof.units[cls] += units;
     g_prof.bytes[cls] += bytes;
+}
+}  // namespace heom
+
+namespace heom {
+heom_status set_tile_partition(heom_hier *h, int per_sm) {
+    if (per_sm < 1 || per_sm > 5) {
+        set_error("tile partition: 1..5 CTAs per SM");
+        return HEOM_EINVAL;
+    }
+    HEOM_CUDA(cudaSetDevice(h->device));
+    RangeCosts rc = range_costs(h);
+    int n_sm = 152;
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, h->device);
+    std::vector<int32_t> ranges;
+    int64_t rt, rs, rn;
+    partition_ranges(h, rc, (int64_t)n_sm * per_sm, kRangeTerms, ranges, rt, rs, rn);
+    dfree(h->d_cta_ado);
+    heom_status st = upload(h->d_cta_ado, ranges);
+    if (st != HEOM_OK) return st;
+    h->n_ranges = (int)ranges.size() - 1;
+    h->range_terms = (int)std::min<int64_t>(rt, INT32_MAX);
+    h->range_slots = (int)std::min<int64_t>(rs, INT32_MAX);
+    h->range_ados = (int)rn;
+    h->tile_per_sm = per_sm;
+    return HEOM_OK;
 }
 }  // namespace heom
 

@@ -106,6 +106,7 @@ struct DevView {
     // ADO ranges of the persistent tiled kernel (one CTA each, balanced by term count)
     const int32_t *cta_ado;   // [n_ranges + 1]
     int n_ranges;
+    int64_t tile_min_b;       // smallest batch that takes the tiled kernel (autotuned, >= 16)
     int range_terms;          // largest program of one range (terms)
     int range_slots;          // largest sum over a range of d2 * (entries + 3)
     int range_ados;           // largest number of ADOs in a range
@@ -160,6 +161,8 @@ struct heom_hier {
     int h_terms = 0, max_terms = 0, max_entries = 0;
     heom::DBuf d_cta_ado, d_pers_ado;
     int n_ranges = 0, range_terms = 0, range_slots = 0, range_ados = 0;
+    int tile_per_sm = 5;        // tiled kernel: ADO ranges per SM (autotuned)
+    int64_t tile_min_b = 16;    // tiled kernel from this batch on (autotuned)
     int pers_ranges = 0, pers_terms = 0, pers_slots = 0, pers_ados = 0;
     // device parameters (per set), both precisions
     heom::DBuf d_hval64, d_hval32, d_coefL64, d_coefL32, d_coefR64, d_coefR32, d_rate64,
@@ -173,6 +176,9 @@ struct heom_hier {
 };
 
 namespace heom {
+
+// re-partition the ADO ranges of the tiled kernel for per_sm CTAs per SM (1..5) and upload
+heom_status set_tile_partition(heom_hier *h, int per_sm);
 
 // error reporting (thread-local message)
 void set_error(const char *fmt, ...);

@@ -453,7 +453,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, 5) k_tile(TileArgs<R> a) {
 // its shared-memory budget.
 template <class R>
 inline bool tile_ok(const DevView<R> &v, int64_t B) {
-    if (B < 16 || v.n_sets != 1 || v.n_ranges < 1) return false;
+    if (B < 16 || B < v.tile_min_b || v.n_sets != 1 || v.n_ranges < 1) return false;
     if (VecT<R>::VC == 2 && (B & 1)) return false;
     if (v.range_terms > kRangeTerms || v.range_slots > kRangeSlots) return false;
     return tile_smem_bytes(v) <= 200 * 1024;

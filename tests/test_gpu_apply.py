@@ -183,3 +183,29 @@ def test_apply_paper_scale_example1_sampled(heom):
     X = x.cpu().numpy()
     Y = lv.apply_loop(prob_o, X, h, only=only)
     assert rel_err(y.cpu().numpy()[only], Y[only]) < TOL["fp64"]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_autotune_choice_keeps_parity(heom, prec):
+    """The autotuner times the per-element and the tiled kernel (1..5 ADO ranges per SM) for
+    64 columns and keeps the fastest; the apply under the chosen configuration still matches
+    the oracle, and a batch too narrow for the tiled kernel tunes to the per-element one."""
+    import torch
+    m = W.siam_model(tier=2)
+    prob = hy.model_to_problem(m)
+    h = hy.problem_hierarchy(prob)
+    g = heom.build_hierarchy(heom.problem_from_model(m))
+    P = heom.FP32 if prec == "fp32" else heom.FP64
+    res = heom.autotune(g, 64, P)
+    cand = res["candidates_us"]
+    valid = [c for c in cand if c > 0]
+    assert cand[0] > 0 and len(valid) >= 2
+    assert res["best_us"] == min(valid)
+    assert res["tiled"] == (res["ctas_per_sm"] > 0)
+    X = W.random_ado_vector(h.n_ado, 4, 64, seed=41)
+    Y = oracle_apply_batched(prob, h, X)
+    dt = torch.complex64 if prec == "fp32" else torch.complex128
+    Yg = heom.apply(g, to_dev(X, dt), torch.empty_like(to_dev(X, dt))).cpu().numpy()
+    assert rel_err(Yg, Y) < TOL[prec]
+    narrow = heom.autotune(g, 8, P)
+    assert not narrow["tiled"] and all(c < 0 for c in narrow["candidates_us"][1:])
