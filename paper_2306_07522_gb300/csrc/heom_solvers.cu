@@ -635,6 +635,19 @@ heom_status bicgstab(heom_hier *h, const cx<R> *bvec, cx<R> *x, int64_t B, const
     std::vector<int> best_it(Bc, 0);
     for (int64_t j = 0; j < Bc; ++j) best[j] = hs[j].acc_nr;
     int it = 0, check = 4;
+    cudaGraphExec_t gexec = nullptr;  // one BiCGStab iteration as a graph (see below)
+    cudaStream_t gcap = nullptr;
+    const void *gkey_x = nullptr;
+    int64_t gkey_B = -1;
+    bool gkey_tiled = false;
+    struct GraphRelease {
+        cudaGraphExec_t &e;
+        cudaStream_t &c;
+        ~GraphRelease() {
+            if (e) cudaGraphExecDestroy(e);
+            if (c) cudaStreamDestroy(c);
+        }
+    } graph_release{gexec, gcap};
     while (n_act > 0 && it < max_iter) {
         // ---- re-compaction when the active columns fall to 60 % of the working width
         if (compact && n_act <= 0.6 * Bc && Bc - n_act >= 16) {
@@ -696,20 +709,60 @@ heom_status bicgstab(heom_hier *h, const cx<R> *bvec, cx<R> *x, int64_t B, const
         const int64_t cps = Bc / h->n_sets;
         const double u_vec = (double)rows * Bc, u_app = (double)h->N * Bc;
         const double sz = sizeof(cx<R>), e_vec = u_vec * sz;
-        for (int k = 0; k < steps; ++k) {
-            { Prof pr(HEOM_KC_KRYLOV_VECTOR, s, u_vec, 5.0 * e_vec);
-              k_bicg_p<R><<<gv.grid, gv.block, 0, s>>>(v, r, p, vv, ph, rh, Bc, cps, shc, 1, st); }
-            { Prof pr(kc_apply, s, u_app, 3.0 * e_vec);
-              if (tiled) { ta.x = ph; ta.out = vv; ta.w = rh; HEOM_CUDA((launch_tile<R, TM_BICG_V>(ta, s))); }
-              else k_bicg_apply<R><<<gd.grid, gd.block, 0, s>>>(v, ph, vv, rh, Bc, cps, mods, 0, st); }
-            { Prof pr(HEOM_KC_KRYLOV_VECTOR, s, u_vec, 4.0 * e_vec);
-              k_bicg_s<R><<<gv.grid, gv.block, 0, s>>>(v, r, vv, sh, Bc, cps, shc, 1, st); }
-            { Prof pr(kc_apply, s, u_app, 3.0 * e_vec);
-              if (tiled) { ta.x = sh; ta.out = t; ta.w = r; HEOM_CUDA((launch_tile<R, TM_BICG_T>(ta, s))); }
-              else k_bicg_apply<R><<<gd.grid, gd.block, 0, s>>>(v, sh, t, r, Bc, cps, mods, 1, st); }
-            { Prof pr(HEOM_KC_KRYLOV_VECTOR, s, u_vec, 8.0 * e_vec);
-              k_bicg_x<R><<<gd.grid, gd.block, 0, s>>>(rows, xw, ph, sh, r, t, rh, Bc, st); }
+        // one iteration: five kernels on stream q (event brackets when accounting is on)
+        auto launch_iter = [&](cudaStream_t q, bool prof, bool set_attr) -> cudaError_t {
+            cudaError_t e = cudaSuccess;
+            { Prof pr(HEOM_KC_KRYLOV_VECTOR, q, u_vec, 5.0 * e_vec); pr.on = pr.on && prof;
+              k_bicg_p<R><<<gv.grid, gv.block, 0, q>>>(v, r, p, vv, ph, rh, Bc, cps, shc, 1, st); }
+            { Prof pr(kc_apply, q, u_app, 3.0 * e_vec); pr.on = pr.on && prof;
+              if (tiled) { ta.x = ph; ta.out = vv; ta.w = rh; e = launch_tile<R, TM_BICG_V>(ta, q, set_attr); }
+              else k_bicg_apply<R><<<gd.grid, gd.block, 0, q>>>(v, ph, vv, rh, Bc, cps, mods, 0, st); }
+            if (e != cudaSuccess) return e;
+            { Prof pr(HEOM_KC_KRYLOV_VECTOR, q, u_vec, 4.0 * e_vec); pr.on = pr.on && prof;
+              k_bicg_s<R><<<gv.grid, gv.block, 0, q>>>(v, r, vv, sh, Bc, cps, shc, 1, st); }
+            { Prof pr(kc_apply, q, u_app, 3.0 * e_vec); pr.on = pr.on && prof;
+              if (tiled) { ta.x = sh; ta.out = t; ta.w = r; e = launch_tile<R, TM_BICG_T>(ta, q, set_attr); }
+              else k_bicg_apply<R><<<gd.grid, gd.block, 0, q>>>(v, sh, t, r, Bc, cps, mods, 1, st); }
+            if (e != cudaSuccess) return e;
+            { Prof pr(HEOM_KC_KRYLOV_VECTOR, q, u_vec, 8.0 * e_vec); pr.on = pr.on && prof;
+              k_bicg_x<R><<<gd.grid, gd.block, 0, q>>>(rows, xw, ph, sh, r, t, rh, Bc, st); }
+            return cudaGetLastError();
+        };
+        // Without launch accounting the iteration runs as a CUDA graph, captured once per
+        // column layout on a private stream and replayed on s (five launches become one);
+        // if capture or instantiation fails, the kernels are launched directly.
+        bool graphed = false;
+        if (!prof_on()) {
+            if (!gexec || gkey_x != (const void *)cur[0] || gkey_B != Bc || gkey_tiled != tiled) {
+                if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+                gkey_x = cur[0];
+                gkey_B = Bc;
+                gkey_tiled = tiled;
+                if (!gcap) cudaStreamCreateWithFlags(&gcap, cudaStreamNonBlocking);
+                if (gcap) {
+                    if (tiled) {  // shared-memory opt-in set outside the capture
+                        HEOM_CUDA((launch_tile_attr<R, TM_BICG_V>(ta)));
+                        HEOM_CUDA((launch_tile_attr<R, TM_BICG_T>(ta)));
+                    }
+                    cudaGraph_t graph = nullptr;
+                    if (cudaStreamBeginCapture(gcap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                        const cudaError_t e1 = launch_iter(gcap, false, false);
+                        const cudaError_t e2 = cudaStreamEndCapture(gcap, &graph);
+                        if (e1 == cudaSuccess && e2 == cudaSuccess && graph &&
+                            cudaGraphInstantiate(&gexec, graph, 0) != cudaSuccess)
+                            gexec = nullptr;
+                        if (graph) cudaGraphDestroy(graph);
+                    }
+                    cudaGetLastError();  // a failed capture leaves no error behind
+                }
+            }
+            if (gexec) {
+                for (int k = 0; k < steps; ++k) HEOM_CUDA(cudaGraphLaunch(gexec, s));
+                graphed = true;
+            }
         }
+        if (!graphed)
+            for (int k = 0; k < steps; ++k) HEOM_CUDA(launch_iter(s, true, true));
         HEOM_CUDA(cudaGetLastError());
         it += steps;
         HEOM_CUDA(memcpy_counted(hs.data(), st, Bc * sizeof(ColState), cudaMemcpyDeviceToHost, s));

@@ -459,10 +459,18 @@ inline bool tile_ok(const DevView<R> &v, int64_t B) {
     return tile_smem_bytes(v) <= 200 * 1024;
 }
 
+// the dynamic shared-memory opt-in of k_tile<R, MODE> for this view (not a stream operation)
 template <class R, int MODE>
-inline cudaError_t launch_tile(const TileArgs<R> &a, cudaStream_t s) {
+inline cudaError_t launch_tile_attr(const TileArgs<R> &a) {
     const size_t sm = tile_smem_bytes(a.v);
-    if (sm > 48 * 1024) {
+    if (sm <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(k_tile<R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+}
+
+template <class R, int MODE>
+inline cudaError_t launch_tile(const TileArgs<R> &a, cudaStream_t s, bool set_attr = true) {
+    const size_t sm = tile_smem_bytes(a.v);
+    if (set_attr && sm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_tile<R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
     }
