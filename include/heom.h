@@ -236,6 +236,19 @@ heom_status heom_spectrum(heom_hier *odd, const void *ss_ados, const heom_c64 *o
                           const double *omega, int64_t n_omega, double tol, int max_iter,
                           double *A_out, int prec, heom_solve_stats *stats, heom_stream s);
 
+/* Power spectral density of the mode op_a (Methods, numerical computation of the spectrum,
+ * bosonic case): pi S(w) = -Re Tr[a^dag x_0] with (M - i w) x = a rho over every ADO, M of the
+ * even-parity hierarchy `even` whose stationary state is ss_ados (device complex128
+ * [N][d][d][n_sets]). Solved by the shift-invariant Krylov method of HEOM_SHIFTED (one
+ * process per parameter set serves every frequency). op_a: host d x d; omega: host
+ * [n_omega]; S_out: host [n_sets][n_omega]; stats: host [n_sets][n_omega] or NULL.
+ * Converged when the residual estimate ||b - (M - i w) x|| / ||b|| <= tol. At w = 0 the
+ * system is singular (M has the stationary state as null vector) unless Tr[a rho] = 0;
+ * such a frequency returns HEOM_ENOCONV in its stats. Synchronises s. */
+heom_status heom_psd(heom_hier *even, const void *ss_ados, const heom_c64 *op_a, const double *omega,
+                     int64_t n_omega, double tol, int max_iter, double *S_out,
+                     heom_solve_stats *stats, heom_stream s);
+
 /* Autotuner of the apply for one batch width (measurement of this GPU; the paper has no
  * counterpart). Times heom_apply on a library-allocated test vector of `batch` columns in
  * precision prec with the per-element kernel and with the tiled kernel at 1..5 ADO ranges

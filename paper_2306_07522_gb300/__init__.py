@@ -75,6 +75,7 @@ _sig = {
     "heom_steady": [_P, _P, _P, C.c_int64, C.c_double, C.c_int, C.c_int, _P, _P],
     "heom_spectrum": [_P, _P, _P, _P, C.c_int64, C.c_double, C.c_int, _P, C.c_int, _P, _P],
     "heom_current": [_P, _P, C.c_int64, _P, C.c_int, _P, _P],
+    "heom_psd": [_P, _P, _P, _P, C.c_int64, C.c_double, C.c_int, _P, _P, _P],
     "heom_autotune": [_P, C.c_int64, C.c_int, _P, _P, _P, _P, _P],
     "heom_mlp_create": [C.c_int, _P, C.c_uint64, C.POINTER(_P)],
     "heom_mlp_info": [_P, _P, _P, _P],
@@ -362,6 +363,21 @@ def autotune(h: Hierarchy, batch: int, prec: int = FP32, stream=None) -> dict:
                               C.byref(best), _stream(stream)), "heom_autotune")
     return {"tiled": bool(t.value), "ctas_per_sm": p.value, "best_us": best.value,
             "candidates_us": cand.tolist()}
+
+
+def psd(even: Hierarchy, ss, op_a, omegas, tol: float = 1e-8, max_iter: int = 2000, stream=None,
+        raise_on_error: bool = True):
+    """Power spectral density S(w) of mode op_a; returns (S, status, stats). With several
+    parameter sets, ss is (N, d, d, n_sets) and S is (n_sets, n_omega)."""
+    op = _c64(op_a)
+    om = np.ascontiguousarray(omegas, np.float64)
+    S = np.zeros(len(om)) if even.n_sets == 1 else np.zeros((even.n_sets, len(om)))
+    stats = (SolveStats * (len(om) * even.n_sets))()
+    st = _lib.heom_psd(even.handle, _dptr(ss), _ptr(op), _ptr(om), len(om), tol, max_iter, _ptr(S),
+                       C.cast(stats, C.c_void_p), _stream(stream))
+    if raise_on_error:
+        _check(st, "heom_psd")
+    return S, st, _stats_list(stats)
 
 
 def current(h: Hierarchy, x, baths, stream=None) -> np.ndarray:

@@ -1224,6 +1224,76 @@ static heom_status spectrum_shifted(heom_hier *odd, const void *ss_ados, const h
     return ret;
 }
 
+// b[row][s] = (a rho_s)[row]: left multiplication of every ADO of set s's stationary state
+// (ss [N][d][d][ns]) by the d x d operator a
+__global__ void k_psd_rhs(int64_t N, int d, const cx<double> *__restrict__ ss, const cx<double> *__restrict__ A,
+                          cx<double> *__restrict__ bvec, int64_t ns) {
+    const int64_t total = N * d * d * ns;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t set = i % ns, row = i / ns;
+        const int64_t n = row / (d * d);
+        const int e = (int)(row - n * d * d), r = e / d, c = e - r * d;
+        cx<double> acc{0.0, 0.0};
+        for (int l = 0; l < d; ++l) fma_to(acc, A[r * d + l], ss[(n * d * d + l * d + c) * ns + set]);
+        bvec[i] = acc;
+    }
+}
+
+extern "C" heom_status heom_psd(heom_hier *even, const void *ss_ados, const heom_c64 *op_a,
+                                const double *omega, int64_t n_omega, double tol, int max_iter,
+                                double *S_out, heom_solve_stats *stats, heom_stream s) {
+    if (!even || !ss_ados || !op_a || !omega || n_omega < 1 || !(tol > 0) || max_iter < 1 || !S_out ||
+        even->parity != 1) {
+        set_error("heom_psd: need an even-parity hierarchy, ss_ados, op_a, omega[n_omega >= 1], S_out, "
+                  "tol > 0 and max_iter >= 1");
+        return HEOM_EINVAL;
+    }
+    HEOM_CUDA(cudaSetDevice(even->device));
+    cudaStream_t st = (cudaStream_t)s;
+    const int d = even->d, d2 = d * d;
+    const int64_t ns = even->n_sets, B = ns, rows = even->N * even->d2, L = rows * B;
+    DBuf buf;
+    heom_status stt = dalloc(buf, L * sizeof(cx<double>) + d2 * sizeof(cx<double>));
+    if (stt != HEOM_OK) return stt;
+    cx<double> *b64 = (cx<double> *)buf.p, *A = b64 + L;
+    HEOM_CUDA(memcpy_counted(A, op_a, d2 * sizeof(cx<double>), cudaMemcpyHostToDevice, st));
+    { Prof pr(HEOM_KC_OTHER, st, (double)L);
+      k_psd_rhs<<<flat_blocks(L), 256, 0, st>>>(even->N, d, (const cx<double> *)ss_ados, A, b64, ns); }
+    const int64_t S = n_omega * ns;
+    std::vector<cx<double>> shift(S);
+    std::vector<int> col_of(S);
+    for (int64_t set = 0; set < ns; ++set)
+        for (int64_t j = 0; j < n_omega; ++j) {
+            shift[set * n_omega + j] = {0.0, -omega[j]};  // (M - i w) x = a rho
+            col_of[set * n_omega + j] = (int)set;
+        }
+    std::vector<cx<double>> x0;
+    std::vector<double> res;
+    int steps = 0;
+    stt = shifted_gmres(even, b64, B, shift, col_of, 0.5 * tol, std::max(1, std::min(max_iter, 2000)), x0,
+                        res, &steps, st);
+    dfree(buf);
+    if (stt != HEOM_OK) return stt;
+    heom_status ret = HEOM_OK;
+    for (int64_t k = 0; k < S; ++k) {
+        // pi S(w) = -Re Tr[a^dag x_0], Tr[a^dag X] = sum_{i,l} conj(a[l][i]) X[l][i]
+        double acc = 0.0;
+        for (int i = 0; i < d; ++i)
+            for (int l = 0; l < d; ++l) {
+                const cx<double> xv = x0[(size_t)k * d2 + l * d + i];
+                const cx<double> ah{op_a[l * d + i].re, -op_a[l * d + i].im};
+                acc += (ah * xv).re;
+            }
+        S_out[k] = -acc / M_PI;
+        const int status = (std::isfinite(res[k]) && res[k] <= tol) ? HEOM_OK : HEOM_ENOCONV;
+        if (status != HEOM_OK && ret == HEOM_OK) ret = HEOM_ENOCONV;
+        if (stats) stats[k] = heom_solve_stats{steps, 0, res[k], status};
+    }
+    if (ret != HEOM_OK) set_error("heom_psd: some frequencies did not converge (see stats)");
+    return ret;
+}
+
 extern "C" heom_status heom_spectrum(heom_hier *odd, const void *ss_ados, const heom_c64 *op_d,
                                      const double *omega, int64_t n_omega, double tol,
                                      int max_iter, double *A_out, int prec,

@@ -261,3 +261,43 @@ def test_current_matches_oracle(heom):
         assert abs(IR[j] - ir) <= 1e-7 * abs(ir), (j, IR[j], ir)
         assert abs(IL[j] + IR[j]) <= 1e-7 * abs(il)
     assert abs(IL1 - IL[0]) <= 1e-8 * abs(IL[0]) and abs(IR1 - IR[0]) <= 1e-8 * abs(IR[0])
+
+
+def test_psd_matches_oracle_and_sum_rule(heom):
+    """Bosonic power spectrum by the shift-invariant solver: spin-boson sigma_z against the
+    oracle's sparse-LU PSD at sampled frequencies and, over 4,000 frequencies, the sum rule
+    (integral of S = <sigma_z sigma_z> = 1 since the stationary <sigma_z> vanishes); SIAM
+    spin-up occupation against the oracle."""
+    import torch
+    m = W.spin_boson_model(tier=4)
+    prob = hy.model_to_problem(m, 1)
+    h = hy.problem_hierarchy(prob)
+    M = lv.build_matrix(prob, h)
+    Xo = so.steady_state(M, m.d)
+    g = heom.build_hierarchy(heom.problem_from_model(m, 1))
+    x = torch.zeros((g.n_ado, 2, 2), dtype=torch.complex128, device="cuda")
+    heom.steady(g, x, tol=1e-11, max_iter=3000, prec=heom.FP64)
+    sz = np.diag([1.0, -1.0]).astype(complex)
+    om = np.linspace(-50, 50, 4000)
+    S, st, stats = heom.psd(g, x, sz, om, tol=1e-10, max_iter=1500)
+    assert st == heom.OK and max(s_["residual"] for s_ in stats) <= 1e-10
+    idx = np.array([0, 700, 1500, 1999, 2000, 2600, 3999])
+    So = so.psd(M, Xo, sz, om[idx])
+    assert np.abs(S[idx] - So).max() < 1e-7 * np.abs(So).max()
+    assert abs(np.trapezoid(S, om) - 1.0) < 1e-6
+    # SIAM (tier 2): occupation of the spin-up level, n = d^dag d
+    ms = W.siam_model(tier=2)
+    ps = hy.model_to_problem(ms, 1)
+    hs = hy.problem_hierarchy(ps)
+    Ms = lv.build_matrix(ps, hs)
+    Xs = so.steady_state(Ms, 4)
+    dup = ms.fermion_baths[0][0]
+    nup = dup.conj().T @ dup
+    gs = heom.build_hierarchy(heom.problem_from_model(ms, 1))
+    xs = torch.zeros((gs.n_ado, 4, 4), dtype=torch.complex128, device="cuda")
+    heom.steady(gs, xs, tol=1e-11, max_iter=3000, prec=heom.FP64)
+    oms = np.array([-12.0, -5.0, -1.3, 0.7, 3.0, 9.0])
+    Sg, st, stats = heom.psd(gs, xs, nup, oms, tol=1e-10, max_iter=1500)
+    assert st == heom.OK
+    Sso = so.psd(Ms, Xs, nup, oms)
+    assert np.abs(Sg - Sso).max() < 1e-7 * np.abs(Sso).max()

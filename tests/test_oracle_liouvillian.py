@@ -273,3 +273,20 @@ def test_integer_tables_reproduce_the_apply(parity):
     Y1 = lv.apply_loop(prob, X, h)
     Y3 = tb.apply_from_tables(prob, X, h)
     assert np.abs(Y1 - Y3).max() <= 1e-13 * np.abs(Y1).max()
+
+
+def test_psd_sum_rule_spin_boson():
+    """The PSD is the real part of the Laplace transform of the correlation function
+    C(t) = Tr[a^dag e^{Mt}(a rho_ss)], so its integral over all frequencies is Re C(0) =
+    <a^dag a> when the stationary <a> vanishes. Spin-boson with H = (Delta/2) sigma_x: the
+    stationary <sigma_z> is 0 by symmetry and <sigma_z sigma_z> = 1."""
+    m = W.spin_boson_model(tier=4)
+    prob = hy.model_to_problem(m, 1)
+    h = hy.problem_hierarchy(prob)
+    M = lv.build_matrix(prob, h)
+    X = so.steady_state(M, m.d)
+    sz = np.diag([1.0, -1.0]).astype(complex)
+    assert abs(np.trace(sz @ X[0])) < 1e-12
+    om = np.linspace(-50, 50, 4000)  # an even count: omega = 0 (the zero mode) is not sampled
+    S = so.psd(M, X, sz, om)
+    assert abs(np.trapezoid(S, om) - 1.0) < 1e-6
