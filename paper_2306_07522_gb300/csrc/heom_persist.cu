@@ -116,12 +116,33 @@ __device__ __forceinline__ bool grid_sum(double (&val)[NV], double *part, int sl
     return true;
 }
 
-__device__ __forceinline__ cx<double> cplx_div(cx<double> a, cx<double> b) { return cdiv(a, b); }
+// 1/x by Newton-Raphson (r <- r (2 - x r), written r + r (1 - x r)) from the FP32 reciprocal
+// as seed: the seed's relative error (<= 2^-23) squares at each step, so two steps reach FP64
+// rounding. An FP64 division is a long instruction sequence on GB300's narrow FP64 pipe; this
+// is six FP64-pipe instructions. Outside the seed's range (and for 0, inf, NaN) the plain
+// division is used.
+__device__ __forceinline__ double nr_rcp(double x) {
+    const double ax = fabs(x);
+    if (!(ax > 1e-30 && ax < 1e30)) return 1.0 / x;
+    double r = (double)__frcp_rn((float)x);
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+}
+__device__ __forceinline__ cx<double> cplx_div(cx<double> a, cx<double> b) {
+    const double inv = nr_rcp(b.re * b.re + b.im * b.im);
+    return cx<double>{(a.re * b.re + a.im * b.im) * inv, (a.im * b.re - a.re * b.im) * inv};
+}
 __device__ __forceinline__ bool finite_c(cx<double> a) { return isfinite(a.re) && isfinite(a.im); }
 
 template <class R>
 __global__ void __launch_bounds__(kPersThreads) k_persist_bicg(PersistArgs<R> a) {
     unsigned gen = 0;  // barriers this block has passed (the barrier starts zeroed)
+    // Krylov scalars are computed once per CTA by thread 0 and broadcast (every CTA derives
+    // the same values from the same grid sums); redundant FP64 divisions in all 16 warps
+    // would queue on the FP64 pipe
+    __shared__ double s_sc[8];
     const DevView<R> &v = a.v;
     const int d2 = v.d2;
     const int n0 = __ldg(v.pers_ado + blockIdx.x), n1 = __ldg(v.pers_ado + blockIdx.x + 1);
@@ -166,14 +187,24 @@ __global__ void __launch_bounds__(kPersThreads) k_persist_bicg(PersistArgs<R> a)
     double best = nr, rhn = nr;  // rhn = ||rh||^2
     int best_it = 0;
     for (int iter = 1; status < 0 && iter <= a.max_iter; ++iter) {
-        // ---- restart when rh has become nearly orthogonal to r: rh = r, p = r
-        const bool restart = iter > 1 && norm2(rho) < kRestartTau2 * rhn * nr;
+        // ---- restart when rh has become nearly orthogonal to r: rh = r, p = r;
+        // beta = (rho / rho_old)(alpha / omega)
+        if (threadIdx.x == 0) {
+            const bool rs = iter > 1 && norm2(rho) < kRestartTau2 * rhn * nr;
+            const cx<double> rr = rs ? cx<double>{nr, 0.0} : rho;
+            const cx<double> bb = cplx_div(rr, rho_old) * cplx_div(alpha, omega);
+            s_sc[0] = rs ? 1.0 : 0.0;
+            s_sc[1] = bb.re;
+            s_sc[2] = bb.im;
+        }
+        __syncthreads();
+        const bool restart = s_sc[0] != 0.0;
+        const cx<double> beta{s_sc[1], s_sc[2]};
         if (restart) {
             rho = cx<double>{nr, 0.0};
             rhn = nr;
         }
         // ---- p = r + beta (p - omega v), ph = P^-1 p
-        const cx<double> beta = cplx_div(rho, rho_old) * cplx_div(alpha, omega);
         const cx<R> bt = cast<R>(beta), om = cast<R>(omega);
         for (int it = threadIdx.x; it < items; it += blockDim.x) {
             const int64_t i = row0 + it;
@@ -197,7 +228,13 @@ __global__ void __launch_bounds__(kPersThreads) k_persist_bicg(PersistArgs<R> a)
         if (!grid_sum<2>(d1, a.part, 1, s_red, s_tot, a.bar, gen)) { status = HEOM_ECUDA; break; }
         const cx<double> rv{d1[0], d1[1]};
         if (norm2(rv) == 0.0) { status = HEOM_EBREAKDOWN; it_done = iter; break; }
-        alpha = cplx_div(rho, rv);
+        if (threadIdx.x == 0) {
+            const cx<double> al0 = cplx_div(rho, rv);
+            s_sc[3] = al0.re;
+            s_sc[4] = al0.im;
+        }
+        __syncthreads();
+        alpha = cx<double>{s_sc[3], s_sc[4]};
         // ---- s = r - alpha v (in r), sh = P^-1 s
         const cx<R> al = cast<R>(alpha);
         for (int it = threadIdx.x; it < items; it += blockDim.x) {
@@ -219,7 +256,13 @@ __global__ void __launch_bounds__(kPersThreads) k_persist_bicg(PersistArgs<R> a)
             d2v[2] += yd.re * yd.re + yd.im * yd.im;
         }
         if (!grid_sum<3>(d2v, a.part, 2, s_red, s_tot, a.bar, gen)) { status = HEOM_ECUDA; break; }
-        omega = d2v[2] == 0.0 ? cx<double>{0.0, 0.0} : cplx_div(cx<double>{d2v[0], d2v[1]}, cx<double>{d2v[2], 0.0});
+        if (threadIdx.x == 0) {
+            const double it2 = d2v[2] == 0.0 ? 0.0 : nr_rcp(d2v[2]);
+            s_sc[5] = d2v[0] * it2;
+            s_sc[6] = d2v[1] * it2;
+        }
+        __syncthreads();
+        omega = cx<double>{s_sc[5], s_sc[6]};
         if (!finite_c(omega) || !finite_c(alpha)) { status = HEOM_EBREAKDOWN; it_done = iter; break; }
         // ---- x += alpha ph + omega sh, r = s - omega t, (rh, r), ||r||^2
         const cx<R> omr = cast<R>(omega);
