@@ -139,6 +139,18 @@ heom_status heom_build_hierarchy(int d, const heom_c64 *H, int n_baths, const he
 heom_status heom_set_params(heom_hier *h, int n_sets, const heom_c64 *H,
                             const heom_c64 *coef, const heom_c64 *rate);
 
+/* Lindblad terms (Eq. Lindbladian, J(F)[X] = F X F^dagger - 1/2 {F^dagger F, X}): replace
+ * the hierarchy's jump operators by n_ops operators F [n_ops][d][d] (row-major, host) with
+ * real rates gamma [n_ops] (host). Every later call then adds
+ *   sum_k gamma_k J(F_k)[X]
+ * to the equation of every ADO X, in every parameter set and in either parity, without
+ * adding ADOs (the weakly coupled baths the terms stand for carry no hierarchy). The
+ * operators survive heom_set_params. n_ops = 0 removes them. The arrays are copied.
+ * Errors: HEOM_EINVAL for n_ops < 0, NULL arrays with n_ops > 0, non-finite entries, or jump
+ * operators so dense that the system superoperator exceeds 2^22 element terms (the previous
+ * operators then stay); HEOM_ENOMEM; HEOM_ECUDA. */
+heom_status heom_set_lindblad(heom_hier *h, int n_ops, const heom_c64 *F, const double *gamma);
+
 /* Sizes: number of ADOs, system dimension, bosonic / fermionic exponent counts, number of
  * parameter sets, number of neighbour-table entries. Any pointer may be NULL. */
 heom_status heom_hier_info(const heom_hier *h, int64_t *n_ado, int *d, int *k_b, int *k_f,

@@ -117,7 +117,9 @@ def model_to_problem(model, parity: int = 1) -> dict:
                           partner=np.array(list(range(h, 2 * h)) + list(range(h)),
                                            dtype=np.int32)))
     return dict(d=model.d, H=np.asarray(model.H, np.complex128), baths=baths,
-                tier_b=model.tier_b, tier_f=model.tier_f, parity=parity)
+                tier_b=model.tier_b, tier_f=model.tier_f, parity=parity,
+                lindblad=[dict(op=np.asarray(F, np.complex128), rate=float(g))
+                          for F, g in model.lindblad])
 
 
 @dataclass

@@ -28,6 +28,13 @@ Readings (the paper fixes the operators but not an ADO order or a storage conven
 * d^{+1} = d^dagger (nu = +1: Hermitian conjugation present), d^{-1} = d.
 * No normalisation factors on the ADOs (the unnormalised form of Eq. HEOM).
 
+Lindblad terms (Eq. Lindbladian): a problem may carry a list ``lindblad`` of jump operators
+F_k with real rates gamma_k. The term sum_k gamma_k J(F_k)[X], J(F)[X] = F X F^dagger -
+1/2 (F^dagger F X + X F^dagger F), is added to the equation of every ADO X, leaving the ADO set
+unchanged (Results: the Lindbladian is added to the HEOMLS without extending the ADO space).
+Reading: the paper gives the one form for every ADO and both parities, so no tier- or
+parity-dependent sign is applied.
+
 Liouville space convention of the sparse path: column stacking, vec(A X B) =
 (B^T kron A) vec(X); the ADO vector is the concatenation of vec(rho_n) in ADO order.
 The loop path works on an array X[n] of d x d matrices (the GPU path's row-major layout).
@@ -71,6 +78,23 @@ def damping(m, S, bos, fer) -> complex:
 # --------------------------------------------------------------------------------------
 
 
+def lindblad_terms(problem: dict):
+    """The (gamma, F) pairs of the problem's Lindblad terms (empty list when it has none)."""
+    return [(float(t["rate"]), np.asarray(t["op"], np.complex128))
+            for t in problem.get("lindblad", [])]
+
+
+def lindblad_apply(terms, X0: np.ndarray) -> np.ndarray:
+    """sum_k gamma_k J(F_k)[X0] with J(F)[X] = F X F^dagger - 1/2 {F^dagger F, X}
+    (Eq. Lindbladian)."""
+    out = np.zeros_like(X0)
+    for g, F in terms:
+        Fd = F.conj().T
+        FdF = Fd @ F
+        out += g * (F @ X0 @ Fd - 0.5 * (FdF @ X0 + X0 @ FdF))
+    return out
+
+
 def apply_loop(problem: dict, X: np.ndarray, hier=None, only=None) -> np.ndarray:
     """Y = M X computed ADO by ADO from Eq. HEOM (target-ADO view).
 
@@ -81,6 +105,7 @@ def apply_loop(problem: dict, X: np.ndarray, hier=None, only=None) -> np.ndarray
     p = problem["parity"]
     bos, fer = flatten_exponents(problem)
     hier = hier or problem_hierarchy(problem)
+    lind = lindblad_terms(problem)
     Y = np.zeros_like(X)
     targets = range(hier.n_ado) if only is None else only
     for i in targets:
@@ -88,6 +113,8 @@ def apply_loop(problem: dict, X: np.ndarray, hier=None, only=None) -> np.ndarray
         n = len(S)
         X0 = X[i]
         acc = -1j * (H @ X0 - X0 @ H) - damping(m, S, bos, fer) * X0
+        if lind:
+            acc += lindblad_apply(lind, X0)
         if sum(m) < hier.tier_b:
             for k, e in enumerate(bos):
                 mu = list(m)
@@ -156,6 +183,11 @@ def build_matrix(problem: dict, hier=None) -> sp.csr_matrix:
         vals.append(block.data)
 
     LH = -1j * (spre(H) - spost(H))
+    for g, F in lindblad_terms(problem):
+        # vec(F X F^dagger) = (conj(F) kron F) vec(X) = spost(F^dagger) spre(F) vec(X)
+        Fd = F.conj().T
+        FdF = Fd @ F
+        LH = LH + g * (spre(F) @ spost(Fd) - 0.5 * (spre(FdF) + spost(FdF)))
     eye = sp.identity(D2, format="csr")
     for i, (m, S) in enumerate(hier.ados):
         put(i, i, LH - damping(m, S, bos, fer) * eye)

@@ -64,6 +64,7 @@ _sig = {
     "heom_build_hierarchy": [C.c_int, _P, C.c_int, _P, C.c_int, C.c_int, C.c_int, C.c_int,
                              C.POINTER(_P)],
     "heom_set_params": [_P, C.c_int, _P, _P, _P],
+    "heom_set_lindblad": [_P, C.c_int, _P, _P],
     "heom_hier_info": [_P, _P, _P, _P, _P, _P, _P],
     "heom_ado_index": [_P, _P, _P],
     "heom_ado_label": [_P, C.c_int64, _P],
@@ -169,7 +170,8 @@ def problem_from_model(model, parity: int = 1) -> dict:
                           nu=np.array([1] * h + [-1] * h, np.int32),
                           partner=np.array(list(range(h, 2 * h)) + list(range(h)), np.int32)))
     return dict(d=model.d, H=_c64(model.H), baths=baths, tier_b=model.tier_b,
-                tier_f=model.tier_f, parity=parity)
+                tier_f=model.tier_f, parity=parity,
+                lindblad=[dict(op=_c64(F), rate=float(g)) for F, g in model.lindblad])
 
 
 # ------------------------------------------------------------------------- hierarchy
@@ -224,7 +226,20 @@ def build_hierarchy(problem: dict) -> Hierarchy:
                                      int(problem["tier_b"]), int(problem["tier_f"]),
                                      int(problem.get("parity", 1)), 0, C.byref(out)),
            "heom_build_hierarchy")
-    return Hierarchy(out, None)
+    h = Hierarchy(out, None)
+    if problem.get("lindblad"):
+        set_lindblad(h, [t["op"] for t in problem["lindblad"]],
+                     [t["rate"] for t in problem["lindblad"]])
+    return h
+
+
+def set_lindblad(h: Hierarchy, ops, rates):
+    """Jump operators F_k [n, d, d] and real rates gamma_k [n] (Eq. Lindbladian) added to every
+    ADO's equation; empty lists remove them."""
+    n = len(rates)
+    F = _c64(np.reshape(ops, (n, h.d, h.d)) if n else np.zeros((1, h.d, h.d)))
+    g = np.ascontiguousarray(rates if n else [0.0], np.float64)
+    _check(_lib.heom_set_lindblad(h.handle, n, _ptr(F), _ptr(g)), "heom_set_lindblad")
 
 
 def set_params(h: Hierarchy, H, coef, rate):

@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <map>
 #include <new>
 
 #include "heom_internal.h"
@@ -289,24 +290,20 @@ void boson_ab(int kind, heom_c64 c, heom_c64 &a, heom_c64 &b) {
 
 heom::DevView<double> heom_hier::view64() const {
     heom::DevView<double> v{};
-    v.N = N; v.d = d; v.d2 = d2; v.K = K; v.n_sets = n_sets; v.nnzH = nnzH;
+    v.N = N; v.d = d; v.d2 = d2; v.K = K; v.n_sets = n_sets; v.nS = nS;
     v.row_ptr = (const int32_t *)d_row_ptr.p; v.ent = (const NbEntry *)d_ent.p;
     v.occ_ptr = (const int32_t *)d_occ_ptr.p; v.occ = (const OccEntry *)d_occ.p;
     v.op_rptr = (const int32_t *)d_op_rptr.p; v.op_rcol = (const int32_t *)d_op_rcol.p;
     v.op_rval = (const cx<double> *)d_op_rval64.p;
     v.op_cptr = (const int32_t *)d_op_cptr.p; v.op_crow = (const int32_t *)d_op_crow.p;
     v.op_cval = (const cx<double> *)d_op_cval64.p;
-    v.h_rptr = (const int32_t *)d_h_rptr.p; v.h_rcol = (const int32_t *)d_h_rcol.p;
-    v.h_rvi = (const int32_t *)d_h_rvi.p; v.h_cptr = (const int32_t *)d_h_cptr.p;
-    v.h_crow = (const int32_t *)d_h_crow.p; v.h_cvi = (const int32_t *)d_h_cvi.p;
-    v.h_val = (const cx<double> *)d_hval64.p;
+    v.s_ptr = (const int32_t *)d_s_ptr.p; v.s_src = (const int32_t *)d_s_src.p;
+    v.s_val = (const cx<double> *)d_sval64.p; v.sdiag = (const cx<double> *)d_sdiag64.p;
     v.coefL = (const cx<double> *)d_coefL64.p; v.coefR = (const cx<double> *)d_coefR64.p;
-    v.rate = (const cx<double> *)d_rate64.p; v.hdiag = (const cx<double> *)d_hdiag64.p;
+    v.rate = (const cx<double> *)d_rate64.p;
     v.floor = (const double *)d_floor64.p;
     v.t_ptr = (const int32_t *)d_t_ptr.p; v.t_src = (const int32_t *)d_t_src.p;
     v.t_val = (const cx<double> *)d_t_val64.p;
-    v.th_ptr = (const int32_t *)d_th_ptr.p; v.th_src = (const int32_t *)d_th_src.p;
-    v.th_vi = (const int32_t *)d_th_vi.p;
     v.max_terms = max_terms; v.max_entries = max_entries;
     v.cta_ado = (const int32_t *)d_cta_ado.p; v.n_ranges = n_ranges; v.range_terms = range_terms;
     v.range_slots = range_slots; v.range_ados = range_ados; v.tile_min_b = tile_min_b;
@@ -317,24 +314,20 @@ heom::DevView<double> heom_hier::view64() const {
 
 heom::DevView<float> heom_hier::view32() const {
     heom::DevView<float> v{};
-    v.N = N; v.d = d; v.d2 = d2; v.K = K; v.n_sets = n_sets; v.nnzH = nnzH;
+    v.N = N; v.d = d; v.d2 = d2; v.K = K; v.n_sets = n_sets; v.nS = nS;
     v.row_ptr = (const int32_t *)d_row_ptr.p; v.ent = (const NbEntry *)d_ent.p;
     v.occ_ptr = (const int32_t *)d_occ_ptr.p; v.occ = (const OccEntry *)d_occ.p;
     v.op_rptr = (const int32_t *)d_op_rptr.p; v.op_rcol = (const int32_t *)d_op_rcol.p;
     v.op_rval = (const cx<float> *)d_op_rval32.p;
     v.op_cptr = (const int32_t *)d_op_cptr.p; v.op_crow = (const int32_t *)d_op_crow.p;
     v.op_cval = (const cx<float> *)d_op_cval32.p;
-    v.h_rptr = (const int32_t *)d_h_rptr.p; v.h_rcol = (const int32_t *)d_h_rcol.p;
-    v.h_rvi = (const int32_t *)d_h_rvi.p; v.h_cptr = (const int32_t *)d_h_cptr.p;
-    v.h_crow = (const int32_t *)d_h_crow.p; v.h_cvi = (const int32_t *)d_h_cvi.p;
-    v.h_val = (const cx<float> *)d_hval32.p;
+    v.s_ptr = (const int32_t *)d_s_ptr.p; v.s_src = (const int32_t *)d_s_src.p;
+    v.s_val = (const cx<float> *)d_sval32.p; v.sdiag = (const cx<float> *)d_sdiag32.p;
     v.coefL = (const cx<float> *)d_coefL32.p; v.coefR = (const cx<float> *)d_coefR32.p;
-    v.rate = (const cx<float> *)d_rate32.p; v.hdiag = (const cx<float> *)d_hdiag32.p;
+    v.rate = (const cx<float> *)d_rate32.p;
     v.floor = (const float *)d_floor32.p;
     v.t_ptr = (const int32_t *)d_t_ptr.p; v.t_src = (const int32_t *)d_t_src.p;
     v.t_val = (const cx<float> *)d_t_val32.p;
-    v.th_ptr = (const int32_t *)d_th_ptr.p; v.th_src = (const int32_t *)d_th_src.p;
-    v.th_vi = (const int32_t *)d_th_vi.p;
     v.max_terms = max_terms; v.max_entries = max_entries;
     v.cta_ado = (const int32_t *)d_cta_ado.p; v.n_ranges = n_ranges; v.range_terms = range_terms;
     v.range_slots = range_slots; v.range_ados = range_ados; v.tile_min_b = tile_min_b;
@@ -348,18 +341,15 @@ namespace {
 void free_all(heom_hier *h) {
     DBuf *bufs[] = {&h->d_row_ptr, &h->d_ent, &h->d_occ_ptr, &h->d_occ, &h->d_op_rptr,
                     &h->d_op_rcol, &h->d_op_cptr, &h->d_op_crow, &h->d_op_rval64,
-                    &h->d_op_cval64, &h->d_op_rval32, &h->d_op_cval32, &h->d_h_rptr,
-                    &h->d_h_rcol, &h->d_h_rvi, &h->d_h_cptr, &h->d_h_crow, &h->d_h_cvi,
-                    &h->d_hval64, &h->d_hval32, &h->d_coefL64, &h->d_coefL32, &h->d_coefR64,
-                    &h->d_coefR32, &h->d_rate64, &h->d_rate32, &h->d_hdiag64, &h->d_hdiag32,
-                    &h->d_floor64, &h->d_floor32, &h->ws, &h->ws_small, &h->d_t_ptr,
-                    &h->d_t_src, &h->d_t_val64, &h->d_t_val32, &h->d_th_ptr, &h->d_th_src,
-                    &h->d_th_vi, &h->d_cta_ado, &h->d_pers_ado, &h->ws_pers};
+                    &h->d_op_cval64, &h->d_op_rval32, &h->d_op_cval32, &h->d_s_ptr,
+                    &h->d_s_src, &h->d_sval64, &h->d_sval32, &h->d_coefL64, &h->d_coefL32,
+                    &h->d_coefR64, &h->d_coefR32, &h->d_rate64, &h->d_rate32, &h->d_sdiag64,
+                    &h->d_sdiag32, &h->d_floor64, &h->d_floor32, &h->ws, &h->ws_small,
+                    &h->d_t_ptr, &h->d_t_src, &h->d_t_val64, &h->d_t_val32, &h->d_cta_ado,
+                    &h->d_pers_ado, &h->ws_pers};
     for (DBuf *b : bufs) heom::dfree(*b);
 }
 
-// Upload the parameter-dependent arrays: H values on the shared pattern, (a, b) pairs,
-// rates, H diagonal and the damping floor, for n_sets sets.
 // Term count and shared-memory slots of every ADO's program (damping 1 per element, H, the
 // neighbour terms, the trace row of ADO 0).
 struct RangeCosts {
@@ -371,7 +361,7 @@ RangeCosts range_costs(const heom_hier *h) {
     rc.terms.resize(h->N);
     rc.slots.resize(h->N);
     for (int64_t i = 0; i < h->N; ++i) {
-        int64_t t = h->d2 + h->h_terms + (i == 0 ? h->d : 0);
+        int64_t t = h->d2 + h->nS + (i == 0 ? h->d : 0);
         for (int32_t k = h->row_ptr[i]; k < h->row_ptr[i + 1]; ++k) t += h->op_terms[h->ent[k].op];
         rc.terms[i] = t;
         rc.slots[i] = (int64_t)h->d2 * (h->row_ptr[i + 1] - h->row_ptr[i] + 3);
@@ -407,35 +397,102 @@ bool partition_ranges(const heom_hier *h, const RangeCosts &rc, int64_t resident
     return false;
 }
 
+// Most system-superoperator terms (all elements together) a hierarchy may carry.
+constexpr int kMaxSystemTerms = 1 << 22;
+
+// Upload the parameter-dependent arrays for n_sets sets: the system superoperator's term
+// lists and values (H and the Lindblad terms), the (a, b) pairs and rates of the exponents,
+// the preconditioner's diagonal and damping floor; then re-partition the ADO ranges, whose
+// term counts depend on the system terms.
 heom_status upload_params(heom_hier *h, int n_sets, const heom_c64 *H, const heom_c64 *coef,
                           const heom_c64 *rate) {
-    const int d = h->d, K = h->K;
-    // H pattern: union of non-zeros over all sets
-    std::vector<char> nz(d * d, 0);
-    for (int s = 0; s < n_sets; ++s)
-        for (int i = 0; i < d * d; ++i)
-            if (H[s * d * d + i].re != 0.0 || H[s * d * d + i].im != 0.0) nz[i] = 1;
-    std::vector<int32_t> rptr(d + 1, 0), rcol, rvi, cptr(d + 1, 0), crow, cvi;
-    std::vector<int> vidx(d * d, -1);
-    int nnz = 0;
-    for (int r = 0; r < d; ++r) {
-        for (int c = 0; c < d; ++c)
-            if (nz[r * d + c]) { vidx[r * d + c] = nnz; rcol.push_back(c); rvi.push_back(nnz); ++nnz; }
-        rptr[r + 1] = nnz;
-    }
-    int cn = 0;
-    for (int c = 0; c < d; ++c) {
+    const int d = h->d, d2 = h->d2, K = h->K;
+    const int n_lind = (int)h->lind_gamma.size();
+    // System superoperator per set: L_s X = -i (H X - X H) + sum_k g_k (F_k X F_k^+ -
+    // 1/2 {F_k^+ F_k, X}) (Eq. HEOM's commutator, Eq. Lindbladian). With G = 1/2 sum_k g_k
+    // F_k^+ F_k, element (r, c) reads
+    //   X[l][c] with (-i H[r][l] - G[r][l]),   X[r][l] with (i H[l][c] - G[l][c]),
+    //   X[l][m] with sum_k g_k F_k[r][l] conj(F_k[c][m]).
+    // Terms are accumulated per (element, source element), so each source appears once.
+    std::vector<heom_c64> G((size_t)d * d, heom_c64{0.0, 0.0});
+    for (int k = 0; k < n_lind; ++k) {
+        const heom_c64 *F = h->lind_F.data() + (size_t)k * d * d;
+        const double g = 0.5 * h->lind_gamma[k];
         for (int r = 0; r < d; ++r)
-            if (nz[r * d + c]) { crow.push_back(r); cvi.push_back(vidx[r * d + c]); ++cn; }
-        cptr[c + 1] = cn;
+            for (int c = 0; c < d; ++c) {
+                double re = 0.0, im = 0.0;  // (F^+ F)[r][c] = sum_l conj(F[l][r]) F[l][c]
+                for (int l = 0; l < d; ++l) {
+                    const heom_c64 a = F[(size_t)l * d + r], b = F[(size_t)l * d + c];
+                    re += a.re * b.re + a.im * b.im;
+                    im += a.re * b.im - a.im * b.re;
+                }
+                G[(size_t)r * d + c].re += g * re;
+                G[(size_t)r * d + c].im += g * im;
+            }
     }
-    std::vector<heom_c64> hval((size_t)n_sets * std::max(nnz, 1)), cl((size_t)n_sets * K),
-        cr((size_t)n_sets * K), rt((size_t)n_sets * K), hd((size_t)n_sets * d);
+    // per element: source element -> value in each set (ordered by source)
+    std::vector<std::map<int, std::vector<heom_c64>>> terms(d2);
+    auto add = [&](int e, int src, int set, double re, double im) {
+        if (re == 0.0 && im == 0.0) return;
+        auto &vals = terms[e][src];
+        if (vals.empty()) vals.assign(n_sets, heom_c64{0.0, 0.0});
+        vals[set].re += re;
+        vals[set].im += im;
+    };
+    for (int s = 0; s < n_sets; ++s) {
+        const heom_c64 *Hs = H + (size_t)s * d * d;
+        for (int r = 0; r < d; ++r)
+            for (int c = 0; c < d; ++c) {
+                const int e = r * d + c;
+                for (int l = 0; l < d; ++l) {
+                    const heom_c64 hl = Hs[(size_t)r * d + l], gl = G[(size_t)r * d + l];
+                    add(e, l * d + c, s, hl.im - gl.re, -hl.re - gl.im);   // -i H[r][l] - G[r][l]
+                    const heom_c64 hr = Hs[(size_t)l * d + c], gr = G[(size_t)l * d + c];
+                    add(e, r * d + l, s, -hr.im - gr.re, hr.re - gr.im);   // i H[l][c] - G[l][c]
+                }
+                for (int k = 0; k < n_lind; ++k) {
+                    const heom_c64 *F = h->lind_F.data() + (size_t)k * d * d;
+                    const double g = h->lind_gamma[k];
+                    for (int l = 0; l < d; ++l) {
+                        const heom_c64 a = F[(size_t)r * d + l];
+                        if (a.re == 0.0 && a.im == 0.0) continue;
+                        for (int m = 0; m < d; ++m) {
+                            const heom_c64 b = F[(size_t)c * d + m];  // conj(F[c][m])
+                            if (b.re == 0.0 && b.im == 0.0) continue;
+                            add(e, l * d + m, s, g * (a.re * b.re + a.im * b.im),
+                                g * (a.im * b.re - a.re * b.im));
+                        }
+                    }
+                }
+            }
+    }
+    std::vector<int32_t> sptr(d2 + 1, 0), ssrc;
+    std::vector<std::vector<heom_c64>> scols;  // per kept term: values per set
+    std::vector<heom_c64> sd((size_t)n_sets * d2, heom_c64{0.0, 0.0});
+    for (int e = 0; e < d2; ++e) {
+        for (auto &kv : terms[e]) {
+            bool nz = false;
+            for (const heom_c64 &v : kv.second) nz = nz || v.re != 0.0 || v.im != 0.0;
+            if (!nz) continue;
+            if (kv.first == e)
+                for (int s = 0; s < n_sets; ++s) sd[(size_t)s * d2 + e] = kv.second[s];
+            ssrc.push_back(kv.first);
+            scols.push_back(kv.second);
+        }
+        sptr[e + 1] = (int32_t)ssrc.size();
+        if (ssrc.size() > (size_t)kMaxSystemTerms) {
+            set_error("system superoperator has more than %d terms (jump operators too dense)",
+                      kMaxSystemTerms);
+            return HEOM_EINVAL;
+        }
+    }
+    const int nS = (int)ssrc.size();
+    std::vector<heom_c64> sval((size_t)n_sets * std::max(nS, 1), heom_c64{0.0, 0.0});
+    for (int j = 0; j < nS; ++j)
+        for (int s = 0; s < n_sets; ++s) sval[(size_t)s * nS + j] = scols[j][s];
+    std::vector<heom_c64> cl((size_t)n_sets * K), cr((size_t)n_sets * K), rt((size_t)n_sets * K);
     std::vector<double> fl(n_sets);
     for (int s = 0; s < n_sets; ++s) {
-        for (int i = 0; i < d * d; ++i)
-            if (vidx[i] >= 0) hval[(size_t)s * nnz + vidx[i]] = H[(size_t)s * d * d + i];
-        for (int r = 0; r < d; ++r) hd[(size_t)s * d + r] = H[(size_t)s * d * d + r * d + r];
         double floor = 0;
         bool first = true;
         for (int k = 0; k < K; ++k) {
@@ -457,23 +514,13 @@ heom_status upload_params(heom_hier *h, int n_sets, const heom_c64 *H, const heo
         fl[s] = first ? 1.0 : floor;
     }
     std::vector<float> fl32(fl.begin(), fl.end());
-    // H term lists for the tiled kernels: element (r,c) reads H[r][l] X[l][c] (left) and
-    // X[r][l] H[l][c] (right)
-    std::vector<int32_t> thp(d * d + 1, 0), ths, thv;
-    for (int r = 0; r < d; ++r)
-        for (int c = 0; c < d; ++c) {
-            for (int l = 0; l < d; ++l)
-                if (vidx[r * d + l] >= 0) { ths.push_back(l * d + c); thv.push_back(vidx[r * d + l]); }
-            for (int l = 0; l < d; ++l)
-                if (vidx[l * d + c] >= 0) { ths.push_back((r * d + l) | (1 << 16)); thv.push_back(vidx[l * d + c]); }
-            thp[r * d + c + 1] = (int32_t)ths.size();
-        }
-    h->h_terms = (int)ths.size();
-    // largest term program of one ADO: damping (1 per element) + H + neighbour terms + trace row
+    h->nS = nS;
+    // largest term program of one ADO: damping (1 per element) + system terms + neighbour
+    // terms + trace row
     {
         int mt = 0, me = 0;
         for (int64_t i = 0; i < h->N; ++i) {
-            int t = h->d2 + h->h_terms + d;
+            int t = h->d2 + h->nS + d;
             for (int32_t k = h->row_ptr[i]; k < h->row_ptr[i + 1]; ++k) t += h->op_terms[h->ent[k].op];
             mt = std::max(mt, t);
             me = std::max(me, (int)(h->row_ptr[i + 1] - h->row_ptr[i]));
@@ -504,19 +551,19 @@ heom_status upload_params(heom_hier *h, int n_sets, const heom_c64 *H, const heo
     }
     heom_status st;
 #define UP(buf, vec) if ((st = upload(h->buf, vec)) != HEOM_OK) return st
-    UP(d_th_ptr, thp); UP(d_th_src, ths); UP(d_th_vi, thv); UP(d_cta_ado, ranges); UP(d_pers_ado, pranges);
-    UP(d_h_rptr, rptr); UP(d_h_rcol, rcol); UP(d_h_rvi, rvi);
-    UP(d_h_cptr, cptr); UP(d_h_crow, crow); UP(d_h_cvi, cvi);
-    UP(d_hval64, to_cx<double>(hval)); UP(d_hval32, to_cx<float>(hval));
+    UP(d_cta_ado, ranges); UP(d_pers_ado, pranges);
+    UP(d_s_ptr, sptr); UP(d_s_src, ssrc);
+    UP(d_sval64, to_cx<double>(sval)); UP(d_sval32, to_cx<float>(sval));
+    UP(d_sdiag64, to_cx<double>(sd)); UP(d_sdiag32, to_cx<float>(sd));
     UP(d_coefL64, to_cx<double>(cl)); UP(d_coefL32, to_cx<float>(cl));
     UP(d_coefR64, to_cx<double>(cr)); UP(d_coefR32, to_cx<float>(cr));
     UP(d_rate64, to_cx<double>(rt)); UP(d_rate32, to_cx<float>(rt));
-    UP(d_hdiag64, to_cx<double>(hd)); UP(d_hdiag32, to_cx<float>(hd));
     UP(d_floor64, fl); UP(d_floor32, fl32);
 #undef UP
-    h->nnzH = nnz;
     h->n_sets = n_sets;
     h->H0.assign(H, H + (size_t)n_sets * d * d);
+    h->coef0.assign(coef, coef + (size_t)n_sets * K);
+    h->rate0.assign(rate, rate + (size_t)n_sets * K);
     return HEOM_OK;
 }
 
@@ -755,6 +802,31 @@ extern "C" heom_status heom_set_params(heom_hier *h, int n_sets, const heom_c64 
         if (!finite(coef[i]) || !finite(rate[i])) { set_error("heom_set_params: non-finite exponent"); return HEOM_EINVAL; }
     HEOM_CUDA(cudaSetDevice(h->device));
     return upload_params(h, n_sets, H, coef, rate);
+}
+
+extern "C" heom_status heom_set_lindblad(heom_hier *h, int n_ops, const heom_c64 *F,
+                                         const double *gamma) {
+    if (!h || n_ops < 0 || (n_ops > 0 && (!F || !gamma))) {
+        set_error("heom_set_lindblad: need a hierarchy, n_ops >= 0 and F/gamma arrays");
+        return HEOM_EINVAL;
+    }
+    for (size_t i = 0; i < (size_t)n_ops * h->d2; ++i)
+        if (!finite(F[i])) { set_error("heom_set_lindblad: non-finite jump operator"); return HEOM_EINVAL; }
+    for (int k = 0; k < n_ops; ++k)
+        if (!std::isfinite(gamma[k])) { set_error("heom_set_lindblad: non-finite rate"); return HEOM_EINVAL; }
+    HEOM_CUDA(cudaSetDevice(h->device));
+    std::vector<heom_c64> oldF, Hs = h->H0, cs = h->coef0, rs = h->rate0;
+    std::vector<double> oldg;
+    oldF.swap(h->lind_F);
+    oldg.swap(h->lind_gamma);
+    h->lind_F.assign(F, F + (size_t)n_ops * h->d2);
+    h->lind_gamma.assign(gamma, gamma + n_ops);
+    const heom_status st = upload_params(h, h->n_sets, Hs.data(), cs.data(), rs.data());
+    if (st != HEOM_OK) {
+        h->lind_F.swap(oldF);
+        h->lind_gamma.swap(oldg);
+    }
+    return st;
 }
 
 extern "C" heom_status heom_hier_info(const heom_hier *h, int64_t *n_ado, int *d, int *k_b,

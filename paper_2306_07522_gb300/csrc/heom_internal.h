@@ -67,7 +67,7 @@ struct OccEntry {  // damping term: count * rate_k
 template <class R>
 struct DevView {
     int64_t N;          // number of ADOs
-    int d, d2, K, n_sets, nnzH;
+    int d, d2, K, n_sets, nS;
     const int32_t *row_ptr;   // [N+1]
     const NbEntry *ent;       // [E]
     const int32_t *occ_ptr;   // [N+1]
@@ -78,29 +78,27 @@ struct DevView {
     const int32_t *op_cptr;   // [n_ops*(d+1)] absolute offsets into op_crow/op_cval
     const int32_t *op_crow;
     const cx<R> *op_cval;
-    const int32_t *h_rptr;    // [d+1]: H pattern by rows (union over parameter sets)
-    const int32_t *h_rcol;
-    const int32_t *h_rvi;     // value index into a set's H value array
-    const int32_t *h_cptr;    // [d+1]: the same pattern by columns
-    const int32_t *h_crow;
-    const int32_t *h_cvi;
-    const cx<R> *h_val;       // [n_sets][nnzH]
     const cx<R> *coefL;       // [n_sets][K]
     const cx<R> *coefR;       // [n_sets][K]
     const cx<R> *rate;        // [n_sets][K]
-    const cx<R> *hdiag;       // [n_sets][d]   diagonal of H (preconditioner)
     const R *floor;           // [n_sets]      damping floor for undamped ADOs (preconditioner)
+    // ADO-local system superoperator L_s X = -i (H X - X H) + sum_k gamma_k J(F_k)[X] (the
+    // commutator of Eq. HEOM plus the Lindblad terms of Eq. Lindbladian), one term list per
+    // output element: element e reads local element s_src[j] of the same ADO with coefficient
+    // s_val[set * nS + j], j = s_ptr[e] .. s_ptr[e+1]-1. Terms with the same source element
+    // are merged; terms that vanish in every parameter set are dropped.
+    const int32_t *s_ptr;     // [d2 + 1]
+    const int32_t *s_src;     // [nS]
+    const cx<R> *s_val;       // [n_sets][nS]
+    const cx<R> *sdiag;       // [n_sets][d2]  coefficient of element e on itself (preconditioner)
     // Per-element term lists of every operator, for the tiled kernels: for operator slot o
     // and output element e = r*d + c, terms t_ptr[o*d2+e] .. t_ptr[o*d2+e+1]-1 read local
     // element (t_src & 0xffff) of the source block, as a left product (bit 16 clear:
     // (O X)[r][c] needs X[l][c] O[r][l]) or a right product (bit 16 set: X[r][l] O[l][c]),
-    // with operator value t_val. th_* is the same for H, values by index into h_val.
+    // with operator value t_val.
     const int32_t *t_ptr;     // [n_ops*d2 + 1]
     const int32_t *t_src;
     const cx<R> *t_val;
-    const int32_t *th_ptr;    // [d2 + 1]
-    const int32_t *th_src;
-    const int32_t *th_vi;
     int max_terms;            // largest term program of one ADO (incl. damping, H, trace row)
     int max_entries;          // largest neighbour-entry count of one ADO
     // ADO ranges of the persistent tiled kernel (one CTA each, balanced by term count)
@@ -149,24 +147,27 @@ struct heom_hier {
     std::vector<int> bath_slot;             // first operator slot of each bath (fermions: d, then d^dagger)
     std::vector<heom_c64> ops;              // [n_ops][d][d]
     std::vector<heom_c64> H0;               // [n_sets][d][d]
+    std::vector<heom_c64> coef0, rate0;     // [n_sets][K] as given (before the kind mapping)
+    std::vector<heom_c64> lind_F;           // [n_lind][d][d] Lindblad jump operators
+    std::vector<double> lind_gamma;         // [n_lind] their rates
     // device tables
     heom::DBuf d_row_ptr, d_ent, d_occ_ptr, d_occ;
     heom::DBuf d_op_rptr, d_op_rcol, d_op_cptr, d_op_crow, d_op_rval64, d_op_cval64,
         d_op_rval32, d_op_cval32;
-    heom::DBuf d_h_rptr, d_h_rcol, d_h_rvi, d_h_cptr, d_h_crow, d_h_cvi;
-    int nnzH = 0;
+    heom::DBuf d_s_ptr, d_s_src;
+    int nS = 0;                             // system terms (all elements)
     // tiled-kernel term lists (see DevView)
-    heom::DBuf d_t_ptr, d_t_src, d_t_val64, d_t_val32, d_th_ptr, d_th_src, d_th_vi;
+    heom::DBuf d_t_ptr, d_t_src, d_t_val64, d_t_val32;
     std::vector<int> op_terms;              // total terms of operator slot o over all elements
-    int h_terms = 0, max_terms = 0, max_entries = 0;
+    int max_terms = 0, max_entries = 0;
     heom::DBuf d_cta_ado, d_pers_ado;
     int n_ranges = 0, range_terms = 0, range_slots = 0, range_ados = 0;
     int tile_per_sm = 5;        // tiled kernel: ADO ranges per SM (autotuned)
     int64_t tile_min_b = 16;    // tiled kernel from this batch on (autotuned)
     int pers_ranges = 0, pers_terms = 0, pers_slots = 0, pers_ados = 0;
     // device parameters (per set), both precisions
-    heom::DBuf d_hval64, d_hval32, d_coefL64, d_coefL32, d_coefR64, d_coefR32, d_rate64,
-        d_rate32, d_hdiag64, d_hdiag32, d_floor64, d_floor32;
+    heom::DBuf d_sval64, d_sval32, d_coefL64, d_coefL32, d_coefR64, d_coefR32, d_rate64,
+        d_rate32, d_sdiag64, d_sdiag32, d_floor64, d_floor32;
     // solver workspace (grown on demand)
     heom::DBuf ws;
     heom::DBuf ws_small;

@@ -61,12 +61,10 @@ __device__ __forceinline__ cx<R> apply_point(const DevView<R> &v, const cx<R> *_
     const cx<R> *Xn = X + n * v.d2 * B + b;
     const cx<R> x0 = Xn[(int64_t)e * B];
     cx<R> acc{-(damp.re * x0.re - damp.im * x0.im), -(damp.re * x0.im + damp.im * x0.re)};
-    // system commutator: -i (H X - X H)
-    const cx<R> *hv = v.h_val + (int64_t)set * v.nnzH;
-    for (int j = __ldg(v.h_rptr + r), j1 = __ldg(v.h_rptr + r + 1); j < j1; ++j)
-        fma_to(acc, mul_mi(ldc(hv + __ldg(v.h_rvi + j))), Xn[(int64_t)(__ldg(v.h_rcol + j) * d + c) * B]);
-    for (int j = __ldg(v.h_cptr + c), j1 = __ldg(v.h_cptr + c + 1); j < j1; ++j)
-        fma_to(acc, mul_i(ldc(hv + __ldg(v.h_cvi + j))), Xn[(int64_t)(r * d + __ldg(v.h_crow + j)) * B]);
+    // system superoperator: -i (H X - X H) plus the Lindblad terms, one merged term list
+    const cx<R> *sv = v.s_val + (int64_t)set * v.nS;
+    for (int j = __ldg(v.s_ptr + e), j1 = __ldg(v.s_ptr + e + 1); j < j1; ++j)
+        fma_to(acc, ldc(sv + j), Xn[(int64_t)__ldg(v.s_src + j) * B]);
     // couplings to the neighbouring ADOs
     const int t1 = __ldg(v.row_ptr + n + 1);
     for (int t = __ldg(v.row_ptr + n); t < t1; ++t) {
@@ -96,14 +94,14 @@ __device__ __forceinline__ cx<R> apply_point(const DevView<R> &v, const cx<R> *_
     return acc;
 }
 
-// Inverse of the ADO-local diagonal: 1 / (-i (H_rr - H_cc) - damp + shift), the undamped
-// tier-0 ADO being given the smallest positive rate as damping so the inverse stays bounded.
+// Inverse of the ADO-local diagonal: 1 / (L_s[e][e] - damp + shift), with L_s[e][e] the
+// coefficient of element e on itself in the system superoperator (-i (H_rr - H_cc) without
+// Lindblad terms); the undamped tier-0 ADO is given the smallest positive rate as damping so
+// the inverse stays bounded.
 template <class R>
 __device__ __forceinline__ cx<R> precond_inv(const DevView<R> &v, int64_t n, int e, int set,
                                              const cx<R> &damp, cx<R> shift) {
-    const int r = e / v.d, c = e - r * v.d;
-    const cx<R> hr = ldc(v.hdiag + (int64_t)set * v.d + r), hc = ldc(v.hdiag + (int64_t)set * v.d + c);
-    cx<R> loc = mul_mi(hr - hc) - damp + shift;
+    cx<R> loc = ldc(v.sdiag + (int64_t)set * v.d2 + e) - damp + shift;
     if (__ldg(v.occ_ptr + n) == __ldg(v.occ_ptr + n + 1)) loc.re -= __ldg(v.floor + set);
     return cdiv(cx<R>{R(1), R(0)}, loc);
 }

@@ -3,15 +3,15 @@
 //
 // For each ADO n the CTA first writes the ADO's whole term program into shared memory:
 // for every output element e of the d x d block the list of (source element, complex
-// coefficient) pairs of Eq. HEOM -- the damping term, the system commutator, and the left
-// and right products of every raising / lowering neighbour with its coupling operator,
+// coefficient) pairs of Eq. HEOM -- the damping term, the system superoperator (commutator
+// with H plus any Lindblad terms), and the left and right products of every raising / lowering neighbour with its coupling operator,
 // coefficients already multiplied by the exponent factors and signs. Every warp then
 // streams its columns through that program: one broadcast shared-memory read, one 16-byte
 // coalesced load of VC complex values and 4*VC FMAs per term and lane. The warp-uniform
 // work (decoding neighbour entries, operator structure, coefficients) is done once per ADO
 // per CTA instead of once per lane and term.
 //
-// Program order per element: damping, system commutator, then every neighbour entry (left
+// Program order per element: damping, system superoperator, then every neighbour entry (left
 // products before right products), then the trace row -- the order in which the
 // per-element kernel (apply_point) adds the same terms.
 #pragma once
@@ -147,9 +147,7 @@ __device__ void build_programs(const DevView<R> &v, ProgSmem<R> &ps, int n0, int
         if (t == 0) {
             op = -3;  // damping: coefficient filled per element below
         } else if (t == 1) {
-            op = -1;  // system commutator: -i H X + i X H
-            cl = cx<R>{R(0), R(-1)};
-            cr = cx<R>{R(0), R(1)};
+            op = -1;  // system superoperator: coefficients taken from s_val
         } else if (t <= E + 1) {
             const int4 raw = __ldg(reinterpret_cast<const int4 *>(v.ent) + e0 + t - 2);
             const int k = (int)(int16_t)(raw.y >> 16);
@@ -185,7 +183,7 @@ __device__ void build_programs(const DevView<R> &v, ProgSmem<R> &ps, int n0, int
         const int op = s_op[s_pb[p] + t];
         int len;
         if (op >= 0) len = __ldg(v.t_ptr + op * d2 + e + 1) - __ldg(v.t_ptr + op * d2 + e);
-        else if (op == -1) len = __ldg(v.th_ptr + e + 1) - __ldg(v.th_ptr + e);
+        else if (op == -1) len = __ldg(v.s_ptr + e + 1) - __ldg(v.s_ptr + e);
         else if (op == -3) len = 1;
         else len = (e == 0 && n0 + p == 0 && aug != R(0)) ? d : 0;
         s_off[z] = len;
@@ -230,7 +228,7 @@ __device__ void build_programs(const DevView<R> &v, ProgSmem<R> &ps, int n0, int
         s_item[i] = s_off[d2 * s_pb[p] + e * (s_pb[p + 1] - s_pb[p])];
     }
     // ---------------- fill the programs
-    const cx<R> *hv = v.h_val + (int64_t)set * v.nnzH;
+    const cx<R> *sv = v.s_val + (int64_t)set * v.nS;
     for (int z = tid; z < n_triples; z += blockDim.x) {
         const int p = ado_of_pair(z / d2);
         const int E1 = s_pb[p + 1] - s_pb[p];
@@ -247,10 +245,9 @@ __device__ void build_programs(const DevView<R> &v, ProgSmem<R> &ps, int n0, int
                 s_coef[pos] = ((src >> 16) ? s_cr[q] : s_cl[q]) * ldc(v.t_val + j);
             }
         } else if (op == -1) {
-            for (int j = __ldg(v.th_ptr + e), j1 = __ldg(v.th_ptr + e + 1); j < j1; ++j, ++pos) {
-                const int32_t src = __ldg(v.th_src + j);
-                s_src[pos] = nbase + (src & 0xffff);
-                s_coef[pos] = ((src >> 16) ? s_cr[q] : s_cl[q]) * ldc(hv + __ldg(v.th_vi + j));
+            for (int j = __ldg(v.s_ptr + e), j1 = __ldg(v.s_ptr + e + 1); j < j1; ++j, ++pos) {
+                s_src[pos] = nbase + __ldg(v.s_src + j);
+                s_coef[pos] = ldc(sv + j);
             }
         } else if (op == -3) {
             const cx<R> dmp = damping_of(v, (int64_t)(n0 + p), set);

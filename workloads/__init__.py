@@ -79,7 +79,8 @@ class Model:
 
     ``boson_baths`` holds (V, BosonDL) pairs, ``fermion_baths`` holds (d, FermionLorentz)
     pairs where d is the annihilation operator the lead couples to. The order of the
-    lists is the order of the exponents in the hierarchy.
+    lists is the order of the exponents in the hierarchy. ``lindblad`` holds (F, gamma)
+    pairs: jump operators of weakly coupled environments that carry no ADOs (Fig. 1c).
     """
 
     name: str
@@ -89,6 +90,7 @@ class Model:
     tier_b: int = 0
     tier_f: int = 0
     rho0: np.ndarray | None = None
+    lindblad: list = field(default_factory=list)  # (F, gamma): jump operator and its rate
 
     @property
     def d(self) -> int:
@@ -205,6 +207,39 @@ def charge_cavity_model(eps: float = -3.0, omega_c: float = 1.0, g: float = 0.5,
     return Model("charge_cavity", H, bos, fer, tier_b=tier_b, tier_f=tier_f, rho0=rho0)
 
 
+def bose_einstein(omega: float, kT: float) -> float:
+    """Occupation 1 / (e^{omega/kT} - 1) of a bosonic mode (textbook definition)."""
+    return 1.0 / np.expm1(omega / kT)
+
+
+def drude_lorentz_density(omega: float, lam: float, W: float) -> float:
+    """J(w) = 4 lam W w / (w^2 + W^2) (Methods, Eq. Drude-Lorentz)."""
+    return 4.0 * lam * W * omega / (omega * omega + W * W)
+
+
+def charge_cavity_me_model(eps: float = -3.0, omega_c: float = 1.0, g: float = 0.5,
+                           Gamma: float = 1.0, Delta: float = 0.01, W_b: float = 0.2,
+                           W_f: float = 10.0, kT: float = 0.5, bias: float = 6.0,
+                           n_fock: int = 12, tier_f: int = 2, n_poles: int = 2) -> Model:
+    """Charge-cavity system of Example 2 with its cavity bath replaced by Lindblad terms.
+
+    The bosonic bath's hierarchy is dropped and the cavity loses and gains photons through
+    the jump operators a (rate J(w_c) (n + 1)) and a^dag (rate J(w_c) n), with J the bath's
+    Drude-Lorentz density and n its Bose-Einstein occupation at w_c: the Born-Markov
+    master-equation variant the example compares against. The fermionic leads keep their
+    hierarchy.
+    """
+    H, d, a, V = charge_cavity_ops(eps, omega_c, g, n_fock)
+    fer = [(d, FermionLorentz(Gamma, W_f, bias / 2, kT, n_poles, "pade")),
+           (d, FermionLorentz(Gamma, W_f, -bias / 2, kT, n_poles, "pade"))]
+    J = drude_lorentz_density(omega_c, Delta, W_b)
+    n = bose_einstein(omega_c, kT)
+    rho0 = np.zeros((2 * n_fock, 2 * n_fock), dtype=np.complex128)
+    rho0[0, 0] = 1.0
+    return Model("charge_cavity_me", H, [], fer, tier_b=0, tier_f=tier_f, rho0=rho0,
+                 lindblad=[(a, J * (n + 1.0)), (dag(a), J * n)])
+
+
 def omega_grid(n: int, lo: float = -20.0, hi: float = 20.0) -> np.ndarray:
     """Uniform frequency grid on [lo, hi] with n points."""
     return np.linspace(lo, hi, n)
@@ -267,14 +302,17 @@ def random_hermitian(d: int, rng) -> np.ndarray:
 
 
 def random_raw_problem(d: int, boson_sizes, fermion_sizes, tier_b: int, tier_f: int,
-                       parity: int = 1, seed: int = SEED_VECTORS, dense_fermion_ops=True):
+                       parity: int = 1, seed: int = SEED_VECTORS, dense_fermion_ops=True,
+                       n_lindblad: int = 0):
     """A random HEOM problem in raw form (the user-supplied-exponent route of Fig. 1a).
 
     boson_sizes: list of (kind, n_exp) with kind in {"R", "I", "RI"};
     fermion_sizes: list of n_exp (even; the first half nu=+1, the second half nu=-1 and the
     partner of exponent h is h +- n_exp/2).
-    Returns a dict with keys d, H, baths, tier_b, tier_f, parity. Every bath is a dict
-    {kind, op, coef, rate[, nu, partner]}.
+    n_lindblad: number of random jump operators (complex normal, half of their entries set
+    to zero) with rates ~ U[0.1, 1].
+    Returns a dict with keys d, H, baths, tier_b, tier_f, parity, lindblad. Every bath is a
+    dict {kind, op, coef, rate[, nu, partner]}; every Lindblad term a dict {op, rate}.
     """
     rng = np.random.default_rng(seed)
     H = random_hermitian(d, rng)
@@ -299,7 +337,13 @@ def random_raw_problem(d: int, boson_sizes, fermion_sizes, tier_b: int, tier_f: 
         nu = np.array([1] * h + [-1] * h, dtype=np.int32)
         partner = np.array([i + h for i in range(h)] + [i for i in range(h)], dtype=np.int32)
         baths.append(dict(kind="F", op=op, coef=coef, rate=rate, nu=nu, partner=partner))
-    return dict(d=d, H=H, baths=baths, tier_b=tier_b, tier_f=tier_f, parity=parity)
+    lind = []
+    for _ in range(n_lindblad):
+        F = random_complex((d, d), rng) * 0.5
+        F[rng.random((d, d)) < 0.5] = 0.0
+        lind.append(dict(op=F, rate=float(rng.uniform(0.1, 1.0))))
+    return dict(d=d, H=H, baths=baths, tier_b=tier_b, tier_f=tier_f, parity=parity,
+                lindblad=lind)
 
 
 def random_ado_vector(n_ado: int, d: int, batch: int | None = None,
