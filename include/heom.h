@@ -131,6 +131,28 @@ heom_status heom_build_hierarchy(int d, const heom_c64 *H, int n_baths, const he
                                  int tier_b, int tier_f, int parity, int flags,
                                  heom_hier **out);
 
+/* heom_build_hierarchy with importance pruning (Eq. importance): of the full hierarchy, keep
+ * every ADO at levels (m, n) in {0, 1} x {0, 1} and every other ADO whose importance
+ *   I = |prod_r xi_{j_r} / (Re chi_{j_r} sum_{x<=r} Re chi_{j_x})|
+ *     x |prod_w eta_{q_w} / (Re gamma_{q_w} sum_{x<=w} Re gamma_{q_x})|
+ * reaches importance_th. The members of j and q are taken in ascending exponent order (the
+ * order that reproduces the paper's Table 3 counts); a zero denominator counts as infinite
+ * importance. The kept ADOs stay in canonical order and are numbered 0 .. N-1; couplings
+ * to dropped ADOs are left out (a dropped ADO is zero). The importance uses the exponents
+ * given here: later heom_set_params calls change values, not the kept set.
+ * importance_th = 0 is heom_build_hierarchy. Errors as heom_build_hierarchy, plus HEOM_EINVAL
+ * for a negative or non-finite threshold or a full hierarchy above 2^29 ADOs. */
+heom_status heom_build_hierarchy_pruned(int d, const heom_c64 *H, int n_baths,
+                                        const heom_bath *baths, int tier_b, int tier_f,
+                                        int parity, double importance_th, heom_hier **out);
+
+/* Number of ADOs the hierarchy of these baths has at tiers tier_b / tier_f after importance
+ * pruning at importance_th (0: no pruning), on the host, without building it (Table 3's
+ * counts). Only the kinds, exponent counts, coefficients and rates of the baths are read.
+ * Errors: HEOM_EINVAL for bad arguments or more than 4e10 ADOs to rate. */
+heom_status heom_count_ados(int n_baths, const heom_bath *baths, int tier_b, int tier_f,
+                            double importance_th, int64_t *count);
+
 /* Replace the parameter sets of a hierarchy by n_sets sets that share its structure
  * (operators, exponent kinds, nu, partner map, tiers) and differ in H and in the
  * exponent values: H [n_sets][d][d], coef [n_sets][K], rate [n_sets][K] with K = K_b + K_f

@@ -17,6 +17,16 @@ bit-exactly by the GPU path) is:
   lexicographically ascending as sorted tuples;
 * mixed index = bosonic index * N_f + fermionic index.
 The enumeration below is a plain recursive construction; the index map is a dictionary.
+
+Importance pruning (Eq. importance and the paragraph around it): an ADO's importance is
+  I = |prod_{r=1..m} xi_{j_r} / (Re chi_{j_r} sum_{x<=r} Re chi_{j_x})|
+    x |prod_{w=1..n} eta_{q_w} / (Re gamma_{q_w} sum_{x<=w} Re gamma_{q_x})|,
+and every ADO outside the levels (m, n) in {0, 1} x {0, 1} with I < I_th is dropped.
+Readings: the paper does not fix the order of j and q inside the cumulative sums; listing
+them by ascending exponent index (the canonical exponent order) reproduces every entry of
+Table 3. Pruning is per ADO (not hereditary): a kept ADO keeps its equation, and the terms
+that couple it to dropped ADOs vanish (a dropped ADO is zero). A zero denominator (an
+undamped exponent) makes the importance infinite: the ADO is kept.
 """
 from __future__ import annotations
 
@@ -80,6 +90,45 @@ def build_hierarchy(K_b: int, K_f: int, tier_b: int, tier_f: int) -> Hierarchy:
     ados = [(m, S) for m in bos for S in fer]
     index = {a: i for i, a in enumerate(ados)}
     return Hierarchy(K_b, K_f, tier_b, tier_f, bos, fer, ados, index)
+
+
+def importance(bos_exps, fer_exps, m, S) -> float:
+    """Eq. importance of the ADO (m, S); bos_exps / fer_exps are (coef, rate) lists in the
+    global exponent order, m an occupation vector, S a sorted tuple."""
+    val = 1.0
+    cum = 0.0
+    for k, mk in enumerate(m):  # bosonic multiset j listed by ascending exponent index
+        for _ in range(mk):
+            xi, chi = bos_exps[k]
+            cum += chi.real
+            den = chi.real * cum
+            if den == 0.0:
+                return np.inf
+            val *= abs(xi / den)
+    cum = 0.0
+    for q in S:  # fermionic set q listed by ascending exponent index
+        eta, gam = fer_exps[q]
+        cum += gam.real
+        den = gam.real * cum
+        if den == 0.0:
+            return np.inf
+        val *= abs(eta / den)
+    return val
+
+
+def always_kept(m, S) -> bool:
+    """Levels (m, n) in {0, 1} x {0, 1} are never pruned."""
+    return sum(m) <= 1 and len(S) <= 1
+
+
+def prune_hierarchy(hier: Hierarchy, bos_exps, fer_exps, importance_th: float) -> Hierarchy:
+    """The ADOs of hier whose importance is >= importance_th (or that are always kept), in
+    the canonical order."""
+    ados = [(m, S) for (m, S) in hier.ados
+            if always_kept(m, S) or importance(bos_exps, fer_exps, m, S) >= importance_th]
+    index = {a: i for i, a in enumerate(ados)}
+    return Hierarchy(hier.K_b, hier.K_f, hier.tier_b, hier.tier_f, hier.bos, hier.fer, ados,
+                     index)
 
 
 def ado_count_closed_form(K_b: int, K_f: int, tier_b: int, tier_f: int) -> int:
@@ -152,5 +201,11 @@ def flatten_exponents(problem: dict):
 
 
 def problem_hierarchy(problem: dict) -> Hierarchy:
+    """The problem's hierarchy; pruned when it carries importance_th > 0."""
     bos, fer = flatten_exponents(problem)
-    return build_hierarchy(len(bos), len(fer), problem["tier_b"], problem["tier_f"])
+    h = build_hierarchy(len(bos), len(fer), problem["tier_b"], problem["tier_f"])
+    th = float(problem.get("importance_th", 0.0))
+    if th > 0.0:
+        h = prune_hierarchy(h, [(e.coef, e.rate) for e in bos], [(e.coef, e.rate) for e in fer],
+                            th)
+    return h

@@ -35,6 +35,9 @@ unchanged (Results: the Lindbladian is added to the HEOMLS without extending the
 Reading: the paper gives the one form for every ADO and both parities, so no tier- or
 parity-dependent sign is applied.
 
+Pruned hierarchies (Eq. importance; hierarchy.prune_hierarchy): the terms that couple a kept
+ADO to a dropped one are left out, a dropped ADO being zero.
+
 Liouville space convention of the sparse path: column stacking, vec(A X B) =
 (B^T kron A) vec(X); the ADO vector is the concatenation of vec(rho_n) in ADO order.
 The loop path works on an array X[n] of d x d matrices (the GPU path's row-major layout).
@@ -119,13 +122,19 @@ def apply_loop(problem: dict, X: np.ndarray, hier=None, only=None) -> np.ndarray
             for k, e in enumerate(bos):
                 mu = list(m)
                 mu[k] += 1
-                Xn = X[hier.index[(tuple(mu), S)]]
+                j = hier.index.get((tuple(mu), S))
+                if j is None:  # pruned neighbour (zero)
+                    continue
+                Xn = X[j]
                 acc += -1j * (e.op @ Xn - Xn @ e.op)
         for k, e in enumerate(bos):
             if m[k] > 0:
                 md = list(m)
                 md[k] -= 1
-                Xn = X[hier.index[(tuple(md), S)]]
+                j = hier.index.get((tuple(md), S))
+                if j is None:
+                    continue
+                Xn = X[j]
                 a, b = boson_lower_coefs(e.kind, e.coef)
                 acc += -1j * m[k] * (a * (e.op @ Xn) - b * (Xn @ e.op))
         sigma = p * (-1) ** n
@@ -134,12 +143,18 @@ def apply_loop(problem: dict, X: np.ndarray, hier=None, only=None) -> np.ndarray
                 if q in S:
                     continue
                 Sq = tuple(sorted(S + (q,)))
-                Xn = X[hier.index[(m, Sq)]]
+                j = hier.index.get((m, Sq))
+                if j is None:
+                    continue
+                Xn = X[j]
                 O = op_power(fer[q].op, -fer[q].nu)
                 acc += -1j * p * ordering_sign(q, S) * (O @ Xn - sigma * (Xn @ O))
         for q in S:
             Sq = tuple(r for r in S if r != q)
-            Xn = X[hier.index[(m, Sq)]]
+            j = hier.index.get((m, Sq))
+            if j is None:
+                continue
+            Xn = X[j]
             O = op_power(fer[q].op, fer[q].nu)
             acc += -1j * p * ordering_sign(q, S) * (
                 fer[q].coef * (O @ Xn) + sigma * np.conj(fer[q].partner_coef) * (Xn @ O))
@@ -197,7 +212,9 @@ def build_matrix(problem: dict, hier=None) -> sp.csr_matrix:
             for k, e in enumerate(bos):
                 mu = list(m)
                 mu[k] += 1
-                j = hier.index[(tuple(mu), S)]
+                j = hier.index.get((tuple(mu), S))
+                if j is None:  # pruned neighbour: both blocks of the edge vanish
+                    continue
                 put(i, j, -1j * (spre(e.op) - spost(e.op)))
                 a, b = boson_lower_coefs(e.kind, e.coef)
                 put(j, i, -1j * mu[k] * (a * spre(e.op) - b * spost(e.op)))
@@ -205,7 +222,9 @@ def build_matrix(problem: dict, hier=None) -> sp.csr_matrix:
             for q in range(hier.K_f):
                 if q in S:
                     continue
-                j = hier.index[(m, tuple(sorted(S + (q,))))]
+                j = hier.index.get((m, tuple(sorted(S + (q,)))))
+                if j is None:
+                    continue
                 eps = ordering_sign(q, S)
                 sig_i = p * (-1) ** n
                 sig_j = p * (-1) ** (n + 1)

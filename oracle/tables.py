@@ -5,6 +5,7 @@ Each term of Eq. HEOM for a target ADO i is written as
 with the integers carrying the tier multiplicity, the parity sign (-1)^{delta_{p,-}}, the
 ordering sign eps(q, S) and the P_s sign sigma = p (-1)^n; (a, b, O) depend only on the
 exponent k and the direction (dir = +1: raised neighbour, a = b = 1; dir = -1: lowered).
+In a pruned hierarchy (Eq. importance) an entry whose neighbour was dropped is left out.
 These are the integer tables the GPU path must reproduce bit for bit. ``apply_from_tables``
 evaluates M from them, which the tests pin against the two paths of liouvillian.py.
 """
@@ -27,24 +28,30 @@ def neighbour_table(problem: dict, hier=None):
         n = len(S)
         sigma = p * (-1) ** n
         rows = []
+
+        def add(key, *rest):
+            j = hier.index.get(key)
+            if j is not None:  # a pruned neighbour contributes no entry
+                rows.append((j,) + rest)
+
         if sum(m) < hier.tier_b:
             for k in range(Kb):
                 mu = list(m)
                 mu[k] += 1
-                rows.append((hier.index[(tuple(mu), S)], k, 1, 1, -1))
+                add((tuple(mu), S), k, 1, 1, -1)
         for k in range(Kb):
             if m[k] > 0:
                 md = list(m)
                 md[k] -= 1
-                rows.append((hier.index[(tuple(md), S)], k, -1, m[k], -m[k]))
+                add((tuple(md), S), k, -1, m[k], -m[k])
         for q in range(len(fer)):
             eps = ordering_sign(q, S)
             if q in S:
                 Sq = tuple(r for r in S if r != q)
-                rows.append((hier.index[(m, Sq)], Kb + q, -1, p * eps, p * eps * sigma))
+                add((m, Sq), Kb + q, -1, p * eps, p * eps * sigma)
             elif n < hier.tier_f:
                 Sq = tuple(sorted(S + (q,)))
-                rows.append((hier.index[(m, Sq)], Kb + q, 1, p * eps, -p * eps * sigma))
+                add((m, Sq), Kb + q, 1, p * eps, -p * eps * sigma)
         table.append(rows)
     return table
 

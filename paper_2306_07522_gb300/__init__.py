@@ -65,6 +65,9 @@ _sig = {
                              C.POINTER(_P)],
     "heom_set_params": [_P, C.c_int, _P, _P, _P],
     "heom_set_lindblad": [_P, C.c_int, _P, _P],
+    "heom_build_hierarchy_pruned": [C.c_int, _P, C.c_int, _P, C.c_int, C.c_int, C.c_int,
+                                    C.c_double, C.POINTER(_P)],
+    "heom_count_ados": [C.c_int, _P, C.c_int, C.c_int, C.c_double, _P],
     "heom_hier_info": [_P, _P, _P, _P, _P, _P, _P],
     "heom_ado_index": [_P, _P, _P],
     "heom_ado_label": [_P, C.c_int64, _P],
@@ -200,18 +203,17 @@ class Hierarchy:
             self._h = None
 
 
-def build_hierarchy(problem: dict) -> Hierarchy:
-    d = int(problem["d"])
-    H = _c64(problem["H"])
-    keep = [H]
-    arr = (Bath * max(len(problem["baths"]), 1))()
-    for i, b in enumerate(problem["baths"]):
-        op = _c64(b["op"])
+def _bath_array(baths, keep):
+    arr = (Bath * max(len(baths), 1))()
+    for i, b in enumerate(baths):
         coef = _c64(b["coef"])
         rate = _c64(b["rate"])
-        keep += [op, coef, rate]
+        keep += [coef, rate]
+        if b.get("op") is not None:  # heom_count_ados reads no operator
+            op = _c64(b["op"])
+            keep.append(op)
+            arr[i].op = op.ctypes.data_as(C.POINTER(c64))
         arr[i].kind = KIND[b["kind"]]
-        arr[i].op = op.ctypes.data_as(C.POINTER(c64))
         arr[i].n_exp = len(coef)
         arr[i].coef = coef.ctypes.data_as(C.POINTER(c64))
         arr[i].rate = rate.ctypes.data_as(C.POINTER(c64))
@@ -221,16 +223,40 @@ def build_hierarchy(problem: dict) -> Hierarchy:
             keep += [nu, partner]
             arr[i].nu = nu.ctypes.data_as(C.POINTER(C.c_int))
             arr[i].partner = partner.ctypes.data_as(C.POINTER(C.c_int))
+    return arr
+
+
+def build_hierarchy(problem: dict) -> Hierarchy:
+    """heom_build_hierarchy, or heom_build_hierarchy_pruned when the problem carries
+    importance_th > 0; then heom_set_lindblad for its Lindblad terms."""
+    d = int(problem["d"])
+    H = _c64(problem["H"])
+    keep = [H]
+    arr = _bath_array(problem["baths"], keep)
     out = C.c_void_p()
-    _check(_lib.heom_build_hierarchy(d, _ptr(H), len(problem["baths"]), C.cast(arr, C.c_void_p),
-                                     int(problem["tier_b"]), int(problem["tier_f"]),
-                                     int(problem.get("parity", 1)), 0, C.byref(out)),
-           "heom_build_hierarchy")
+    th = float(problem.get("importance_th", 0.0))
+    args = (d, _ptr(H), len(problem["baths"]), C.cast(arr, C.c_void_p), int(problem["tier_b"]),
+            int(problem["tier_f"]), int(problem.get("parity", 1)))
+    if th > 0.0:
+        _check(_lib.heom_build_hierarchy_pruned(*args, th, C.byref(out)),
+               "heom_build_hierarchy_pruned")
+    else:
+        _check(_lib.heom_build_hierarchy(*args, 0, C.byref(out)), "heom_build_hierarchy")
     h = Hierarchy(out, None)
     if problem.get("lindblad"):
         set_lindblad(h, [t["op"] for t in problem["lindblad"]],
                      [t["rate"] for t in problem["lindblad"]])
     return h
+
+
+def count_ados(baths, tier_b: int, tier_f: int, importance_th: float = 0.0) -> int:
+    """heom_count_ados: hierarchy size after importance pruning, computed on the host."""
+    keep = []
+    arr = _bath_array(baths, keep)
+    n = C.c_int64()
+    _check(_lib.heom_count_ados(len(baths), C.cast(arr, C.c_void_p), int(tier_b), int(tier_f),
+                                float(importance_th), C.byref(n)), "heom_count_ados")
+    return n.value
 
 
 def set_lindblad(h: Hierarchy, ops, rates):

@@ -5,7 +5,8 @@
 // which sign), the definitions of A, B, C, D and P_s below it; Methods (exponents of the
 // Lorentzian and Drude-Lorentz baths). The enumeration here is combinatorial ranking
 // (compositions for bosons, the combinatorial number system for fermionic subsets), so a
-// neighbour's index is computed, not looked up.
+// neighbour's index is computed, not looked up; with importance pruning (Eq. importance) the
+// computed full index goes through one table to the kept ADO's index.
 #include <cmath>
 #include <complex>
 #include <cstdarg>
@@ -569,14 +570,119 @@ heom_status upload_params(heom_hier *h, int n_sets, const heom_c64 *H, const heo
 
 }  // namespace
 
+namespace {
+
+// Largest full hierarchy (bosonic x fermionic product) that importance pruning enumerates.
+constexpr int64_t kMaxPruneFull = int64_t(1) << 29;
+
+// Eq. importance, evaluated in one fixed sequence: the bosonic multiset j listed by
+// ascending exponent index (exponent k repeated m_k times), then the fermionic set q by
+// ascending index; each member multiplies the running product by |c / (Re r * cum)| with cum
+// the running sum of Re r within its part. A zero denominator makes the importance infinite.
+struct Importance {
+    const heom_c64 *coef, *rate;  // global exponent order (bosonic first)
+    int Kb;
+    double bosonic(const std::vector<int> &m) const {
+        double val = 1.0, cum = 0.0;
+        for (int k = 0; k < Kb; ++k)
+            for (int c = 0; c < m[k]; ++c) {
+                const double r = rate[k].re;
+                cum += r;
+                const double den = r * cum;
+                if (den == 0.0) return INFINITY;
+                val *= std::hypot(coef[k].re / den, coef[k].im / den);
+            }
+        return val;
+    }
+    // continue the running product val of the bosonic part over the fermionic set S
+    double with_fermionic(double val, uint64_t S) const {
+        if (std::isinf(val)) return val;
+        double cum = 0.0;
+        for (uint64_t T = S; T; T &= T - 1) {
+            const int g = Kb + __builtin_ctzll(T);
+            const double r = rate[g].re;
+            cum += r;
+            const double den = r * cum;
+            if (den == 0.0) return INFINITY;
+            val *= std::hypot(coef[g].re / den, coef[g].im / den);
+        }
+        return val;
+    }
+};
+
+// Levels (m, n) in {0, 1} x {0, 1} are never pruned; every other ADO is kept when its
+// importance reaches the threshold.
+bool keep_ado(const Importance &imp, double bos_val, int tb, uint64_t S, double th) {
+    const int n = __builtin_popcountll(S);
+    if (tb <= 1 && n <= 1) return true;
+    return imp.with_fermionic(bos_val, S) >= th;
+}
+
+// Every fermionic subset of {0..Kf-1} with at most tf elements: size ascending, then
+// lexicographically ascending (the canonical order).
+template <class F>
+void for_each_subset(int Kf, int tf, F &&fn) {
+    for (int n = 0; n <= tf; ++n) {
+        if (n == 0) { fn(0ULL); continue; }
+        std::vector<int> c(n);
+        for (int i = 0; i < n; ++i) c[i] = i;
+        while (true) {
+            uint64_t S = 0;
+            for (int v : c) S |= 1ULL << v;
+            fn(S);
+            int i = n - 1;
+            while (i >= 0 && c[i] == Kf - n + i) --i;
+            if (i < 0) break;
+            ++c[i];
+            for (int j = i + 1; j < n; ++j) c[j] = c[j - 1] + 1;
+        }
+    }
+}
+
+// Every bosonic occupation vector with |m| <= tb: tier ascending, lexicographically
+// descending inside a tier (the canonical order).
+template <class F>
+void for_each_occupation(int Kb, int tb, F &&fn) {
+    for (int t = 0; t <= tb; ++t) {
+        std::vector<int> m(Kb, 0);
+        if (Kb == 0) { if (t == 0) fn(m); continue; }
+        m[0] = t;
+        do { fn(m); } while (next_comp(m));
+    }
+}
+
+heom_status build_impl(int d, const heom_c64 *H, int n_baths, const heom_bath *baths, int tier_b,
+                       int tier_f, int parity, double th, heom_hier **out);
+
+}  // namespace
+
 extern "C" heom_status heom_build_hierarchy(int d, const heom_c64 *H, int n_baths,
                                             const heom_bath *baths, int tier_b, int tier_f,
                                             int parity, int flags, heom_hier **out) {
+    if (flags != 0) { set_error("heom_build_hierarchy: flags must be 0"); return HEOM_EINVAL; }
+    return build_impl(d, H, n_baths, baths, tier_b, tier_f, parity, 0.0, out);
+}
+
+extern "C" heom_status heom_build_hierarchy_pruned(int d, const heom_c64 *H, int n_baths,
+                                                   const heom_bath *baths, int tier_b, int tier_f,
+                                                   int parity, double importance_th,
+                                                   heom_hier **out) {
+    if (!(importance_th >= 0.0) || !std::isfinite(importance_th)) {
+        set_error("heom_build_hierarchy_pruned: importance_th must be finite and >= 0");
+        return HEOM_EINVAL;
+    }
+    return build_impl(d, H, n_baths, baths, tier_b, tier_f, parity, importance_th, out);
+}
+
+namespace {
+
+heom_status build_impl(int d, const heom_c64 *H, int n_baths, const heom_bath *baths, int tier_b,
+                       int tier_f, int parity, double th, heom_hier **out) {
     if (!out) { set_error("heom_build_hierarchy: out is NULL"); return HEOM_EINVAL; }
     *out = nullptr;
     if (d < 1 || d > 64 || !H || n_baths < 0 || (n_baths > 0 && !baths) || tier_b < 0 ||
-        tier_f < 0 || (parity != 1 && parity != -1) || flags != 0) {
-        set_error("heom_build_hierarchy: need 1 <= d <= 64, H, tiers >= 0, parity = +-1, flags 0");
+        tier_f < 0 || (parity != 1 && parity != -1)) {
+        set_error("heom_build_hierarchy: need 1 <= d <= 64, H, tiers >= 0, parity = +-1");
         return HEOM_EINVAL;
     }
     for (int i = 0; i < d * d; ++i)
@@ -657,79 +763,84 @@ extern "C" heom_status heom_build_hierarchy(int d, const heom_c64 *H, int n_bath
     h->N = h->N_b * h->N_f;
     try {
         h->bos.reserve(rk.Nb);
-        for (int t = 0; t <= h->tier_b; ++t) {
-            std::vector<int> m(Kb, 0);
-            if (Kb == 0) { if (t == 0) h->bos.push_back(m); continue; }
-            m[0] = t;
-            do { h->bos.push_back(m); } while (next_comp(m));
-        }
+        for_each_occupation(Kb, h->tier_b, [&](const std::vector<int> &m) { h->bos.push_back(m); });
         h->fer.reserve(rk.Nf);
-        for (int n = 0; n <= h->tier_f; ++n) {
-            if (n == 0) { h->fer.push_back(0); continue; }
-            std::vector<int> c(n);
-            for (int i = 0; i < n; ++i) c[i] = i;
-            while (true) {
-                uint64_t S = 0;
-                for (int v : c) S |= 1ULL << v;
-                h->fer.push_back(S);
-                int i = n - 1;
-                while (i >= 0 && c[i] == Kf - n + i) --i;
-                if (i < 0) break;
-                ++c[i];
-                for (int j = i + 1; j < n; ++j) c[j] = c[j - 1] + 1;
+        for_each_subset(Kf, h->tier_f, [&](uint64_t S) { h->fer.push_back(S); });
+        // ---- importance pruning (Eq. importance): keep the ADOs that reach the threshold
+        if (th > 0.0) {
+            if (h->N > kMaxPruneFull) {
+                set_error("heom_build_hierarchy_pruned: the full hierarchy has more than 2^29 ADOs");
+                delete h; return HEOM_EINVAL;
             }
+            const Importance imp{coef.data(), rate.data(), Kb};
+            h->importance_th = th;
+            h->f2c.assign((size_t)h->N, -1);
+            for (int64_t ib = 0; ib < h->N_b; ++ib) {
+                const std::vector<int> &m = h->bos[ib];
+                int tb = 0;
+                for (int v : m) tb += v;
+                const double bv = imp.bosonic(m);
+                for (int64_t jf = 0; jf < h->N_f; ++jf)
+                    if (keep_ado(imp, bv, tb, h->fer[jf], th)) {
+                        h->f2c[(size_t)(ib * h->N_f + jf)] = (int32_t)h->c2f.size();
+                        h->c2f.push_back(ib * h->N_f + jf);
+                    }
+            }
+            h->N = (int64_t)h->c2f.size();
         }
-        // ---- neighbour / sign tables
+        // ---- neighbour / sign tables (an entry whose neighbour was pruned is left out)
         const int p = parity;
         std::vector<int32_t> occ_ptr(h->N + 1, 0);
         std::vector<OccEntry> occ;
         h->row_ptr.assign(h->N + 1, 0);
         std::vector<int> mm(Kb);
-        for (int64_t ib = 0; ib < h->N_b; ++ib) {
+        for (int64_t i = 0; i < h->N; ++i) {
+            const int64_t full = h->full_of(i), ib = full / h->N_f, jf = full % h->N_f;
             const std::vector<int> &m = h->bos[ib];
             int tb = 0;
             for (int v : m) tb += v;
-            for (int64_t jf = 0; jf < h->N_f; ++jf) {
-                const uint64_t S = h->fer[jf];
-                const int64_t i = ib * h->N_f + jf;
-                const int n = __builtin_popcountll(S);
-                const int sigma = ((n & 1) ? -p : p);
-                if (tb < h->tier_b) {
-                    for (int k = 0; k < Kb; ++k) {
-                        mm = m; mm[k] += 1;
-                        int64_t j = rk.rank_bos(mm.data()) * h->N_f + jf;
-                        h->ent.push_back({(int32_t)j, (int16_t)op_slot_of_bath[h->exp_bath[k]], (int16_t)k, 1, 1, -1, 0});
-                    }
-                }
+            const uint64_t S = h->fer[jf];
+            const int n = __builtin_popcountll(S);
+            const int sigma = ((n & 1) ? -p : p);
+            if (tb < h->tier_b) {
                 for (int k = 0; k < Kb; ++k) {
-                    if (m[k] == 0) continue;
-                    mm = m; mm[k] -= 1;
-                    int64_t j = rk.rank_bos(mm.data()) * h->N_f + jf;
-                    h->ent.push_back({(int32_t)j, (int16_t)op_slot_of_bath[h->exp_bath[k]], (int16_t)k, -1,
-                                      (int16_t)m[k], (int16_t)(-m[k]), 0});
+                    mm = m; mm[k] += 1;
+                    const int64_t j = h->compact_of(rk.rank_bos(mm.data()) * h->N_f + jf);
+                    if (j < 0) continue;
+                    h->ent.push_back({(int32_t)j, (int16_t)op_slot_of_bath[h->exp_bath[k]], (int16_t)k, 1, 1, -1, 0});
                 }
-                for (int q = 0; q < Kf; ++q) {
-                    const int g = Kb + q;
-                    const int slot = op_slot_of_bath[h->exp_bath[g]];
-                    const int nu = h->exp_nu[g];
-                    const int eps = (__builtin_popcountll(S & ((1ULL << q) - 1ULL)) & 1) ? -1 : 1;
-                    if (S >> q & 1ULL) {  // lowered neighbour: C term, O = d^{nu}
-                        int64_t j = ib * h->N_f + rk.rank_fer(S & ~(1ULL << q));
-                        h->ent.push_back({(int32_t)j, (int16_t)(slot + (nu == 1 ? 1 : 0)), (int16_t)g, -1,
-                                          (int16_t)(p * eps), (int16_t)(p * eps * sigma), 0});
-                    } else if (n < h->tier_f) {  // raised neighbour: A term, O = d^{-nu}
-                        int64_t j = ib * h->N_f + rk.rank_fer(S | (1ULL << q));
-                        h->ent.push_back({(int32_t)j, (int16_t)(slot + (nu == 1 ? 0 : 1)), (int16_t)g, 1,
-                                          (int16_t)(p * eps), (int16_t)(-p * eps * sigma), 0});
-                    }
-                }
-                h->row_ptr[i + 1] = (int32_t)h->ent.size();
-                for (int k = 0; k < Kb; ++k)
-                    if (m[k]) occ.push_back({(int16_t)k, (int16_t)m[k]});
-                for (int q = 0; q < Kf; ++q)
-                    if (S >> q & 1ULL) occ.push_back({(int16_t)(Kb + q), 1});
-                occ_ptr[i + 1] = (int32_t)occ.size();
             }
+            for (int k = 0; k < Kb; ++k) {
+                if (m[k] == 0) continue;
+                mm = m; mm[k] -= 1;
+                const int64_t j = h->compact_of(rk.rank_bos(mm.data()) * h->N_f + jf);
+                if (j < 0) continue;
+                h->ent.push_back({(int32_t)j, (int16_t)op_slot_of_bath[h->exp_bath[k]], (int16_t)k, -1,
+                                  (int16_t)m[k], (int16_t)(-m[k]), 0});
+            }
+            for (int q = 0; q < Kf; ++q) {
+                const int g = Kb + q;
+                const int slot = op_slot_of_bath[h->exp_bath[g]];
+                const int nu = h->exp_nu[g];
+                const int eps = (__builtin_popcountll(S & ((1ULL << q) - 1ULL)) & 1) ? -1 : 1;
+                if (S >> q & 1ULL) {  // lowered neighbour: C term, O = d^{nu}
+                    const int64_t j = h->compact_of(ib * h->N_f + rk.rank_fer(S & ~(1ULL << q)));
+                    if (j < 0) continue;
+                    h->ent.push_back({(int32_t)j, (int16_t)(slot + (nu == 1 ? 1 : 0)), (int16_t)g, -1,
+                                      (int16_t)(p * eps), (int16_t)(p * eps * sigma), 0});
+                } else if (n < h->tier_f) {  // raised neighbour: A term, O = d^{-nu}
+                    const int64_t j = h->compact_of(ib * h->N_f + rk.rank_fer(S | (1ULL << q)));
+                    if (j < 0) continue;
+                    h->ent.push_back({(int32_t)j, (int16_t)(slot + (nu == 1 ? 0 : 1)), (int16_t)g, 1,
+                                      (int16_t)(p * eps), (int16_t)(-p * eps * sigma), 0});
+                }
+            }
+            h->row_ptr[i + 1] = (int32_t)h->ent.size();
+            for (int k = 0; k < Kb; ++k)
+                if (m[k]) occ.push_back({(int16_t)k, (int16_t)m[k]});
+            for (int q = 0; q < Kf; ++q)
+                if (S >> q & 1ULL) occ.push_back({(int16_t)(Kb + q), 1});
+            occ_ptr[i + 1] = (int32_t)occ.size();
         }
         h->E = (int64_t)h->ent.size();
         if (h->E > INT32_MAX) { set_error("heom_build_hierarchy: table too large"); delete h; return HEOM_EINVAL; }
@@ -787,6 +898,60 @@ extern "C" heom_status heom_build_hierarchy(int d, const heom_c64 *H, int n_bath
         return HEOM_ENOMEM;
     }
     *out = h;
+    return HEOM_OK;
+}
+
+}  // namespace
+
+extern "C" heom_status heom_count_ados(int n_baths, const heom_bath *baths, int tier_b, int tier_f,
+                                       double importance_th, int64_t *count) {
+    if (!count || n_baths < 0 || (n_baths > 0 && !baths) || tier_b < 0 || tier_f < 0 ||
+        !(importance_th >= 0.0) || !std::isfinite(importance_th)) {
+        set_error("heom_count_ados: need count, baths, tiers >= 0 and a finite importance_th >= 0");
+        return HEOM_EINVAL;
+    }
+    // exponents in the global order: bosonic baths first, then fermionic, each in call order
+    std::vector<heom_c64> coef, rate;
+    int Kb = 0, Kf = 0;
+    for (int pass = 0; pass < 2; ++pass)
+        for (int b = 0; b < n_baths; ++b) {
+            const heom_bath &B = baths[b];
+            if (B.kind < 0 || B.kind > 3 || B.n_exp < 0 || (B.n_exp > 0 && (!B.coef || !B.rate))) {
+                set_error("heom_count_ados: bath %d: bad kind, n_exp or NULL arrays", b);
+                return HEOM_EINVAL;
+            }
+            if ((pass == 0) == (B.kind == HEOM_FERMION)) continue;
+            for (int k = 0; k < B.n_exp; ++k) {
+                if (!finite(B.coef[k]) || !finite(B.rate[k])) {
+                    set_error("heom_count_ados: bath %d exponent %d: non-finite value", b, k);
+                    return HEOM_EINVAL;
+                }
+                coef.push_back(B.coef[k]);
+                rate.push_back(B.rate[k]);
+            }
+            (pass == 0 ? Kb : Kf) += B.n_exp;
+        }
+    if (Kf > 64) { set_error("heom_count_ados: at most 64 fermionic exponents"); return HEOM_EINVAL; }
+    Ranker rk;
+    rk.init(Kb, Kf, tier_b, tier_f);
+    if (importance_th == 0.0) {
+        if ((double)rk.Nb * (double)rk.Nf > 9.0e18) { set_error("heom_count_ados: count overflows"); return HEOM_EINVAL; }
+        *count = (int64_t)(rk.Nb * rk.Nf);
+        return HEOM_OK;
+    }
+    if ((double)rk.Nb * (double)rk.Nf > 4.0e10) {
+        set_error("heom_count_ados: more than 4e10 ADOs to rate");
+        return HEOM_EINVAL;
+    }
+    const Importance imp{coef.data(), rate.data(), Kb};
+    int64_t n_keep = 0;
+    for_each_occupation(Kb, rk.tb, [&](const std::vector<int> &m) {
+        int tb = 0;
+        for (int v : m) tb += v;
+        const double bv = imp.bosonic(m);
+        for_each_subset(Kf, rk.tf, [&](uint64_t S) { n_keep += keep_ado(imp, bv, tb, S, importance_th); });
+    });
+    *count = n_keep;
     return HEOM_OK;
 }
 
@@ -854,7 +1019,7 @@ extern "C" heom_status heom_ado_index(const heom_hier *h, const int *occ, int64_
         if (v) S |= 1ULL << q;
     }
     int64_t ib = rk.rank_bos(occ), jf = rk.rank_fer(S);
-    *idx = (ib < 0 || jf < 0) ? -1 : ib * h->N_f + jf;
+    *idx = (ib < 0 || jf < 0) ? -1 : h->compact_of(ib * h->N_f + jf);
     return HEOM_OK;
 }
 
@@ -863,8 +1028,9 @@ extern "C" heom_status heom_ado_label(const heom_hier *h, int64_t idx, int *occ_
         set_error("heom_ado_label: index out of range or NULL argument");
         return HEOM_EINVAL;
     }
-    const std::vector<int> &m = h->bos[idx / h->N_f];
-    uint64_t S = h->fer[idx % h->N_f];
+    const int64_t full = h->full_of(idx);
+    const std::vector<int> &m = h->bos[full / h->N_f];
+    uint64_t S = h->fer[full % h->N_f];
     for (int k = 0; k < h->K_b; ++k) occ_out[k] = m[k];
     for (int q = 0; q < h->K_f; ++q) occ_out[h->K_b + q] = (int)(S >> q & 1ULL);
     return HEOM_OK;

@@ -138,6 +138,14 @@ struct heom_hier {
     // host copies (dictionary and table export)
     std::vector<std::vector<int>> bos;      // bosonic occupation vectors in order
     std::vector<uint64_t> fer;              // fermionic subsets (bit masks) in order
+    // Importance pruning (heom_build_hierarchy_pruned): the ADOs are the kept subset of the
+    // full product hierarchy (full index = bosonic rank * N_f + fermionic rank), in the same
+    // order. Both maps are empty without pruning (ADO index = full index).
+    double importance_th = 0.0;
+    std::vector<int64_t> c2f;               // [N] full index of each ADO
+    std::vector<int32_t> f2c;               // [N_b * N_f] ADO of each full index, -1 if dropped
+    int64_t full_of(int64_t n) const { return c2f.empty() ? n : c2f[(size_t)n]; }
+    int64_t compact_of(int64_t f) const { return f2c.empty() ? f : (int64_t)f2c[(size_t)f]; }
     std::vector<int32_t> row_ptr;
     std::vector<heom::NbEntry> ent;
     std::vector<int> exp_kind;              // heom_kind per global exponent

@@ -557,7 +557,7 @@ extern "C" heom_status heom_mlp_train_step(heom_mlp *net, const float *x, const 
 static std::vector<int> tier1_ados(const heom_hier *h) {
     std::vector<int> out;
     for (int64_t n = 0; n < h->N; ++n) {
-        const int64_t bi = n / h->N_f, fi = n % h->N_f;
+        const int64_t full = h->full_of(n), bi = full / h->N_f, fi = full % h->N_f;
         int tier = __builtin_popcountll(h->fer[fi]);
         for (int m : h->bos[bi]) tier += m;
         if (tier == 1) out.push_back((int)n);

@@ -1418,11 +1418,11 @@ extern "C" heom_status heom_current(const heom_hier *h, const void *x, int64_t b
         if (h->exp_kind[g] != HEOM_FERMION || !in_lead[bath]) continue;
         int64_t idx = -1;
         for (int64_t f = 0; f < h->N_f; ++f)
-            if (h->fer[f] == (1ULL << q)) { idx = f; break; }
+            if (h->fer[f] == (1ULL << q)) { idx = h->compact_of(f); break; }  // bosonic rank 0
         if (idx < 0) continue;
         const int nu = h->exp_nu[g];
         const int slot = h->bath_slot[bath] + (nu == 1 ? 0 : 1);
-        ado.push_back((int)idx);  // bosonic index 0: ADO index = fermionic index
+        ado.push_back((int)idx);
         sign.push_back(nu);
         O.insert(O.end(), h->ops.begin() + (size_t)slot * d2, h->ops.begin() + (size_t)(slot + 1) * d2);
     }
