@@ -81,22 +81,25 @@ def test_pruned_apply_matches_oracle(heom, prec, batch, parity):
     assert rel_err(Yg, Y) < (1e-10 if prec == "fp64" else 1e-5)
 
 
-def _example1(n_max, th, bias=4.0):
+def _example1(heom, n_max, th, bias=4.0):
+    """Example 1 with the oracle's exponents and with the library's own."""
     m = W.siam_model(eps=-5.0, U=10.0, Gamma=1.0, W=10.0, kT=0.5, mu=bias / 2, n_poles=6,
                      tier=n_max)
-    return m, dict(hy.model_to_problem(m), importance_th=th)
+    return (dict(hy.model_to_problem(m), importance_th=th),
+            dict(heom.problem_from_model(m), importance_th=th))
 
 
 @pytest.mark.parametrize("prec", ["FP64", "MIXED"])
 def test_pruned_example1_steady_state_and_current(heom, prec):
     """Example 1 (K_f = 56) at n_max = 2, I_th = 1e-4: 873 ADOs (Table 3)."""
     import torch
-    m, prob = _example1(2, 1e-4)
+    prob, prob_g = _example1(heom, 2, 1e-4)
     h = hy.problem_hierarchy(prob)
     assert h.n_ado == 873
     M = lv.build_matrix(prob, h)
     Xo = so.steady_state(M, 4)
-    g = heom.build_hierarchy(prob)
+    g = heom.build_hierarchy(prob_g)
+    assert g.n_ado == 873
     x = torch.zeros((h.n_ado, 4, 4), dtype=torch.complex128, device="cuda")
     st, stats = heom.steady(g, x, tol=1e-10, max_iter=3000, prec=getattr(heom, prec))
     X = x.cpu().numpy()
@@ -117,8 +120,7 @@ def test_example1_current_converges_with_threshold(heom):
     import torch
 
     def solve(bias, th):
-        m, prob = _example1(4, th, bias)
-        g = heom.build_hierarchy(prob)
+        g = heom.build_hierarchy(_example1(heom, 4, th, bias)[1])
         x = torch.zeros((g.n_ado, 4, 4), dtype=torch.complex128, device="cuda")
         st, stats = heom.steady(g, x, tol=1e-10, max_iter=20000, prec=heom.MIXED)
         assert st == heom.OK
