@@ -18,7 +18,8 @@
  * - ADO order (the "hierarchy dictionary", Fig. 1e): bosonic occupation vectors m
  *   (|m| <= tier_b) by tier ascending then lexicographically descending, fermionic index
  *   sets S (|S| <= tier_f) by size ascending then lexicographically ascending as sorted
- *   tuples; ADO index = bosonic index * N_f + fermionic index. Exponents are numbered in
+ *   tuples; ADO index = bosonic index * N_f + fermionic index (in an importance-pruned
+ *   hierarchy the kept ADOs in this order, renumbered 0 .. N-1). Exponents are numbered in
  *   bath order, then in order within each bath; bosonic exponents come first
  *   (0 .. K_b-1), fermionic ones after (K_b .. K_b+K_f-1) in the occupation arrays below.
  * - Ownership: every input array is copied by the call that receives it. Device vectors are
@@ -220,6 +221,27 @@ heom_status heom_apply(const heom_hier *h, const void *x, void *y, int64_t batch
  * Library workspace is allocated on first use and kept in h. Synchronises s. */
 heom_status heom_evolve(heom_hier *h, void *ados, int64_t batch, double dt, int64_t n_steps,
                         int64_t save_every, void *rho_traj, int prec, heom_stream s);
+
+/* Time-dependent system Hamiltonian H_s(t) (Eq. H_total; the commutator L_s(t) = [H_s(t), .]
+ * of Eq. HEOM acts on every ADO): H_s(t) = H + sum_k f_k(t) H_k, with H the hierarchy's
+ * Hamiltonian (of each parameter set) and H_k the n_drive operators given here
+ * ([n_drive][d][d], row-major, host; copied). The scalar functions f_k are supplied per call
+ * to heom_evolve_td; every other call (apply, evolve, solvers, spectra) uses f_k = 0.
+ * n_drive = 0 removes them. Errors: HEOM_EINVAL for n_drive outside [0, 64], NULL operators
+ * with n_drive > 0 or non-finite entries (the previous operators then stay); HEOM_ENOMEM;
+ * HEOM_ECUDA. */
+heom_status heom_set_drive(heom_hier *h, int n_drive, const heom_c64 *Hk);
+
+/* heom_evolve with H_s(t) = H + sum_k f_k(t) H_k (heom_set_drive). f: host array
+ * [n_drive][2 n_steps + 1], f[k][j] = f_k(t0 + j dt / 2) for the start time t0 of the call;
+ * stage 1 of step n (n = 0 .. n_steps-1) uses sample 2n, stages 2 and 3 sample 2n + 1 and
+ * stage 4 sample 2n + 2 (classical RK4 evaluates the right-hand side at t, t + dt/2 twice and
+ * t + dt). f may be NULL when the hierarchy has no drive operators. Other arguments, layout
+ * and errors as heom_evolve, plus HEOM_EINVAL for a non-finite f. Allocates the drive table
+ * and the values of up to 1,025 samples on the device. Synchronises s. */
+heom_status heom_evolve_td(heom_hier *h, void *ados, int64_t batch, double dt, int64_t n_steps,
+                           const double *f, int64_t save_every, void *rho_traj, int prec,
+                           heom_stream s);
 
 /* heom_evolve without any allocation. The paper has no counterpart: this serves callers
  * that cannot let a library call cudaMalloc or cudaFree -- a process whose device memory is

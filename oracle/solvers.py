@@ -12,6 +12,8 @@ Paper passages followed:
 
 Readings (the paper does not fix them):
 * Dynamics: classical fixed-step RK4 (the paper's adaptive ODE solvers are not specified).
+  A time-dependent H_s(t) (Eq. H_total) is written H + sum_k f_k(t) H_k with scalar f_k
+  sampled on the half-step grid, which is where classical RK4 evaluates the right-hand side.
 * Stationary state: the equation of the (0,0) element of the tier-0 ADO is replaced by the
   normalisation Tr rho_sys = 1 (that equation is redundant because M preserves the trace).
 * b = O rho_n for every ADO n (left multiplication, no extra sign) in the spectra.
@@ -40,6 +42,47 @@ def rk4(apply, x0: np.ndarray, dt: float, n_steps: int, save_every: int = 1,
         k4 = apply(x + dt * k3)
         x = x + (dt / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
         if (s + 1) % save_every == 0:
+            snaps.append(observe(x))
+    return x, snaps
+
+
+def drive_superoperators(n_ado: int, ops):
+    """-i [H_k, .] on every ADO for each drive operator H_k: a time-dependent system
+    Hamiltonian H_s(t) = H + sum_k f_k(t) H_k enters Eq. HEOM only through the commutator
+    L_s(t) = [H_s(t), .], which acts on every ADO alike. Column stacking, block diagonal."""
+    from .liouvillian import spost, spre
+
+    out = []
+    for Hk in ops:
+        Hk = np.asarray(Hk, np.complex128)
+        blk = -1j * (spre(Hk) - spost(Hk))
+        out.append(sp.kron(sp.identity(n_ado, format="csr"), blk, format="csr"))
+    return out
+
+
+def rk4_td(M0, Ls, f, x0: np.ndarray, dt: float, n_steps: int, save_every: int = 1,
+           observe=lambda x: x.copy()):
+    """Classical RK4 for dx/dt = (M0 + sum_k f_k(t) L_k) x. f[k][j] = f_k(t0 + j dt / 2): the
+    four stages of step n evaluate the right-hand side at t_n (sample 2n), t_n + dt/2 (sample
+    2n + 1, twice) and t_n + dt (sample 2n + 2)."""
+    f = np.asarray(f, np.float64).reshape(len(Ls), 2 * n_steps + 1)
+
+    def rhs(j, v):
+        y = M0 @ v
+        for k, L in enumerate(Ls):
+            y = y + f[k, j] * (L @ v)
+        return y
+
+    x = x0.copy()
+    snaps = [observe(x)]
+    for n in range(n_steps):
+        j = 2 * n
+        k1 = rhs(j, x)
+        k2 = rhs(j + 1, x + 0.5 * dt * k1)
+        k3 = rhs(j + 1, x + 0.5 * dt * k2)
+        k4 = rhs(j + 2, x + dt * k3)
+        x = x + (dt / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+        if (n + 1) % save_every == 0:
             snaps.append(observe(x))
     return x, snaps
 

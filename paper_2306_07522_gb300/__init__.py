@@ -65,6 +65,8 @@ _sig = {
                              C.POINTER(_P)],
     "heom_set_params": [_P, C.c_int, _P, _P, _P],
     "heom_set_lindblad": [_P, C.c_int, _P, _P],
+    "heom_set_drive": [_P, C.c_int, _P],
+    "heom_evolve_td": [_P, _P, C.c_int64, C.c_double, C.c_int64, _P, C.c_int64, _P, C.c_int, _P],
     "heom_build_hierarchy_pruned": [C.c_int, _P, C.c_int, _P, C.c_int, C.c_int, C.c_int,
                                     C.c_double, C.POINTER(_P)],
     "heom_count_ados": [C.c_int, _P, C.c_int, C.c_int, C.c_double, _P],
@@ -346,6 +348,34 @@ def evolve(h: Hierarchy, ados, dt: float, n_steps: int, save_every: int = 0, str
     _check(_lib.heom_evolve(h.handle, _dptr(ados), B, dt, n_steps, max(save_every, 1),
                             _dptr(traj) if traj is not None else None, prec, _stream(stream)),
            "heom_evolve")
+    return traj
+
+
+def set_drive(h: Hierarchy, ops):
+    """Drive operators H_k of H(t) = H + sum_k f_k(t) H_k ([n, d, d]); [] removes them."""
+    n = len(ops)
+    Hk = _c64(np.reshape(ops, (n, h.d, h.d)) if n else np.zeros((1, h.d, h.d)))
+    _check(_lib.heom_set_drive(h.handle, n, _ptr(Hk)), "heom_set_drive")
+    h.n_drive = n
+
+
+def evolve_td(h: Hierarchy, ados, dt: float, n_steps: int, f, save_every: int = 0, stream=None):
+    """RK4 in place with H(t) = H + sum_k f_k(t) H_k; f [n_drive, 2 n_steps + 1] holds
+    f_k(t0 + j dt / 2). Returns the rho_sys snapshots (n_saves, d, d[, batch]) or None."""
+    import torch
+    prec = _prec_of(ados)
+    B = _batch_of(h, ados)
+    fa = np.ascontiguousarray(f, np.float64).reshape(-1)
+    if fa.size != getattr(h, "n_drive", 0) * (2 * n_steps + 1):
+        raise ValueError("f must have shape (n_drive, 2 n_steps + 1)")
+    traj = None
+    if save_every:
+        shape = (n_steps // save_every + 1, h.d, h.d) + ((B,) if ados.dim() == 4 else ())
+        traj = torch.empty(shape, dtype=ados.dtype, device=ados.device)
+    _check(_lib.heom_evolve_td(h.handle, _dptr(ados), B, dt, n_steps,
+                               _ptr(fa) if fa.size else None, max(save_every, 1),
+                               _dptr(traj) if traj is not None else None, prec, _stream(stream)),
+           "heom_evolve_td")
     return traj
 
 

@@ -345,7 +345,8 @@ void free_all(heom_hier *h) {
                     &h->d_op_cval64, &h->d_op_rval32, &h->d_op_cval32, &h->d_s_ptr,
                     &h->d_s_src, &h->d_sval64, &h->d_sval32, &h->d_coefL64, &h->d_coefL32,
                     &h->d_coefR64, &h->d_coefR32, &h->d_rate64, &h->d_rate32, &h->d_sdiag64,
-                    &h->d_sdiag32, &h->d_floor64, &h->d_floor32, &h->ws, &h->ws_small,
+                    &h->d_sdiag32, &h->d_tdval64, &h->d_floor64, &h->d_floor32, &h->ws,
+                    &h->ws_small,
                     &h->d_t_ptr, &h->d_t_src, &h->d_t_val64, &h->d_t_val32, &h->d_cta_ado,
                     &h->d_pers_ado, &h->ws_pers};
     for (DBuf *b : bufs) heom::dfree(*b);
@@ -431,15 +432,27 @@ heom_status upload_params(heom_hier *h, int n_sets, const heom_c64 *H, const heo
                 G[(size_t)r * d + c].im += g * im;
             }
     }
-    // per element: source element -> value in each set (ordered by source)
+    // per element: source element -> value in each set, then in each drive operator H_k of
+    // H(t) = H + sum_k f_k(t) H_k (-i H_k[r][l] left, i H_k[l][c] right), ordered by source
+    const int n_drive = h->n_drive, n_val = n_sets + n_drive;
     std::vector<std::map<int, std::vector<heom_c64>>> terms(d2);
     auto add = [&](int e, int src, int set, double re, double im) {
         if (re == 0.0 && im == 0.0) return;
         auto &vals = terms[e][src];
-        if (vals.empty()) vals.assign(n_sets, heom_c64{0.0, 0.0});
+        if (vals.empty()) vals.assign(n_val, heom_c64{0.0, 0.0});
         vals[set].re += re;
         vals[set].im += im;
     };
+    for (int k = 0; k < n_drive; ++k) {
+        const heom_c64 *Hk = h->drive.data() + (size_t)k * d * d;
+        for (int r = 0; r < d; ++r)
+            for (int c = 0; c < d; ++c)
+                for (int l = 0; l < d; ++l) {
+                    const heom_c64 hl = Hk[(size_t)r * d + l], hr = Hk[(size_t)l * d + c];
+                    add(r * d + c, l * d + c, n_sets + k, hl.im, -hl.re);
+                    add(r * d + c, r * d + l, n_sets + k, -hr.im, hr.re);
+                }
+    }
     for (int s = 0; s < n_sets; ++s) {
         const heom_c64 *Hs = H + (size_t)s * d * d;
         for (int r = 0; r < d; ++r)
@@ -489,8 +502,11 @@ heom_status upload_params(heom_hier *h, int n_sets, const heom_c64 *H, const heo
     }
     const int nS = (int)ssrc.size();
     std::vector<heom_c64> sval((size_t)n_sets * std::max(nS, 1), heom_c64{0.0, 0.0});
-    for (int j = 0; j < nS; ++j)
+    std::vector<heom_c64> tdval((size_t)std::max(n_drive, 1) * std::max(nS, 1), heom_c64{0.0, 0.0});
+    for (int j = 0; j < nS; ++j) {
         for (int s = 0; s < n_sets; ++s) sval[(size_t)s * nS + j] = scols[j][s];
+        for (int k = 0; k < n_drive; ++k) tdval[(size_t)k * nS + j] = scols[j][n_sets + k];
+    }
     std::vector<heom_c64> cl((size_t)n_sets * K), cr((size_t)n_sets * K), rt((size_t)n_sets * K);
     std::vector<double> fl(n_sets);
     for (int s = 0; s < n_sets; ++s) {
@@ -556,6 +572,7 @@ heom_status upload_params(heom_hier *h, int n_sets, const heom_c64 *H, const heo
     UP(d_s_ptr, sptr); UP(d_s_src, ssrc);
     UP(d_sval64, to_cx<double>(sval)); UP(d_sval32, to_cx<float>(sval));
     UP(d_sdiag64, to_cx<double>(sd)); UP(d_sdiag32, to_cx<float>(sd));
+    UP(d_tdval64, to_cx<double>(tdval));
     UP(d_coefL64, to_cx<double>(cl)); UP(d_coefL32, to_cx<float>(cl));
     UP(d_coefR64, to_cx<double>(cr)); UP(d_coefR32, to_cx<float>(cr));
     UP(d_rate64, to_cx<double>(rt)); UP(d_rate32, to_cx<float>(rt));
@@ -990,6 +1007,27 @@ extern "C" heom_status heom_set_lindblad(heom_hier *h, int n_ops, const heom_c64
     if (st != HEOM_OK) {
         h->lind_F.swap(oldF);
         h->lind_gamma.swap(oldg);
+    }
+    return st;
+}
+
+extern "C" heom_status heom_set_drive(heom_hier *h, int n_drive, const heom_c64 *Hk) {
+    if (!h || n_drive < 0 || n_drive > 64 || (n_drive > 0 && !Hk)) {
+        set_error("heom_set_drive: need a hierarchy, 0 <= n_drive <= 64 and the operators");
+        return HEOM_EINVAL;
+    }
+    for (size_t i = 0; i < (size_t)n_drive * h->d2; ++i)
+        if (!finite(Hk[i])) { set_error("heom_set_drive: non-finite drive operator"); return HEOM_EINVAL; }
+    HEOM_CUDA(cudaSetDevice(h->device));
+    std::vector<heom_c64> old, Hs = h->H0, cs = h->coef0, rs = h->rate0;
+    old.swap(h->drive);
+    const int old_n = h->n_drive;
+    h->drive.assign(Hk, Hk + (size_t)n_drive * h->d2);
+    h->n_drive = n_drive;
+    const heom_status st = upload_params(h, h->n_sets, Hs.data(), cs.data(), rs.data());
+    if (st != HEOM_OK) {
+        h->drive.swap(old);
+        h->n_drive = old_n;
     }
     return st;
 }

@@ -158,11 +158,14 @@ struct heom_hier {
     std::vector<heom_c64> coef0, rate0;     // [n_sets][K] as given (before the kind mapping)
     std::vector<heom_c64> lind_F;           // [n_lind][d][d] Lindblad jump operators
     std::vector<double> lind_gamma;         // [n_lind] their rates
+    std::vector<heom_c64> drive;            // [n_drive][d][d] drive operators H_k of H(t)
+    int n_drive = 0;
     // device tables
     heom::DBuf d_row_ptr, d_ent, d_occ_ptr, d_occ;
     heom::DBuf d_op_rptr, d_op_rcol, d_op_cptr, d_op_crow, d_op_rval64, d_op_cval64,
         d_op_rval32, d_op_cval32;
     heom::DBuf d_s_ptr, d_s_src;
+    heom::DBuf d_tdval64;                   // [n_drive][nS] system-term values of -i[H_k, .]
     int nS = 0;                             // system terms (all elements)
     // tiled-kernel term lists (see DevView)
     heom::DBuf d_t_ptr, d_t_src, d_t_val64, d_t_val32;

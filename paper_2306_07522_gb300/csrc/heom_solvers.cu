@@ -1008,9 +1008,37 @@ heom_status solve_system(heom_hier *h, const cx<double> *b64, cx<double> *x64, i
     return HEOM_OK;
 }
 
+// System-term values of H(t) = H + sum_k f_k(t) H_k at cnt consecutive samples j0 .. j0+cnt-1
+// of the drive table f [n_drive][T] (row-major): sv[j][set][t] = s_val[set][t] +
+// sum_k f[k][j0 + j] td[k][t], formed in FP64 and stored in the apply's precision.
+template <class R>
+__global__ void k_td_sval(cx<R> *__restrict__ sv, const cx<double> *__restrict__ s_val,
+                          const cx<double> *__restrict__ td, const double *__restrict__ f, int64_t T,
+                          int64_t j0, int64_t cnt, int n_sets, int nS, int n_drive) {
+    const int64_t per = (int64_t)n_sets * nS, total = cnt * per;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = i / per, r = i - j * per;
+        const int t = (int)(r % nS);
+        cx<double> v = s_val[r];
+        for (int k = 0; k < n_drive; ++k) {
+            const double fk = f[(int64_t)k * T + j0 + j];
+            v.re += fk * td[(int64_t)k * nS + t].re;
+            v.im += fk * td[(int64_t)k * nS + t].im;
+        }
+        sv[i] = cast<R>(v);
+    }
+}
+
+// Classical RK4 over n_steps. With a drive table f (host, [n_drive][2 n_steps + 1], f_k at
+// t0 + j dt / 2) the system terms follow H(t): stage 1 of step n reads sample 2n, stages 2
+// and 3 sample 2n + 1, stage 4 sample 2n + 2; the values of up to kTdChunk samples are formed
+// on the device at a time.
+constexpr int64_t kTdChunk = 1025;
+
 template <class R>
 heom_status evolve_impl(heom_hier *h, cx<R> *y, int64_t B, double dt, int64_t n_steps,
-                        int64_t save_every, cx<R> *traj, cudaStream_t s) {
+                        int64_t save_every, cx<R> *traj, const double *f_host, cudaStream_t s) {
     const DevView<R> v = view_of<R>(h);
     const int64_t rows = h->N * h->d2, L = rows * B;
     heom_status st = ensure_ws(h->ws, 3 * L * sizeof(cx<R>));
@@ -1023,26 +1051,65 @@ heom_status evolve_impl(heom_hier *h, cx<R> *y, int64_t B, double dt, int64_t n_
     if (traj) HEOM_CUDA(memcpy_counted(traj, y, blk, cudaMemcpyDeviceToDevice, s));
     const double u = (double)h->N * B, pass = (double)L * sizeof(cx<R>);
     const bool tiled = tile_ok(v, B);
+    // time-dependent system terms: drive table and per-sample values on the device
+    const bool td = f_host && h->n_drive > 0 && n_steps > 0;
+    const int64_t T = 2 * n_steps + 1, per = (int64_t)h->n_sets * h->nS;
+    DBuf tdbuf;
+    double *fdev = nullptr;
+    cx<R> *sv = nullptr;
+    int64_t j0 = 0, jcnt = 0;
+    if (td) {
+        const int64_t fb = (int64_t)h->n_drive * T * sizeof(double);
+        const int64_t ch = std::min(T, kTdChunk);
+        if ((st = dalloc(tdbuf, fb + ch * std::max<int64_t>(per, 1) * sizeof(cx<R>) + 16)) != HEOM_OK) return st;
+        fdev = (double *)tdbuf.p;
+        sv = (cx<R> *)((char *)tdbuf.p + ((fb + 15) / 16) * 16);
+        HEOM_CUDA(memcpy_counted(fdev, f_host, fb, cudaMemcpyHostToDevice, s));
+    }
+    auto view_at = [&](int64_t j) -> heom_status {  // values of sample j (refills the chunk)
+        if (j < j0 || j >= j0 + jcnt) {
+            j0 = j;
+            jcnt = std::min(kTdChunk, T - j);
+            Prof pr(HEOM_KC_OTHER, s, (double)(jcnt * per));
+            k_td_sval<R><<<flat_blocks(jcnt * per), 256, 0, s>>>(
+                sv, (const cx<double> *)h->d_sval64.p, (const cx<double> *)h->d_tdval64.p, fdev, T, j0,
+                jcnt, h->n_sets, h->nS, h->n_drive);
+            HEOM_CUDA(cudaGetLastError());
+        }
+        return HEOM_OK;
+    };
     TileArgs<R> ta{};
     ta.v = v;
     ta.y = y;
     ta.acc = acc;
     ta.dt = (R)dt;
     ta.B = B;
+    DevView<R> vt = v;
     auto stage = [&](const cx<R> *zi, cx<R> *zo, int st_no) -> cudaError_t {
         if (tiled) {
+            ta.v = vt;
             ta.x = zi;
             ta.out = zo;
             ta.stage = st_no;
             return launch_tile<R, TM_RK4>(ta, s);
         }
-        k_rk4_stage<R><<<g.grid, g.block, 0, s>>>(v, zi, zo, y, acc, B, cps, (R)dt, st_no);
+        k_rk4_stage<R><<<g.grid, g.block, 0, s>>>(vt, zi, zo, y, acc, B, cps, (R)dt, st_no);
         return cudaGetLastError();
     };
+    auto at = [&](int64_t j) -> heom_status {
+        if (!td) return HEOM_OK;
+        const heom_status r = view_at(j);
+        if (r == HEOM_OK) vt.s_val = sv + (j - j0) * per;
+        return r;
+    };
     for (int64_t step = 1; step <= n_steps; ++step) {
+        const int64_t j = 2 * (step - 1);
+        if ((st = at(j)) != HEOM_OK) { dfree(tdbuf); return st; }
         { Prof pr(HEOM_KC_RK4, s, u, 3.0 * pass); HEOM_CUDA(stage(y, za, 1)); }
+        if ((st = at(j + 1)) != HEOM_OK) { dfree(tdbuf); return st; }
         { Prof pr(HEOM_KC_RK4, s, u, 5.0 * pass); HEOM_CUDA(stage(za, zb, 2)); }
         { Prof pr(HEOM_KC_RK4, s, u, 5.0 * pass); HEOM_CUDA(stage(zb, za, 3)); }
+        if ((st = at(j + 2)) != HEOM_OK) { dfree(tdbuf); return st; }
         { Prof pr(HEOM_KC_RK4, s, u, 4.0 * pass); HEOM_CUDA(stage(za, zb, 4)); }
         if (traj && step % save_every == 0) {
             ++saved;
@@ -1051,6 +1118,7 @@ heom_status evolve_impl(heom_hier *h, cx<R> *y, int64_t B, double dt, int64_t n_
     }
     HEOM_CUDA(cudaGetLastError());
     HEOM_CUDA(cudaStreamSynchronize(s));
+    dfree(tdbuf);
     return HEOM_OK;
 }
 
@@ -1072,9 +1140,31 @@ extern "C" heom_status heom_evolve(heom_hier *h, void *ados, int64_t batch, doub
     HEOM_CUDA(cudaSetDevice(h->device));
     if (prec == HEOM_FP64)
         return evolve_impl<double>(h, (cx<double> *)ados, batch, dt, n_steps, save_every,
-                                   (cx<double> *)rho_traj, (cudaStream_t)s);
+                                   (cx<double> *)rho_traj, nullptr, (cudaStream_t)s);
     return evolve_impl<float>(h, (cx<float> *)ados, batch, dt, n_steps, save_every,
-                              (cx<float> *)rho_traj, (cudaStream_t)s);
+                              (cx<float> *)rho_traj, nullptr, (cudaStream_t)s);
+}
+
+extern "C" heom_status heom_evolve_td(heom_hier *h, void *ados, int64_t batch, double dt,
+                                      int64_t n_steps, const double *f, int64_t save_every,
+                                      void *rho_traj, int prec, heom_stream s) {
+    if (!h || !ados || batch < 1 || batch % h->n_sets != 0 || !std::isfinite(dt) || n_steps < 0 ||
+        (rho_traj && save_every < 1) || (prec != HEOM_FP64 && prec != HEOM_FP32) ||
+        batch > 65535LL * 32 || (h->n_drive > 0 && n_steps > 0 && !f)) {
+        set_error("heom_evolve_td: need a hierarchy, ados, batch >= 1 (multiple of n_sets), finite "
+                  "dt, n_steps >= 0, the drive table, save_every >= 1 with a trajectory, prec FP64 "
+                  "or FP32");
+        return HEOM_EINVAL;
+    }
+    if (h->n_drive > 0)
+        for (int64_t i = 0; i < (int64_t)h->n_drive * (2 * n_steps + 1); ++i)
+            if (!std::isfinite(f[i])) { set_error("heom_evolve_td: non-finite drive value"); return HEOM_EINVAL; }
+    HEOM_CUDA(cudaSetDevice(h->device));
+    if (prec == HEOM_FP64)
+        return evolve_impl<double>(h, (cx<double> *)ados, batch, dt, n_steps, save_every,
+                                   (cx<double> *)rho_traj, f, (cudaStream_t)s);
+    return evolve_impl<float>(h, (cx<float> *)ados, batch, dt, n_steps, save_every,
+                              (cx<float> *)rho_traj, f, (cudaStream_t)s);
 }
 
 static void fill_stats(heom_solve_stats *stats, const Solve &r, int64_t off, int64_t n) {
