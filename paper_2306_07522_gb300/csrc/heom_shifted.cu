@@ -417,6 +417,82 @@ __global__ void __launch_bounds__(kSolveThreads) k_shift_solve(int m, int mmax, 
 }
 constexpr int kSolveSmemMax = 200 * 1024;
 
+// Strict upper part of every shift's triangular factor R = Q^H (H - s I), one thread per
+// (shift, column l): the thread applies the shift's stored rotations 0 .. l-1 to column l of
+// the shifted Hessenberg matrix and writes R[i][l], i < l, to R + k * rtri + l (l - 1) / 2 + i.
+// Columns are independent, so the m chains of a shift run in parallel (grid y = column); a
+// block holds 64 shifts of one column, which read the same Hessenberg column.
+__global__ void __launch_bounds__(64) k_shift_rform(int m, int mmax, int64_t rtri, int64_t B, int64_t S,
+                                                    const cx<double> *__restrict__ Hb,
+                                                    const cx<double> *__restrict__ shift,
+                                                    const int *__restrict__ col_of,
+                                                    const double *__restrict__ rot_c,
+                                                    const cx<double> *__restrict__ rot_s,
+                                                    cx<double> *__restrict__ R) {
+    const int l = (int)blockIdx.y + 1;  // column 0 has no entries above the diagonal
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= m || k >= S) return;
+    const int64_t b = col_of[k];
+    const cx<double> shk = shift[k];
+    const double *rc = rot_c + k * mmax;
+    const cx<double> *rs = rot_s + k * mmax;
+    cx<double> *Rl = R + k * rtri + (int64_t)l * (l - 1) / 2;
+    cx<double> carry = Hb[hb_at(0, l, mmax, B, b)];
+    for (int i = 0; i < l; ++i) {
+        cx<double> a1 = Hb[hb_at(i + 1, l, mmax, B, b)];
+        if (i + 1 == l) a1 = a1 + shk;
+        const double c = rc[i];
+        const cx<double> sn = rs[i];
+        Rl[i] = c * carry + sn * a1;
+        carry = c * a1 - conj(sn) * carry;
+    }
+}
+
+// Back substitution from the stored triangular factor (no rotation chain is walked here):
+// y = R^{-1} g column by column (l = m-1 .. 0: y_l = g_l / R_ll, then g_i -= R_il y_l for
+// i < l), then x0 = V_0 y on the tier-0 elements. Four lanes per shift, eight shifts per
+// 32-thread block (enough blocks to reach every SM); lane q of a quad updates the rows
+// i = q mod 4 and sums the elements e = q mod 4. g and y of the block's shifts sit in shared
+// memory: 2 * 8 * m complex values.
+constexpr int kBsShifts = 8;
+__global__ void __launch_bounds__(32) k_shift_backsub(int m, int mmax, int64_t rtri, int64_t B, int64_t S,
+                                                      int d2, const int *__restrict__ col_of,
+                                                      const cx<double> *__restrict__ R,
+                                                      const cx<double> *__restrict__ rdiag,
+                                                      const cx<double> *__restrict__ g,
+                                                      const cx<double> *__restrict__ V, int64_t vstride,
+                                                      cx<double> *__restrict__ x0) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x, q = lane & 3, slot = lane >> 2;
+    cx<double> *sg = reinterpret_cast<cx<double> *>(smem_raw) + (int64_t)slot * m;
+    cx<double> *sy = reinterpret_cast<cx<double> *>(smem_raw) + (int64_t)(kBsShifts + slot) * m;
+    const int64_t k_raw = (int64_t)blockIdx.x * kBsShifts + slot;
+    const bool valid = k_raw < S;
+    const int64_t k = valid ? k_raw : S - 1;  // idle quads repeat the last shift, store nothing
+    const int64_t b = col_of[k];
+    for (int i = q; i < m; i += 4) sg[i] = g[k * (mmax + 1) + i];
+    __syncwarp();
+    const cx<double> *Rk = R + k * rtri;
+    for (int l = m - 1; l >= 0; --l) {
+        cx<double> yl{0.0, 0.0};
+        if (q == (l & 3)) {
+            yl = cdiv(sg[l], rdiag[k * mmax + l]);
+            sy[l] = yl;
+        }
+        const int src = (lane & ~3) | (l & 3);
+        yl.re = __shfl_sync(0xffffffffu, yl.re, src);
+        yl.im = __shfl_sync(0xffffffffu, yl.im, src);
+        const cx<double> *Rl = Rk + (int64_t)l * (l - 1) / 2;
+        for (int i = q; i < l; i += 4) sg[i] = sg[i] - Rl[i] * yl;
+        __syncwarp();
+    }
+    for (int e = q; e < d2; e += 4) {
+        cx<double> acc{0.0, 0.0};
+        for (int l = 0; l < m; ++l) fma_to(acc, V[(int64_t)l * vstride + (int64_t)e * B + b], sy[l]);
+        if (valid) x0[k * d2 + e] = acc;
+    }
+}
+
 // The same solve for any m, one thread per shift walking the rotation chains (used when m
 // exceeds the register budget of k_shift_solve). Work arrays gw [S][mmax+1], y [S][mmax].
 __global__ void k_shift_solve_long(int m, int mmax, int64_t B, int64_t S, int d2,
@@ -515,6 +591,13 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
     const bool ffgs = B <= kDotThreads && (kDotThreads % B) == 0;
     const size_t oVf = ffgs ? take((size_t)(mmax + 1) * L * 16) : 0,
                  ohf = ffgs ? take((size_t)(mmax + 2) * B * 16) : 0;
+    // every shift's triangular factor (strict upper part) for the final solve, for up to mp
+    // steps when that fits 1 GiB (more steps solve by walking the rotation chains instead)
+    const bool pers = ffgs && arnoldi_persistent_ok(h, B, mmax);
+    const int mp = std::min(mmax, arnoldi_max_steps());
+    const int64_t rtri = (int64_t)mp * (mp - 1) / 2;
+    const bool keepR = (double)S * (double)rtri * 16.0 <= (double)(1ull << 30);
+    const size_t oR = keepR ? take((size_t)S * std::max<int64_t>(rtri, 1) * 16) : 0;
     heom_status st = ensure_ws(h->ws, off);
     if (st != HEOM_OK) return st;
     char *base = (char *)h->ws.p;
@@ -533,6 +616,7 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
     int *dskip = (int *)(base + oskip);
     float4 *Vf = ffgs ? (float4 *)(base + oVf) : nullptr;
     float4 *hft = ffgs ? (float4 *)(base + ohf) : nullptr;
+    cx<double> *Rst = keepR ? (cx<double> *)(base + oR) : nullptr;
     HEOM_CUDA(memcpy_counted(dsh, shift.data(), S * 16, cudaMemcpyHostToDevice, s));
     HEOM_CUDA(memcpy_counted(dco, col_of.data(), S * 4, cudaMemcpyHostToDevice, s));
     HEOM_CUDA(cudaMemsetAsync(Hb, 0, (size_t)(mmax + 1) * mmax * B * 16, s));
@@ -559,11 +643,11 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
     std::vector<double> hres(S, 1.0);
     int m = 0, check = 5, j_done = 0;
     bool done = false;
-    if (ffgs && arnoldi_persistent_ok(h, B, mmax)) {
+    if (pers) {
         // the whole solve (up to its shared-memory limit of steps) in one cooperative launch
         int steps = 0;
-        heom_status pst = arnoldi_persistent(h, B, mmax, std::min(mmax, arnoldi_max_steps()), Vf, V, Hb, S, dsh,
-                                             dco, rot_c, rot_s, rdiag, g, beta, dres, tol, &steps, &done, s);
+        heom_status pst = arnoldi_persistent(h, B, mmax, mp, Vf, V, Hb, S, dsh, dco, rot_c, rot_s, rdiag, g,
+                                             beta, dres, tol, &steps, &done, s);
         if (pst != HEOM_OK) return pst;
         m = j_done = steps;
     }
@@ -656,7 +740,19 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
             check = std::min(check + 5, 20);
         }
     }
-    {
+    if (keepR && m <= mp && m > 0) {
+        // R from the stored rotations (all columns at once), then back substitution
+        Prof pr(HEOM_KC_OTHER, s, (double)S, (double)S * m * 16);
+        pr.kernels = m > 1 ? 2 : 1;
+        if (m > 1)
+            k_shift_rform<<<dim3((unsigned)((S + 63) / 64), (unsigned)(m - 1)), 64, 0, s>>>(
+                m, mmax, rtri, B, S, Hb, dsh, dco, rot_c, rot_s, Rst);
+        const size_t smb = (size_t)2 * kBsShifts * m * sizeof(cx<double>);
+        if (smb > 48 * 1024)
+            HEOM_CUDA(cudaFuncSetAttribute(k_shift_backsub, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
+        k_shift_backsub<<<(unsigned)((S + kBsShifts - 1) / kBsShifts), 32, smb, s>>>(
+            m, mmax, rtri, B, S, d2, dco, Rst, rdiag, g, V, L, dx0);
+    } else {
         Prof pr(HEOM_KC_OTHER, s, (double)S, (double)S * m * 16);
         const size_t smb = (size_t)m * kSolveThreads * (3 * sizeof(cx<double>) + sizeof(double));
         if (smb <= (size_t)kSolveSmemMax) {
