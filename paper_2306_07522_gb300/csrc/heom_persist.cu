@@ -6,10 +6,12 @@
 // block sums written to per-block slots, added in a fixed order by every CTA after the next
 // barrier, so every CTA derives the same Krylov scalars and the same convergence decision
 // without any host round trip. Five grid barriers per iteration; the host reads the result
-// once, at the end.
+// once, at the end. In the FP64 solve the two applies of an iteration run in float-float (the
+// Krylov vectors, dot products and scalars stay FP64).
 #include <algorithm>
 #include <cmath>
 
+#include "heom_ff.cuh"
 #include "heom_grid.cuh"
 #include "heom_tile.cuh"
 
@@ -32,6 +34,7 @@ struct PersistArgs {
     R aug;
     int precond;
     cx<R> *r, *rh, *p, *vv, *ph, *sh, *t;
+    float4 *phf, *shf;  // FP64 solve: float-float copies of ph and sh (the apply operands)
     double *part;  // [kSlots][G][4]
     GridBar *bar;
     double tol;
@@ -76,6 +79,34 @@ __device__ __forceinline__ cx<R> prog_apply(const ProgSmem<R> &ps, int it, const
         for (int u = 0; u < 8; ++u) fma_to(acc, cf[u], xv[u]);
     }
     return acc;
+}
+
+// The same apply in float-float for the FP64 solve: float-float coefficients (the shift
+// already folded into each item's first term) and a float-float copy of X, so that the
+// multiply-adds run on the FP32 pipe instead of GB300's 1/64-rate FP64 pipe; about 48
+// significant bits per product and sum.
+__device__ __forceinline__ cx<double> prog_apply_ff(const ProgSmem<double> &ps, int it, const float4 *X) {
+    const float4 *coef = reinterpret_cast<const float4 *>(ps.coef);
+    const int j0 = ps.item[it], j1 = ps.item[it + 1];
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    for (int jj = j0; jj < j1; jj += 8) {
+        float4 c[8], x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const bool ok = jj + u < j1;
+            const int idx = ok ? jj + u : j1 - 1;
+            c[u] = ok ? coef[idx] : make_float4(0.f, 0.f, 0.f, 0.f);
+            x[u] = __ldcg(X + ps.src[idx]);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            ff_mac(rh, rl, c[u].x, c[u].z, x[u].x, x[u].z);
+            ff_mac(rh, rl, -c[u].y, -c[u].w, x[u].y, x[u].w);
+            ff_mac(ih, il, c[u].x, c[u].z, x[u].y, x[u].w);
+            ff_mac(ih, il, c[u].y, c[u].w, x[u].x, x[u].z);
+        }
+    }
+    return cx<double>{(double)rh + (double)rl, (double)ih + (double)il};
 }
 
 // Grid-wide sum of NV doubles: block sums to part[slot][block], grid barrier, then in every
@@ -179,6 +210,20 @@ __global__ void __launch_bounds__(kPersThreads) k_persist_bicg(PersistArgs<R> a)
         val2[0] += (double)norm2(ri);
         val2[1] += (double)norm2(bi);
     }
+    if constexpr (sizeof(R) == 8) {
+        // float-float programs for the iteration: fold the shift into every item's first
+        // (damping) term, then split the coefficients in place (16 bytes either way)
+        __syncthreads();
+        if (a.shift)
+            for (int it = threadIdx.x; it < items; it += blockDim.x) {
+                cx<R> &c0 = ps.coef[ps.item[it]];
+                c0 = c0 + shift;
+            }
+        __syncthreads();
+        float4 *cf = reinterpret_cast<float4 *>(ps.coef);
+        for (int t = threadIdx.x; t < ps.item[items]; t += blockDim.x) cf[t] = ff_split(ps.coef[t]);
+        __syncthreads();
+    }
     const bool started = grid_sum<2>(val2, a.part, 0, s_red, s_tot, a.bar, gen);
     double nr = val2[0];
     const double bn = val2[1], tol2 = a.tol * a.tol;
@@ -212,14 +257,18 @@ __global__ void __launch_bounds__(kPersThreads) k_persist_bicg(PersistArgs<R> a)
             const cx<R> pi = restart ? ri : ri + bt * (a.p[i] - om * a.vv[i]);
             if (restart) a.rh[i] = ri;
             a.p[i] = pi;
-            a.ph[i] = pi * s_pinv[it];
+            const cx<R> phi = pi * s_pinv[it];
+            a.ph[i] = phi;
+            if constexpr (sizeof(R) == 8) a.phf[i] = ff_split(phi);
         }
         if (!grid_barrier(a.bar, gen)) { status = HEOM_ECUDA; break; }
         // ---- v = A ph, (rh, v)
         double d1[2] = {0.0, 0.0};
         for (int it = threadIdx.x; it < items; it += blockDim.x) {
             const int64_t i = row0 + it;
-            const cx<R> y = prog_apply(ps, it, a.ph, shift);
+            cx<R> y;
+            if constexpr (sizeof(R) == 8) y = prog_apply_ff(ps, it, a.phf);
+            else y = prog_apply(ps, it, a.ph, shift);
             a.vv[i] = y;
             const cx<double> yd = cast<double>(y), wd = cast<double>(a.rh[i]);
             d1[0] += wd.re * yd.re + wd.im * yd.im;
@@ -241,14 +290,18 @@ __global__ void __launch_bounds__(kPersThreads) k_persist_bicg(PersistArgs<R> a)
             const int64_t i = row0 + it;
             const cx<R> si = a.r[i] - al * a.vv[i];
             a.r[i] = si;
-            a.sh[i] = si * s_pinv[it];
+            const cx<R> shi = si * s_pinv[it];
+            a.sh[i] = shi;
+            if constexpr (sizeof(R) == 8) a.shf[i] = ff_split(shi);
         }
         if (!grid_barrier(a.bar, gen)) { status = HEOM_ECUDA; break; }
         // ---- t = A sh, (t, s), (t, t)
         double d2v[3] = {0.0, 0.0, 0.0};
         for (int it = threadIdx.x; it < items; it += blockDim.x) {
             const int64_t i = row0 + it;
-            const cx<R> y = prog_apply(ps, it, a.sh, shift);
+            cx<R> y;
+            if constexpr (sizeof(R) == 8) y = prog_apply_ff(ps, it, a.shf);
+            else y = prog_apply(ps, it, a.sh, shift);
             a.t[i] = y;
             const cx<double> yd = cast<double>(y), wd = cast<double>(a.r[i]);
             d2v[0] += yd.re * wd.re + yd.im * wd.im;
@@ -328,7 +381,8 @@ heom_status bicgstab_persistent(heom_hier *h, const cx<R> *b, cx<R> *x, bool x_z
     const int64_t rows = h->N * h->d2;
     const int G = h->pers_ranges;
     const size_t vec = ((size_t)rows * sizeof(cx<R>) + 255) & ~size_t(255);
-    const size_t bytes = 7 * vec + (size_t)kSlots * G * 4 * sizeof(double) + 512;
+    const size_t fvec = sizeof(R) == 8 ? (((size_t)rows * sizeof(float4) + 255) & ~size_t(255)) : 0;
+    const size_t bytes = 7 * vec + 2 * fvec + (size_t)kSlots * G * 4 * sizeof(double) + 512;
     heom_status st = ensure_ws(h->ws_pers, bytes);
     if (st != HEOM_OK) return st;
     char *base = (char *)h->ws_pers.p;
@@ -342,8 +396,12 @@ heom_status bicgstab_persistent(heom_hier *h, const cx<R> *b, cx<R> *x, bool x_z
     a.precond = 1;
     cx<R> **vecs[7] = {&a.r, &a.rh, &a.p, &a.vv, &a.ph, &a.sh, &a.t};
     for (int i = 0; i < 7; ++i) *vecs[i] = (cx<R> *)(base + i * vec);
-    a.part = (double *)(base + 7 * vec);
-    a.out = (PersistOut *)(base + 7 * vec + (size_t)kSlots * G * 4 * sizeof(double));
+    if (fvec) {
+        a.phf = (float4 *)(base + 7 * vec);
+        a.shf = (float4 *)(base + 7 * vec + fvec);
+    }
+    a.part = (double *)(base + 7 * vec + 2 * fvec);
+    a.out = (PersistOut *)((char *)a.part + (size_t)kSlots * G * 4 * sizeof(double));
     a.bar = (GridBar *)((char *)a.out + 128);
     HEOM_CUDA(cudaMemsetAsync(a.bar, 0, sizeof(GridBar), s));
     a.tol = tol;
