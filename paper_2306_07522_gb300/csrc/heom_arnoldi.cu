@@ -80,7 +80,23 @@ __device__ void own_dots(const ArnoldiArgs &a, const float4 *W, int nv, int64_t 
         // float-float accumulation over the lane's elements, one conversion to FP64 at the end
         // (GB300's FP64 pipe is the scarce one)
         float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
-        for (int t = lane; t < nel; t += 32) {
+        int t = lane;
+        for (; t + 96 < nel; t += 128) {  // four elements per lane, eight loads in flight
+            float4 x[4], y[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                x[u] = Vi[t + 32 * u];
+                y[u] = Wo[t + 32 * u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                ff_mac(rh, rl, x[u].x, x[u].z, y[u].x, y[u].z);
+                ff_mac(rh, rl, x[u].y, x[u].w, y[u].y, y[u].w);
+                ff_mac(ih, il, x[u].x, x[u].z, y[u].y, y[u].w);
+                ff_mac(ih, il, -x[u].y, -x[u].w, y[u].x, y[u].z);
+            }
+        }
+        for (; t < nel; t += 32) {
             const float4 x = Vi[t], y = Wo[t];
             ff_mac(rh, rl, x.x, x.z, y.x, y.z);
             ff_mac(rh, rl, x.y, x.w, y.y, y.w);
@@ -263,12 +279,17 @@ __global__ void __launch_bounds__(kArThreads, 1) k_arnoldi(ArnoldiArgs a) {
             }
         }
         if (!grid_barrier(a.bar, gen)) { status = 1; break; }
-        if (tid < B) {
+        if (warp < B) {  // warp b adds column b's partials of all CTAs: lane-strided, fixed tree
             double sacc = 0.0;
-            for (int gi = 0; gi < G; ++gi) sacc += __ldcg(a.part + (int64_t)gi * kPartStride + 4 * (kArMaxSteps + 2) * kArMaxB + tid);
-            const double n = std::sqrt(sacc);
-            s_nrm[tid] = n > 0.0 ? 1.0 / n : 0.0;  // the inverse, used by every element
-            s_hcol[(j + 1) * B + tid] = cx<double>{n, 0.0};
+            for (int gi = lane; gi < G; gi += 32)
+                sacc += __ldcg(a.part + (int64_t)gi * kPartStride + 4 * (kArMaxSteps + 2) * kArMaxB + warp);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sacc += __shfl_down_sync(0xffffffffu, sacc, o);
+            if (lane == 0) {
+                const double n = std::sqrt(sacc);
+                s_nrm[warp] = n > 0.0 ? 1.0 / n : 0.0;  // the inverse, used by every element
+                s_hcol[(j + 1) * B + warp] = cx<double>{n, 0.0};
+            }
         }
         __syncthreads();
         // v_{j+1} = w / |w| (FP64 copy for the final tier-0 combination, float-float for the
@@ -339,11 +360,13 @@ __global__ void __launch_bounds__(kArThreads, 1) k_arnoldi(ArnoldiArgs a) {
         }
         steps = j + 1;
         if (!grid_barrier(a.bar, gen)) { status = 1; break; }
-        if (tid == 0) {
+        if (warp == 0) {  // largest residual estimate over all CTAs
             double mx = 0.0;
-            for (int gi = 0; gi < G; ++gi)
+            for (int gi = lane; gi < G; gi += 32)
                 mx = fmax(mx, __ldcg(a.part + (int64_t)gi * kPartStride + 4 * (kArMaxSteps + 2) * kArMaxB + kArMaxB));
-            s_flag[1] = mx <= a.tol * a.tol;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+            if (lane == 0) s_flag[1] = mx <= a.tol * a.tol;
         }
         __syncthreads();
         if (s_flag[1]) { converged = 1; break; }
@@ -361,12 +384,23 @@ size_t arnoldi_smem(const DevView<double> &v, int hcap) {
            prog_smem_bytes<double>(v.pers_terms, v.pers_slots, v.pers_ados, v.d2) + 64;
 }
 
+// The FP64 view with the Arnoldi's own ADO ranges in place of the persistent solver's.
+DevView<double> arnoldi_view(const heom_hier *h) {
+    DevView<double> v = h->view64();
+    v.pers_ado = (const int32_t *)h->d_ar_ado.p;
+    v.pers_ranges = h->ar_ranges;
+    v.pers_terms = h->ar_terms;
+    v.pers_slots = h->ar_slots;
+    v.pers_ados = h->ar_ados;
+    return v;
+}
+
 }  // namespace
 
 bool arnoldi_persistent_ok(const heom_hier *h, int64_t B, int max_steps) {
-    if (h->pers_ranges < 1 || B < 1 || B > kArMaxB || (32 % B) != 0 || (kArThreads % B) != 0) return false;
+    if (h->ar_ranges < 1 || B < 1 || B > kArMaxB || (32 % B) != 0 || (kArThreads % B) != 0) return false;
     const int steps = std::min(max_steps, kArMaxSteps);
-    return arnoldi_smem(h->view64(), (steps + 2) * (int)B) <= 200 * 1024;
+    return arnoldi_smem(arnoldi_view(h), (steps + 2) * (int)B) <= 200 * 1024;
 }
 
 int arnoldi_max_steps() { return kArMaxSteps; }
@@ -380,14 +414,14 @@ heom_status arnoldi_persistent(heom_hier *h, int64_t B, int mmax, int max_steps,
                                double *rot_c, cx<double> *rot_s, cx<double> *rdiag, cx<double> *g,
                                const double *beta, double *res, double tol, int *steps, bool *converged,
                                cudaStream_t s) {
-    const int G = h->pers_ranges;
+    const int G = h->ar_ranges;
     const size_t part_bytes = (size_t)G * kPartStride * sizeof(double);
     const size_t hred_bytes = (size_t)2 * (kArMaxSteps + 2) * kArMaxB * sizeof(cx<double>);
     heom_status st = ensure_ws(h->ws_pers, part_bytes + hred_bytes + 512);
     if (st != HEOM_OK) return st;
     char *base = (char *)h->ws_pers.p;
     ArnoldiArgs a{};
-    a.v = h->view64();
+    a.v = arnoldi_view(h);
     a.B = B;
     a.L = h->N * h->d2 * B;
     a.S = S;

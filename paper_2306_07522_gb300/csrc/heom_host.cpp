@@ -348,7 +348,7 @@ void free_all(heom_hier *h) {
                     &h->d_sdiag32, &h->d_tdval64, &h->d_floor64, &h->d_floor32, &h->ws,
                     &h->ws_small,
                     &h->d_t_ptr, &h->d_t_src, &h->d_t_val64, &h->d_t_val32, &h->d_cta_ado,
-                    &h->d_pers_ado, &h->ws_pers};
+                    &h->d_pers_ado, &h->d_ar_ado, &h->ws_pers};
     for (DBuf *b : bufs) heom::dfree(*b);
 }
 
@@ -374,22 +374,27 @@ RangeCosts range_costs(const heom_hier *h) {
 
 // At most `resident` contiguous ranges; a range closes once it reaches the target term count
 // (or a shared-memory bound). Returns whether every range fits within the bounds.
+// Balance on weight[i] when given (its sum in wtotal), else on the term counts; the bounds
+// always apply to the real term and slot counts.
 bool partition_ranges(const heom_hier *h, const RangeCosts &rc, int64_t resident, int64_t cap_terms,
-                      std::vector<int32_t> &rg, int64_t &rt, int64_t &rs, int64_t &rn) {
-    int64_t target = std::max<int64_t>(1, (rc.total + resident - 1) / resident);
+                      std::vector<int32_t> &rg, int64_t &rt, int64_t &rs, int64_t &rn,
+                      const std::vector<int64_t> *weight = nullptr, int64_t wtotal = 0) {
+    const int64_t total = weight ? wtotal : rc.total;
+    int64_t target = std::max<int64_t>(1, (total + resident - 1) / resident);
     for (int attempt = 0; attempt < 64; ++attempt) {
         rg.assign(1, 0);
-        int64_t cur_t = 0, cur_s = 0, cur_n = 0;
+        int64_t cur_t = 0, cur_s = 0, cur_n = 0, cur_w = 0;
         rt = rs = rn = 0;
         for (int64_t i = 0; i < h->N; ++i) {
-            const bool full = cur_n > 0 && (cur_t >= target || cur_t + rc.terms[i] > cap_terms ||
+            const bool full = cur_n > 0 && (cur_w >= target || cur_t + rc.terms[i] > cap_terms ||
                                             cur_s + rc.slots[i] > heom::kRangeSlots ||
                                             cur_n >= heom::kRangeAdos);
             if (full) {
                 rg.push_back((int32_t)i);
-                cur_t = cur_s = cur_n = 0;
+                cur_t = cur_s = cur_n = cur_w = 0;
             }
             cur_t += rc.terms[i]; cur_s += rc.slots[i]; ++cur_n;
+            cur_w += weight ? (*weight)[i] : rc.terms[i];
             rt = std::max(rt, cur_t); rs = std::max(rs, cur_s); rn = std::max(rn, cur_n);
         }
         rg.push_back((int32_t)h->N);
@@ -549,7 +554,7 @@ heom_status upload_params(heom_hier *h, int n_sets, const heom_c64 *H, const heo
     // bounded for shared memory. Tiled kernel: tile_per_sm CTAs per SM (five unless the
     // autotuner chose otherwise), all resident at once. Cooperative persistent solvers: one
     // range per SM.
-    std::vector<int32_t> ranges, pranges;
+    std::vector<int32_t> ranges, pranges, arranges;
     {
         RangeCosts rc = range_costs(h);
         int n_sm = 152;
@@ -565,10 +570,33 @@ heom_status upload_params(heom_hier *h, int n_sets, const heom_c64 *H, const heo
         h->pers_terms = (int)std::min<int64_t>(rt, INT32_MAX);
         h->pers_slots = (int)std::min<int64_t>(rs, INT32_MAX);
         h->pers_ados = (int)rn;
+        // The persistent Arnoldi's Gram-Schmidt work grows with the elements a range owns
+        // (about 2 (j + 1) float-float multiply-adds per element and step), the apply with its
+        // terms: its ranges balance terms + kArElemWeight * d2 per ADO. Without a fitting
+        // partition it keeps the one above.
+        std::vector<int64_t> w(h->N);
+        int64_t wt = 0;
+        for (int64_t i = 0; i < h->N; ++i) { w[i] = rc.terms[i] + heom::kArElemWeight * h->d2; wt += w[i]; }
+        std::vector<int32_t> ar;
+        const bool afit = partition_ranges(h, rc, n_sm, heom::kPersistTerms, ar, rt, rs, rn, &w, wt) &&
+                          rt <= heom::kPersistTerms && rs <= heom::kRangeSlots;
+        if (afit) {
+            arranges = ar;
+            h->ar_ranges = (int)ar.size() - 1;
+            h->ar_terms = (int)rt;
+            h->ar_slots = (int)rs;
+            h->ar_ados = (int)rn;
+        } else {
+            arranges = pranges;
+            h->ar_ranges = h->pers_ranges;
+            h->ar_terms = h->pers_terms;
+            h->ar_slots = h->pers_slots;
+            h->ar_ados = h->pers_ados;
+        }
     }
     heom_status st;
 #define UP(buf, vec) if ((st = upload(h->buf, vec)) != HEOM_OK) return st
-    UP(d_cta_ado, ranges); UP(d_pers_ado, pranges);
+    UP(d_cta_ado, ranges); UP(d_pers_ado, pranges); UP(d_ar_ado, arranges);
     UP(d_s_ptr, sptr); UP(d_s_src, ssrc);
     UP(d_sval64, to_cx<double>(sval)); UP(d_sval32, to_cx<float>(sval));
     UP(d_sdiag64, to_cx<double>(sd)); UP(d_sdiag32, to_cx<float>(sd));

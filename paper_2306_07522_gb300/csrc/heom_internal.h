@@ -176,6 +176,8 @@ struct heom_hier {
     int tile_per_sm = 5;        // tiled kernel: ADO ranges per SM (autotuned)
     int64_t tile_min_b = 16;    // tiled kernel from this batch on (autotuned)
     int pers_ranges = 0, pers_terms = 0, pers_slots = 0, pers_ados = 0;
+    heom::DBuf d_ar_ado;        // ADO ranges of the persistent Arnoldi (elements weighted)
+    int ar_ranges = 0, ar_terms = 0, ar_slots = 0, ar_ados = 0;
     // device parameters (per set), both precisions
     heom::DBuf d_sval64, d_sval32, d_coefL64, d_coefL32, d_coefR64, d_coefR32, d_rate64,
         d_rate32, d_sdiag64, d_sdiag32, d_floor64, d_floor32;
@@ -211,6 +213,7 @@ constexpr int kRangeTerms = 4096;
 constexpr int kRangeSlots = 8192;
 constexpr int kRangeAdos = 64;
 constexpr int kPersistTerms = 6144;  // terms of one persistent range (FP64: 20 B each)
+constexpr int64_t kArElemWeight = 128;  // persistent Arnoldi: balance weight of one element
 
 // launch geometry shared by every row x column kernel: block (bx, by), grid (gx, gy)
 struct Geom {

@@ -111,17 +111,21 @@ __device__ __forceinline__ cx<double> prog_apply_ff(const ProgSmem<double> &ps, 
 
 // Grid-wide sum of NV doubles: block sums to part[slot][block], grid barrier, then in every
 // block warp k adds value k over all blocks (lane-strided loads through L2, then a fixed
-// shuffle tree; lane 0's result is used), so every block derives bit-identical totals.
+// shuffle tree; lane 0's result is used), so every block derives bit-identical totals. Only
+// the first nw warps hold values (the warps past the block's elements add nothing), so only
+// they run the FP64 shuffle trees.
 template <int NV>
 __device__ __forceinline__ bool grid_sum(double (&val)[NV], double *part, int slot, double *s_red,
-                                         double *s_tot, GridBar *bar, unsigned &gen) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+                                         double *s_tot, GridBar *bar, unsigned &gen, int nw) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp < nw) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        double x = val[k];
+        for (int k = 0; k < NV; ++k) {
+            double x = val[k];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-        if (lane == 0) s_red[warp * 4 + k] = x;
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            if (lane == 0) s_red[warp * 4 + k] = x;
+        }
     }
     __syncthreads();
     if (threadIdx.x < NV) {
@@ -187,6 +191,8 @@ __global__ void __launch_bounds__(kPersThreads) k_persist_bicg(PersistArgs<R> a)
     const cx<R> shift = a.shift ? a.shift[0] : cx<R>{R(0), R(0)};
     const int items = (n1 - n0) * d2;
     const int64_t row0 = (int64_t)n0 * d2;
+    // warps that hold elements (thread t takes items t, t + blockDim.x, ...)
+    const int nw_act = max(1, min((int)(blockDim.x >> 5), (items + 31) >> 5));
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
         const int pp = it / d2, e = it - pp * d2;
         const int64_t n = n0 + pp;
@@ -224,7 +230,7 @@ __global__ void __launch_bounds__(kPersThreads) k_persist_bicg(PersistArgs<R> a)
         for (int t = threadIdx.x; t < ps.item[items]; t += blockDim.x) cf[t] = ff_split(ps.coef[t]);
         __syncthreads();
     }
-    const bool started = grid_sum<2>(val2, a.part, 0, s_red, s_tot, a.bar, gen);
+    const bool started = grid_sum<2>(val2, a.part, 0, s_red, s_tot, a.bar, gen, nw_act);
     double nr = val2[0];
     const double bn = val2[1], tol2 = a.tol * a.tol;
     cx<double> rho{nr, 0.0}, rho_old{1.0, 0.0}, alpha{1.0, 0.0}, omega{1.0, 0.0};
@@ -274,7 +280,7 @@ __global__ void __launch_bounds__(kPersThreads) k_persist_bicg(PersistArgs<R> a)
             d1[0] += wd.re * yd.re + wd.im * yd.im;
             d1[1] += wd.re * yd.im - wd.im * yd.re;
         }
-        if (!grid_sum<2>(d1, a.part, 1, s_red, s_tot, a.bar, gen)) { status = HEOM_ECUDA; break; }
+        if (!grid_sum<2>(d1, a.part, 1, s_red, s_tot, a.bar, gen, nw_act)) { status = HEOM_ECUDA; break; }
         const cx<double> rv{d1[0], d1[1]};
         if (norm2(rv) == 0.0) { status = HEOM_EBREAKDOWN; it_done = iter; break; }
         if (threadIdx.x == 0) {
@@ -308,7 +314,7 @@ __global__ void __launch_bounds__(kPersThreads) k_persist_bicg(PersistArgs<R> a)
             d2v[1] += yd.re * wd.im - yd.im * wd.re;
             d2v[2] += yd.re * yd.re + yd.im * yd.im;
         }
-        if (!grid_sum<3>(d2v, a.part, 2, s_red, s_tot, a.bar, gen)) { status = HEOM_ECUDA; break; }
+        if (!grid_sum<3>(d2v, a.part, 2, s_red, s_tot, a.bar, gen, nw_act)) { status = HEOM_ECUDA; break; }
         if (threadIdx.x == 0) {
             const double it2 = d2v[2] == 0.0 ? 0.0 : nr_rcp(d2v[2]);
             s_sc[5] = d2v[0] * it2;
@@ -330,7 +336,7 @@ __global__ void __launch_bounds__(kPersThreads) k_persist_bicg(PersistArgs<R> a)
             d3[1] += hd.re * rd.im - hd.im * rd.re;
             d3[2] += rd.re * rd.re + rd.im * rd.im;
         }
-        if (!grid_sum<3>(d3, a.part, 3, s_red, s_tot, a.bar, gen)) { status = HEOM_ECUDA; break; }
+        if (!grid_sum<3>(d3, a.part, 3, s_red, s_tot, a.bar, gen, nw_act)) { status = HEOM_ECUDA; break; }
         rho_old = rho;
         rho = cx<double>{d3[0], d3[1]};
         nr = d3[2];
