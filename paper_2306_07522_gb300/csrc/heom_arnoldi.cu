@@ -45,6 +45,8 @@ struct ArnoldiArgs {
     const int *col_of;
     double *rot_c;
     cx<double> *rot_s, *rdiag, *g;
+    float2 *rot_cf;    // the rotations again, split into float-float for the chains
+    float4 *rot_sf;
     const double *beta;
     double *res;
     double tol;
@@ -57,6 +59,30 @@ struct ArnoldiArgs {
 constexpr int kPartStride = 2 * 2 * (kArMaxSteps + 2) * kArMaxB + kArMaxB + 2;  // doubles per CTA
 
 __device__ __forceinline__ float4 ld_l2_f4(const float4 *p) { return __ldcg(p); }
+
+// (h, l) += (bh, bl), float-float sum by Knuth's two-sum, renormalised
+__device__ __forceinline__ void ff_add(float &h, float &l, float bh, float bl) {
+    const float s = h + bh;
+    const float bb = s - h;
+    const float t = (h - (s - bb)) + (bh - bb) + l + bl;
+    h = s + t;
+    l = t - (h - s);
+}
+
+// One Givens step of a rotation chain in float-float: h <- c a - conj(s) h, with c real
+// {hi, lo}, s, a, h complex {re hi, im hi, re lo, im lo}.
+__device__ __forceinline__ float4 ff_rot_step(float2 c, float4 s, float4 a, float4 h) {
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    ff_mac(rh, rl, c.x, c.y, a.x, a.z);
+    ff_mac(rh, rl, -s.x, -s.z, h.x, h.z);
+    ff_mac(rh, rl, -s.y, -s.w, h.y, h.w);
+    ff_mac(ih, il, c.x, c.y, a.y, a.w);
+    ff_mac(ih, il, -s.x, -s.z, h.y, h.w);
+    ff_mac(ih, il, s.y, s.w, h.x, h.z);
+    ff_norm(rh, rl);
+    ff_norm(ih, il);
+    return make_float4(rh, ih, rl, il);
+}
 
 // acc += c x (complex float-float; acc = {re hi, im hi, re lo, im lo})
 __device__ __forceinline__ void ff_cmac(float &rh, float &rl, float &ih, float &il, const float4 &c,
@@ -299,47 +325,67 @@ __global__ void __launch_bounds__(kArThreads, 1) k_arnoldi(ArnoldiArgs a) {
             a.V[(int64_t)(j + 1) * a.L + e0 + idx] = x;
             W[e0 + idx] = ff_split(x);
         }
-        // Hessenberg column j to global memory (CTA 0)
+        // Hessenberg column j to global memory (CTA 0); its rows 0 .. j split into float-float
+        // for the rotation chains (s_hf is free again: the Gram-Schmidt update has used it)
         if (blockIdx.x == 0)
             for (int p = tid; p < (j + 2) * B; p += bd) {
                 const int i = p / B, b = p - i * B;
                 a.Hb[((int64_t)j * (a.mmax + 1) + i) * a.B + b] = s_hcol[p];
             }
+        for (int p = tid; p < (j + 1) * B; p += bd) s_hf[p] = ff_split(s_hcol[p]);
+        __syncthreads();
         // ---- 4. Givens QR of every shift, one thread per shift, shifts dealt round-robin over
-        // the CTAs so that every SM's FP64 pipe takes its share
+        // the CTAs. The chain that brings column j up to date with the earlier rotations runs
+        // in float-float (FP32 pipe; the FP64 instructions of GB300 are few and slow to
+        // complete); the new rotation itself and g stay FP64.
         double rmax = 0.0;
         for (int64_t k = (int64_t)tid * G + blockIdx.x; k < a.S; k += (int64_t)G * bd) {
             const int b = a.col_of[k];
             const cx<double> shk = a.shift[k];
             double *rc = a.rot_c + k * a.mmax;
             cx<double> *rs = a.rot_s + k * a.mmax;
+            float2 *rcf = a.rot_cf + k * a.mmax;
+            float4 *rsf = a.rot_sf + k * a.mmax;
             cx<double> *gk = a.g + k * (a.mmax + 1);
-            cx<double> hj = s_hcol[b];
-            if (j == 0) hj = hj + shk;
+            const float4 shf = ff_split(shk);
+            float4 h = s_hf[b];
+            if (j == 0) {
+                ff_add(h.x, h.z, shf.x, shf.z);
+                ff_add(h.y, h.w, shf.y, shf.w);
+            }
             for (int i0 = 0; i0 < j; i0 += 8) {  // the rotations, 8 loads in flight
-                double cr[8];
-                cx<double> sr[8];
+                float2 cr[8];
+                float4 sr[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const int i = i0 + u < j ? i0 + u : j - 1;
-                    cr[u] = rc[i];
-                    sr[u] = rs[i];
+                    cr[u] = rcf[i];
+                    sr[u] = rsf[i];
                 }
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const int i = i0 + u;
                     if (i >= j) break;
-                    cx<double> hi1 = s_hcol[(i + 1) * B + b];
-                    if (i + 1 == j) hi1 = hi1 + shk;
-                    hj = cr[u] * hi1 - conj(sr[u]) * hj;
+                    float4 hi1 = s_hf[(i + 1) * B + b];
+                    if (i + 1 == j) {
+                        ff_add(hi1.x, hi1.z, shf.x, shf.z);
+                        ff_add(hi1.y, hi1.w, shf.y, shf.w);
+                    }
+                    h = ff_rot_step(cr[u], sr[u], hi1, h);
                 }
             }
+            const cx<double> hj = ff_join(h);
             const cx<double> hsub = s_hcol[(j + 1) * B + b];
             double c;
             cx<double> sn, r;
             givens_rot(hj, hsub, c, sn, r);
             rc[j] = c;
             rs[j] = sn;
+            {
+                const float ch = __double2float_rn(c);
+                rcf[j] = make_float2(ch, __double2float_rn(c - (double)ch));
+                rsf[j] = ff_split(sn);
+            }
             a.rdiag[k * a.mmax + j] = r;
             const cx<double> gj = gk[j];
             gk[j] = c * gj;
@@ -412,8 +458,8 @@ int arnoldi_max_steps() { return kArMaxSteps; }
 heom_status arnoldi_persistent(heom_hier *h, int64_t B, int mmax, int max_steps, float4 *Vf, cx<double> *V,
                                cx<double> *Hb, int64_t S, const cx<double> *shift, const int *col_of,
                                double *rot_c, cx<double> *rot_s, cx<double> *rdiag, cx<double> *g,
-                               const double *beta, double *res, double tol, int *steps, bool *converged,
-                               cudaStream_t s) {
+                               float2 *rot_cf, float4 *rot_sf, const double *beta, double *res,
+                               double tol, int *steps, bool *converged, cudaStream_t s) {
     const int G = h->ar_ranges;
     const size_t part_bytes = (size_t)G * kPartStride * sizeof(double);
     const size_t hred_bytes = (size_t)2 * (kArMaxSteps + 2) * kArMaxB * sizeof(cx<double>);
@@ -437,6 +483,8 @@ heom_status arnoldi_persistent(heom_hier *h, int64_t B, int mmax, int max_steps,
     a.rot_s = rot_s;
     a.rdiag = rdiag;
     a.g = g;
+    a.rot_cf = rot_cf;
+    a.rot_sf = rot_sf;
     a.beta = beta;
     a.res = res;
     a.tol = tol;

@@ -274,8 +274,8 @@ int arnoldi_max_steps();
 heom_status arnoldi_persistent(heom_hier *h, int64_t B, int mmax, int max_steps, float4 *Vf, cx<double> *V,
                                cx<double> *Hb, int64_t S, const cx<double> *shift, const int *col_of,
                                double *rot_c, cx<double> *rot_s, cx<double> *rdiag, cx<double> *g,
-                               const double *beta, double *res, double tol, int *steps, bool *converged,
-                               cudaStream_t s);
+                               float2 *rot_cf, float4 *rot_sf, const double *beta, double *res,
+                               double tol, int *steps, bool *converged, cudaStream_t s);
 
 // one fused RK4 stage over all ADOs and columns (the launch heom_evolve uses)
 template <class R>

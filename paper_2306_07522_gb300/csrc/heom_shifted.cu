@@ -598,6 +598,8 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
     const int64_t rtri = (int64_t)mp * (mp - 1) / 2;
     const bool keepR = (double)S * (double)rtri * 16.0 <= (double)(1ull << 30);
     const size_t oR = keepR ? take((size_t)S * std::max<int64_t>(rtri, 1) * 16) : 0;
+    // the persistent Arnoldi's float-float copies of the rotations
+    const size_t orcf = pers ? take((size_t)S * mmax * 8) : 0, orsf = pers ? take((size_t)S * mmax * 16) : 0;
     heom_status st = ensure_ws(h->ws, off);
     if (st != HEOM_OK) return st;
     char *base = (char *)h->ws.p;
@@ -617,6 +619,8 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
     float4 *Vf = ffgs ? (float4 *)(base + oVf) : nullptr;
     float4 *hft = ffgs ? (float4 *)(base + ohf) : nullptr;
     cx<double> *Rst = keepR ? (cx<double> *)(base + oR) : nullptr;
+    float2 *rot_cf = pers ? (float2 *)(base + orcf) : nullptr;
+    float4 *rot_sf = pers ? (float4 *)(base + orsf) : nullptr;
     HEOM_CUDA(memcpy_counted(dsh, shift.data(), S * 16, cudaMemcpyHostToDevice, s));
     HEOM_CUDA(memcpy_counted(dco, col_of.data(), S * 4, cudaMemcpyHostToDevice, s));
     HEOM_CUDA(cudaMemsetAsync(Hb, 0, (size_t)(mmax + 1) * mmax * B * 16, s));
@@ -647,7 +651,7 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
         // the whole solve (up to its shared-memory limit of steps) in one cooperative launch
         int steps = 0;
         heom_status pst = arnoldi_persistent(h, B, mmax, mp, Vf, V, Hb, S, dsh, dco, rot_c, rot_s, rdiag, g,
-                                             beta, dres, tol, &steps, &done, s);
+                                             rot_cf, rot_sf, beta, dres, tol, &steps, &done, s);
         if (pst != HEOM_OK) return pst;
         m = j_done = steps;
     }
