@@ -129,15 +129,19 @@ __device__ void own_dots(const ArnoldiArgs &a, const float4 *W, int nv, int64_t 
             ff_mac(ih, il, x.x, x.z, y.y, y.w);
             ff_mac(ih, il, -x.y, -x.w, y.x, y.z);
         }
-        double re = (double)rh + (double)rl, im = (double)ih + (double)il;
-        // lanes with the same column: reduce over the lane bits above log2(B)
+        // lanes with the same column: reduce over the lane bits above log2(B), in float-float
+        // (a tree of dependent FP64 additions is slow on GB300), then one conversion
+        ff_norm(rh, rl);
+        ff_norm(ih, il);
         for (int o = 16; o >= B; o >>= 1) {
-            re += __shfl_down_sync(0xffffffffu, re, o);
-            im += __shfl_down_sync(0xffffffffu, im, o);
+            const float a0 = __shfl_down_sync(0xffffffffu, rh, o), a1 = __shfl_down_sync(0xffffffffu, rl, o);
+            const float b0 = __shfl_down_sync(0xffffffffu, ih, o), b1 = __shfl_down_sync(0xffffffffu, il, o);
+            ff_add(rh, rl, a0, a1);
+            ff_add(ih, il, b0, b1);
         }
         if (lane < B) {
-            mypart[2 * (i * B + lane)] = re;
-            mypart[2 * (i * B + lane) + 1] = im;
+            mypart[2 * (i * B + lane)] = (double)rh + (double)rl;
+            mypart[2 * (i * B + lane) + 1] = (double)ih + (double)il;
         }
     }
 }
@@ -179,7 +183,7 @@ __global__ void __launch_bounds__(kArThreads, 1) k_arnoldi(ArnoldiArgs a) {
     double *s_red = reinterpret_cast<double *>(s_hf + a.hcap);     // [32][kArMaxB]
     double *s_nrm = s_red + 32 * kArMaxB;                              // [kArMaxB]
     double *s_ib2 = s_nrm + kArMaxB;                                   // [kArMaxB] 1 / beta^2
-    int *s_flag = reinterpret_cast<int *>(s_ib2 + kArMaxB);           // [4]
+    int *s_flag = reinterpret_cast<int *>(s_ib2 + kArMaxB);           // [2 + kArMaxB]
     ProgSmem<double> ps = prog_layout<double>(v.pers_terms, v.pers_slots, v.pers_ados, d2,
                                               reinterpret_cast<unsigned char *>(s_flag + 4));
     if (threadIdx.x < B) {
@@ -237,18 +241,25 @@ __global__ void __launch_bounds__(kArThreads, 1) k_arnoldi(ArnoldiArgs a) {
             s_hf[p] = ff_split(h);
         }
         __syncthreads();
-        if (tid == 0) {  // second pass needed? (identical in every CTA)
-            int need = 0;
-            for (int b = 0; b < B; ++b) {
-                double sacc = 0.0;
-                for (int i = 0; i <= j; ++i) sacc += norm2(s_hcol[i * B + b]);
-                const double w2 = s_hcol[(j + 1) * B + b].re;
-                if (!(w2 - sacc >= kArKeep2 * w2)) need = 1;
+        // second pass needed? warp b tests column b: sum of |h_i|^2 in float (a threshold
+        // test), lane-strided with a fixed tree, so every CTA takes the same decision
+        if (warp < B) {
+            float sacc = 0.f;
+            for (int i = lane; i <= j; i += 32) {
+                const cx<double> hv = s_hcol[i * B + warp];
+                const float hr = (float)hv.re, hi = (float)hv.im;
+                sacc += hr * hr + hi * hi;
             }
-            s_flag[0] = need;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sacc += __shfl_down_sync(0xffffffffu, sacc, o);
+            if (lane == 0) {
+                const float w2 = (float)s_hcol[(j + 1) * B + warp].re;
+                s_flag[2 + warp] = !(w2 - sacc >= (float)kArKeep2 * w2);
+            }
         }
         __syncthreads();
-        const int need2 = s_flag[0];
+        int need2 = 0;
+        for (int b = 0; b < B; ++b) need2 |= s_flag[2 + b];
         for (int pass = 0; pass < 1 + need2; ++pass) {
             if (pass == 1) {
                 own_dots(a, W, j + 1, e0, nel, mypart + 2 * (kArMaxSteps + 2) * kArMaxB);
@@ -298,10 +309,11 @@ __global__ void __launch_bounds__(kArThreads, 1) k_arnoldi(ArnoldiArgs a) {
             for (int o = 16; o >= B; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
             if (lane < B) s_red[warp * kArMaxB + lane] = acc;
             __syncthreads();
-            if (tid < B) {
-                double sacc = 0.0;
-                for (int w = 0; w < (bd >> 5); ++w) sacc += s_red[w * kArMaxB + tid];
-                mypart[4 * (kArMaxSteps + 2) * kArMaxB + tid] = sacc;
+            if (warp < B) {  // warp b adds column b over the CTA's warps (a tree, not a chain)
+                double sacc = lane < (bd >> 5) ? s_red[lane * kArMaxB + warp] : 0.0;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) sacc += __shfl_down_sync(0xffffffffu, sacc, o);
+                if (lane == 0) mypart[4 * (kArMaxSteps + 2) * kArMaxB + warp] = sacc;
             }
         }
         if (!grid_barrier(a.bar, gen)) { status = 1; break; }
@@ -318,11 +330,12 @@ __global__ void __launch_bounds__(kArThreads, 1) k_arnoldi(ArnoldiArgs a) {
             }
         }
         __syncthreads();
-        // v_{j+1} = w / |w| (FP64 copy for the final tier-0 combination, float-float for the
-        // next steps)
+        // v_{j+1} = w / |w| in float-float for the next steps; the FP64 copy only of the
+        // tier-0 rows (elements below d2 * B), which the final combination x_0 = V_0 y reads,
+        // so that the basis held in L2 is the float-float one alone
         for (int idx = tid; idx < nel; idx += bd) {
             const cx<double> x = s_nrm[idx % B] * ff_join(W[e0 + idx]);  // zero norm: zeros
-            a.V[(int64_t)(j + 1) * a.L + e0 + idx] = x;
+            if (e0 + idx < (int64_t)d2 * B) a.V[(int64_t)(j + 1) * a.L + e0 + idx] = x;
             W[e0 + idx] = ff_split(x);
         }
         // Hessenberg column j to global memory (CTA 0); its rows 0 .. j split into float-float
@@ -338,7 +351,7 @@ __global__ void __launch_bounds__(kArThreads, 1) k_arnoldi(ArnoldiArgs a) {
         // the CTAs. The chain that brings column j up to date with the earlier rotations runs
         // in float-float (FP32 pipe; the FP64 instructions of GB300 are few and slow to
         // complete); the new rotation itself and g stay FP64.
-        double rmax = 0.0;
+        float rmax = 0.f;  // largest (|g_{j+1}| / beta)^2 of the CTA's shifts (a threshold test)
         for (int64_t k = (int64_t)tid * G + blockIdx.x; k < a.S; k += (int64_t)G * bd) {
             const int b = a.col_of[k];
             const cx<double> shk = a.shift[k];
@@ -393,30 +406,36 @@ __global__ void __launch_bounds__(kArThreads, 1) k_arnoldi(ArnoldiArgs a) {
             gk[j + 1] = gn;
             const double rk2 = norm2(gn) * s_ib2[b];  // (|g_{j+1}| / beta)^2
             a.res[k] = (double)sqrtf((float)rk2);     // reported estimate
-            rmax = fmax(rmax, isfinite(rk2) ? rk2 : 1e300);
+            rmax = fmaxf(rmax, isfinite(rk2) ? (float)rk2 : 3.0e38f);
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_down_sync(0xffffffffu, rmax, o));
-        if (lane == 0) s_red[warp] = rmax;
+        for (int o = 16; o > 0; o >>= 1) rmax = fmaxf(rmax, __shfl_down_sync(0xffffffffu, rmax, o));
+        float *s_redf = reinterpret_cast<float *>(s_red);
+        if (lane == 0) s_redf[warp] = rmax;
         __syncthreads();
-        if (tid == 0) {
-            double mx = 0.0;
-            for (int w = 0; w < (bd >> 5); ++w) mx = fmax(mx, s_red[w]);
-            mypart[4 * (kArMaxSteps + 2) * kArMaxB + kArMaxB] = mx;
+        if (warp == 0) {
+            float mx = lane < (bd >> 5) ? s_redf[lane] : 0.f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+            if (lane == 0) mypart[4 * (kArMaxSteps + 2) * kArMaxB + kArMaxB] = (double)mx;
         }
         steps = j + 1;
         if (!grid_barrier(a.bar, gen)) { status = 1; break; }
         if (warp == 0) {  // largest residual estimate over all CTAs
-            double mx = 0.0;
+            float mx = 0.f;
             for (int gi = lane; gi < G; gi += 32)
-                mx = fmax(mx, __ldcg(a.part + (int64_t)gi * kPartStride + 4 * (kArMaxSteps + 2) * kArMaxB + kArMaxB));
+                mx = fmaxf(mx, (float)__ldcg(a.part + (int64_t)gi * kPartStride + 4 * (kArMaxSteps + 2) * kArMaxB + kArMaxB));
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
-            if (lane == 0) s_flag[1] = mx <= a.tol * a.tol;
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+            if (lane == 0) s_flag[1] = mx <= (float)(a.tol * a.tol);
         }
         __syncthreads();
         if (s_flag[1]) { converged = 1; break; }
     }
+    // the last basis vector in FP64 as a whole: the step-by-step continuation starts from it
+    if (!status)
+        for (int idx = tid; idx < nel; idx += bd)
+            a.V[(int64_t)steps * a.L + e0 + idx] = ff_join(a.Vf[(int64_t)steps * a.L + e0 + idx]);
     if (blockIdx.x == 0 && tid == 0) {
         a.out[0] = steps;
         a.out[1] = converged;
@@ -426,7 +445,7 @@ __global__ void __launch_bounds__(kArThreads, 1) k_arnoldi(ArnoldiArgs a) {
 
 size_t arnoldi_smem(const DevView<double> &v, int hcap) {
     return (size_t)hcap * (sizeof(cx<double>) + sizeof(float4)) +
-           32 * kArMaxB * sizeof(double) + 2 * kArMaxB * sizeof(double) + 4 * sizeof(int) +
+           32 * kArMaxB * sizeof(double) + 2 * kArMaxB * sizeof(double) + (2 + kArMaxB) * sizeof(int) +
            prog_smem_bytes<double>(v.pers_terms, v.pers_slots, v.pers_ados, v.d2) + 64;
 }
 
