@@ -109,21 +109,22 @@ class ClockSampler:
 
 
 def _traffic_record(kernel_class: str):
-    """ncu DRAM bytes per launch recorded under profiles/, valid only for unchanged kernels."""
+    """ncu DRAM bytes per launch recorded under profiles/, valid only while the source files
+    that define the measured kernels (the record's "sources", in csrc/) are unchanged."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         rec = json.load(f)
     entry = rec.get(kernel_class)
-    if not entry:
+    if not entry or not entry.get("sources"):
         return None
     src = os.path.join(ROOT, "paper_2306_07522_gb300", "csrc")
     h = hashlib.sha256()
-    for name in sorted(os.listdir(src)):
+    for name in sorted(entry["sources"]):
         with open(os.path.join(src, name), "rb") as f:
             h.update(f.read())
-    if entry.get("csrc_sha256") != h.hexdigest():
+    if entry.get("sources_sha256") != h.hexdigest():
         return None
     return entry.get("dram_bytes_per_launch")
 

@@ -452,8 +452,10 @@ __global__ void __launch_bounds__(64) k_shift_rform(int m, int mmax, int64_t rtr
 // y = R^{-1} g column by column (l = m-1 .. 0: y_l = g_l / R_ll, then g_i -= R_il y_l for
 // i < l), then x0 = V_0 y on the tier-0 elements. Four lanes per shift, eight shifts per
 // 32-thread block (enough blocks to reach every SM); lane q of a quad updates the rows
-// i = q mod 4 and sums the elements e = q mod 4. g and y of the block's shifts sit in shared
-// memory: 2 * 8 * m complex values.
+// i = q mod 4 and sums the elements e = q mod 4. The reciprocals 1 / R_ll are formed before
+// the column loop (independent divisions that overlap), so the loop's serial chain holds one
+// complex product per column instead of a division. g, y and the reciprocals of the block's
+// shifts sit in shared memory: 3 * 8 * m complex values.
 constexpr int kBsShifts = 8;
 __global__ void __launch_bounds__(32) k_shift_backsub(int m, int mmax, int64_t rtri, int64_t B, int64_t S,
                                                       int d2, const int *__restrict__ col_of,
@@ -466,17 +468,22 @@ __global__ void __launch_bounds__(32) k_shift_backsub(int m, int mmax, int64_t r
     const int lane = threadIdx.x, q = lane & 3, slot = lane >> 2;
     cx<double> *sg = reinterpret_cast<cx<double> *>(smem_raw) + (int64_t)slot * m;
     cx<double> *sy = reinterpret_cast<cx<double> *>(smem_raw) + (int64_t)(kBsShifts + slot) * m;
+    cx<double> *sinv = reinterpret_cast<cx<double> *>(smem_raw) + (int64_t)(2 * kBsShifts + slot) * m;
     const int64_t k_raw = (int64_t)blockIdx.x * kBsShifts + slot;
     const bool valid = k_raw < S;
     const int64_t k = valid ? k_raw : S - 1;  // idle quads repeat the last shift, store nothing
     const int64_t b = col_of[k];
-    for (int i = q; i < m; i += 4) sg[i] = g[k * (mmax + 1) + i];
+    for (int i = q; i < m; i += 4) {
+        sg[i] = g[k * (mmax + 1) + i];
+        const cx<double> d = rdiag[k * mmax + i];
+        sinv[i] = (1.0 / norm2(d)) * conj(d);
+    }
     __syncwarp();
     const cx<double> *Rk = R + k * rtri;
     for (int l = m - 1; l >= 0; --l) {
         cx<double> yl{0.0, 0.0};
         if (q == (l & 3)) {
-            yl = cdiv(sg[l], rdiag[k * mmax + l]);
+            yl = sg[l] * sinv[l];
             sy[l] = yl;
         }
         const int src = (lane & ~3) | (l & 3);
@@ -751,7 +758,7 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
         if (m > 1)
             k_shift_rform<<<dim3((unsigned)((S + 63) / 64), (unsigned)(m - 1)), 64, 0, s>>>(
                 m, mmax, rtri, B, S, Hb, dsh, dco, rot_c, rot_s, Rst);
-        const size_t smb = (size_t)2 * kBsShifts * m * sizeof(cx<double>);
+        const size_t smb = (size_t)3 * kBsShifts * m * sizeof(cx<double>);
         if (smb > 48 * 1024)
             HEOM_CUDA(cudaFuncSetAttribute(k_shift_backsub, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
         k_shift_backsub<<<(unsigned)((S + kBsShifts - 1) / kBsShifts), 32, smb, s>>>(
