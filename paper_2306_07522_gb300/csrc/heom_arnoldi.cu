@@ -302,12 +302,22 @@ __global__ void __launch_bounds__(kArThreads, 1) k_arnoldi(ArnoldiArgs a) {
             __syncthreads();
         }
         if (status) break;
-        // ---- 3. |w| (FP64 partials, fixed order)
+        // ---- 3. |w| (float-float within a warp, FP64 across warps and CTAs; fixed order)
         {
-            double acc = 0.0;  // thread's own elements all have column tid % B when B | bd
-            for (int idx = tid; idx < nel; idx += bd) acc += norm2(ff_join(W[e0 + idx]));
-            for (int o = 16; o >= B; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-            if (lane < B) s_red[warp * kArMaxB + lane] = acc;
+            // |w|^2 of the own elements in float-float (FP32 pipe), one conversion per warp;
+            // a thread's elements all have column tid % B when B | bd
+            float ah = 0.f, al = 0.f;
+            for (int idx = tid; idx < nel; idx += bd) {
+                const float4 x = W[e0 + idx];
+                ff_mac(ah, al, x.x, x.z, x.x, x.z);
+                ff_mac(ah, al, x.y, x.w, x.y, x.w);
+            }
+            ff_norm(ah, al);
+            for (int o = 16; o >= B; o >>= 1) {
+                const float oh = __shfl_down_sync(0xffffffffu, ah, o), ol = __shfl_down_sync(0xffffffffu, al, o);
+                ff_add(ah, al, oh, ol);
+            }
+            if (lane < B) s_red[warp * kArMaxB + lane] = (double)ah + (double)al;
             __syncthreads();
             if (warp < B) {  // warp b adds column b over the CTA's warps (a tree, not a chain)
                 double sacc = lane < (bd >> 5) ? s_red[lane * kArMaxB + warp] : 0.0;
