@@ -114,3 +114,25 @@ def test_pruned_apply_is_the_projection_of_the_full_apply(parity):
     np.testing.assert_allclose(lv.apply_loop(pr, X, h), want, atol=1e-12)
     Y = lv.from_liouville(lv.build_matrix(pr, h) @ lv.to_liouville(X), 3)
     np.testing.assert_allclose(Y, want, atol=1e-12)
+
+
+@pytest.mark.parametrize("seed", [71, 72])
+def test_library_host_count_matches_oracle_hybrid(seed):
+    """The library's host count (C++ enumeration and Eq. importance with bosonic R / I / RI
+    exponents and fermions) equals the oracle's pruned hierarchy size, at thresholds between
+    the oracle's own importance values (decisions far from ties)."""
+    pytest.importorskip("paper_2306_07522_gb300")
+    from paper_2306_07522_gb300 import count_ados
+    prob = W.random_raw_problem(2, [("RI", 2), ("R", 1), ("I", 1)], [4, 2], 3, 3, seed=seed)
+    full = hy.problem_hierarchy(prob)
+    bos, fer = hy.flatten_exponents(prob)
+    be = [(e.coef, e.rate) for e in bos]
+    fe = [(e.coef, e.rate) for e in fer]
+    imp = np.unique([hy.importance(be, fe, m, S) for (m, S) in full.ados if not hy.always_kept(m, S)])
+    assert len(imp) > 20
+    for q in (0.1, 0.35, 0.6, 0.9):
+        k = int(q * (len(imp) - 1))
+        th = float(np.sqrt(imp[k] * imp[k + 1]))  # strictly between two importance values
+        want = hy.prune_hierarchy(full, be, fe, th).n_ado
+        assert count_ados(prob["baths"], prob["tier_b"], prob["tier_f"], th) == want
+    assert count_ados(prob["baths"], prob["tier_b"], prob["tier_f"], 0.0) == full.n_ado
