@@ -134,7 +134,7 @@ def test_warm_start_gain_on_held_out_solves(heom):
     (1) the network's rho_sys is far closer to the solved one than the best answer without
     it (the mean training state), at the cost of one forward pass instead of a solve;
     (2) a solve seeded with the prediction still reaches the 1e-8 residual (the cold solve
-    is the fallback and the judge). Iterations are recorded for both starts: a guess made of
+    is the fallback and the measure of its error). Iterations are recorded for both starts: a guess made of
     rho_sys and the tier-1 ADOs (higher tiers zero) has a residual larger than ||b||, so
     heom_steady discards it and starts cold; the warm solve costs what the cold one does."""
     import torch

@@ -146,7 +146,7 @@ def charge_cavity_ops(eps: float, omega_c: float, g: float, n_fock: int):
 
 
 # --------------------------------------------------------------------------------------
-# Workloads (BASELINE configurations, read as stated in the design doc).
+# Workloads: the paper's example systems with their Table 1 parameters, and the benchmark shapes.
 # --------------------------------------------------------------------------------------
 
 
