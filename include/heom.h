@@ -53,7 +53,7 @@ typedef enum {
     HEOM_ECUDA = 3,       /* CUDA runtime error, or no usable device                    */
     HEOM_ENOCONV = 4,     /* a solver reached max_iter; stats hold the last residual    */
     HEOM_EBREAKDOWN = 5,  /* Krylov breakdown or a non-finite value in a solver         */
-    HEOM_ENOTSUP = 6      /* valid request this build does not implement               */
+    HEOM_ENOTSUP = 6      /* valid request the library does not implement              */
 } heom_status;
 
 /* Kinds of exponent lists (one per bath). Results: Eqs. C_beta_RI and C_beta_u; D_j. */
