@@ -292,6 +292,23 @@ heom_status heom_spectrum(heom_hier *odd, const void *ss_ados, const heom_c64 *o
                           const double *omega, int64_t n_omega, double tol, int max_iter,
                           double *A_out, int prec, heom_solve_stats *stats, heom_stream s);
 
+/* Densities of states of n_hier odd-parity hierarchies of different shapes (tiers, exponent
+ * counts, d) on one frequency grid (Methods, spectrum). Hierarchy h takes its stationary
+ * state ss_ados[h] (device, [N_h][d_h][d_h][n_sets_h]) and its mode op_d[h] (host,
+ * d_h x d_h). Each hierarchy is the heom_spectrum call with the same tol, max_iter and
+ * prec; the calls run one after the other on s, and each fills the GPU (parameter sets of
+ * one structure belong in one hierarchy, where they share one launch). Outputs are
+ * concatenated in hierarchy order: A_out (host) holds n_sets_h rows of n_omega per
+ * hierarchy; stats (host, or NULL) holds 2 * n_omega * n_sets_h entries per hierarchy. A
+ * solver status (HEOM_ENOCONV, HEOM_EBREAKDOWN) of one hierarchy does not stop the others,
+ * and the first status other than HEOM_OK is returned; an argument, memory or CUDA error
+ * stops at that hierarchy (HEOM_EINVAL before any solve when the arrays are invalid).
+ * Synchronises s. */
+heom_status heom_spectrum_batched(int n_hier, heom_hier *const *odd, const void *const *ss_ados,
+                                  const heom_c64 *const *op_d, const double *omega,
+                                  int64_t n_omega, double tol, int max_iter, double *A_out,
+                                  int prec, heom_solve_stats *stats, heom_stream s);
+
 /* Power spectral density of the mode op_a (Methods, numerical computation of the spectrum,
  * bosonic case): pi S(w) = -Re Tr[a^dag x_0] with (M - i w) x = a rho over every ADO, M of the
  * even-parity hierarchy `even` whose stationary state is ss_ados (device complex128

@@ -80,6 +80,8 @@ _sig = {
                             _P],
     "heom_steady": [_P, _P, _P, C.c_int64, C.c_double, C.c_int, C.c_int, _P, _P],
     "heom_spectrum": [_P, _P, _P, _P, C.c_int64, C.c_double, C.c_int, _P, C.c_int, _P, _P],
+    "heom_spectrum_batched": [C.c_int, _P, _P, _P, _P, C.c_int64, C.c_double, C.c_int, _P, C.c_int,
+                              _P, _P],
     "heom_current": [_P, _P, C.c_int64, _P, C.c_int, _P, _P],
     "heom_psd": [_P, _P, _P, _P, C.c_int64, C.c_double, C.c_int, _P, _P, _P],
     "heom_autotune": [_P, C.c_int64, C.c_int, _P, _P, _P, _P, _P],
@@ -424,6 +426,32 @@ def spectrum(odd: Hierarchy, ss, op_d, omegas, tol: float = 1e-8, max_iter: int 
     if raise_on_error:
         _check(st, "heom_spectrum")
     return A, st, _stats_list(stats)
+
+
+def spectrum_batched(odds, sss, ops, omegas, tol: float = 1e-8, max_iter: int = 2000,
+                     prec: int = SHIFTED, stream=None, raise_on_error: bool = True):
+    """heom_spectrum_batched: densities of states of several odd hierarchies of different
+    shapes on one grid. Returns (list of A per hierarchy, (n_sets, n_omega) or (n_omega,),
+    status, stats concatenated in hierarchy order)."""
+    n = len(odds)
+    om = np.ascontiguousarray(omegas, np.float64)
+    rows = [o.n_sets for o in odds]
+    A = np.zeros((sum(rows), len(om)))
+    stats = (SolveStats * (2 * len(om) * sum(rows)))()
+    keep = [_c64(op) for op in ops]
+    hp = (C.c_void_p * n)(*[C.cast(o.handle, C.c_void_p).value for o in odds])
+    sp = (C.c_void_p * n)(*[_dptr(x).value for x in sss])
+    opp = (C.c_void_p * n)(*[k.ctypes.data for k in keep])
+    st = _lib.heom_spectrum_batched(n, C.cast(hp, C.c_void_p), C.cast(sp, C.c_void_p),
+                                    C.cast(opp, C.c_void_p), _ptr(om), len(om), tol, max_iter,
+                                    _ptr(A), prec, C.cast(stats, C.c_void_p), _stream(stream))
+    if raise_on_error:
+        _check(st, "heom_spectrum_batched")
+    out, r = [], 0
+    for ns in rows:
+        out.append(A[r] if ns == 1 else A[r:r + ns])
+        r += ns
+    return out, st, _stats_list(stats)
 
 
 def autotune(h: Hierarchy, batch: int, prec: int = FP32, stream=None) -> dict:

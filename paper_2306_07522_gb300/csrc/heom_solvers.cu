@@ -1384,6 +1384,34 @@ extern "C" heom_status heom_psd(heom_hier *even, const void *ss_ados, const heom
     return ret;
 }
 
+extern "C" heom_status heom_spectrum_batched(int n_hier, heom_hier *const *odd, const void *const *ss_ados,
+                                             const heom_c64 *const *op_d, const double *omega,
+                                             int64_t n_omega, double tol, int max_iter, double *A_out,
+                                             int prec, heom_solve_stats *stats, heom_stream s) {
+    if (n_hier < 1 || !odd || !ss_ados || !op_d || !omega || n_omega < 1 || !A_out) {
+        set_error("heom_spectrum_batched: need n_hier >= 1 and the per-hierarchy arrays, omega, A_out");
+        return HEOM_EINVAL;
+    }
+    for (int h = 0; h < n_hier; ++h)
+        if (!odd[h] || !ss_ados[h] || !op_d[h] || odd[h]->parity != -1) {
+            set_error("heom_spectrum_batched: hierarchy %d: need an odd-parity hierarchy, its "
+                      "stationary state and its operator", h);
+            return HEOM_EINVAL;
+        }
+    heom_status first = HEOM_OK;
+    int64_t row = 0;
+    for (int h = 0; h < n_hier; ++h) {
+        const int64_t ns = odd[h]->n_sets;
+        const heom_status st = heom_spectrum(odd[h], ss_ados[h], op_d[h], omega, n_omega, tol, max_iter,
+                                             A_out + row * n_omega, prec,
+                                             stats ? stats + 2 * row * n_omega : nullptr, s);
+        if (st != HEOM_OK && first == HEOM_OK) first = st;
+        if (st == HEOM_EINVAL || st == HEOM_ECUDA || st == HEOM_ENOMEM) return st;
+        row += ns;
+    }
+    return first;
+}
+
 extern "C" heom_status heom_spectrum(heom_hier *odd, const void *ss_ados, const heom_c64 *op_d,
                                      const double *omega, int64_t n_omega, double tol,
                                      int max_iter, double *A_out, int prec,

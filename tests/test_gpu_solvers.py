@@ -301,3 +301,36 @@ def test_psd_matches_oracle_and_sum_rule(heom):
     assert st == heom.OK
     Sso = so.psd(Ms, Xs, nup, oms)
     assert np.abs(Sg - Sso).max() < 1e-7 * np.abs(Sso).max()
+
+
+def test_spectrum_batched_over_hierarchies_of_different_shapes(heom):
+    """heom_spectrum_batched over SIAM tier 1, a single level (d = 2, its own exponents) and
+    SIAM tier 2: every hierarchy's result equals its own heom_spectrum call bit for bit, and
+    the SIAM ones match the oracle's sparse LU."""
+    import torch
+    models = [W.siam_model(tier=1), W.single_level_model(tier=2), W.siam_model(tier=2)]
+    om = np.array([-9.0, -3.0, 0.4, 5.0])
+    odds, sss, ops, singles = [], [], [], []
+    for m in models:
+        even = heom.build_hierarchy(heom.problem_from_model(m, 1))
+        odd = heom.build_hierarchy(heom.problem_from_model(m, -1))
+        x = torch.zeros((even.n_ado, m.d, m.d), dtype=torch.complex128, device="cuda")
+        heom.steady(even, x, tol=1e-11, max_iter=3000, prec=heom.FP64)
+        dop = m.fermion_baths[0][0]
+        A1, st, _ = heom.spectrum(odd, x, dop, om, tol=1e-10, max_iter=2000, prec=heom.SHIFTED)
+        assert st == heom.OK
+        odds.append(odd)
+        sss.append(x)
+        ops.append(dop)
+        singles.append(A1)
+    As, st, stats = heom.spectrum_batched(odds, sss, ops, om, tol=1e-10, max_iter=2000)
+    assert st == heom.OK and len(stats) == 2 * len(om) * 3
+    for A, A1 in zip(As, singles):
+        assert np.array_equal(A, A1)
+    for i in (0, 2):
+        m = models[i]
+        prob = hy.model_to_problem(m)
+        h = hy.problem_hierarchy(prob)
+        Xo = so.steady_state(lv.build_matrix(prob, h), m.d)
+        Ao = so.dos(lv.build_matrix(hy.model_to_problem(m, -1), h), Xo, m.fermion_baths[0][0], om)
+        assert np.abs(As[i] - Ao).max() < 1e-8 * np.abs(Ao).max()
