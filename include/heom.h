@@ -66,13 +66,17 @@ typedef enum {
 
 /* Arithmetic of a call. */
 typedef enum {
-    HEOM_FP64 = 0,   /* complex FP64 throughout (the plain path)                       */
+    HEOM_FP64 = 0,   /* complex FP64 storage and arithmetic (the plain path); the
+                        single-column stationary solve runs its Krylov applies in
+                        float-float (about 48 significant bits), its residuals in FP64  */
     HEOM_FP32 = 1,   /* complex FP32 storage and arithmetic                            */
     HEOM_MIXED = 2,  /* solvers: FP32 inner Krylov solves inside FP64 iterative
                         refinement; FP64 residuals, dot products and normalisation      */
-    HEOM_SHIFTED = 3 /* heom_spectrum: one FP64 Arnoldi process per right-hand side serves
-                        every frequency (the shifted systems share one Krylov space);
-                        residual per frequency from its shifted Hessenberg problem      */
+    HEOM_SHIFTED = 3 /* heom_spectrum: one Arnoldi process per right-hand side serves
+                        every frequency (the shifted systems share one Krylov space):
+                        apply, Gram-Schmidt and rotation chains in float-float (about
+                        48 significant bits), Hessenberg matrix, rotations and solutions
+                        FP64; residual per frequency from its shifted Hessenberg problem */
 } heom_prec;
 
 /* One bath = one coupling operator + its exponent list (Fig. 1b). */
