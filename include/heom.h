@@ -203,6 +203,13 @@ heom_status heom_export_tables(const heom_hier *h, int32_t *row_ptr, int32_t *nb
 
 void heom_destroy(heom_hier *h);
 
+/* Solver workspaces (Krylov bases and vectors, up to gigabytes) of destroyed hierarchies are
+ * kept in a process-wide cache per device, at most 8 buffers, and reused by later solves of
+ * any hierarchy on that device: cudaFree of such buffers is slow and synchronises the device.
+ * This call frees every cached buffer. A workspace allocation that fails frees the device's
+ * cached buffers and tries again by itself. Call it only while no library call is running. */
+heom_status heom_release_workspace_cache(void);
+
 /* Message of the last error on the calling thread ("" if none). */
 const char *heom_last_error(void);
 

@@ -95,6 +95,7 @@ _sig = {
     "heom_mlp_train_step": [_P, _P, _P, C.c_int64, C.c_float, _P, _P],
     "heom_warm_start_features": [_P, _P, C.c_int64, _P, C.c_int, _P],
     "heom_warm_start": [_P, _P, _P, C.c_int64, _P, _P],
+    "heom_release_workspace_cache": [],
     "heom_profile_enable": [C.c_int],
     "heom_profile_read": [C.c_int, _P, _P, _P, _P],
     "heom_profile_copies": [_P, _P],
@@ -491,6 +492,11 @@ def current(h: Hierarchy, x, baths, stream=None) -> np.ndarray:
 
 
 # ------------------------------------------------------------------------- launch accounting
+def release_workspace_cache():
+    """heom_release_workspace_cache: free the solver workspaces kept for reuse."""
+    _check(_lib.heom_release_workspace_cache(), "heom_release_workspace_cache")
+
+
 def profile_enable(on: bool = True):
     _check(_lib.heom_profile_enable(int(on)), "heom_profile_enable")
 

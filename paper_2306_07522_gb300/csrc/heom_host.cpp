@@ -14,6 +14,7 @@
 #include <cstring>
 #include <algorithm>
 #include <map>
+#include <mutex>
 #include <new>
 
 #include "heom_internal.h"
@@ -60,10 +61,90 @@ void dfree(DBuf &b) {
     b.bytes = 0;
 }
 
+// Process-wide cache of solver workspaces, per device. A destroyed hierarchy hands its
+// workspace buffers (up to gigabytes: the Krylov bases) to the cache instead of cudaFree,
+// which is slow for such buffers and synchronises the whole device; the next workspace
+// request on the same device takes the smallest cached buffer that is large enough. At
+// most kWsCacheMax buffers are kept (the oldest is freed beyond that);
+// heom_release_workspace_cache frees them all, and a failed allocation frees the device's
+// cached buffers and tries once more.
+namespace {
+struct WsEntry {
+    int device;
+    DBuf buf;
+};
+std::mutex g_ws_mu;
+std::vector<WsEntry> g_ws_cache;
+constexpr size_t kWsCacheMax = 8;
+
+void free_on_device(const WsEntry &e) {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != e.device) cudaSetDevice(e.device);
+    cudaFree(e.buf.p);
+    if (cur != e.device) cudaSetDevice(cur);
+}
+
+void release_cached(int device) {  // device < 0: every device
+    std::vector<WsEntry> out;
+    {
+        std::lock_guard<std::mutex> lk(g_ws_mu);
+        for (size_t i = 0; i < g_ws_cache.size();) {
+            if (device < 0 || g_ws_cache[i].device == device) {
+                out.push_back(g_ws_cache[i]);
+                g_ws_cache.erase(g_ws_cache.begin() + (std::ptrdiff_t)i);
+            } else {
+                ++i;
+            }
+        }
+    }
+    for (const WsEntry &e : out) free_on_device(e);
+}
+}  // namespace
+
+void ws_release(DBuf &b, int device) {
+    if (!b.p) return;
+    WsEntry evict{-1, DBuf{}};
+    {
+        std::lock_guard<std::mutex> lk(g_ws_mu);
+        g_ws_cache.push_back(WsEntry{device, b});
+        if (g_ws_cache.size() > kWsCacheMax) {
+            evict = g_ws_cache.front();
+            g_ws_cache.erase(g_ws_cache.begin());
+        }
+    }
+    b = DBuf{};
+    if (evict.buf.p) free_on_device(evict);
+}
+
 heom_status ensure_ws(DBuf &b, size_t bytes) {
     if (b.bytes >= bytes && b.p) return HEOM_OK;
-    return dalloc(b, bytes);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (b.p) ws_release(b, dev);
+    {
+        std::lock_guard<std::mutex> lk(g_ws_mu);
+        size_t best = g_ws_cache.size();
+        for (size_t i = 0; i < g_ws_cache.size(); ++i)
+            if (g_ws_cache[i].device == dev && g_ws_cache[i].buf.bytes >= bytes &&
+                (best == g_ws_cache.size() || g_ws_cache[i].buf.bytes < g_ws_cache[best].buf.bytes))
+                best = i;
+        if (best < g_ws_cache.size()) {
+            b = g_ws_cache[best].buf;
+            g_ws_cache.erase(g_ws_cache.begin() + (std::ptrdiff_t)best);
+            return HEOM_OK;
+        }
+    }
+    heom_status st = dalloc(b, bytes);
+    if (st == HEOM_ENOMEM) {
+        release_cached(dev);
+        cudaGetLastError();  // clear the failed allocation's error
+        st = dalloc(b, bytes);
+    }
+    return st;
 }
+
+void ws_release_all() { release_cached(-1); }
 
 }  // namespace heom
 
@@ -1121,8 +1202,18 @@ extern "C" heom_status heom_export_tables(const heom_hier *h, int32_t *row_ptr, 
 extern "C" void heom_destroy(heom_hier *h) {
     if (!h) return;
     cudaSetDevice(h->device);
+    // the solver workspaces go to the process-wide cache (every solver has synchronised
+    // its stream before returning, so no kernel still uses them)
+    heom::ws_release(h->ws, h->device);
+    heom::ws_release(h->ws_small, h->device);
+    heom::ws_release(h->ws_pers, h->device);
     free_all(h);
     delete h;
+}
+
+extern "C" heom_status heom_release_workspace_cache(void) {
+    heom::ws_release_all();
+    return HEOM_OK;
 }
 
 extern "C" const char *heom_last_error(void) { return heom::g_err.c_str(); }

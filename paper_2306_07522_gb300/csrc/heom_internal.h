@@ -206,7 +206,9 @@ heom_status cuda_fail(cudaError_t e, const char *what);
 
 heom_status dalloc(DBuf &b, size_t bytes);
 void dfree(DBuf &b);
-heom_status ensure_ws(DBuf &b, size_t bytes);
+heom_status ensure_ws(DBuf &b, size_t bytes);  // grows b, from the workspace cache when it can
+void ws_release(DBuf &b, int device);           // hands b to the workspace cache
+void ws_release_all();
 
 // bounds of one ADO range of the persistent tiled kernel (shared-memory budget)
 constexpr int kRangeTerms = 4096;
