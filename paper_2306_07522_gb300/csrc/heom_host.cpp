@@ -344,13 +344,14 @@ bool next_comp(std::vector<int> &m) {
 bool finite(const heom_c64 &z) { return std::isfinite(z.re) && std::isfinite(z.im); }
 
 template <class T>
+// A copy from pageable host memory has staged the data when it returns, so v may go at once;
+// the callers synchronise stream 0 once after their last upload, so that the tables are on
+// the device before the call returns (kernels on other streams may read them next).
 heom_status upload(DBuf &b, const std::vector<T> &v) {
     heom_status st = heom::dalloc(b, v.size() * sizeof(T));
     if (st != HEOM_OK) return st;
-    if (!v.empty()) {
+    if (!v.empty())
         HEOM_CUDA(heom::memcpy_counted(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, 0));
-        HEOM_CUDA(cudaStreamSynchronize(0));
-    }
     return HEOM_OK;
 }
 
@@ -687,6 +688,7 @@ heom_status upload_params(heom_hier *h, int n_sets, const heom_c64 *H, const heo
     UP(d_rate64, to_cx<double>(rt)); UP(d_rate32, to_cx<float>(rt));
     UP(d_floor64, fl); UP(d_floor32, fl32);
 #undef UP
+    HEOM_CUDA(cudaStreamSynchronize(0));  // every upload of this call (and of the build) landed
     h->n_sets = n_sets;
     h->H0.assign(H, H + (size_t)n_sets * d * d);
     h->coef0.assign(coef, coef + (size_t)n_sets * K);
@@ -1308,6 +1310,7 @@ heom_status set_tile_partition(heom_hier *h, int per_sm) {
     dfree(h->d_cta_ado);
     heom_status st = upload(h->d_cta_ado, ranges);
     if (st != HEOM_OK) return st;
+    HEOM_CUDA(cudaStreamSynchronize(0));
     h->n_ranges = (int)ranges.size() - 1;
     h->range_terms = (int)std::min<int64_t>(rt, INT32_MAX);
     h->range_slots = (int)std::min<int64_t>(rs, INT32_MAX);
