@@ -136,3 +136,24 @@ def test_library_host_count_matches_oracle_hybrid(seed):
         want = hy.prune_hierarchy(full, be, fe, th).n_ado
         assert count_ados(prob["baths"], prob["tier_b"], prob["tier_f"], th) == want
     assert count_ados(prob["baths"], prob["tier_b"], prob["tier_f"], 0.0) == full.n_ado
+
+
+@pytest.mark.parametrize("parity", [1, -1])
+def test_pruned_integer_tables_reproduce_the_apply(parity):
+    """oracle/tables.py on a pruned hierarchy (entries to dropped ADOs left out): the apply
+    from the integer tables equals the loop path, which the projection test above pins."""
+    from oracle import tables as tb
+    prob = W.random_raw_problem(3, [("RI", 2), ("I", 1)], [4, 2], 3, 3, parity=parity, seed=54)
+    full = hy.problem_hierarchy(prob)
+    bos, fer = hy.flatten_exponents(prob)
+    imp = sorted(hy.importance([(e.coef, e.rate) for e in bos], [(e.coef, e.rate) for e in fer], m, S)
+                 for (m, S) in full.ados if not hy.always_kept(m, S))
+    pr = dict(prob, importance_th=imp[len(imp) // 3])
+    h = hy.problem_hierarchy(pr)
+    assert full.n_ado > h.n_ado
+    X = W.random_ado_vector(h.n_ado, 3, seed=55)
+    Y1 = lv.apply_loop(pr, X, h)
+    Y2 = tb.apply_from_tables(pr, X, h)
+    assert np.abs(Y1 - Y2).max() <= 1e-13 * np.abs(Y1).max()
+    # every table entry points at a kept ADO
+    assert all(0 <= nb < h.n_ado for row in tb.neighbour_table(pr, h) for (nb, *_rest) in row)
