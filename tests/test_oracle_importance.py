@@ -157,3 +157,25 @@ def test_pruned_integer_tables_reproduce_the_apply(parity):
     assert np.abs(Y1 - Y2).max() <= 1e-13 * np.abs(Y1).max()
     # every table entry points at a kept ADO
     assert all(0 <= nb < h.n_ado for row in tb.neighbour_table(pr, h) for (nb, *_rest) in row)
+
+
+def test_library_host_count_edge_cases():
+    """heom_count_ados (host only): no baths, tier 0, the closed-form full count without a
+    threshold, and the refusals (non-finite or negative threshold, negative tier, more than
+    64 fermionic exponents)."""
+    heom = pytest.importorskip("paper_2306_07522_gb300")
+    from paper_2306_07522_gb300 import HeomError, count_ados
+    assert count_ados([], 0, 0) == 1
+    assert count_ados([], 3, 2) == 1  # tiers without exponents add nothing
+    prob = W.random_raw_problem(2, [("RI", 3)], [6], 3, 2, seed=91)
+    assert count_ados(prob["baths"], 0, 0) == 1
+    assert count_ados(prob["baths"], 3, 2) == hy.ado_count_closed_form(3, 6, 3, 2)
+    for th in (float("nan"), -1e-3):
+        with pytest.raises(HeomError):
+            count_ados(prob["baths"], 3, 2, th)
+    with pytest.raises(HeomError):
+        count_ados(prob["baths"], -1, 2)
+    big = W.random_raw_problem(2, [], [66], 0, 1, seed=92)
+    with pytest.raises(HeomError):
+        count_ados(big["baths"], 0, 1)
+    assert heom is not None
