@@ -53,7 +53,10 @@ typedef enum {
     HEOM_ECUDA = 3,       /* CUDA runtime error, or no usable device                    */
     HEOM_ENOCONV = 4,     /* a solver reached max_iter; stats hold the last residual    */
     HEOM_EBREAKDOWN = 5,  /* Krylov breakdown or a non-finite value in a solver         */
-    HEOM_ENOTSUP = 6      /* valid request the library does not implement              */
+    HEOM_ENOTSUP = 6,     /* valid request the library does not implement              */
+    HEOM_ETIMEOUT = 7     /* a device-side wait (a grid barrier of a persistent solver)
+                             ran out (heom_set_wait_limit); every CTA left the launch, the
+                             device and the hierarchy stay usable, stats are filled       */
 } heom_status;
 
 /* Kinds of exponent lists (one per bath). Results: Eqs. C_beta_RI and C_beta_u; D_j. */
@@ -210,6 +213,17 @@ void heom_destroy(heom_hier *h);
  * cached buffers and tries again by itself. Call it only while no library call is running. */
 heom_status heom_release_workspace_cache(void);
 
+/* Bound, in SM clock cycles, of every device-side wait the library's kernels make: the grid
+ * barriers of the persistent stationary-state and spectrum solvers, the only spin-waits in
+ * the library. cycles <= 0 restores the default, 4e9 (about 2 s at 2 GHz). A wait that runs
+ * out raises a flag on which every CTA of the launch leaves its wait, the launch ends, and
+ * the call returns HEOM_ETIMEOUT with its statistics filled (stationary state: the true
+ * residual of the current iterate per column; spectrum: status HEOM_ETIMEOUT per
+ * frequency); the device and the hierarchy stay usable. Process-wide, read at each launch.
+ * For tests of this failure path and for callers that need a tighter bound. The paper has no
+ * counterpart. */
+heom_status heom_set_wait_limit(int64_t cycles);
+
 /* Message of the last error on the calling thread ("" if none). */
 const char *heom_last_error(void);
 
@@ -259,13 +273,16 @@ heom_status heom_evolve_td(heom_hier *h, void *ados, int64_t batch, double dt, i
  * held by another allocator (a framework's caching pool, a fixed budget) can see cudaMalloc
  * fail, and cudaFree waits for the whole device. Same arguments, layout and results as
  * heom_evolve, but the three RK4 stage buffers come from one static 16 MiB device array of
- * the library (held on every GPU that loads the library until the process exits), so
- * 3 * N * d * d * batch * (16 bytes for HEOM_FP64, 8 for HEOM_FP32) must not exceed
- * 16 MiB; larger requests return HEOM_EINVAL and allocate nothing. The first call on a
+ * the library, so 3 * N * d * d * batch * (16 bytes for HEOM_FP64, 8 for HEOM_FP32) must not
+ * exceed 16 MiB; larger requests return HEOM_EINVAL and allocate nothing. The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress, with that device
- * current); make that first call before any stream capture. All calls share the one array:
- * calls whose work overlaps on the GPU (other threads, other streams) race on it and must
- * be serialised by the caller. Synchronises s. */
+ * current). Under the CUDA runtime's lazy module loading (the default since CUDA 12.2) that
+ * lookup is what makes the runtime reserve the 16 MiB on that device, which it then holds
+ * until the process exits; if the device has no room left the call returns HEOM_ENOMEM.
+ * So make one call with n_steps = 0 on each device at start-up, before the other allocator
+ * fills device memory and before any stream capture. All calls share the one array: calls
+ * whose work overlaps on the GPU (other threads, other streams) race on it and must be
+ * serialised by the caller. Synchronises s. */
 heom_status heom_evolve_noalloc(heom_hier *h, void *ados, int64_t batch, double dt,
                                 int64_t n_steps, int64_t save_every, void *rho_traj, int prec,
                                 heom_stream s);
@@ -336,15 +353,26 @@ heom_status heom_psd(heom_hier *even, const void *ss_ados, const heom_c64 *op_a,
 /* Autotuner of the apply for one batch width (measurement of this GPU; the paper has no
  * counterpart). Times heom_apply on a library-allocated test vector of `batch` columns in
  * precision prec with the per-element kernel and with the tiled kernel at 1..5 ADO ranges
- * per SM, and keeps the fastest in h: the tiled granularity for every later batched apply
- * and solve, or, when the per-element kernel wins, the per-element kernel for batches up to
- * `batch` columns. candidates_us: host [6] or NULL (index 0 per-element, p = 1..5 tiled with
- * p ranges per SM, -1 where not applicable); tiled, ctas_per_sm, best_us: host or NULL.
- * Results of the apply do not depend on the choice (the same terms, summed in the same
- * order). Allocates two vectors of N d^2 batch elements for the duration of the call.
- * Synchronises s. */
+ * per SM -- in FP32 each with every kernel variant (columns per lane / terms per item in
+ * flight / items per warp in flight / CTAs per SM the registers are sized for -- 0: 2/4/1/3;
+ * 1: 2/4/1/4; 2: 2/3/1/4; 3: 2/2/1/5; 4: 2/6/1/3; 5: 4/4/1/2) -- and keeps the fastest in h: the tiled granularity and variant for every later
+ * batched apply and solve, or, when the per-element kernel wins, the per-element kernel for
+ * batches up to `batch` columns. candidates_us: host [6] or NULL (index 0 per-element,
+ * p = 1..5 the fastest variant of the tiled kernel with p ranges per SM, -1 where not
+ * applicable); tiled, ctas_per_sm, best_us, variant (-1 when the per-element kernel won):
+ * host or NULL. Results do not depend on the granularity (the same terms, summed in the
+ * same order); the tiled and per-element kernels agree to rounding. Allocates two vectors
+ * of N d^2 batch elements for the duration of the call. Synchronises s. */
 heom_status heom_autotune(heom_hier *h, int64_t batch, int prec, double *candidates_us,
-                          int *tiled, int *ctas_per_sm, double *best_us, heom_stream s);
+                          int *tiled, int *ctas_per_sm, double *best_us, int *variant,
+                          heom_stream s);
+
+/* Pin the configuration the autotuner would choose (the paper has no counterpart): the
+ * tiled kernel for every batch of 16 or more columns, at ctas_per_sm ADO ranges per SM
+ * (1..5) and FP32 variant `variant` (0..5, as listed for heom_autotune; FP64 ignores it). For
+ * reproducible timings and for tests of each variant. Results agree with every other
+ * configuration to rounding. Errors: HEOM_EINVAL for arguments out of range. */
+heom_status heom_set_tile_config(heom_hier *h, int ctas_per_sm, int variant);
 
 /* Electronic current into lead alpha (Methods, electronic current; e = 1):
  * <I_alpha> = Re( i sum_q s_q Tr[d^{-nu_q} rho_q] ) over the fermionic exponents q of the
@@ -437,6 +465,14 @@ heom_status heom_profile_read(int cls, int64_t *launches, double *device_ms, dou
 /* Bytes the library copied host -> device and device -> host while accounting was on
  * (table and parameter uploads, right-hand sides, convergence flags, results). */
 heom_status heom_profile_copies(int64_t *h2d_bytes, int64_t *d2h_bytes);
+
+/* Process-wide allocation counts since the library was loaded (always on, any pointer may
+ * be NULL): device_allocs = cudaMalloc calls the library made (tables, workspaces, test
+ * vectors; every device allocation of the library goes through one counted routine),
+ * device_bytes = their total size, workspace_takes = times a solver workspace was grown
+ * (taken from the workspace cache or newly allocated). */
+heom_status heom_profile_allocs(int64_t *device_allocs, int64_t *device_bytes,
+                                int64_t *workspace_takes);
 
 #ifdef __cplusplus
 }

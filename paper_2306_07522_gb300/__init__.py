@@ -22,7 +22,7 @@ if not os.path.exists(LIBRARY_PATH):
 _lib = C.CDLL(LIBRARY_PATH)
 
 # ------------------------------------------------------------------------- ABI types
-OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EBREAKDOWN, ENOTSUP = range(7)
+OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EBREAKDOWN, ENOTSUP, ETIMEOUT = range(8)
 BOSON_R, BOSON_I, BOSON_RI, FERMION = range(4)
 FP64, FP32, MIXED, SHIFTED = range(4)
 KERNEL_CLASSES = ("apply", "rk4", "krylov_apply_fp32", "krylov_apply_fp64", "krylov_vector",
@@ -30,7 +30,8 @@ KERNEL_CLASSES = ("apply", "rk4", "krylov_apply_fp32", "krylov_apply_fp64", "kry
 APPLY_CLASSES = ("apply", "rk4", "krylov_apply_fp32", "krylov_apply_fp64", "residual_fp64")
 KIND = {"R": BOSON_R, "I": BOSON_I, "RI": BOSON_RI, "F": FERMION}
 STATUS_NAMES = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA",
-                ENOCONV: "ENOCONV", EBREAKDOWN: "EBREAKDOWN", ENOTSUP: "ENOTSUP"}
+                ENOCONV: "ENOCONV", EBREAKDOWN: "EBREAKDOWN", ENOTSUP: "ENOTSUP",
+                ETIMEOUT: "ETIMEOUT"}
 
 
 class c64(C.Structure):
@@ -84,7 +85,8 @@ _sig = {
                               _P, _P],
     "heom_current": [_P, _P, C.c_int64, _P, C.c_int, _P, _P],
     "heom_psd": [_P, _P, _P, _P, C.c_int64, C.c_double, C.c_int, _P, _P, _P],
-    "heom_autotune": [_P, C.c_int64, C.c_int, _P, _P, _P, _P, _P],
+    "heom_autotune": [_P, C.c_int64, C.c_int, _P, _P, _P, _P, _P, _P],
+    "heom_set_tile_config": [_P, C.c_int, C.c_int],
     "heom_mlp_create": [C.c_int, _P, C.c_uint64, C.POINTER(_P)],
     "heom_mlp_info": [_P, _P, _P, _P],
     "heom_mlp_set_standardisation": [_P, _P, _P, _P, _P],
@@ -99,6 +101,8 @@ _sig = {
     "heom_profile_enable": [C.c_int],
     "heom_profile_read": [C.c_int, _P, _P, _P, _P],
     "heom_profile_copies": [_P, _P],
+    "heom_profile_allocs": [_P, _P, _P],
+    "heom_set_wait_limit": [C.c_int64],
 }
 EXPORTED = sorted(list(_sig) + ["heom_destroy", "heom_last_error", "heom_mlp_destroy"])
 for _name, _args in _sig.items():
@@ -194,6 +198,10 @@ class Hierarchy:
                                    C.byref(ns), C.byref(ne)), "heom_hier_info")
         self.n_ado, self.d, self.k_b, self.k_f = n_ado.value, d.value, kb.value, kf.value
         self.n_sets, self.n_entries = ns.value, ne.value
+        if not hasattr(self, "device"):
+            # the library builds a hierarchy on the device current at the call
+            import torch
+            self.device = torch.cuda.current_device() if torch.cuda.is_available() else None
 
     @property
     def handle(self):
@@ -320,13 +328,25 @@ def _prec_of(t) -> int:
 
 
 def _batch_of(h: Hierarchy, t) -> int:
-    if not t.is_cuda or not t.is_contiguous():
-        raise ValueError("ADO vectors must be contiguous CUDA tensors")
-    if t.dim() == 3:
-        return 1
-    if t.dim() == 4:
-        return t.shape[3]
-    raise ValueError("ADO vector shape must be (N, d, d) or (N, d, d, batch)")
+    """Batch width of an ADO vector of hierarchy h, after checking that its shape is
+    (N, d, d) or (N, d, d, batch) with h's N and d, that it is contiguous and that it lives on
+    h's device: the library indexes N d^2 batch elements from h's tables, so a tensor of any
+    other shape would be read and written out of bounds."""
+    if t.dim() not in (3, 4):
+        raise ValueError("ADO vector shape must be (N, d, d) or (N, d, d, batch)")
+    if tuple(t.shape[:3]) != (h.n_ado, h.d, h.d):
+        raise ValueError(f"ADO vector shape {tuple(t.shape)} does not match the hierarchy "
+                         f"(N, d, d) = ({h.n_ado}, {h.d}, {h.d})")
+    if t.dim() == 4 and t.shape[3] < 1:
+        raise ValueError("ADO vector batch must be >= 1")
+    if not t.is_contiguous():
+        raise ValueError("ADO vectors must be contiguous")
+    if not t.is_cuda:
+        raise ValueError("ADO vectors must be CUDA tensors")
+    dev = getattr(h, "device", None)
+    if dev is not None and t.device.index != dev:
+        raise ValueError(f"ADO vector on cuda:{t.device.index}, hierarchy on cuda:{dev}")
+    return 1 if t.dim() == 3 else t.shape[3]
 
 
 def apply(h: Hierarchy, x, y, stream=None):
@@ -382,18 +402,55 @@ def evolve_td(h: Hierarchy, ados, dt: float, n_steps: int, f, save_every: int = 
     return traj
 
 
+def _check_traj(h: Hierarchy, ados, B: int, n_steps: int, save_every: int, traj):
+    """A caller-owned snapshot buffer must hold n_steps // save_every + 1 blocks of d x d x B
+    elements of the ADO vector's dtype, contiguous, on its device: the library writes that many
+    elements and nothing checks the buffer on the device side."""
+    if traj is None:
+        if save_every:
+            raise ValueError("evolve_noalloc needs a caller-owned traj tensor when save_every > 0")
+        return
+    if not save_every:
+        raise ValueError("traj given with save_every = 0: no snapshot would be written")
+    if save_every < 0 or n_steps < 0:
+        raise ValueError("save_every and n_steps must be >= 0")
+    need = (n_steps // save_every + 1) * h.d * h.d * B
+    if traj.dtype != ados.dtype:
+        raise ValueError(f"traj dtype {traj.dtype} differs from the ADO vector's {ados.dtype}")
+    if traj.numel() < need:
+        raise ValueError(f"traj holds {traj.numel()} elements; {need} are written")
+    if not traj.is_contiguous():
+        raise ValueError("traj must be contiguous")
+    if traj.device != ados.device:
+        raise ValueError("traj must be on the ADO vector's device")
+
+
 def evolve_noalloc(h: Hierarchy, ados, dt: float, n_steps: int, save_every: int = 0,
                    traj=None, stream=None):
     """heom_evolve_noalloc: RK4 in place on ``ados`` with no allocation in the library; the
     optional snapshot buffer ``traj`` is the caller's (this wrapper allocates nothing either)."""
     prec = _prec_of(ados)
     B = _batch_of(h, ados)
-    if save_every and traj is None:
-        raise ValueError("evolve_noalloc needs a caller-owned traj tensor when save_every > 0")
+    _check_traj(h, ados, B, n_steps, save_every, traj)
     _check(_lib.heom_evolve_noalloc(h.handle, _dptr(ados), B, dt, n_steps, max(save_every, 1),
                                     _dptr(traj) if save_every else None, prec, _stream(stream)),
            "heom_evolve_noalloc")
     return traj
+
+
+def _need_c128(t, name: str):
+    import torch
+    if t.dtype != torch.complex128:
+        raise TypeError(f"{name} must be a complex128 tensor")
+
+
+def _check_sets(h: Hierarchy, ss, name: str = "ss"):
+    """An ADO vector with one column per parameter set of h (complex128)."""
+    _need_c128(ss, name)
+    cols = ss.shape[3] if ss.dim() == 4 else 1
+    if cols != h.n_sets:
+        raise ValueError(f"{name} must be (N, d, d) or (N, d, d, n_sets) with n_sets = {h.n_sets}")
+    _batch_of(h, ss)
 
 
 def _stats_list(arr):
@@ -405,6 +462,11 @@ def steady(h: Hierarchy, x_out, x0=None, tol: float = 1e-8, max_iter: int = 2000
            prec: int = MIXED, stream=None, raise_on_error: bool = True):
     """Stationary state into x_out (complex128). Returns (status, per-column stats)."""
     B = _batch_of(h, x_out)
+    _need_c128(x_out, "x_out")
+    if x0 is not None:
+        _need_c128(x0, "x0")
+        if tuple(x0.shape) != tuple(x_out.shape) or _batch_of(h, x0) != B:
+            raise ValueError("x0 must have the shape of x_out")
     stats = (SolveStats * B)()
     st = _lib.heom_steady(h.handle, _dptr(x0) if x0 is not None else None, _dptr(x_out), B, tol,
                           max_iter, prec, C.cast(stats, C.c_void_p), _stream(stream))
@@ -418,6 +480,7 @@ def spectrum(odd: Hierarchy, ss, op_d, omegas, tol: float = 1e-8, max_iter: int 
     """Density of states A(w) of mode op_d; returns (A, status, stats of x_+ then x_-).
     With a hierarchy holding several parameter sets (SHIFTED only), ss is (N, d, d, n_sets),
     A is (n_sets, n_omega) and the stats run set by set."""
+    _check_sets(odd, ss)
     op = _c64(op_d)
     om = np.ascontiguousarray(omegas, np.float64)
     A = np.zeros(len(om)) if odd.n_sets == 1 else np.zeros((odd.n_sets, len(om)))
@@ -435,6 +498,10 @@ def spectrum_batched(odds, sss, ops, omegas, tol: float = 1e-8, max_iter: int = 
     shapes on one grid. Returns (list of A per hierarchy, (n_sets, n_omega) or (n_omega,),
     status, stats concatenated in hierarchy order)."""
     n = len(odds)
+    if len(sss) != n or len(ops) != n:
+        raise ValueError("one stationary state and one mode operator per hierarchy")
+    for o, x in zip(odds, sss):
+        _check_sets(o, x)
     om = np.ascontiguousarray(omegas, np.float64)
     rows = [o.n_sets for o in odds]
     A = np.zeros((sum(rows), len(om)))
@@ -458,17 +525,23 @@ def spectrum_batched(odds, sss, ops, omegas, tol: float = 1e-8, max_iter: int = 
 def autotune(h: Hierarchy, batch: int, prec: int = FP32, stream=None) -> dict:
     """heom_autotune: time the apply's kernel choices for `batch` columns, keep the fastest."""
     cand = np.zeros(6)
-    t, p, best = C.c_int(), C.c_int(), C.c_double()
+    t, p, best, var = C.c_int(), C.c_int(), C.c_double(), C.c_int()
     _check(_lib.heom_autotune(h.handle, batch, prec, _ptr(cand), C.byref(t), C.byref(p),
-                              C.byref(best), _stream(stream)), "heom_autotune")
-    return {"tiled": bool(t.value), "ctas_per_sm": p.value, "best_us": best.value,
-            "candidates_us": cand.tolist()}
+                              C.byref(best), C.byref(var), _stream(stream)), "heom_autotune")
+    return {"tiled": bool(t.value), "ctas_per_sm": p.value, "variant": var.value,
+            "best_us": best.value, "candidates_us": cand.tolist()}
+
+
+def set_tile_config(h: Hierarchy, ctas_per_sm: int, variant: int):
+    """heom_set_tile_config: pin the tiled kernel's ranges per SM and FP32 variant."""
+    _check(_lib.heom_set_tile_config(h.handle, ctas_per_sm, variant), "heom_set_tile_config")
 
 
 def psd(even: Hierarchy, ss, op_a, omegas, tol: float = 1e-8, max_iter: int = 2000, stream=None,
         raise_on_error: bool = True):
     """Power spectral density S(w) of mode op_a; returns (S, status, stats). With several
     parameter sets, ss is (N, d, d, n_sets) and S is (n_sets, n_omega)."""
+    _check_sets(even, ss)
     op = _c64(op_a)
     om = np.ascontiguousarray(omegas, np.float64)
     S = np.zeros(len(om)) if even.n_sets == 1 else np.zeros((even.n_sets, len(om)))
@@ -484,6 +557,7 @@ def current(h: Hierarchy, x, baths, stream=None) -> np.ndarray:
     """Electronic current into the lead made of ``baths`` for stationary states x
     (N, d, d[, batch], complex128); one value per batch column."""
     B = _batch_of(h, x)
+    _need_c128(x, "x")
     idx = np.ascontiguousarray(baths, np.int32)
     out = np.zeros(B)
     _check(_lib.heom_current(h.handle, _dptr(x), B, _ptr(idx), len(idx), _ptr(out), _stream(stream)),
@@ -492,6 +566,12 @@ def current(h: Hierarchy, x, baths, stream=None) -> np.ndarray:
 
 
 # ------------------------------------------------------------------------- launch accounting
+def set_wait_limit(cycles: int = 0):
+    """heom_set_wait_limit: bound (SM clock cycles) of the persistent solvers' grid-barrier
+    waits; 0 restores the default."""
+    _check(_lib.heom_set_wait_limit(int(cycles)), "heom_set_wait_limit")
+
+
 def release_workspace_cache():
     """heom_release_workspace_cache: free the solver workspaces kept for reuse."""
     _check(_lib.heom_release_workspace_cache(), "heom_release_workspace_cache")
@@ -510,6 +590,14 @@ def profile_read() -> dict:
                "heom_profile_read")
         out[name] = dict(launches=n.value, ms=ms.value, units=u.value, bytes=by.value)
     return out
+
+
+def profile_allocs() -> dict:
+    """heom_profile_allocs: the library's device allocations (count, bytes) and workspace
+    grows since it was loaded."""
+    a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(_lib.heom_profile_allocs(C.byref(a), C.byref(b), C.byref(c)), "heom_profile_allocs")
+    return {"device_allocs": a.value, "device_bytes": b.value, "workspace_takes": c.value}
 
 
 def profile_copies():
@@ -589,7 +677,8 @@ class Mlp:
 def warm_start_features(h: "Hierarchy", x, n_features: int, stream=None):
     """Features (torch float32 [n_sets][n_features]) of states x (N, d, d[, n_sets])."""
     import torch
-    n_sets = x.shape[3] if x.dim() == 4 else 1
+    _need_c128(x, "x")
+    n_sets = _batch_of(h, x)
     f = torch.empty((n_sets, n_features), dtype=torch.float32, device=x.device)
     _check(_lib.heom_warm_start_features(h.handle, _dptr(x), n_sets, _dptr(f), n_features,
                                          _stream(stream)), "heom_warm_start_features")
@@ -598,7 +687,8 @@ def warm_start_features(h: "Hierarchy", x, n_features: int, stream=None):
 
 def warm_start(h: "Hierarchy", net: Mlp, params, x_out, stream=None):
     """x_out (N, d, d[, n_sets], complex128) = the ADO vector net predicts for params."""
-    n_sets = x_out.shape[3] if x_out.dim() == 4 else 1
+    _need_c128(x_out, "x_out")
+    n_sets = _batch_of(h, x_out)
     if params.shape[0] != n_sets:
         raise ValueError("params must have one row per column of x_out")
     _check(_lib.heom_warm_start(h.handle, net.handle, _dptr(params), n_sets, _dptr(x_out),

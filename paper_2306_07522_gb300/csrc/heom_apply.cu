@@ -58,7 +58,8 @@ __global__ void __launch_bounds__(256) k_apply(DevView<R> v, const cx<R> *__rest
 template <class R>
 cudaError_t launch_apply(const DevView<R> &v, const cx<R> *x, cx<R> *y, int64_t B,
                          const ApplyMods<R> &mods, cudaStream_t s) {
-    if (tile_ok(v, B)) {
+    // the tiled kernel reads and writes 16-byte vectors: both buffers must be 16-byte aligned
+    if (tile_ok(v, B) && (((uintptr_t)x | (uintptr_t)y) & 15) == 0) {
         TileArgs<R> a{};
         a.v = v;
         a.x = x;
@@ -100,7 +101,7 @@ extern "C" heom_status heom_apply(const heom_hier *h, const void *x, void *y, in
         heom::set_error("heom_apply: x and y overlap");
         return HEOM_EINVAL;
     }
-    HEOM_CUDA(cudaSetDevice(h->device));
+    HEOM_DEVICE(h->device);
     cudaError_t e;
     // accounted here, not in launch_apply: the solvers that call launch_apply account the
     // launch under their own kernel class
@@ -165,56 +166,66 @@ heom_status tune_time(heom_hier *h, const cx<R> *x, cx<R> *y, int64_t B, cudaStr
 }
 
 template <class R>
-heom_status autotune(heom_hier *h, int64_t B, double *cand, int *tiled, int *per_sm, double *best,
-                     cudaStream_t s) {
+heom_status autotune(heom_hier *h, int64_t B, double *cand, int *tiled, int *per_sm, int *variant,
+                     double *best, cudaStream_t s) {
     const int64_t total = h->N * h->d2 * B;
     DBuf buf;
     heom_status st = dalloc(buf, 2 * total * sizeof(cx<R>));
     if (st != HEOM_OK) return st;
     cx<R> *x = (cx<R> *)buf.p, *y = x + total;
     k_tune_fill<R><<<(unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16), 256, 0, s>>>(total, x);
-    const int per_sm0 = h->tile_per_sm;
+    const int per_sm0 = h->tile_per_sm, var0 = h->tile_var;
     const int64_t min_b0 = h->tile_min_b;
     // candidate 0: the per-element kernel (tiled kernel switched off)
     h->tile_min_b = INT64_MAX;
     double t0 = 0.0;
     st = tune_time<R>(h, x, y, B, s, &t0);
     cand[0] = t0;
-    int best_p = 0;
+    int best_p = 0, best_v = var0;
     double best_t = t0;
-    // candidates 1..5: the tiled kernel with 1..5 ADO ranges per SM
+    // candidates 1..5: the tiled kernel with 1..5 ADO ranges per SM, each with every FP32
+    // variant (FP64 has one); cand[p] keeps the fastest variant at p ranges per SM
     const bool tile_possible = B >= 16 && h->n_sets == 1 && !(sizeof(R) == 4 && (B & 1));
+    const int n_var = sizeof(R) == 4 ? kTileVariants : 1;
     for (int p = 1; p <= 5 && st == HEOM_OK; ++p) {
         cand[p] = -1.0;
         if (!tile_possible) continue;
         if ((st = set_tile_partition(h, p)) != HEOM_OK) break;
         h->tile_min_b = 16;
-        bool ok;
-        if constexpr (sizeof(R) == 8) ok = tile_ok(h->view64(), B);
-        else ok = tile_ok(h->view32(), B);
-        if (!ok) continue;  // ranges exceed the shared-memory budget
-        double t = 0.0;
-        if ((st = tune_time<R>(h, x, y, B, s, &t)) != HEOM_OK) break;
-        cand[p] = t;
-        if (t < best_t) { best_t = t; best_p = p; }
+        for (int var = 0; var < n_var && st == HEOM_OK; ++var) {
+            h->tile_var = var;
+            bool ok;
+            if constexpr (sizeof(R) == 8) ok = tile_ok(h->view64(), B);
+            else ok = tile_ok(h->view32(), B) && tile_var_of(h->view32(), B) == var;
+            if (!ok) continue;  // ranges exceed the shared-memory budget, or B too narrow
+            double t = 0.0;
+            if ((st = tune_time<R>(h, x, y, B, s, &t)) != HEOM_OK) break;
+            if (cand[p] < 0 || t < cand[p]) cand[p] = t;
+            if (t < best_t) { best_t = t; best_p = p; best_v = var; }
+        }
     }
     dfree(buf);
     if (st != HEOM_OK) {  // leave the configuration as it was
         set_tile_partition(h, per_sm0);
         h->tile_min_b = min_b0;
+        h->tile_var = var0;
         return st;
     }
-    // keep the winner: tiled with best_p ranges per SM, or the per-element kernel for batches
-    // up to this width (wider batches keep the tiled kernel at its default granularity)
+    // keep the winner: tiled with best_p ranges per SM and variant best_v, or the per-element
+    // kernel for batches up to this width (wider batches keep the tiled kernel at its default
+    // granularity)
     if (best_p > 0) {
         st = set_tile_partition(h, best_p);
         h->tile_min_b = 16;
+        if (sizeof(R) == 4) h->tile_var = best_v;
     } else {
-        st = set_tile_partition(h, per_sm0 > 0 ? per_sm0 : 5);
+        st = set_tile_partition(h, per_sm0 > 0 ? per_sm0 : 2);
         h->tile_min_b = B + 1;
+        h->tile_var = var0;
     }
     *tiled = best_p > 0;
     *per_sm = best_p;
+    *variant = best_p > 0 ? (sizeof(R) == 4 ? best_v : 0) : -1;
     *best = best_t;
     return st;
 }
@@ -223,21 +234,38 @@ heom_status autotune(heom_hier *h, int64_t B, double *cand, int *tiled, int *per
 }  // namespace heom
 
 extern "C" heom_status heom_autotune(heom_hier *h, int64_t batch, int prec, double *candidates_us,
-                                     int *tiled, int *ctas_per_sm, double *best_us, heom_stream s) {
+                                     int *tiled, int *ctas_per_sm, double *best_us, int *variant,
+                                     heom_stream s) {
     if (!h || batch < 1 || batch > 65535LL * 32 || (prec != HEOM_FP64 && prec != HEOM_FP32)) {
         heom::set_error("heom_autotune: need a hierarchy, 1 <= batch <= 2097120, prec FP64 or FP32");
         return HEOM_EINVAL;
     }
-    HEOM_CUDA(cudaSetDevice(h->device));
+    HEOM_DEVICE(h->device);
     double cand[6], best = 0.0;
-    int t = 0, p = 0;
+    int t = 0, p = 0, var = -1;
     const heom_status st = prec == HEOM_FP64
-                               ? heom::autotune<double>(h, batch, cand, &t, &p, &best, (cudaStream_t)s)
-                               : heom::autotune<float>(h, batch, cand, &t, &p, &best, (cudaStream_t)s);
+                               ? heom::autotune<double>(h, batch, cand, &t, &p, &var, &best, (cudaStream_t)s)
+                               : heom::autotune<float>(h, batch, cand, &t, &p, &var, &best, (cudaStream_t)s);
     if (st != HEOM_OK) return st;
     if (candidates_us) for (int i = 0; i < 6; ++i) candidates_us[i] = cand[i];
     if (tiled) *tiled = t;
     if (ctas_per_sm) *ctas_per_sm = p;
     if (best_us) *best_us = best;
+    if (variant) *variant = var;
+    return HEOM_OK;
+}
+
+extern "C" heom_status heom_set_tile_config(heom_hier *h, int ctas_per_sm, int variant) {
+    if (!h || ctas_per_sm < 1 || ctas_per_sm > 5 || variant < 0 ||
+        variant >= heom::kTileVariants) {
+        heom::set_error("heom_set_tile_config: need a hierarchy, 1 <= ctas_per_sm <= 5 and "
+                        "0 <= variant < %d", heom::kTileVariants);
+        return HEOM_EINVAL;
+    }
+    HEOM_DEVICE(h->device);
+    const heom_status st = heom::set_tile_partition(h, ctas_per_sm);
+    if (st != HEOM_OK) return st;
+    h->tile_var = variant;
+    h->tile_min_b = 16;
     return HEOM_OK;
 }

@@ -53,6 +53,7 @@ struct ArnoldiArgs {
     double *part;      // per CTA: dot partials [2][kArMaxSteps + 2][B] complex, norm [B], res max
     cx<double> *hred;  // reduced h of the two passes [2][kArMaxSteps + 2][B]
     GridBar *bar;
+    long long wait_cycles;  // bound of every grid-barrier wait (SM clock cycles)
     int *out;          // [0] steps done, [1] converged, [2] barrier failure
 };
 
@@ -231,9 +232,9 @@ __global__ void __launch_bounds__(kArThreads, 1) k_arnoldi(ArnoldiArgs a) {
         __syncthreads();
         // ---- 2. Gram-Schmidt pass 1 (+ |w|^2 as the dot of w with itself, slot j + 1)
         own_dots(a, W, j + 2, e0, nel, mypart);
-        if (!grid_barrier(a.bar, gen)) { status = 1; break; }
+        if (!grid_barrier(a.bar, gen, a.wait_cycles)) { status = 1; break; }
         slice_reduce(a, 0, j + 2);
-        if (!grid_barrier(a.bar, gen)) { status = 1; break; }
+        if (!grid_barrier(a.bar, gen, a.wait_cycles)) { status = 1; break; }
         for (int p = tid; p < (j + 2) * B; p += bd) {  // written by other CTAs: through L2
             const double2 hv = __ldcg(reinterpret_cast<const double2 *>(a.hred + p));
             const cx<double> h{hv.x, hv.y};
@@ -263,9 +264,9 @@ __global__ void __launch_bounds__(kArThreads, 1) k_arnoldi(ArnoldiArgs a) {
         for (int pass = 0; pass < 1 + need2; ++pass) {
             if (pass == 1) {
                 own_dots(a, W, j + 1, e0, nel, mypart + 2 * (kArMaxSteps + 2) * kArMaxB);
-                if (!grid_barrier(a.bar, gen)) { status = 1; break; }
+                if (!grid_barrier(a.bar, gen, a.wait_cycles)) { status = 1; break; }
                 slice_reduce(a, 1, j + 1);
-                if (!grid_barrier(a.bar, gen)) { status = 1; break; }
+                if (!grid_barrier(a.bar, gen, a.wait_cycles)) { status = 1; break; }
                 for (int p = tid; p < (j + 1) * B; p += bd) {
                     const double2 hv = __ldcg(reinterpret_cast<const double2 *>(
                         a.hred + (int64_t)(kArMaxSteps + 2) * kArMaxB + p));
@@ -326,7 +327,7 @@ __global__ void __launch_bounds__(kArThreads, 1) k_arnoldi(ArnoldiArgs a) {
                 if (lane == 0) mypart[4 * (kArMaxSteps + 2) * kArMaxB + warp] = sacc;
             }
         }
-        if (!grid_barrier(a.bar, gen)) { status = 1; break; }
+        if (!grid_barrier(a.bar, gen, a.wait_cycles)) { status = 1; break; }
         if (warp < B) {  // warp b adds column b's partials of all CTAs: lane-strided, fixed tree
             double sacc = 0.0;
             for (int gi = lane; gi < G; gi += 32)
@@ -430,7 +431,7 @@ __global__ void __launch_bounds__(kArThreads, 1) k_arnoldi(ArnoldiArgs a) {
             if (lane == 0) mypart[4 * (kArMaxSteps + 2) * kArMaxB + kArMaxB] = (double)mx;
         }
         steps = j + 1;
-        if (!grid_barrier(a.bar, gen)) { status = 1; break; }
+        if (!grid_barrier(a.bar, gen, a.wait_cycles)) { status = 1; break; }
         if (warp == 0) {  // largest residual estimate over all CTAs
             float mx = 0.f;
             for (int gi = lane; gi < G; gi += 32)
@@ -521,6 +522,7 @@ heom_status arnoldi_persistent(heom_hier *h, int64_t B, int mmax, int max_steps,
     a.hred = (cx<double> *)(base + part_bytes);
     a.bar = (GridBar *)(base + part_bytes + hred_bytes);
     a.out = (int *)(base + part_bytes + hred_bytes + 256);
+    a.wait_cycles = wait_limit_cycles();
     HEOM_CUDA(cudaMemsetAsync(a.bar, 0, 512, s));
     const size_t sm = arnoldi_smem(a.v, a.hcap);
     HEOM_CUDA(cudaFuncSetAttribute(k_arnoldi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -532,11 +534,13 @@ heom_status arnoldi_persistent(heom_hier *h, int64_t B, int mmax, int max_steps,
     int out[3] = {0, 0, 0};
     HEOM_CUDA(memcpy_counted(out, a.out, sizeof(out), cudaMemcpyDeviceToHost, s));
     HEOM_CUDA(cudaStreamSynchronize(s));
-    if (out[2]) {
-        set_error("persistent Arnoldi: a grid barrier wait ran out (CTAs not co-resident?)");
-        return HEOM_ECUDA;
-    }
     *steps = out[0];
+    if (out[2]) {  // every CTA has left the launch; the device stays usable
+        *converged = false;
+        set_error("persistent Arnoldi: a grid-barrier wait ran out after %lld cycles",
+                  (long long)a.wait_cycles);
+        return HEOM_ETIMEOUT;
+    }
     *converged = out[1] != 0;
     // launch accounting: one apply of B columns per step
     prof_add(HEOM_KC_KRYLOV_APPLY64, (double)out[0] * h->N * B, (double)out[0] * 2.0 * a.L * 16.0);

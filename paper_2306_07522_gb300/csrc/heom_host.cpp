@@ -14,6 +14,7 @@
 #include <cstring>
 #include <algorithm>
 #include <map>
+#include <atomic>
 #include <mutex>
 #include <new>
 
@@ -42,6 +43,15 @@ heom_status cuda_fail(cudaError_t e, const char *what) {
     return HEOM_ECUDA;
 }
 
+// Process-wide counts for heom_profile_allocs: device allocations made, workspace buffers
+// taken (from the cache or newly allocated).
+std::atomic<int64_t> g_dev_allocs{0}, g_dev_alloc_bytes{0}, g_ws_takes{0};
+
+// Bound, in SM clock cycles, of every device-side wait (heom_set_wait_limit).
+constexpr long long kDefaultWaitCycles = 4000000000LL;
+std::atomic<long long> g_wait_cycles{kDefaultWaitCycles};
+long long wait_limit_cycles() { return g_wait_cycles.load(); }
+
 heom_status dalloc(DBuf &b, size_t bytes) {
     dfree(b);
     if (bytes == 0) bytes = 16;
@@ -52,6 +62,8 @@ heom_status dalloc(DBuf &b, size_t bytes) {
         return e == cudaErrorMemoryAllocation ? HEOM_ENOMEM : HEOM_ECUDA;
     }
     b.bytes = bytes;
+    g_dev_allocs.fetch_add(1);
+    g_dev_alloc_bytes.fetch_add((int64_t)bytes);
     return HEOM_OK;
 }
 
@@ -119,6 +131,7 @@ void ws_release(DBuf &b, int device) {
 
 heom_status ensure_ws(DBuf &b, size_t bytes) {
     if (b.bytes >= bytes && b.p) return HEOM_OK;
+    g_ws_takes.fetch_add(1);
     int dev = 0;
     cudaGetDevice(&dev);
     if (b.p) ws_release(b, dev);
@@ -390,6 +403,7 @@ heom::DevView<double> heom_hier::view64() const {
     v.max_terms = max_terms; v.max_entries = max_entries;
     v.cta_ado = (const int32_t *)d_cta_ado.p; v.n_ranges = n_ranges; v.range_terms = range_terms;
     v.range_slots = range_slots; v.range_ados = range_ados; v.tile_min_b = tile_min_b;
+    v.tile_var = tile_var;
     v.pers_ado = (const int32_t *)d_pers_ado.p; v.pers_ranges = pers_ranges;
     v.pers_terms = pers_terms; v.pers_slots = pers_slots; v.pers_ados = pers_ados;
     return v;
@@ -414,6 +428,7 @@ heom::DevView<float> heom_hier::view32() const {
     v.max_terms = max_terms; v.max_entries = max_entries;
     v.cta_ado = (const int32_t *)d_cta_ado.p; v.n_ranges = n_ranges; v.range_terms = range_terms;
     v.range_slots = range_slots; v.range_ados = range_ados; v.tile_min_b = tile_min_b;
+    v.tile_var = tile_var;
     v.pers_ado = (const int32_t *)d_pers_ado.p; v.pers_ranges = pers_ranges;
     v.pers_terms = pers_terms; v.pers_slots = pers_slots; v.pers_ados = pers_ados;
     return v;
@@ -460,7 +475,8 @@ RangeCosts range_costs(const heom_hier *h) {
 // always apply to the real term and slot counts.
 bool partition_ranges(const heom_hier *h, const RangeCosts &rc, int64_t resident, int64_t cap_terms,
                       std::vector<int32_t> &rg, int64_t &rt, int64_t &rs, int64_t &rn,
-                      const std::vector<int64_t> *weight = nullptr, int64_t wtotal = 0) {
+                      const std::vector<int64_t> *weight = nullptr, int64_t wtotal = 0,
+                      bool nearest = false) {
     const int64_t total = weight ? wtotal : rc.total;
     int64_t target = std::max<int64_t>(1, (total + resident - 1) / resident);
     for (int attempt = 0; attempt < 64; ++attempt) {
@@ -468,7 +484,12 @@ bool partition_ranges(const heom_hier *h, const RangeCosts &rc, int64_t resident
         int64_t cur_t = 0, cur_s = 0, cur_n = 0, cur_w = 0;
         rt = rs = rn = 0;
         for (int64_t i = 0; i < h->N; ++i) {
-            const bool full = cur_n > 0 && (cur_w >= target || cur_t + rc.terms[i] > cap_terms ||
+            // a range closes once it reaches the target weight, or (nearest) once taking the
+            // next ADO would overshoot the target by more than half of that ADO's weight: ranges
+            // of a few heavy ADOs then stay near the target instead of near twice it
+            const int64_t wi = weight ? (*weight)[i] : rc.terms[i];
+            const bool reached = nearest ? cur_w + wi / 2 > target : cur_w >= target;
+            const bool full = cur_n > 0 && (reached || cur_t + rc.terms[i] > cap_terms ||
                                             cur_s + rc.slots[i] > heom::kRangeSlots ||
                                             cur_n >= heom::kRangeAdos);
             if (full) {
@@ -476,7 +497,7 @@ bool partition_ranges(const heom_hier *h, const RangeCosts &rc, int64_t resident
                 cur_t = cur_s = cur_n = cur_w = 0;
             }
             cur_t += rc.terms[i]; cur_s += rc.slots[i]; ++cur_n;
-            cur_w += weight ? (*weight)[i] : rc.terms[i];
+            cur_w += wi;
             rt = std::max(rt, cur_t); rs = std::max(rs, cur_s); rn = std::max(rn, cur_n);
         }
         rg.push_back((int32_t)h->N);
@@ -484,6 +505,21 @@ bool partition_ranges(const heom_hier *h, const RangeCosts &rc, int64_t resident
         target += target / 8 + 1;
     }
     return false;
+}
+
+// ADO ranges of the tiled kernel: balanced on the terms plus a per-item cost of the item's
+// own work (its first load, the accumulator set-up and the epilogue, about kTileItemWeight
+// terms), nearest-target closing.
+constexpr int64_t kTileItemWeight = 2;
+bool tile_partition(const heom_hier *h, const RangeCosts &rc, int64_t resident,
+                    std::vector<int32_t> &rg, int64_t &rt, int64_t &rs, int64_t &rn) {
+    std::vector<int64_t> w(h->N);
+    int64_t wt = 0;
+    for (int64_t i = 0; i < h->N; ++i) {
+        w[i] = rc.terms[i] + kTileItemWeight * h->d2;
+        wt += w[i];
+    }
+    return partition_ranges(h, rc, resident, heom::kRangeTerms, rg, rt, rs, rn, &w, wt, true);
 }
 
 // Most system-superoperator terms (all elements together) a hierarchy may carry.
@@ -633,7 +669,7 @@ heom_status upload_params(heom_hier *h, int n_sets, const heom_c64 *H, const heo
         h->max_entries = me;
     }
     // ADO ranges: contiguous, about equal term counts, each range's program and bookkeeping
-    // bounded for shared memory. Tiled kernel: tile_per_sm CTAs per SM (five unless the
+    // bounded for shared memory. Tiled kernel: tile_per_sm CTAs per SM (two unless the
     // autotuner chose otherwise), all resident at once. Cooperative persistent solvers: one
     // range per SM.
     std::vector<int32_t> ranges, pranges, arranges;
@@ -642,7 +678,7 @@ heom_status upload_params(heom_hier *h, int n_sets, const heom_c64 *H, const heo
         int n_sm = 152;
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, h->device);
         int64_t rt, rs, rn;
-        partition_ranges(h, rc, (int64_t)n_sm * h->tile_per_sm, heom::kRangeTerms, ranges, rt, rs, rn);
+        tile_partition(h, rc, (int64_t)n_sm * h->tile_per_sm, ranges, rt, rs, rn);
         h->n_ranges = (int)ranges.size() - 1;
         h->range_terms = (int)std::min<int64_t>(rt, INT32_MAX);
         h->range_slots = (int)std::min<int64_t>(rs, INT32_MAX);
@@ -1093,7 +1129,7 @@ extern "C" heom_status heom_set_params(heom_hier *h, int n_sets, const heom_c64 
         if (!finite(H[i])) { set_error("heom_set_params: non-finite H"); return HEOM_EINVAL; }
     for (size_t i = 0; i < (size_t)n_sets * h->K; ++i)
         if (!finite(coef[i]) || !finite(rate[i])) { set_error("heom_set_params: non-finite exponent"); return HEOM_EINVAL; }
-    HEOM_CUDA(cudaSetDevice(h->device));
+    HEOM_DEVICE(h->device);
     return upload_params(h, n_sets, H, coef, rate);
 }
 
@@ -1107,7 +1143,7 @@ extern "C" heom_status heom_set_lindblad(heom_hier *h, int n_ops, const heom_c64
         if (!finite(F[i])) { set_error("heom_set_lindblad: non-finite jump operator"); return HEOM_EINVAL; }
     for (int k = 0; k < n_ops; ++k)
         if (!std::isfinite(gamma[k])) { set_error("heom_set_lindblad: non-finite rate"); return HEOM_EINVAL; }
-    HEOM_CUDA(cudaSetDevice(h->device));
+    HEOM_DEVICE(h->device);
     std::vector<heom_c64> oldF, Hs = h->H0, cs = h->coef0, rs = h->rate0;
     std::vector<double> oldg;
     oldF.swap(h->lind_F);
@@ -1129,7 +1165,7 @@ extern "C" heom_status heom_set_drive(heom_hier *h, int n_drive, const heom_c64 
     }
     for (size_t i = 0; i < (size_t)n_drive * h->d2; ++i)
         if (!finite(Hk[i])) { set_error("heom_set_drive: non-finite drive operator"); return HEOM_EINVAL; }
-    HEOM_CUDA(cudaSetDevice(h->device));
+    HEOM_DEVICE(h->device);
     std::vector<heom_c64> old, Hs = h->H0, cs = h->coef0, rs = h->rate0;
     old.swap(h->drive);
     const int old_n = h->n_drive;
@@ -1203,7 +1239,8 @@ extern "C" heom_status heom_export_tables(const heom_hier *h, int32_t *row_ptr, 
 
 extern "C" void heom_destroy(heom_hier *h) {
     if (!h) return;
-    cudaSetDevice(h->device);
+    heom::DeviceScope scope;
+    scope.set(h->device);
     // the solver workspaces go to the process-wide cache (every solver has synchronised
     // its stream before returning, so no kernel still uses them)
     heom::ws_release(h->ws, h->device);
@@ -1300,13 +1337,13 @@ heom_status set_tile_partition(heom_hier *h, int per_sm) {
         set_error("tile partition: 1..5 CTAs per SM");
         return HEOM_EINVAL;
     }
-    HEOM_CUDA(cudaSetDevice(h->device));
+    HEOM_DEVICE(h->device);
     RangeCosts rc = range_costs(h);
     int n_sm = 152;
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, h->device);
     std::vector<int32_t> ranges;
     int64_t rt, rs, rn;
-    partition_ranges(h, rc, (int64_t)n_sm * per_sm, kRangeTerms, ranges, rt, rs, rn);
+    tile_partition(h, rc, (int64_t)n_sm * per_sm, ranges, rt, rs, rn);
     dfree(h->d_cta_ado);
     heom_status st = upload(h->d_cta_ado, ranges);
     if (st != HEOM_OK) return st;
@@ -1319,6 +1356,19 @@ heom_status set_tile_partition(heom_hier *h, int per_sm) {
     return HEOM_OK;
 }
 }  // namespace heom
+
+extern "C" heom_status heom_set_wait_limit(int64_t cycles) {
+    heom::g_wait_cycles.store(cycles > 0 ? (long long)cycles : heom::kDefaultWaitCycles);
+    return HEOM_OK;
+}
+
+extern "C" heom_status heom_profile_allocs(int64_t *device_allocs, int64_t *device_bytes,
+                                           int64_t *workspace_takes) {
+    if (device_allocs) *device_allocs = heom::g_dev_allocs.load();
+    if (device_bytes) *device_bytes = heom::g_dev_alloc_bytes.load();
+    if (workspace_takes) *workspace_takes = heom::g_ws_takes.load();
+    return HEOM_OK;
+}
 
 extern "C" heom_status heom_profile_enable(int on) {
     prof_drain();

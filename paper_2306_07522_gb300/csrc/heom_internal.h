@@ -105,6 +105,7 @@ struct DevView {
     const int32_t *cta_ado;   // [n_ranges + 1]
     int n_ranges;
     int64_t tile_min_b;       // smallest batch that takes the tiled kernel (autotuned, >= 16)
+    int tile_var;             // FP32 variant of the tiled kernel (kTileVariant, autotuned)
     int range_terms;          // largest program of one range (terms)
     int range_slots;          // largest sum over a range of d2 * (entries + 3)
     int range_ados;           // largest number of ADOs in a range
@@ -173,8 +174,9 @@ struct heom_hier {
     int max_terms = 0, max_entries = 0;
     heom::DBuf d_cta_ado, d_pers_ado;
     int n_ranges = 0, range_terms = 0, range_slots = 0, range_ados = 0;
-    int tile_per_sm = 5;        // tiled kernel: ADO ranges per SM (autotuned)
+    int tile_per_sm = 2;        // tiled kernel: ADO ranges per SM (autotuned)
     int64_t tile_min_b = 16;    // tiled kernel from this batch on (autotuned)
+    int tile_var = 0;           // FP32 tiled-kernel variant (autotuned)
     int pers_ranges = 0, pers_terms = 0, pers_slots = 0, pers_ados = 0;
     heom::DBuf d_ar_ado;        // ADO ranges of the persistent Arnoldi (elements weighted)
     int ar_ranges = 0, ar_terms = 0, ar_slots = 0, ar_ados = 0;
@@ -204,7 +206,36 @@ heom_status cuda_fail(cudaError_t e, const char *what);
         if (e__ != cudaSuccess) return heom::cuda_fail(e__, #call); \
     } while (0)
 
-heom_status dalloc(DBuf &b, size_t bytes);
+// Makes a device current for the scope of an entry point and gives the calling thread its
+// previous current device back when the scope ends, so a caller that drives several GPUs
+// keeps its own thread state.
+struct DeviceScope {
+    int prev = -1;
+    cudaError_t set(int device) {
+        cudaError_t e = cudaGetDevice(&prev);
+        if (e != cudaSuccess) {
+            prev = -1;
+            return e;
+        }
+        if (prev == device) {
+            prev = -1;
+            return cudaSuccess;
+        }
+        return cudaSetDevice(device);
+    }
+    DeviceScope() = default;
+    DeviceScope(const DeviceScope &) = delete;
+    DeviceScope &operator=(const DeviceScope &) = delete;
+    ~DeviceScope() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+#define HEOM_DEVICE(dev)              \
+    heom::DeviceScope device_scope__; \
+    HEOM_CUDA(device_scope__.set(dev))
+
+heom_status dalloc(DBuf &b, size_t bytes);  // the library's only cudaMalloc (counted)
+long long wait_limit_cycles();               // bound of device-side waits (heom_set_wait_limit)
 void dfree(DBuf &b);
 heom_status ensure_ws(DBuf &b, size_t bytes);  // grows b, from the workspace cache when it can
 void ws_release(DBuf &b, int device);           // hands b to the workspace cache

@@ -463,21 +463,21 @@ extern "C" heom_status heom_mlp_set_standardisation(heom_mlp *net, const float *
         nm[2 * in + i] = out_mean[i];
         nm[2 * in + o + i] = out_sd[i];
     }
-    HEOM_CUDA(cudaSetDevice(net->device));
+    HEOM_DEVICE(net->device);
     HEOM_CUDA(cudaMemcpy(net->norm.p, nm.data(), nm.size() * 4, cudaMemcpyHostToDevice));
     return HEOM_OK;
 }
 
 extern "C" heom_status heom_mlp_get_params(const heom_mlp *net, float *host_out) {
     if (!net || !host_out) { set_error("heom_mlp_get_params: null argument"); return HEOM_EINVAL; }
-    HEOM_CUDA(cudaSetDevice(net->device));
+    HEOM_DEVICE(net->device);
     HEOM_CUDA(cudaMemcpy(host_out, net->params.p, net->n_params * 4, cudaMemcpyDeviceToHost));
     return HEOM_OK;
 }
 
 extern "C" heom_status heom_mlp_set_params(heom_mlp *net, const float *host_in) {
     if (!net || !host_in) { set_error("heom_mlp_set_params: null argument"); return HEOM_EINVAL; }
-    HEOM_CUDA(cudaSetDevice(net->device));
+    HEOM_DEVICE(net->device);
     HEOM_CUDA(cudaMemcpy(net->params.p, host_in, net->n_params * 4, cudaMemcpyHostToDevice));
     return HEOM_OK;
 }
@@ -487,7 +487,7 @@ extern "C" heom_status heom_mlp_forward(heom_mlp *net, const float *x, float *y,
         set_error("heom_mlp_forward: need a network, x, y and 1 <= batch <= 2^24");
         return HEOM_EINVAL;
     }
-    HEOM_CUDA(cudaSetDevice(net->device));
+    HEOM_DEVICE(net->device);
     cudaStream_t st = (cudaStream_t)s;
     heom::Work w;
     heom_status r = heom::work_for(net, batch, w);
@@ -510,7 +510,7 @@ extern "C" heom_status heom_mlp_gradients(heom_mlp *net, const float *x, const f
         set_error("heom_mlp_gradients: need a network, x, t and 1 <= batch <= 2^24");
         return HEOM_EINVAL;
     }
-    HEOM_CUDA(cudaSetDevice(net->device));
+    HEOM_DEVICE(net->device);
     cudaStream_t st = (cudaStream_t)s;
     heom::Work w;
     heom_status r = heom::work_for(net, batch, w);
@@ -595,7 +595,7 @@ extern "C" heom_status heom_warm_start_features(const heom_hier *h, const void *
         set_error("heom_warm_start_features: need a hierarchy, x, f and n_sets >= 1");
         return HEOM_EINVAL;
     }
-    HEOM_CUDA(cudaSetDevice(h->device));
+    HEOM_DEVICE(h->device);
     return feature_call(h, const_cast<void *>(x), f, n_sets, n_features, 0, (cudaStream_t)s,
                         "heom_warm_start_features");
 }
@@ -606,7 +606,7 @@ extern "C" heom_status heom_warm_start(const heom_hier *h, heom_mlp *net, const 
         set_error("heom_warm_start: need a hierarchy, a network, params, x_out and n_sets >= 1");
         return HEOM_EINVAL;
     }
-    HEOM_CUDA(cudaSetDevice(h->device));
+    HEOM_DEVICE(h->device);
     cudaStream_t st = (cudaStream_t)s;
     const int nf = net->width[net->n_layers];
     heom::DBuf y;

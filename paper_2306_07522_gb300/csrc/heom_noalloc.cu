@@ -7,11 +7,15 @@
 // allocates its three RK4 stage buffers in the hierarchy's workspace on first use; this
 // variant takes them from a fixed static device array instead, so it never allocates.
 //
-// The array lives in this file. Every GPU that loads the library holds it until the
-// process exits. Host code cannot use the array's name as a device address (on the host it
-// names a host-side stand-in), so the device address is looked up with
-// cudaGetSymbolAddress once per device, with that device current, on the first call made
-// on that device.
+// The array lives in this file, which holds no kernel. Host code cannot use the array's name
+// as a device address (on the host it names a host-side stand-in), so the device address is
+// looked up with cudaGetSymbolAddress once per device, with that device current, on the
+// first call made on that device. Under the CUDA runtime's lazy module loading (the default
+// since CUDA 12.2) that lookup is what loads this file's module, so the CUDA runtime reserves
+// the 16 MiB on a device at the first call there, not when the library is loaded; from then
+// on the device holds it until the process exits. Callers make one call with n_steps = 0 at
+// start-up, before the other allocator fills the device and before any stream capture; a
+// lookup that fails for want of memory returns HEOM_ENOMEM.
 #include <cmath>
 #include <mutex>
 
@@ -39,6 +43,14 @@ heom_status scratch_address(int device, void **out) {
     if (!g_scratch_addr[device]) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e == cudaErrorMemoryAllocation) {
+            cudaGetLastError();
+            set_error("heom_evolve_noalloc: the CUDA runtime could not reserve the %zu-byte "
+                      "static scratch on device %d (its first call there loads it); make one "
+                      "call with n_steps = 0 at start-up, before device memory fills",
+                      kNoAllocScratchBytes, device);
+            return HEOM_ENOMEM;
+        }
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
         g_scratch_addr[device] = p;
     }
@@ -59,16 +71,19 @@ heom_status evolve_static(heom_hier *h, cx<R> *y, int64_t B, double dt, int64_t 
     // and stage 2 writes z_b before stage 3 reads it.
     cx<R> *za = (cx<R> *)scratch, *zb = za + L, *acc = za + 2 * L;
     const size_t blk = (size_t)h->d2 * B * sizeof(cx<R>);
+    const double u = (double)h->N * B, pass = (double)L * sizeof(cx<R>);
     int64_t saved = 0;
-    if (traj) HEOM_CUDA(cudaMemcpyAsync(traj, y, blk, cudaMemcpyDeviceToDevice, s));
+    if (traj) HEOM_CUDA(memcpy_counted(traj, y, blk, cudaMemcpyDeviceToDevice, s));
     for (int64_t step = 1; step <= n_steps; ++step) {
-        HEOM_CUDA(launch_rk4_stage<R>(v, y, za, y, acc, B, (R)dt, 1, s));
-        HEOM_CUDA(launch_rk4_stage<R>(v, za, zb, y, acc, B, (R)dt, 2, s));
-        HEOM_CUDA(launch_rk4_stage<R>(v, zb, za, y, acc, B, (R)dt, 3, s));
-        HEOM_CUDA(launch_rk4_stage<R>(v, za, zb, y, acc, B, (R)dt, 4, s));
+        // accounted like heom_evolve's stages: stage 1 streams 3 vector passes, 2 and 3 five,
+        // 4 four
+        { Prof pr(HEOM_KC_RK4, s, u, 3.0 * pass); HEOM_CUDA(launch_rk4_stage<R>(v, y, za, y, acc, B, (R)dt, 1, s)); }
+        { Prof pr(HEOM_KC_RK4, s, u, 5.0 * pass); HEOM_CUDA(launch_rk4_stage<R>(v, za, zb, y, acc, B, (R)dt, 2, s)); }
+        { Prof pr(HEOM_KC_RK4, s, u, 5.0 * pass); HEOM_CUDA(launch_rk4_stage<R>(v, zb, za, y, acc, B, (R)dt, 3, s)); }
+        { Prof pr(HEOM_KC_RK4, s, u, 4.0 * pass); HEOM_CUDA(launch_rk4_stage<R>(v, za, zb, y, acc, B, (R)dt, 4, s)); }
         if (traj && step % save_every == 0) {
             ++saved;
-            HEOM_CUDA(cudaMemcpyAsync((char *)traj + saved * blk, y, blk, cudaMemcpyDeviceToDevice, s));
+            HEOM_CUDA(memcpy_counted((char *)traj + saved * blk, y, blk, cudaMemcpyDeviceToDevice, s));
         }
     }
     HEOM_CUDA(cudaStreamSynchronize(s));
@@ -97,7 +112,7 @@ extern "C" heom_status heom_evolve_noalloc(heom_hier *h, void *ados, int64_t bat
                   (long long)(h->N * h->d2 * batch), need, kNoAllocScratchBytes);
         return HEOM_EINVAL;
     }
-    HEOM_CUDA(cudaSetDevice(h->device));
+    HEOM_DEVICE(h->device);
     void *scratch = nullptr;
     heom_status st = scratch_address(h->device, &scratch);
     if (st != HEOM_OK) return st;

@@ -37,6 +37,7 @@ struct PersistArgs {
     float4 *phf, *shf;  // FP64 solve: float-float copies of ph and sh (the apply operands)
     double *part;  // [kSlots][G][4]
     GridBar *bar;
+    long long wait_cycles;  // bound of every grid-barrier wait (SM clock cycles)
     double tol;
     int max_iter, stall_iters;
     PersistOut *out;
@@ -116,7 +117,8 @@ __device__ __forceinline__ cx<double> prog_apply_ff(const ProgSmem<double> &ps, 
 // they run the FP64 shuffle trees.
 template <int NV>
 __device__ __forceinline__ bool grid_sum(double (&val)[NV], double *part, int slot, double *s_red,
-                                         double *s_tot, GridBar *bar, unsigned &gen, int nw) {
+                                         double *s_tot, GridBar *bar, unsigned &gen, int nw,
+                                         long long limit) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (warp < nw) {
 #pragma unroll
@@ -133,7 +135,7 @@ __device__ __forceinline__ bool grid_sum(double (&val)[NV], double *part, int sl
         for (int w = 0; w < nw; ++w) x += s_red[w * 4 + threadIdx.x];
         part[((size_t)slot * gridDim.x + blockIdx.x) * 4 + threadIdx.x] = x;
     }
-    if (!grid_barrier(bar, gen)) return false;
+    if (!grid_barrier(bar, gen, limit)) return false;
     if (warp < NV) {
         // written by the other CTAs since this CTA last read the slot: through L2, so that
         // no line of an earlier iteration cached in L1 is reused
@@ -230,11 +232,11 @@ __global__ void __launch_bounds__(kPersThreads) k_persist_bicg(PersistArgs<R> a)
         for (int t = threadIdx.x; t < ps.item[items]; t += blockDim.x) cf[t] = ff_split(ps.coef[t]);
         __syncthreads();
     }
-    const bool started = grid_sum<2>(val2, a.part, 0, s_red, s_tot, a.bar, gen, nw_act);
+    const bool started = grid_sum<2>(val2, a.part, 0, s_red, s_tot, a.bar, gen, nw_act, a.wait_cycles);
     double nr = val2[0];
     const double bn = val2[1], tol2 = a.tol * a.tol;
     cx<double> rho{nr, 0.0}, rho_old{1.0, 0.0}, alpha{1.0, 0.0}, omega{1.0, 0.0};
-    int status = !started ? HEOM_ECUDA : (nr <= tol2 * bn) ? 0 : -1, it_done = 0;
+    int status = !started ? HEOM_ETIMEOUT : (nr <= tol2 * bn) ? 0 : -1, it_done = 0;
     double best = nr, rhn = nr;  // rhn = ||rh||^2
     int best_it = 0;
     for (int iter = 1; status < 0 && iter <= a.max_iter; ++iter) {
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(kPersThreads) k_persist_bicg(PersistArgs<R> a)
             a.ph[i] = phi;
             if constexpr (sizeof(R) == 8) a.phf[i] = ff_split(phi);
         }
-        if (!grid_barrier(a.bar, gen)) { status = HEOM_ECUDA; break; }
+        if (!grid_barrier(a.bar, gen, a.wait_cycles)) { status = HEOM_ETIMEOUT; break; }
         // ---- v = A ph, (rh, v)
         double d1[2] = {0.0, 0.0};
         for (int it = threadIdx.x; it < items; it += blockDim.x) {
@@ -280,7 +282,7 @@ __global__ void __launch_bounds__(kPersThreads) k_persist_bicg(PersistArgs<R> a)
             d1[0] += wd.re * yd.re + wd.im * yd.im;
             d1[1] += wd.re * yd.im - wd.im * yd.re;
         }
-        if (!grid_sum<2>(d1, a.part, 1, s_red, s_tot, a.bar, gen, nw_act)) { status = HEOM_ECUDA; break; }
+        if (!grid_sum<2>(d1, a.part, 1, s_red, s_tot, a.bar, gen, nw_act, a.wait_cycles)) { status = HEOM_ETIMEOUT; break; }
         const cx<double> rv{d1[0], d1[1]};
         if (norm2(rv) == 0.0) { status = HEOM_EBREAKDOWN; it_done = iter; break; }
         if (threadIdx.x == 0) {
@@ -300,7 +302,7 @@ __global__ void __launch_bounds__(kPersThreads) k_persist_bicg(PersistArgs<R> a)
             a.sh[i] = shi;
             if constexpr (sizeof(R) == 8) a.shf[i] = ff_split(shi);
         }
-        if (!grid_barrier(a.bar, gen)) { status = HEOM_ECUDA; break; }
+        if (!grid_barrier(a.bar, gen, a.wait_cycles)) { status = HEOM_ETIMEOUT; break; }
         // ---- t = A sh, (t, s), (t, t)
         double d2v[3] = {0.0, 0.0, 0.0};
         for (int it = threadIdx.x; it < items; it += blockDim.x) {
@@ -314,7 +316,7 @@ __global__ void __launch_bounds__(kPersThreads) k_persist_bicg(PersistArgs<R> a)
             d2v[1] += yd.re * wd.im - yd.im * wd.re;
             d2v[2] += yd.re * yd.re + yd.im * yd.im;
         }
-        if (!grid_sum<3>(d2v, a.part, 2, s_red, s_tot, a.bar, gen, nw_act)) { status = HEOM_ECUDA; break; }
+        if (!grid_sum<3>(d2v, a.part, 2, s_red, s_tot, a.bar, gen, nw_act, a.wait_cycles)) { status = HEOM_ETIMEOUT; break; }
         if (threadIdx.x == 0) {
             const double it2 = d2v[2] == 0.0 ? 0.0 : nr_rcp(d2v[2]);
             s_sc[5] = d2v[0] * it2;
@@ -336,7 +338,7 @@ __global__ void __launch_bounds__(kPersThreads) k_persist_bicg(PersistArgs<R> a)
             d3[1] += hd.re * rd.im - hd.im * rd.re;
             d3[2] += rd.re * rd.re + rd.im * rd.im;
         }
-        if (!grid_sum<3>(d3, a.part, 3, s_red, s_tot, a.bar, gen, nw_act)) { status = HEOM_ECUDA; break; }
+        if (!grid_sum<3>(d3, a.part, 3, s_red, s_tot, a.bar, gen, nw_act, a.wait_cycles)) { status = HEOM_ETIMEOUT; break; }
         rho_old = rho;
         rho = cx<double>{d3[0], d3[1]};
         nr = d3[2];
@@ -413,6 +415,7 @@ heom_status bicgstab_persistent(heom_hier *h, const cx<R> *b, cx<R> *x, bool x_z
     a.tol = tol;
     a.max_iter = max_iter;
     a.stall_iters = stall_iters;
+    a.wait_cycles = wait_limit_cycles();
     if (x_zero) HEOM_CUDA(cudaMemsetAsync(x, 0, rows * sizeof(cx<R>), s));
     const size_t sm = persist_smem(v);
     HEOM_CUDA(cudaFuncSetAttribute(k_persist_bicg<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -425,13 +428,12 @@ heom_status bicgstab_persistent(heom_hier *h, const cx<R> *b, cx<R> *x, bool x_z
     PersistOut o{};
     HEOM_CUDA(memcpy_counted(&o, a.out, sizeof(o), cudaMemcpyDeviceToHost, s));
     HEOM_CUDA(cudaStreamSynchronize(s));
-    if (o.status == HEOM_ECUDA) {
-        set_error("persistent BiCGStab: a grid barrier wait ran out (CTAs not co-resident?)");
-        return HEOM_ECUDA;
-    }
     *iters = o.iterations;
     *status = o.status;
     *rel_res = o.bn > 0 ? std::sqrt(o.nr / o.bn) : 0.0;
+    if (o.status == HEOM_ETIMEOUT)  // every CTA has left; the caller reports the column
+        set_error("persistent BiCGStab: a grid-barrier wait ran out after %lld cycles",
+                  (long long)a.wait_cycles);
     // launch accounting: two applies per iteration, ADO-applies as units
     prof_add(sizeof(R) == 4 ? HEOM_KC_KRYLOV_APPLY32 : HEOM_KC_KRYLOV_APPLY64,
              2.0 * o.iterations * (double)h->N, 2.0 * o.iterations * 3.0 * (double)rows * sizeof(cx<R>));

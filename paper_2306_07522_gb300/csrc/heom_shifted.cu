@@ -656,11 +656,14 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
     bool done = false;
     if (pers) {
         // the whole solve (up to its shared-memory limit of steps) in one cooperative launch
-        int steps = 0;
+        int psteps = 0;
         heom_status pst = arnoldi_persistent(h, B, mmax, mp, Vf, V, Hb, S, dsh, dco, rot_c, rot_s, rdiag, g,
-                                             rot_cf, rot_sf, beta, dres, tol, &steps, &done, s);
-        if (pst != HEOM_OK) return pst;
-        m = j_done = steps;
+                                             rot_cf, rot_sf, beta, dres, tol, &psteps, &done, s);
+        if (pst != HEOM_OK) {
+            *steps = psteps;
+            return pst;
+        }
+        m = j_done = psteps;
     }
     for (int j = m; j < mmax && !done; ++j) {
         const cx<double> *vj = V + (int64_t)j * L;

@@ -952,6 +952,13 @@ heom_status refine_solve(heom_hier *h, const cx<double> *b64, cx<double> *x64, i
         for (int64_t b = 0; b < B; ++b) {
             if (!active[b]) continue;
             res.iters[b] += o.iters[b];
+            if (o.status[b] == HEOM_ETIMEOUT) {  // a device wait ran out: keep x64, stop
+                hs[b].active = 0;
+                skip_any = true;
+                res.status[b] = HEOM_ETIMEOUT;
+                active[b] = 0;
+                continue;
+            }
             if (o.status[b] == HEOM_EBREAKDOWN) {  // keep x64; retry from it next sweep
                 hs[b].active = 0;
                 skip_any = true;
@@ -1137,7 +1144,7 @@ extern "C" heom_status heom_evolve(heom_hier *h, void *ados, int64_t batch, doub
                   "n_steps >= 0, save_every >= 1 with a trajectory, prec FP64 or FP32");
         return HEOM_EINVAL;
     }
-    HEOM_CUDA(cudaSetDevice(h->device));
+    HEOM_DEVICE(h->device);
     if (prec == HEOM_FP64)
         return evolve_impl<double>(h, (cx<double> *)ados, batch, dt, n_steps, save_every,
                                    (cx<double> *)rho_traj, nullptr, (cudaStream_t)s);
@@ -1159,7 +1166,7 @@ extern "C" heom_status heom_evolve_td(heom_hier *h, void *ados, int64_t batch, d
     if (h->n_drive > 0)
         for (int64_t i = 0; i < (int64_t)h->n_drive * (2 * n_steps + 1); ++i)
             if (!std::isfinite(f[i])) { set_error("heom_evolve_td: non-finite drive value"); return HEOM_EINVAL; }
-    HEOM_CUDA(cudaSetDevice(h->device));
+    HEOM_DEVICE(h->device);
     if (prec == HEOM_FP64)
         return evolve_impl<double>(h, (cx<double> *)ados, batch, dt, n_steps, save_every,
                                    (cx<double> *)rho_traj, f, (cudaStream_t)s);
@@ -1186,7 +1193,7 @@ extern "C" heom_status heom_steady(heom_hier *h, const void *x0, void *x_out, in
                   "n_sets), tol > 0, max_iter >= 1, prec FP64 or MIXED");
         return HEOM_EINVAL;
     }
-    HEOM_CUDA(cudaSetDevice(h->device));
+    HEOM_DEVICE(h->device);
     cudaStream_t st = (cudaStream_t)s;
     const int64_t rows = h->N * h->d2, L = rows * batch;
     // the right-hand side e_(0,(0,0)) lives behind the solver workspace in ws_small's sibling
@@ -1238,7 +1245,8 @@ extern "C" heom_status heom_steady(heom_hier *h, const void *x0, void *x_out, in
     dfree(tmp);
     heom_status ret = HEOM_OK;
     for (int64_t b = 0; b < batch; ++b) {
-        r.res[b] = std::sqrt(hn[2 * b] / hn[2 * b + 1]);
+        // r_ss = ||M x|| / ||x||; a zero iterate (a solve that never started) has none
+        r.res[b] = hn[2 * b + 1] > 0.0 ? std::sqrt(hn[2 * b] / hn[2 * b + 1]) : INFINITY;
         if (r.status[b] == HEOM_OK && !(r.res[b] <= tol)) r.status[b] = HEOM_ENOCONV;
         if (r.status[b] != HEOM_OK && ret == HEOM_OK) ret = (heom_status)r.status[b];
     }
@@ -1288,6 +1296,12 @@ static heom_status spectrum_shifted(heom_hier *odd, const void *ss_ados, const h
     stt = shifted_gmres(odd, b64, B, shift, col_of, 0.5 * tol, std::max(1, std::min(max_iter, 2000)),
                         x0, res, &steps, st);
     dfree(buf);
+    if (stt == HEOM_ETIMEOUT) {  // a device wait ran out: no solution, every frequency flagged
+        for (int64_t k = 0; k < ns * n_omega; ++k) A_out[k] = NAN;
+        if (stats)
+            for (int64_t k = 0; k < S; ++k) stats[k] = heom_solve_stats{steps, 0, NAN, HEOM_ETIMEOUT};
+        return stt;
+    }
     if (stt != HEOM_OK) return stt;
     heom_status ret = HEOM_OK;
     const int d2 = d * d;
@@ -1339,7 +1353,7 @@ extern "C" heom_status heom_psd(heom_hier *even, const void *ss_ados, const heom
                   "tol > 0 and max_iter >= 1");
         return HEOM_EINVAL;
     }
-    HEOM_CUDA(cudaSetDevice(even->device));
+    HEOM_DEVICE(even->device);
     cudaStream_t st = (cudaStream_t)s;
     const int d = even->d, d2 = d * d;
     const int64_t ns = even->n_sets, B = ns, rows = even->N * even->d2, L = rows * B;
@@ -1364,6 +1378,13 @@ extern "C" heom_status heom_psd(heom_hier *even, const void *ss_ados, const heom
     stt = shifted_gmres(even, b64, B, shift, col_of, 0.5 * tol, std::max(1, std::min(max_iter, 2000)), x0,
                         res, &steps, st);
     dfree(buf);
+    if (stt == HEOM_ETIMEOUT) {  // a device wait ran out: no solution, every frequency flagged
+        for (int64_t k = 0; k < S; ++k) {
+            S_out[k] = NAN;
+            if (stats) stats[k] = heom_solve_stats{steps, 0, NAN, HEOM_ETIMEOUT};
+        }
+        return stt;
+    }
     if (stt != HEOM_OK) return stt;
     heom_status ret = HEOM_OK;
     for (int64_t k = 0; k < S; ++k) {
@@ -1425,7 +1446,7 @@ extern "C" heom_status heom_spectrum(heom_hier *odd, const void *ss_ados, const 
                   "prec FP64, MIXED or SHIFTED");
         return HEOM_EINVAL;
     }
-    HEOM_CUDA(cudaSetDevice(odd->device));
+    HEOM_DEVICE(odd->device);
     cudaStream_t st = (cudaStream_t)s;
     const int d = odd->d;
     if (prec == HEOM_SHIFTED) return spectrum_shifted(odd, ss_ados, op_d, omega, n_omega, tol,
@@ -1548,7 +1569,7 @@ extern "C" heom_status heom_current(const heom_hier *h, const void *x, int64_t b
         set_error("heom_current: the baths hold no fermionic exponents");
         return HEOM_EINVAL;
     }
-    HEOM_CUDA(cudaSetDevice(h->device));
+    HEOM_DEVICE(h->device);
     cudaStream_t st = (cudaStream_t)s;
     const int nt = (int)ado.size();
     const size_t obytes = O.size() * sizeof(cx<double>), ooff = (obytes + (size_t)nt * 8 + 15) & ~size_t(15);

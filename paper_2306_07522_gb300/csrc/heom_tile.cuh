@@ -1,35 +1,32 @@
-// Tiled HEOM apply for batched columns (B >= 32): one CTA per (group of ADOs, chunk of up
-// to 8 x 32 x VC columns), one warp per 32 x VC-column slice of the chunk.
+// Tiled HEOM apply for batched columns (B >= 16): one CTA per range of ADOs, persistent over
+// the batch; one warp per 32 x VC-column slice of a column chunk.
 //
 // For each ADO n the CTA first writes the ADO's whole term program into shared memory:
 // for every output element e of the d x d block the list of (source element, complex
 // coefficient) pairs of Eq. HEOM -- the damping term, the system superoperator (commutator
-// with H plus any Lindblad terms), and the left and right products of every raising / lowering neighbour with its coupling operator,
-// coefficients already multiplied by the exponent factors and signs. Every warp then
-// streams its columns through that program: one broadcast shared-memory read, one 16-byte
-// coalesced load of VC complex values and 4*VC FMAs per term and lane. The warp-uniform
-// work (decoding neighbour entries, operator structure, coefficients) is done once per ADO
-// per CTA instead of once per lane and term.
+// with H plus any Lindblad terms), and the left and right products of every raising /
+// lowering neighbour with its coupling operator, coefficients already multiplied by the
+// exponent factors and signs. Every warp then streams its columns through that program. Per
+// term and lane: one broadcast shared-memory read of the term's record (coefficient and row
+// offset: FP32) or two (FP64), VC/2 16-byte coalesced loads (FP32, VC = 4 or 2 columns) or one
+// (FP64), and two packed f32x2 FMAs per column (FP32) or one complex FMA (FP64). The warp-uniform
+// work (decoding neighbour entries, operator structure, coefficients, row offsets) is done
+// once per ADO per CTA instead of once per lane and term.
 //
 // Program order per element: damping, system superoperator, then every neighbour entry (left
 // products before right products), then the trace row -- the order in which the
-// per-element kernel (apply_point) adds the same terms.
+// per-element kernel (apply_point) adds the same terms. The FP32 sweep accumulates the real
+// and imaginary parts of the coefficients in separate sums, so its rounding differs from the
+// per-element kernel's (both within FP32 accuracy of the exact apply).
 #pragma once
+
+#include <algorithm>
 
 #include "heom_kernels.cuh"
 
 namespace heom {
 
-template <class R> struct VecT;
-template <> struct VecT<float> {
-    static constexpr int VC = 2;   // complex values per lane (one float4)
-};
-template <> struct VecT<double> {
-    static constexpr int VC = 1;   // one double2
-};
-
 constexpr int kTileWarps = 8;
-constexpr int kBatch = 8;  // term loads in flight per lane
 
 // Epilogue modes of the tiled kernel
 enum TileMode {
@@ -264,158 +261,331 @@ __device__ void build_programs(const DevView<R> &v, ProgSmem<R> &ps, int n0, int
 
 }
 
-// Shared-memory footprint of one CTA (one ADO range) for a hierarchy view.
+// Variants of the FP32 tiled kernel. P: float4 loads per lane and term (VC = 2P columns per
+// lane; lane L reads columns 2L, 2L+1 of each 64-column half of its chunk, so every load
+// instruction of a warp covers 512 contiguous bytes); U: terms per item loaded into registers
+// together (their loads are in flight at once); KI: items (consecutive elements of one ADO,
+// of similar term counts) in flight per warp; minb: the CTAs per SM the register budget is
+// sized for. The kernel is bound by the latency of the neighbour gathers from L2, so what
+// matters is the loads a warp keeps in flight times the warps an SM holds; the autotuner
+// picks one variant per hierarchy. FP64 runs one (one double2 per lane, four terms, one
+// item): the FP64 pipe bounds it. (Measured and dropped: a per-warp cp.async ring 8 to 24
+// terms deep, with the terms of all the warp's items in one stream -- twice as slow: its
+// per-term bookkeeping made it issue-bound.)
+struct TileVariant {
+    int P, U, KI, minb;
+};
+constexpr int kTileVariants = 6;
+constexpr TileVariant kTileVariant[kTileVariants] = {
+    {1, 4, 1, 3}, {1, 4, 1, 4}, {1, 3, 1, 4}, {1, 2, 1, 5}, {1, 6, 1, 3}, {2, 4, 1, 2}};
+
+// Columns of one chunk (one warp-wide slice) of a variant.
 template <class R>
-__host__ __device__ inline size_t tile_smem_bytes(const DevView<R> &v) {
-    const size_t cw = 32 * VecT<R>::VC;
-    return kTileWarps * cw * 3 * sizeof(double) +  // per-warp dot partials
+inline int tile_cw(int var) {
+    return sizeof(R) == 8 ? 32 : 64 * kTileVariant[var].P;
+}
+
+// Whether an epilogue mode sums per-column dot products (and needs the per-warp partials).
+__host__ __device__ constexpr bool tile_mode_dots(int mode) {
+    return mode == TM_BICG_V || mode == TM_BICG_T || mode == TM_RESID || mode == TM_NORMS;
+}
+
+// Shared-memory footprint of one CTA (one ADO range): per-warp dot partials (dot modes only),
+// the FP32 broadcast coefficient records, the term programs.
+template <class R>
+__host__ __device__ inline size_t tile_smem_bytes(const DevView<R> &v, int cw, bool dots) {
+    const size_t rec = sizeof(R) == 4 ? 16 * (size_t)v.range_terms : 0;
+    return (dots ? kTileWarps * (size_t)cw * 3 * sizeof(double) : 0) + rec +
            prog_smem_bytes<R>(v.range_terms, v.range_slots, v.range_ados, v.d2);
+}
+template <class R>
+inline size_t tile_smem_bytes_var(const DevView<R> &v, int var) {  // the largest (dot modes)
+    return tile_smem_bytes(v, sizeof(R) == 8 ? 32 : 64 * kTileVariant[var].P, true);
+}
+
+// d = a * b + c on a pair of floats: one packed FP32 FMA (fma.rn.f32x2).
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
+// A = sum cr (re, im), Bq = sum ci (re, im) over a term with record (cr, ci, row offset, -)
+// and the two columns x = (re0, im0, re1, im1) of one float4.
+__device__ __forceinline__ void term_f32(float4 c, float4 x, float2 &A0, float2 &B0, float2 &A1,
+                                         float2 &B1) {
+    const float2 cr = make_float2(c.x, c.x), ci = make_float2(c.y, c.y);
+    const float2 x0 = make_float2(x.x, x.y), x1 = make_float2(x.z, x.w);
+    A0 = ffma2(cr, x0, A0);
+    B0 = ffma2(ci, x0, B0);
+    A1 = ffma2(cr, x1, A1);
+    B1 = ffma2(ci, x1, B1);
+}
+
+// Sum of the terms of KI items for the 2P columns of this lane (register path): item k's
+// terms are jb[k] .. jb[k] + len[k] - 1 (its damping term excluded), taken U at a time from
+// every item at once. Each term's record s_c4[j] = (cr, ci, row offset as int bits, 0) is one
+// 16-byte broadcast read. With x = (re, im) per column the lane keeps A = sum cr (re, im) and
+// Bq = sum ci (re, im) in packed pairs -- two f32x2 FMAs per term and column -- and forms
+// sum c x = (A.re - Bq.im, A.im + Bq.re) at the end. Terms past an item's end are predicated
+// off (no load, no arithmetic). pv[p]: pair p of this lane lies inside the batch (only the
+// last chunk has invalid pairs).
+template <int P, int U, int KI>
+__device__ __forceinline__ void tile_terms_f32(const float4 *__restrict__ s_c4,
+                                               const int32_t *__restrict__ s_off,
+                                               const cx<float> *__restrict__ Xb,
+                                               const int (&jb)[KI], const int (&len)[KI],
+                                               int maxlen, const bool (&pv)[P],
+                                               float2 (&A)[KI][2 * P], float2 (&Bq)[KI][2 * P]) {
+    for (int t = 0; t < maxlen; t += U) {
+        float4 cc[KI][U];
+        float4 xv[KI][U][P];
+#pragma unroll
+        for (int k = 0; k < KI; ++k)
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (t + u < len[k]) {
+                    cc[k][u] = s_c4[jb[k] + t + u];  // one shared-memory read per term
+                    const float4 *p = reinterpret_cast<const float4 *>(Xb + __float_as_int(cc[k][u].z));
+#pragma unroll
+                    for (int q = 0; q < P; ++q)
+                        xv[k][u][q] = pv[q] ? __ldg(p + 32 * q) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+#pragma unroll
+        for (int k = 0; k < KI; ++k)
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (t + u < len[k]) {
+#pragma unroll
+                    for (int q = 0; q < P; ++q)
+                        term_f32(cc[k][u], xv[k][u][q], A[k][2 * q], Bq[k][2 * q], A[k][2 * q + 1],
+                                 Bq[k][2 * q + 1]);
+                }
+    }
+}
+
+// FP64: complex FMAs (GB300 has no packed FP64 FMA; the FP64 pipe bounds this path).
+template <int U>
+__device__ __forceinline__ void tile_terms_f64(const cx<double> *__restrict__ s_coef,
+                                               const int32_t *__restrict__ s_off,
+                                               const cx<double> *__restrict__ Xb, int j0, int j1,
+                                               cx<double> &acc) {
+    for (int j = j0; j < j1; j += U) {
+        cx<double> cc[U], xv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (j + u < j1) {
+                cc[u] = s_coef[j + u];
+                const double2 t = __ldg(reinterpret_cast<const double2 *>(Xb + s_off[j + u]));
+                xv[u] = cx<double>{t.x, t.y};
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (j + u < j1) fma_to(acc, cc[u], xv[u]);
+    }
+}
+
+// The epilogue of one item: its output y (VC values of this lane) and own input xo, written
+// or folded into the solver's per-column sums according to MODE. rb: the item's row at the
+// chunk start; co(q): column offset of value q inside the chunk; pv: valid pairs.
+template <class R, int MODE, int VC, int NP, class CO>
+__device__ __forceinline__ void tile_epilogue(const TileArgs<R> &a, int64_t rb, const CO &co,
+                                              const bool (&pv)[NP], const cx<R> (&y)[VC],
+                                              const cx<R> (&xo)[VC], double (&dsum)[3][VC]) {
+    constexpr bool F32 = sizeof(R) == 4;
+    if constexpr (MODE == TM_STORE) {
+        if constexpr (F32) {
+#pragma unroll
+            for (int p = 0; p < NP; ++p)
+                if (pv[p])
+                    __stcs(reinterpret_cast<float4 *>(a.out + rb + co(2 * p)),
+                           make_float4(y[2 * p].re, y[2 * p].im, y[2 * p + 1].re, y[2 * p + 1].im));
+        } else {
+            __stcs(reinterpret_cast<double2 *>(a.out + rb + co(0)), make_double2(y[0].re, y[0].im));
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < VC; ++q) {
+            if (!pv[F32 ? q >> 1 : 0]) continue;
+            const int64_t i = rb + co(q);
+            const cx<R> yj = y[q];
+            if constexpr (MODE == TM_BICG_V) {
+                a.out[i] = yj;
+                const cx<double> yd = cast<double>(yj), wd = cast<double>(a.w[i]);
+                dsum[0][q] += wd.re * yd.re + wd.im * yd.im;
+                dsum[1][q] += wd.re * yd.im - wd.im * yd.re;
+            } else if constexpr (MODE == TM_BICG_T) {
+                a.out[i] = yj;
+                const cx<double> yd = cast<double>(yj), wd = cast<double>(a.w[i]);
+                dsum[0][q] += yd.re * wd.re + yd.im * wd.im;
+                dsum[1][q] += yd.re * wd.im - yd.im * wd.re;
+                dsum[2][q] += yd.re * yd.re + yd.im * yd.im;
+            } else if constexpr (MODE == TM_RESID) {
+                const cx<R> bb = a.w[i];
+                const cx<R> r = bb - yj;
+                a.out[i] = r;
+                dsum[0][q] += (double)norm2(r);
+                dsum[1][q] += (double)norm2(bb);
+            } else if constexpr (MODE == TM_RK4) {
+                const R dt = a.dt;
+                if (a.stage == 1) {
+                    a.acc[i] = yj;
+                    a.out[i] = a.y[i] + (R(0.5) * dt) * yj;
+                } else if (a.stage == 2) {
+                    a.acc[i] = a.acc[i] + R(2) * yj;
+                    a.out[i] = a.y[i] + (R(0.5) * dt) * yj;
+                } else if (a.stage == 3) {
+                    a.acc[i] = a.acc[i] + R(2) * yj;
+                    a.out[i] = a.y[i] + dt * yj;
+                } else {
+                    a.y[i] = a.y[i] + (dt / R(6)) * (a.acc[i] + yj);
+                }
+            } else if constexpr (MODE == TM_NORMS) {
+                dsum[0][q] += (double)norm2(yj);
+                dsum[1][q] += (double)norm2(xo[q]);
+            }
+        }
+    }
 }
 
 // One CTA per ADO range (persistent: all ranges resident at once). The CTA builds the term
-// programs of its ADOs in shared memory once per launch, then sweeps the batch columns in
-// chunks of 32 x VC; every CTA sweeps the chunks in the same order, so the data in use at
-// any moment is one column chunk of every ADO (about 19 MB per vector for 2,325 ADOs of
-// 4 x 4 FP32 blocks), which L2 holds while the neighbours re-read it.
-//
-// Program layout: triples (ADO p, element e, entry t) in that order, entry t = 0 damping,
-// t = 1 system commutator, t = 2 .. E_p + 1 neighbour entries, t = E_p + 2 trace row (ADO 0
-// of the steady-state system only); an exclusive scan of their term counts gives every
-// term's slot, so each (p, e) item's terms are contiguous and in the apply_point order.
-template <class R, int MODE>
-__global__ void __launch_bounds__(kTileWarps * 32, 5) k_tile(TileArgs<R> a) {
-    constexpr int VC = VecT<R>::VC;
-    constexpr int CW = 32 * VC;
+// programs of its ADOs in shared memory once per launch and turns each term's source element
+// into a row offset (source * B, 32-bit: the launch needs N d^2 B < 2^31) and, in FP32, a
+// broadcast coefficient record; then it sweeps the batch columns in chunks of CW columns
+// (FP32: 64 P; FP64: 32). Every CTA sweeps the chunks in the same order, so the data in use
+// at any moment is one column chunk of every ADO (19 MB per vector for 2,325 ADOs of 4 x 4
+// FP32 blocks at CW = 64), which L2 holds while the neighbours re-read it. The output row of
+// item it is n0 d^2 + it. An item's first term is its damping term on its own element
+// (build_programs), which also supplies the input element x_own. Value q of a lane is column
+// c0 + 64 (q / 2) + 2 lane + q % 2 (FP32) or c0 + lane (FP64).
+template <class R, int MODE, int P, int U, int KI, int MINB>
+__global__ void __launch_bounds__(kTileWarps * 32, MINB) k_tile(TileArgs<R> a) {
+    constexpr bool F32 = sizeof(R) == 4;
+    constexpr int VC = F32 ? 2 * P : 1;   // values (columns) per lane
+    constexpr int NP = F32 ? P : 1;       // 16-byte loads per lane and term
+    constexpr int CW = F32 ? 64 * P : 32;
+    constexpr int K = F32 ? KI : 1;       // items in flight per warp
     const DevView<R> &v = a.v;
-    const int d = v.d, d2 = v.d2, set = a.set;
+    const int d2 = v.d2, set = a.set;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tid = threadIdx.x;
     const int64_t B = a.B;
     const int n0 = __ldg(v.cta_ado + blockIdx.x), n1 = __ldg(v.cta_ado + blockIdx.x + 1);
-    const int P = n1 - n0;
+    const int P_ados = n1 - n0;
 
     extern __shared__ __align__(16) unsigned char smem[];
     double *s_red = reinterpret_cast<double *>(smem);  // [warps][CW][3] per-warp dot partials
+    unsigned char *after_red = smem + (tile_mode_dots(MODE) ? (size_t)kTileWarps * CW * 3 * sizeof(double) : 0);
+    float4 *s_c4 = reinterpret_cast<float4 *>(after_red);  // FP32 records [range_terms]
     ProgSmem<R> ps = prog_layout<R>(v.range_terms, v.range_slots, v.range_ados, d2,
-                                    smem + (size_t)kTileWarps * CW * 3 * sizeof(double));
+                                    after_red + (F32 ? 16 * (size_t)v.range_terms : 0));
     build_programs<R>(v, ps, n0, n1, a.aug, set);
-    const int32_t *s_item = ps.item;
-    const int32_t *s_src = ps.src;
-    const cx<R> *s_coef = ps.coef;
-    (void)lane;
+    const int n_items = P_ados * d2;
+    const int n_terms = ps.item[n_items];
+    // row offsets, and in FP32 one 16-byte record per term: (cr, ci, row offset, 0)
+    for (int j = tid; j < n_terms; j += blockDim.x) {
+        ps.src[j] = (int32_t)((int64_t)ps.src[j] * B);
+        if constexpr (F32) {
+            const cx<float> c = ps.coef[j];
+            s_c4[j] = make_float4(c.re, c.im, __int_as_float(ps.src[j]), 0.f);
+        }
+    }
+    __syncthreads();
+    const int32_t *__restrict__ s_item = ps.item;
+    const int32_t *__restrict__ s_off = ps.src;
+    const cx<R> *__restrict__ s_coef = ps.coef;
+    const int64_t row0 = (int64_t)n0 * d2;
+    // column offset of value q inside a chunk
+    auto co = [&](int q) -> int { return F32 ? (q >> 1) * 64 + 2 * lane + (q & 1) : lane; };
 
     // ---------------- sweep the column chunks
-    const cx<R> *__restrict__ X = a.x;
-    const int n_items = P * d2;
     for (int64_t c0 = 0; c0 < B; c0 += CW) {
-        const int64_t b = c0 + (int64_t)lane * VC;
-        const bool col_ok = b < B;  // B is a multiple of VC
+        bool pv[NP];
+#pragma unroll
+        for (int p = 0; p < NP; ++p) pv[p] = c0 + co(2 * p) < B;  // B is even (FP32)
+        const cx<R> *__restrict__ Xb = a.x + c0 + co(0);
         cx<R> shv[VC];
         double dsum[3][VC];
 #pragma unroll
-        for (int j = 0; j < VC; ++j) {
-            shv[j] = (a.shift && col_ok) ? a.shift[b + j] : cx<R>{R(0), R(0)};
-            dsum[0][j] = dsum[1][j] = dsum[2][j] = 0.0;
+        for (int q = 0; q < VC; ++q) {
+            const bool ok = pv[F32 ? q >> 1 : 0];
+            shv[q] = (a.shift && ok) ? a.shift[c0 + co(q)] : cx<R>{R(0), R(0)};
+            dsum[0][q] = dsum[1][q] = dsum[2][q] = 0.0;
         }
-        if (col_ok) {
-            for (int it = warp; it < n_items; it += kTileWarps) {
-                const int j0 = s_item[it], j1 = s_item[it + 1];
-                cx<R> acc[VC], xo[VC];
-                {
-                    const cx<R> cf = s_coef[j0];
-                    const cx<R> *pp = X + (int64_t)s_src[j0] * B + b;
+        if (pv[0]) {
+            for (int it0 = warp * K; it0 < n_items; it0 += kTileWarps * K) {
+                int jb[K], len[K], maxlen = 0;
+                cx<R> xo[K][VC], y[K][VC];
+                cx<R> cf0[K];
 #pragma unroll
-                    for (int j = 0; j < VC; ++j) {
-                        xo[j] = pp[j];
-                        acc[j] = (cf + shv[j]) * xo[j];
-                    }
-                }
-                // terms in batches of kBatch so that kBatch loads are in flight at once; the
-                // last batch repeats the item's final term with a zero coefficient
-                for (int jj = j0 + 1; jj < j1; jj += kBatch) {
-                    cx<R> cf[kBatch];
-                    const cx<R> *pp[kBatch];
+                for (int k = 0; k < K; ++k) {
+                    const bool ok = it0 + k < n_items;
+                    const int j0 = ok ? s_item[it0 + k] : 0;
+                    jb[k] = j0 + 1;
+                    len[k] = ok ? s_item[it0 + k + 1] - j0 - 1 : 0;
+                    maxlen = max(maxlen, len[k]);
+                    cf0[k] = ok ? s_coef[j0] : cx<R>{R(0), R(0)};
+                    // first term: damping (+ shift) on the item's own element
+                    const cx<R> *pp = Xb + (ok ? s_off[j0] : 0);
+                    if constexpr (F32) {
 #pragma unroll
-                    for (int u = 0; u < kBatch; ++u) {
-                        const bool ok = jj + u < j1;
-                        const int idx = ok ? jj + u : j1 - 1;
-                        cf[u] = ok ? s_coef[idx] : cx<R>{R(0), R(0)};
-                        pp[u] = X + (int64_t)s_src[idx] * B + b;
-                    }
-                    cx<R> xv[kBatch][VC];
-#pragma unroll
-                    for (int u = 0; u < kBatch; ++u) {
-                        if constexpr (VC == 2) {
-                            const float4 tq = __ldg(reinterpret_cast<const float4 *>(pp[u]));
-                            xv[u][0] = cx<R>{(R)tq.x, (R)tq.y};
-                            xv[u][1] = cx<R>{(R)tq.z, (R)tq.w};
-                        } else {
-                            const double2 tq = __ldg(reinterpret_cast<const double2 *>(pp[u]));
-                            xv[u][0] = cx<R>{(R)tq.x, (R)tq.y};
+                        for (int p = 0; p < NP; ++p) {
+                            const float4 t = (ok && pv[p]) ? __ldg(reinterpret_cast<const float4 *>(pp) + 32 * p)
+                                                           : make_float4(0.f, 0.f, 0.f, 0.f);
+                            xo[k][2 * p] = cx<R>{t.x, t.y};
+                            xo[k][2 * p + 1] = cx<R>{t.z, t.w};
                         }
+                    } else {
+                        const double2 t = ok ? __ldg(reinterpret_cast<const double2 *>(pp)) : make_double2(0.0, 0.0);
+                        xo[k][0] = cx<R>{t.x, t.y};
                     }
-#pragma unroll
-                    for (int u = 0; u < kBatch; ++u)
-#pragma unroll
-                        for (int j = 0; j < VC; ++j) fma_to(acc[j], cf[u], xv[u][j]);
                 }
-                const int p = it / d2, e = it - p * d2;
-                const int64_t i = ((int64_t)(n0 + p) * d2 + e) * B + b;
+                if constexpr (F32) {
+                    float2 A[K][VC], Bq[K][VC];
 #pragma unroll
-                for (int j = 0; j < VC; ++j) {
-                    const cx<R> y = acc[j];
-                    if constexpr (MODE == TM_STORE) {
-                        a.out[i + j] = y;
-                    } else if constexpr (MODE == TM_BICG_V) {
-                        a.out[i + j] = y;
-                        const cx<double> yd = cast<double>(y), wd = cast<double>(a.w[i + j]);
-                        dsum[0][j] += wd.re * yd.re + wd.im * yd.im;
-                        dsum[1][j] += wd.re * yd.im - wd.im * yd.re;
-                    } else if constexpr (MODE == TM_BICG_T) {
-                        a.out[i + j] = y;
-                        const cx<double> yd = cast<double>(y), wd = cast<double>(a.w[i + j]);
-                        dsum[0][j] += yd.re * wd.re + yd.im * wd.im;
-                        dsum[1][j] += yd.re * wd.im - yd.im * wd.re;
-                        dsum[2][j] += yd.re * yd.re + yd.im * yd.im;
-                    } else if constexpr (MODE == TM_RESID) {
-                        const cx<R> bb = a.w[i + j];
-                        const cx<R> r = bb - y;
-                        a.out[i + j] = r;
-                        dsum[0][j] += (double)norm2(r);
-                        dsum[1][j] += (double)norm2(bb);
-                    } else if constexpr (MODE == TM_RK4) {
-                        const R dt = a.dt;
-                        if (a.stage == 1) {
-                            a.acc[i + j] = y;
-                            a.out[i + j] = a.y[i + j] + (R(0.5) * dt) * y;
-                        } else if (a.stage == 2) {
-                            a.acc[i + j] = a.acc[i + j] + R(2) * y;
-                            a.out[i + j] = a.y[i + j] + (R(0.5) * dt) * y;
-                        } else if (a.stage == 3) {
-                            a.acc[i + j] = a.acc[i + j] + R(2) * y;
-                            a.out[i + j] = a.y[i + j] + dt * y;
-                        } else {
-                            a.y[i + j] = a.y[i + j] + (dt / R(6)) * (a.acc[i + j] + y);
+                    for (int k = 0; k < K; ++k)
+#pragma unroll
+                        for (int q = 0; q < VC; ++q) {
+                            const cx<float> f = (cf0[k] + shv[q]) * xo[k][q];
+                            A[k][q] = make_float2(f.re, f.im);
+                            Bq[k][q] = make_float2(0.f, 0.f);
                         }
-                    } else if constexpr (MODE == TM_NORMS) {
-                        dsum[0][j] += (double)norm2(y);
-                        dsum[1][j] += (double)norm2(xo[j]);
-                    }
+                    tile_terms_f32<P, U, K>(s_c4, s_off, Xb, jb, len, maxlen, pv, A, Bq);
+#pragma unroll
+                    for (int k = 0; k < K; ++k)
+#pragma unroll
+                        for (int q = 0; q < VC; ++q)
+                            y[k][q] = cx<R>{A[k][q].x - Bq[k][q].y, A[k][q].y + Bq[k][q].x};
+                } else {
+                    cx<double> acc = (cf0[0] + shv[0]) * xo[0][0];
+                    tile_terms_f64<U>(reinterpret_cast<const cx<double> *>(s_coef), s_off,
+                                      reinterpret_cast<const cx<double> *>(Xb), jb[0], jb[0] + len[0], acc);
+                    y[0][0] = cx<R>{acc.re, acc.im};
                 }
+#pragma unroll
+                for (int k = 0; k < K; ++k)
+                    if (it0 + k < n_items)
+                        tile_epilogue<R, MODE, VC, NP>(a, (row0 + it0 + k) * B + c0, co, pv, y[k], xo[k], dsum);
             }
         }
         // ---------------- per-column reductions of this chunk: one atomic per column and CTA
-        if constexpr (MODE == TM_BICG_V || MODE == TM_BICG_T || MODE == TM_RESID || MODE == TM_NORMS) {
+        if constexpr (tile_mode_dots(MODE)) {
 #pragma unroll
-            for (int j = 0; j < VC; ++j)
+            for (int q = 0; q < VC; ++q)
 #pragma unroll
-                for (int qv = 0; qv < 3; ++qv) s_red[(warp * CW + lane * VC + j) * 3 + qv] = dsum[qv][j];
+                for (int qv = 0; qv < 3; ++qv) s_red[(warp * CW + co(q)) * 3 + qv] = dsum[qv][q];
             __syncthreads();
-            if (tid < CW && c0 + tid < B) {
+            for (int t = tid; t < CW && c0 + t < B; t += blockDim.x) {
                 double sum[3] = {0.0, 0.0, 0.0};
                 for (int w = 0; w < kTileWarps; ++w)
 #pragma unroll
-                    for (int qv = 0; qv < 3; ++qv) sum[qv] += s_red[(w * CW + tid) * 3 + qv];
-                const int64_t col = c0 + tid;
+                    for (int qv = 0; qv < 3; ++qv) sum[qv] += s_red[(w * CW + t) * 3 + qv];
+                const int64_t col = c0 + t;
                 if constexpr (MODE == TM_NORMS) {
                     atomicAdd(a.norms + 2 * col, sum[0]);
                     atomicAdd(a.norms + 2 * col + 1, sum[1]);
@@ -445,34 +615,85 @@ __global__ void __launch_bounds__(kTileWarps * 32, 5) k_tile(TileArgs<R> a) {
     }
 }
 
+// Variant the tiled kernel runs for a launch of B columns: the hierarchy's (autotuned) FP32
+// variant, or variant 0 (one float4 per lane) when B does not fill a 128-column chunk; FP64
+// has one.
+template <class R>
+inline int tile_var_of(const DevView<R> &v, int64_t B) {
+    if (sizeof(R) == 8) return 0;
+    int var = v.tile_var;
+    if (var < 0 || var >= kTileVariants) var = 0;
+    if (kTileVariant[var].P == 2 && B < 128) var = 0;
+    return var;
+}
+
 // Whether the tiled kernel can run this launch: one parameter set for all columns, enough
-// columns to fill a warp, FP32 column count even (float4 loads), every ADO range within
-// its shared-memory budget.
+// columns to fill a warp, FP32 column count even (16-byte loads), 32-bit row offsets
+// (N d^2 B < 2^31), every ADO range within its shared-memory budget.
 template <class R>
 inline bool tile_ok(const DevView<R> &v, int64_t B) {
     if (B < 16 || B < v.tile_min_b || v.n_sets != 1 || v.n_ranges < 1) return false;
-    if (VecT<R>::VC == 2 && (B & 1)) return false;
+    if (sizeof(R) == 4 && (B & 1)) return false;
+    if ((double)v.N * v.d2 * (double)B >= 2147483647.0) return false;
     if (v.range_terms > kRangeTerms || v.range_slots > kRangeSlots) return false;
-    return tile_smem_bytes(v) <= 200 * 1024;
+    return tile_smem_bytes_var(v, tile_var_of(v, B)) <= 200 * 1024;
 }
 
-// the dynamic shared-memory opt-in of k_tile<R, MODE> for this view (not a stream operation)
+// attr_only: set the dynamic shared-memory opt-in and launch nothing (needed before a launch
+// is captured into a graph; not a stream operation)
+template <class R, int MODE, int P, int U, int KI, int MINB>
+inline cudaError_t launch_tile_var(const TileArgs<R> &a, cudaStream_t s, bool set_attr, bool attr_only) {
+    constexpr int CW = sizeof(R) == 8 ? 32 : 64 * P;
+    const size_t sm = tile_smem_bytes(a.v, CW, tile_mode_dots(MODE));
+    if (set_attr || attr_only) {
+        if (sm > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(k_tile<R, MODE, P, U, KI, MINB>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
+        }
+        // shared memory for the resident CTAs only: the rest of the SM's 256 KB of L1/shared
+        // storage stays L1, which serves the neighbour re-reads
+        const int pct = (int)std::min<size_t>(100, (MINB * (sm + 1024) * 100 + 232447) / 232448);
+        cudaError_t e = cudaFuncSetAttribute(k_tile<R, MODE, P, U, KI, MINB>,
+                                             cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+        if (e != cudaSuccess) return e;
+    }
+    if (attr_only) return cudaSuccess;
+    k_tile<R, MODE, P, U, KI, MINB><<<a.v.n_ranges, kTileWarps * 32, sm, s>>>(a);
+    return cudaGetLastError();
+}
+
+#define HEOM_TILE_VAR(i)                                                                    \
+    launch_tile_var<R, MODE, kTileVariant[i].P, kTileVariant[i].U, kTileVariant[i].KI,       \
+                    kTileVariant[i].minb>(a, s, set_attr, attr_only)
+
+template <class R, int MODE>
+inline cudaError_t launch_tile_dispatch(const TileArgs<R> &a, cudaStream_t s, bool set_attr,
+                                        bool attr_only) {
+    if constexpr (sizeof(R) == 8) {
+        return launch_tile_var<R, MODE, 1, 4, 1, 3>(a, s, set_attr, attr_only);
+    } else {
+        switch (tile_var_of(a.v, a.B)) {
+        case 0: return HEOM_TILE_VAR(0);
+        case 1: return HEOM_TILE_VAR(1);
+        case 2: return HEOM_TILE_VAR(2);
+        case 3: return HEOM_TILE_VAR(3);
+        case 4: return HEOM_TILE_VAR(4);
+        default: return HEOM_TILE_VAR(5);
+        }
+    }
+}
+#undef HEOM_TILE_VAR
+
+// the dynamic shared-memory opt-in of the kernel a launch of these arguments runs
 template <class R, int MODE>
 inline cudaError_t launch_tile_attr(const TileArgs<R> &a) {
-    const size_t sm = tile_smem_bytes(a.v);
-    if (sm <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(k_tile<R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    return launch_tile_dispatch<R, MODE>(a, 0, true, true);
 }
 
 template <class R, int MODE>
 inline cudaError_t launch_tile(const TileArgs<R> &a, cudaStream_t s, bool set_attr = true) {
-    const size_t sm = tile_smem_bytes(a.v);
-    if (set_attr && sm > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_tile<R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-    }
-    k_tile<R, MODE><<<a.v.n_ranges, kTileWarps * 32, sm, s>>>(a);
-    return cudaGetLastError();
+    return launch_tile_dispatch<R, MODE>(a, s, set_attr, false);
 }
 
 }  // namespace heom

@@ -209,3 +209,28 @@ def test_autotune_choice_keeps_parity(heom, prec):
     assert rel_err(Yg, Y) < TOL[prec]
     narrow = heom.autotune(g, 8, P)
     assert not narrow["tiled"] and all(c < 0 for c in narrow["candidates_us"][1:])
+
+
+@pytest.mark.parametrize("variant", range(6))
+@pytest.mark.parametrize("batch", [18, 130, 132, 256])
+def test_apply_tile_variants(heom, variant, batch):
+    """Every FP32 variant of the tiled kernel (columns per lane, terms in flight) at batches
+    with a ragged last chunk: 18 (one float4 per lane, lanes 9..31 idle), 130 and 132 (the
+    second 128-column chunk holds 2 or 4 columns), 256 (full chunks); FP64 beside it."""
+    import torch
+    prob = W.random_raw_problem(3, [("RI", 2), ("I", 1)], [4, 2], 2, 2, parity=-1, seed=44)
+    h = hy.problem_hierarchy(prob)
+    X = W.random_ado_vector(h.n_ado, 3, batch, seed=45)
+    Y = oracle_apply_batched(prob, h, X)
+    g = heom.build_hierarchy(prob)
+    heom.set_tile_config(g, 1 + variant % 5, variant)
+    for dt, prec in ((torch.complex64, "fp32"), (torch.complex128, "fp64")):
+        x = to_dev(X, dt)
+        y = torch.empty_like(x)
+        heom.apply(g, x, y)
+        torch.cuda.synchronize()
+        assert rel_err(y.cpu().numpy().astype(np.complex128), Y) < TOL[prec], (variant, batch, prec)
+    with pytest.raises(heom.HeomError):
+        heom.set_tile_config(g, 0, variant)
+    with pytest.raises(heom.HeomError):
+        heom.set_tile_config(g, 2, 6)

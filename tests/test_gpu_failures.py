@@ -67,3 +67,48 @@ def test_solvers_refuse_invalid_arguments(heom, siam):
     assert st == heom.EINVAL
     _, st, _ = heom.psd(odd, x, m.fermion_baths[0][0], np.array([1.0]), raise_on_error=False)
     assert st == heom.EINVAL  # the PSD needs the even sector
+
+
+def test_device_wait_timeout_returns_etimeout(heom, siam):
+    """The persistent solvers' grid barriers are the library's only device-side waits. With
+    the wait bound set to 300 SM cycles, ordinary skew between CTAs makes a wait run out: the
+    CTA raises the shared flag, every CTA leaves the launch, and the call returns
+    HEOM_ETIMEOUT with its statistics filled. Nothing hangs or faults. With the default bound
+    restored the same hierarchies solve normally."""
+    import torch
+    m, even, odd = siam
+    x = torch.zeros((even.n_ado, 4, 4), dtype=torch.complex128, device="cuda")
+    try:
+        heom.set_wait_limit(300)
+        st, stats = heom.steady(even, x, tol=1e-10, prec=heom.FP64, raise_on_error=False)
+        assert st == heom.ETIMEOUT
+        # the solve stopped at its first barrier: x is still zero, r_ss = ||M x|| / ||x|| has
+        # no value and is reported as +inf
+        assert stats[0]["status"] == heom.ETIMEOUT and stats[0]["residual"] > 1e-10
+        A, st, stats = heom.spectrum(odd, x, m.fermion_baths[0][0], np.array([-5.0, 5.0]),
+                                     tol=1e-8, prec=heom.SHIFTED, raise_on_error=False)
+        assert st == heom.ETIMEOUT and all(s_["status"] == heom.ETIMEOUT for s_ in stats)
+        assert np.all(np.isnan(A))
+    finally:
+        heom.set_wait_limit(0)
+    st, stats = heom.steady(even, x, tol=1e-10, prec=heom.FP64)
+    assert st == heom.OK and stats[0]["residual"] <= 1e-10
+    A, st, stats = heom.spectrum(odd, x, m.fermion_baths[0][0], np.array([-5.0, 5.0]), tol=1e-8,
+                                 prec=heom.SHIFTED)
+    assert st == heom.OK and np.all(np.isfinite(A))
+
+
+def test_entry_points_restore_the_callers_device(heom, siam):
+    """Every entry point makes the hierarchy's device current for its work and gives the
+    calling thread its previous current device back (checked on one GPU: the current device
+    is still the caller's after apply, evolve, steady and spectrum)."""
+    import torch
+    m, even, odd = siam
+    dev = torch.cuda.current_device()
+    x = torch.zeros((even.n_ado, 4, 4), dtype=torch.complex128, device="cuda")
+    heom.steady(even, x, tol=1e-8, prec=heom.FP64)
+    y = torch.empty_like(x)
+    heom.apply(even, x, y)
+    heom.evolve(even, y, 0.01, 2)
+    heom.spectrum(odd, x, m.fermion_baths[0][0], np.array([0.0]), tol=1e-8, prec=heom.SHIFTED)
+    assert torch.cuda.current_device() == dev

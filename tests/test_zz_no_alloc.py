@@ -46,6 +46,30 @@ def test_noalloc_matches_evolve_on_two_calls_in_a_row(heom):
     assert rel_err(x, ref) < 1e-10 and rel_err(t, rt) < 1e-10
 
 
+def test_noalloc_call_allocates_nothing(heom):
+    """After the first call on the device (which looks up the static scratch), further calls
+    make no device allocation and grow no workspace: the library's allocation counters
+    (every cudaMalloc of the library goes through one counted routine) stay put, and the
+    hierarchy's own RK4 workspace is never taken."""
+    import torch
+    model = W.siam_model(tier=2)
+    g = heom.build_hierarchy(heom.problem_from_model(model))
+    X = so.initial_vector(g.n_ado, model.rho0)
+    x = to_dev(X, torch.complex128)
+    traj = torch.empty((5, 4, 4), dtype=torch.complex128, device="cuda")
+    heom.evolve_noalloc(g, x, 0.01, 0)  # set-up call: n_steps = 0 does the lookup only
+    torch.cuda.synchronize()
+    before = heom.profile_allocs()
+    heom.evolve_noalloc(g, x, 0.01, 40, 10, traj=traj)
+    heom.evolve_noalloc(g, x, 0.01, 40, 10, traj=traj)
+    torch.cuda.synchronize()
+    assert heom.profile_allocs() == before
+    ref = to_dev(X, torch.complex128)
+    heom.evolve(g, ref, 0.01, 80)  # heom_evolve on the same hierarchy does take a workspace
+    assert heom.profile_allocs()["workspace_takes"] == before["workspace_takes"] + 1
+    assert rel_err(x.cpu().numpy(), ref.cpu().numpy()) < 1e-10
+
+
 def test_noalloc_refuses_requests_beyond_its_scratch(heom):
     import torch
     g = heom.build_hierarchy(heom.problem_from_model(W.siam_model(tier=3)))
