@@ -169,6 +169,19 @@ heom_status heom_count_ados(int n_baths, const heom_bath *baths, int tier_b, int
 heom_status heom_set_params(heom_hier *h, int n_sets, const heom_c64 *H,
                             const heom_c64 *coef, const heom_c64 *rate);
 
+/* Per-set truncation: parameter set s (heom_set_params) keeps only the ADOs with bosonic
+ * tier <= tier_b[s] and fermionic tier <= tier_f[s] (host arrays of n_sets entries, each at
+ * most the hierarchy's own tiers) and holds every other ADO at zero. The hierarchy truncated
+ * at tiers (t_b, t_f) is the restriction of this one to those ADOs (in the same relative
+ * canonical order; for a single kind of bath they are the leading ADOs; truncation (Eq. HEOM)
+ * drops exactly the couplings into the dropped tiers), so every later call -- apply, RK4,
+ * stationary states, spectra -- computes
+ * set s's own, shallower hierarchy, and parameter sets of different depths share one batched
+ * call. Input vectors must be zero beyond a set's tiers (the solvers' are); the apply writes
+ * zero there. Tables are not rebuilt. NULL, NULL removes the truncation; heom_set_params
+ * removes it too. Errors: HEOM_EINVAL for tiers out of range or one NULL array. */
+heom_status heom_set_truncation(heom_hier *h, const int *tier_b, const int *tier_f);
+
 /* Lindblad terms (Eq. Lindbladian, J(F)[X] = F X F^dagger - 1/2 {F^dagger F, X}): replace
  * the hierarchy's jump operators by n_ops operators F [n_ops][d][d] (row-major, host) with
  * real rates gamma [n_ops] (host). Every later call then adds

@@ -65,6 +65,7 @@ _sig = {
     "heom_build_hierarchy": [C.c_int, _P, C.c_int, _P, C.c_int, C.c_int, C.c_int, C.c_int,
                              C.POINTER(_P)],
     "heom_set_params": [_P, C.c_int, _P, _P, _P],
+    "heom_set_truncation": [_P, _P, _P],
     "heom_set_lindblad": [_P, C.c_int, _P, _P],
     "heom_set_drive": [_P, C.c_int, _P],
     "heom_evolve_td": [_P, _P, C.c_int64, C.c_double, C.c_int64, _P, C.c_int64, _P, C.c_int, _P],
@@ -290,6 +291,30 @@ def set_params(h: Hierarchy, H, coef, rate):
     _check(_lib.heom_set_params(h.handle, n_sets, _ptr(H), _ptr(coef), _ptr(rate)),
            "heom_set_params")
     h.refresh()
+
+
+def set_params_from_models(h: Hierarchy, models, parity: int = 1):
+    """heom_set_params with one parameter set per model of h's structure (exponents from the
+    library's helpers, as problem_from_model)."""
+    Hs, coefs, rates = [], [], []
+    for m in models:
+        p = problem_from_model(m, parity)
+        Hs.append(p["H"])
+        coefs.append(np.concatenate([b["coef"] for b in p["baths"]]) if p["baths"] else np.zeros(0))
+        rates.append(np.concatenate([b["rate"] for b in p["baths"]]) if p["baths"] else np.zeros(0))
+    set_params(h, np.array(Hs), np.array(coefs), np.array(rates))
+
+
+def set_truncation(h: Hierarchy, tier_b=None, tier_f=None):
+    """heom_set_truncation: per parameter set tiers [n_sets] (both None: remove)."""
+    if tier_b is None and tier_f is None:
+        _check(_lib.heom_set_truncation(h.handle, None, None), "heom_set_truncation")
+        return
+    tb = np.ascontiguousarray(tier_b, np.int32)
+    tf = np.ascontiguousarray(tier_f, np.int32)
+    if tb.shape != (h.n_sets,) or tf.shape != (h.n_sets,):
+        raise ValueError(f"tier arrays need one entry per parameter set ({h.n_sets})")
+    _check(_lib.heom_set_truncation(h.handle, _ptr(tb), _ptr(tf)), "heom_set_truncation")
 
 
 def ado_index(h: Hierarchy, occ) -> int:

@@ -474,6 +474,8 @@ DevView<double> arnoldi_view(const heom_hier *h) {
 }  // namespace
 
 bool arnoldi_persistent_ok(const heom_hier *h, int64_t B, int max_steps) {
+    // the resident term programs carry one parameter set's coefficients
+    if (h->n_sets != 1 || h->has_caps) return false;
     if (h->ar_ranges < 1 || B < 1 || B > kArMaxB || (32 % B) != 0 || (kArThreads % B) != 0) return false;
     const int steps = std::min(max_steps, kArMaxSteps);
     return arnoldi_smem(arnoldi_view(h), (steps + 2) * (int)B) <= 200 * 1024;

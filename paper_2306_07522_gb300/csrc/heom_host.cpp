@@ -404,6 +404,9 @@ heom::DevView<double> heom_hier::view64() const {
     v.cta_ado = (const int32_t *)d_cta_ado.p; v.n_ranges = n_ranges; v.range_terms = range_terms;
     v.range_slots = range_slots; v.range_ados = range_ados; v.tile_min_b = tile_min_b;
     v.tile_var = tile_var;
+    v.ado_tier = has_caps ? (const int32_t *)d_ado_tier.p : nullptr;
+    v.set_cap = has_caps ? (const int32_t *)d_set_cap.p : nullptr;
+    v.act_sets = (has_caps && has_act) ? (const int32_t *)d_act_sets.p : nullptr;
     v.pers_ado = (const int32_t *)d_pers_ado.p; v.pers_ranges = pers_ranges;
     v.pers_terms = pers_terms; v.pers_slots = pers_slots; v.pers_ados = pers_ados;
     return v;
@@ -429,6 +432,9 @@ heom::DevView<float> heom_hier::view32() const {
     v.cta_ado = (const int32_t *)d_cta_ado.p; v.n_ranges = n_ranges; v.range_terms = range_terms;
     v.range_slots = range_slots; v.range_ados = range_ados; v.tile_min_b = tile_min_b;
     v.tile_var = tile_var;
+    v.ado_tier = has_caps ? (const int32_t *)d_ado_tier.p : nullptr;
+    v.set_cap = has_caps ? (const int32_t *)d_set_cap.p : nullptr;
+    v.act_sets = (has_caps && has_act) ? (const int32_t *)d_act_sets.p : nullptr;
     v.pers_ado = (const int32_t *)d_pers_ado.p; v.pers_ranges = pers_ranges;
     v.pers_terms = pers_terms; v.pers_slots = pers_slots; v.pers_ados = pers_ados;
     return v;
@@ -445,7 +451,7 @@ void free_all(heom_hier *h) {
                     &h->d_sdiag32, &h->d_tdval64, &h->d_floor64, &h->d_floor32, &h->ws,
                     &h->ws_small,
                     &h->d_t_ptr, &h->d_t_src, &h->d_t_val64, &h->d_t_val32, &h->d_cta_ado,
-                    &h->d_pers_ado, &h->d_ar_ado, &h->ws_pers};
+                    &h->d_pers_ado, &h->d_ar_ado, &h->ws_pers, &h->d_ado_tier, &h->d_set_cap, &h->d_act_sets};
     for (DBuf *b : bufs) heom::dfree(*b);
 }
 
@@ -1130,7 +1136,74 @@ extern "C" heom_status heom_set_params(heom_hier *h, int n_sets, const heom_c64 
     for (size_t i = 0; i < (size_t)n_sets * h->K; ++i)
         if (!finite(coef[i]) || !finite(rate[i])) { set_error("heom_set_params: non-finite exponent"); return HEOM_EINVAL; }
     HEOM_DEVICE(h->device);
+    // a new set count invalidates per-set truncation tiers
+    h->has_caps = h->has_act = false;
+    heom::dfree(h->d_set_cap);
+    heom::dfree(h->d_act_sets);
     return upload_params(h, n_sets, H, coef, rate);
+}
+
+extern "C" heom_status heom_set_truncation(heom_hier *h, const int *tier_b, const int *tier_f) {
+    if (!h) {
+        set_error("heom_set_truncation: need a hierarchy");
+        return HEOM_EINVAL;
+    }
+    HEOM_DEVICE(h->device);
+    if (!tier_b && !tier_f) {  // remove
+        h->has_caps = h->has_act = false;
+        heom::dfree(h->d_set_cap);
+        heom::dfree(h->d_act_sets);
+        return HEOM_OK;
+    }
+    if (!tier_b || !tier_f) {
+        set_error("heom_set_truncation: need both tier arrays (or neither, to remove)");
+        return HEOM_EINVAL;
+    }
+    std::vector<int32_t> cap(h->n_sets);
+    for (int s = 0; s < h->n_sets; ++s) {
+        if (tier_b[s] < 0 || tier_b[s] > h->tier_b || tier_f[s] < 0 || tier_f[s] > h->tier_f) {
+            set_error("heom_set_truncation: set %d asks for tiers (%d, %d) outside [0, %d] x [0, %d]",
+                      s, tier_b[s], tier_f[s], h->tier_b, h->tier_f);
+            return HEOM_EINVAL;
+        }
+        cap[s] = tier_f[s] | (tier_b[s] << 16);
+    }
+    heom_status st;
+    std::vector<int32_t> at(h->N);
+    for (int64_t n = 0; n < h->N; ++n) {
+        const int64_t f = h->full_of(n);
+        const std::vector<int> &m = h->bos[(size_t)(f / h->N_f)];
+        int nb = 0;
+        for (int k : m) nb += k;
+        const int nf = __builtin_popcountll(h->fer[(size_t)(f % h->N_f)]);
+        at[n] = nf | (nb << 16);
+    }
+    if (!h->d_ado_tier.p && (st = upload(h->d_ado_tier, at)) != HEOM_OK) return st;
+    if ((st = upload(h->d_set_cap, cap)) != HEOM_OK) return st;
+    // caps that never increase from one set to the next: each ADO is kept by a leading run of
+    // sets, whose length the Gram-Schmidt kernels use to skip the columns held at zero
+    h->kept_rowsets = 0;
+    for (int64_t n = 0; n < h->N; ++n)
+        for (int s = 0; s < h->n_sets; ++s)
+            if ((at[n] & 0xffff) <= tier_f[s] && (at[n] >> 16) <= tier_b[s]) h->kept_rowsets += h->d2;
+    bool mono = true;
+    for (int s = 1; s < h->n_sets; ++s)
+        mono = mono && tier_b[s] <= tier_b[s - 1] && tier_f[s] <= tier_f[s - 1];
+    h->has_act = false;
+    heom::dfree(h->d_act_sets);
+    if (mono) {  // per row (d2 rows per ADO), so kernels index it without a division
+        std::vector<int32_t> act((size_t)h->N * h->d2);
+        for (int64_t n = 0; n < h->N; ++n) {
+            int k = 0;
+            while (k < h->n_sets && (at[n] & 0xffff) <= tier_f[k] && (at[n] >> 16) <= tier_b[k]) ++k;
+            for (int e = 0; e < h->d2; ++e) act[(size_t)n * h->d2 + e] = k;
+        }
+        if ((st = upload(h->d_act_sets, act)) != HEOM_OK) return st;
+        h->has_act = true;
+    }
+    HEOM_CUDA(cudaStreamSynchronize(0));
+    h->has_caps = true;
+    return HEOM_OK;
 }
 
 extern "C" heom_status heom_set_lindblad(heom_hier *h, int n_ops, const heom_c64 *F,

@@ -113,7 +113,25 @@ struct DevView {
     // whole hierarchy resident in shared memory (pers_ranges = 0 when they do not fit)
     const int32_t *pers_ado;  // [pers_ranges + 1]
     int pers_ranges, pers_terms, pers_slots, pers_ados;
+    // Per-set truncation (heom_set_truncation; both null when unused): ADO n has fermionic
+    // tier ado_tier[n] & 0xffff and bosonic tier ado_tier[n] >> 16; parameter set s keeps
+    // the ADOs with fermionic tier <= set_cap[s] & 0xffff and bosonic tier <= set_cap[s] >> 16
+    // and holds every other ADO at zero (the apply writes zero there).
+    const int32_t *ado_tier;  // [N]
+    const int32_t *set_cap;   // [n_sets]
+    // When the sets' truncation tiers do not increase from one set to the next, the sets that
+    // keep the ADO of row r (= r / d2) are sets 0 .. act_sets[r]-1, so the columns of a vector
+    // that can be nonzero in row r are a leading block (null otherwise).
+    const int32_t *act_sets;  // [N d2]
 };
+
+// Whether ADO n lies beyond the truncation of parameter set s.
+template <class R>
+HD bool beyond_cap(const DevView<R> &v, int64_t n, int s) {
+    if (!v.set_cap) return false;
+    const int t = v.ado_tier[n], c = v.set_cap[s];
+    return (t & 0xffff) > (c & 0xffff) || (t >> 16) > (c >> 16);
+}
 
 // Optional modifiers of the apply used by the solvers (all may be null / zero).
 template <class R>
@@ -173,6 +191,11 @@ struct heom_hier {
     std::vector<int> op_terms;              // total terms of operator slot o over all elements
     int max_terms = 0, max_entries = 0;
     heom::DBuf d_cta_ado, d_pers_ado;
+    heom::DBuf d_ado_tier, d_set_cap;    // per-set truncation (heom_set_truncation)
+    heom::DBuf d_act_sets;               // leading sets that keep each row's ADO (monotone caps)
+    bool has_act = false;
+    int64_t kept_rowsets = 0;            // sum over rows of the sets that keep the row's ADO
+    bool has_caps = false;
     int n_ranges = 0, range_terms = 0, range_slots = 0, range_ados = 0;
     int tile_per_sm = 2;        // tiled kernel: ADO ranges per SM (autotuned)
     int64_t tile_min_b = 16;    // tiled kernel from this batch on (autotuned)

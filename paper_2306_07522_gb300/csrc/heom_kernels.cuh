@@ -51,11 +51,15 @@ __device__ __forceinline__ cx<R> damping_of(const DevView<R> &v, int64_t n, int 
 }
 
 // (M X)[n][e][b]: Eq. HEOM evaluated at ADO n, element e = r*d + c, batch column b.
-// X points at the start of the ADO vector ([N][d2][B]).
+// X points at the start of the ADO vector ([N][d2][B]). Zero for an ADO beyond the
+// truncation of the column's parameter set (heom_set_truncation): with the input zero there
+// too, this is the apply of that set's own, shallower hierarchy, whose ADOs are those of this
+// one within the set's tiers, in the same relative order.
 template <class R>
 __device__ __forceinline__ cx<R> apply_point(const DevView<R> &v, const cx<R> *__restrict__ X,
                                              int64_t n, int e, int64_t b, int64_t B, int set,
                                              const cx<R> &damp) {
+    if (beyond_cap(v, n, set)) return cx<R>{R(0), R(0)};  // held at zero by its set's truncation
     const int d = v.d;
     const int r = e / d, c = e - r * d;
     const cx<R> *Xn = X + n * v.d2 * B + b;

@@ -372,7 +372,7 @@ size_t persist_smem(const DevView<R> &v) {
 
 template <class R>
 bool persist_ok(const heom_hier *h) {
-    if (h->pers_ranges < 1 || h->n_sets != 1) return false;
+    if (h->pers_ranges < 1 || h->n_sets != 1 || h->has_caps) return false;
     const DevView<R> v = view_of_p<R>(h);
     return persist_smem(v) <= 200 * 1024;
 }

@@ -25,6 +25,18 @@ namespace {
 
 constexpr int kDotThreads = 256;
 
+// Columns of a [rows][B] vector that can be nonzero in a row: with truncated parameter sets
+// ordered deepest first (heom_set_truncation), row r's are columns 0 .. act[r] * cps - 1 (cps
+// columns per set); the other entries of every Krylov vector are zero and the float-float
+// Gram-Schmidt kernels neither read nor write them. act = null: every column.
+struct ActCols {
+    const int32_t *act;
+    int64_t cps;
+    __device__ __forceinline__ bool on(int64_t row, int64_t b) const {
+        return !act || b < (int64_t)__ldg(act + row) * cps;
+    }
+};
+
 // Hessenberg matrices of all columns, column-major: entry (i, j) of column b's matrix at
 // Hb[(j (mmax + 1) + i) B + b], so that one Hessenberg column is contiguous.
 __device__ __forceinline__ int64_t hb_at(int i, int j, int mmax, int64_t B, int64_t b) {
@@ -94,61 +106,120 @@ __global__ void __launch_bounds__(kDotThreads) k_multidot(int64_t rows, int64_t 
     }
 }
 
-// wf[t] = split(w[t])
+// wf[t] = split(w[t]); entries outside the active columns (ac) are left alone: only the
+// float-float Gram-Schmidt kernels read wf, and they skip the same entries.
 __global__ void k_split(int64_t total, const cx<double> *__restrict__ w, float4 *__restrict__ wf) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x)
         wf[t] = ff_split(w[t]);
 }
+__global__ void k_split_act(int64_t total, int64_t B, const cx<double> *__restrict__ w,
+                            float4 *__restrict__ wf, ActCols ac) {
+    // the grid stride is a multiple of B (B divides the block): the column is fixed per thread
+    const int64_t t_first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x, b = t_first % B, rstep = stride / B;
+    int64_t row = t_first / B;
+    for (int64_t t = t_first; t < total; t += stride, row += rstep)
+        if (ac.on(row, b)) wf[t] = ff_split(w[t]);
+}
 
 // Float-float partial dot products over a chunk of rows: part[c][i][b] = sum_{rows of chunk
-// c} conj(V_i[row][b]) w[row][b] (FP64 result); grid (i, chunk). B must be a power of two
-// dividing the block (checked by the caller), so every thread keeps one column.
-__global__ void __launch_bounds__(kDotThreads) k_multidot_ff(int64_t rows, int64_t B, int nv,
-                                                             const float4 *__restrict__ Vf,
-                                                             int64_t vstride,
-                                                             const float4 *__restrict__ wf,
-                                                             cx<double> *__restrict__ part,
-                                                             const int *__restrict__ skip) {
+// c} conj(V_i[row][b]) w[row][b] (FP64 result), the basis vectors taken kMdTile at a time:
+// block (tile, chunk) reads its chunk of w once for the tile's basis vectors, with one
+// float-float accumulator pair per basis vector; the tile's loads of an element are
+// independent, so they are in flight together. B must be a power of two dividing the block
+// (checked by the caller), so every thread keeps one column. Entries outside the active
+// columns (ac) are neither read nor summed.
+constexpr int kMdTile = 8;
+__global__ void __launch_bounds__(kDotThreads) k_multidot_ff_tiled(int64_t rows, int64_t B, int nv,
+                                                                   const float4 *__restrict__ Vf,
+                                                                   int64_t vstride,
+                                                                   const float4 *__restrict__ wf,
+                                                                   cx<double> *__restrict__ part,
+                                                                   const int *__restrict__ skip, ActCols ac) {
     if (skip && *skip) return;
-    const int i = blockIdx.x, c = blockIdx.y, nc = gridDim.y;
+    const int i0 = blockIdx.x * kMdTile, c = blockIdx.y, nc = gridDim.y;
+    const int nt = min(kMdTile, nv - i0);
     const int64_t L = rows * B;
     const int64_t t0 = L * c / nc, t1 = L * (c + 1) / nc;
-    const float4 *Vi = Vf + (int64_t)i * vstride;
-    __shared__ double sre[kDotThreads], sim[kDotThreads];
+    __shared__ double sre[kMdTile][kDotThreads], sim[kMdTile][kDotThreads];
     const int64_t tb = t0 - t0 % B;
-    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
-    for (int64_t t = tb + threadIdx.x; t < t1; t += kDotThreads) {
-        if (t < t0) continue;
-        const float4 a = Vi[t], x = wf[t];
-        // conj(a) x: re = a.re x.re + a.im x.im, im = a.re x.im - a.im x.re
-        ff_mac(rh, rl, a.x, a.z, x.x, x.z);
-        ff_mac(rh, rl, a.y, a.w, x.y, x.w);
-        ff_mac(ih, il, a.x, a.z, x.y, x.w);
-        ff_mac(ih, il, -a.y, -a.w, x.x, x.z);
-    }
-    sre[threadIdx.x] = (double)rh + (double)rl;
-    sim[threadIdx.x] = (double)ih + (double)il;
-    __syncthreads();
-    for (int s = kDotThreads >> 1; s >= B; s >>= 1) {
-        if (threadIdx.x < s) {
-            sre[threadIdx.x] += sre[threadIdx.x + s];
-            sim[threadIdx.x] += sim[threadIdx.x + s];
+    // B divides the block: this thread's column is tid % B, its row advances by kDotThreads / B
+    const int64_t cb = threadIdx.x % B, rstep = kDotThreads / B;
+    int64_t row = (tb + threadIdx.x) / B;
+    float rh[kMdTile], rl[kMdTile], ih[kMdTile], il[kMdTile];
+#pragma unroll
+    for (int k = 0; k < kMdTile; ++k) rh[k] = rl[k] = ih[k] = il[k] = 0.f;
+    const float4 *V0 = Vf + (int64_t)i0 * vstride;
+    // the active column counts of the chunk's rows, staged in shared memory 1,024 rows at a
+    // time, so that no element's loads wait on a load of its row's count
+    __shared__ int s_act[1024];
+    const int64_t r_first = tb / B, r_end = (t1 + B - 1) / B;
+    for (int64_t ra = r_first; ra < r_end; ra += 1024) {
+        const int64_t rb = min(r_end, ra + 1024);
+        if (ac.act) {
+            __syncthreads();
+            for (int64_t r = ra + threadIdx.x; r < rb; r += kDotThreads)
+                s_act[r - ra] = (int)(__ldg(ac.act + r) * ac.cps);
+            __syncthreads();
         }
+        int64_t t = ra * B + threadIdx.x;
+        row = ra + threadIdx.x / B;
+    for (; t < rb * B && t < t1; t += kDotThreads, row += rstep) {
+        if (t < t0 || (ac.act && cb >= s_act[row - ra])) continue;
+        const float4 x = wf[t];
+        float4 a[kMdTile];
+#pragma unroll
+        for (int k = 0; k < kMdTile; ++k)
+            if (k < nt) a[k] = V0[(int64_t)k * vstride + t];
+#pragma unroll
+        for (int k = 0; k < kMdTile; ++k) {
+            if (k < nt) {  // conj(a) x
+                ff_mac(rh[k], rl[k], a[k].x, a[k].z, x.x, x.z);
+                ff_mac(rh[k], rl[k], a[k].y, a[k].w, x.y, x.w);
+                ff_mac(ih[k], il[k], a[k].x, a[k].z, x.y, x.w);
+                ff_mac(ih[k], il[k], -a[k].y, -a[k].w, x.x, x.z);
+            }
+        }
+    }
+    }
+#pragma unroll
+    for (int k = 0; k < kMdTile; ++k) {
+        sre[k][threadIdx.x] = (double)rh[k] + (double)rl[k];
+        sim[k][threadIdx.x] = (double)ih[k] + (double)il[k];
+    }
+    __syncthreads();
+    for (int st = kDotThreads >> 1; st >= B; st >>= 1) {
+        if (threadIdx.x < st)
+#pragma unroll
+            for (int k = 0; k < kMdTile; ++k) {
+                sre[k][threadIdx.x] += sre[k][threadIdx.x + st];
+                sim[k][threadIdx.x] += sim[k][threadIdx.x + st];
+            }
         __syncthreads();
     }
-    if (threadIdx.x < B) part[((int64_t)c * nv + i) * B + threadIdx.x] = cx<double>{sre[threadIdx.x], sim[threadIdx.x]};
+    if (threadIdx.x < B)
+        for (int k = 0; k < nt; ++k)
+            part[((int64_t)c * nv + i0 + k) * B + threadIdx.x] =
+                cx<double>{sre[k][threadIdx.x], sim[k][threadIdx.x]};
 }
 
 // wf[row][b] -= sum_i V_i[row][b] h_i[b] in float-float (hf = split h)
 __global__ void k_gs_update_ff(int64_t rows, int64_t B, int nv, const float4 *__restrict__ Vf,
                                int64_t vstride, const float4 *__restrict__ hf,
-                               float4 *__restrict__ wf, const int *__restrict__ skip) {
+                               float4 *__restrict__ wf, const int *__restrict__ skip, ActCols ac) {
     if (skip && *skip) return;
     const int64_t total = rows * B;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b = t % B;
+    // the grid stride is a multiple of B (B divides the block): the column is fixed per thread
+    const int64_t t_first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x, b = t_first % B, rstep = stride / B;
+    int64_t row = t_first / B;
+    // the next element's active count is loaded one element ahead
+    int64_t act_next = (ac.act && t_first < total) ? (int64_t)__ldg(ac.act + row) * ac.cps : B;
+    for (int64_t t = t_first; t < total; t += stride, row += rstep) {
+        const int64_t act_here = act_next;
+        if (ac.act && t + stride < total) act_next = (int64_t)__ldg(ac.act + row + rstep) * ac.cps;
+        if (b >= act_here) continue;
         const float4 w0 = wf[t];
         float rh = w0.x, rl = w0.z, ih = w0.y, il = w0.w;
         for (int i = 0; i < nv; ++i) {
@@ -169,13 +240,14 @@ __global__ void k_gs_update_ff(int64_t rows, int64_t B, int nv, const float4 *__
 // Partial squared column norms (FP64) of a float-float vector over a chunk of rows.
 __global__ void __launch_bounds__(kDotThreads) k_colnorm_part_ff(int64_t rows, int64_t B,
                                                                  const float4 *__restrict__ wf,
-                                                                 double *__restrict__ part) {
+                                                                 double *__restrict__ part, ActCols ac) {
     const int c = blockIdx.x, nc = gridDim.x;
     const int64_t b = blockIdx.y;
     const int64_t r0 = rows * c / nc, r1 = rows * (c + 1) / nc;
     __shared__ double sh[kDotThreads];
     double acc = 0.0;
-    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) acc += norm2(ff_join(wf[r * B + b]));
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x)
+        if (ac.on(r, b)) acc += norm2(ff_join(wf[r * B + b]));
     sh[threadIdx.x] = acc;
     __syncthreads();
     for (int k = blockDim.x >> 1; k > 0; k >>= 1) {
@@ -188,10 +260,14 @@ __global__ void __launch_bounds__(kDotThreads) k_colnorm_part_ff(int64_t rows, i
 // v = w / nrm[b] in FP64 (for the apply) and its float-float split (for Gram-Schmidt); in
 // place on wf. nrm = 0 leaves zeros (exact invariant subspace).
 __global__ void k_scale_ff(int64_t total, int64_t B, float4 *__restrict__ wf,
-                           const double *__restrict__ nrm, cx<double> *__restrict__ v) {
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const double n = nrm[t % B];
+                           const double *__restrict__ nrm, cx<double> *__restrict__ v, ActCols ac) {
+    // the grid stride is a multiple of B (B divides the block): the column is fixed per thread
+    const int64_t t_first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x, b = t_first % B, rstep = stride / B;
+    int64_t row = t_first / B;
+    const double n = b < B ? nrm[b] : 0.0;
+    for (int64_t t = t_first; t < total; t += stride, row += rstep) {
+        if (!ac.on(row, b)) continue;  // zero in v and wf already
         const cx<double> x = n > 0.0 ? (1.0 / n) * ff_join(wf[t]) : cx<double>{0.0, 0.0};
         v[t] = x;
         wf[t] = ff_split(x);
@@ -564,6 +640,7 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
         // them within 60 % of the free device memory
         size_t free_b = 0, total_b = 0;
         if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+            free_b += h->ws.bytes;  // the hierarchy's own workspace is reused (or grown)
             const double per_step = 32.0 * (double)L + 88.0 * (double)S + 64.0 * (double)B;
             const double fixed = 64.0 * (double)L + 48.0 * (double)S + (double)(64 * 2 + 2) * B * 16.0;
             const double avail = 0.6 * (double)free_b - fixed;
@@ -589,8 +666,9 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
                  oy = take((size_t)S * mmax * 16), ocb = take((size_t)S * mmax * 16),
                  ox0 = take((size_t)S * d2 * 16), ores = take((size_t)S * 8),
                  osh = take((size_t)S * 16), oco = take((size_t)S * 4);
-    // row chunks of the partial dot products: enough blocks to fill the GPU at small j
-    const int nchunk = (int)std::max<int64_t>(1, std::min<int64_t>(64, L / 4096));
+    // row chunks of the partial dot products: enough blocks to fill the GPU (three per SM) with
+    // one tile of basis vectors
+    const int nchunk = (int)std::max<int64_t>(1, std::min<int64_t>(456, L / 4096));
     const size_t opart = take((size_t)nchunk * (mmax + 2) * B * 16), oskip = take(sizeof(int));
     const size_t onp = take((size_t)nchunk * B * 8);
     // float-float Gram-Schmidt (B a power of two up to the block size): a split copy of the
@@ -648,6 +726,12 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
     }
     const DevView<double> v = h->view64();
     const bool tiled = tile_ok(v, B);
+    const ActCols ac{v.act_sets, v.act_sets ? B / h->n_sets : 0};
+    // elements of one vector that can be nonzero (truncated sets: the kept rows of each
+    // column), and the ADO-applies of one apply: the work and the algorithmic bytes counted
+    const int64_t cps = B / h->n_sets;
+    const double Lk = h->has_caps ? (double)h->kept_rowsets * cps : (double)L;
+    const double Lg = ac.act ? Lk : (double)L;  // what the Gram-Schmidt kernels stream
     TileArgs<double> ta{};
     ta.v = v;
     ta.B = B;
@@ -669,7 +753,7 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
         const cx<double> *vj = V + (int64_t)j * L;
         cx<double> *w = V + (int64_t)(j + 1) * L;  // the new vector is built in place
         {   // w = M v_j
-            Prof pr(HEOM_KC_KRYLOV_APPLY64, s, (double)h->N * B, 2.0 * L * 16);
+            Prof pr(HEOM_KC_KRYLOV_APPLY64, s, Lk / h->d2, 2.0 * Lk * 16);
             if (tiled) {
                 ta.x = vj;
                 ta.out = w;
@@ -683,31 +767,31 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
             float4 *wf = Vf + (int64_t)(j + 1) * L;
             {   // classical Gram-Schmidt in float-float; pass 1 also yields |w|^2 (w's dot with
                 // itself), from which k_reorth_flag decides on the device whether pass 2 runs
-                Prof pr(HEOM_KC_KRYLOV_VECTOR, s, (double)(j + 1) * L, (2.0 * (j + 1) + 5.0) * L * 16);
+                Prof pr(HEOM_KC_KRYLOV_VECTOR, s, (double)(j + 1) * Lg, (2.0 * (j + 1) + 5.0) * Lg * 16);
                 pr.kernels = 5;
-                k_split<<<blocks_for(L), 256, 0, s>>>(L, w, wf);
-                k_multidot_ff<<<dim3((unsigned)(j + 2), (unsigned)nchunk), kDotThreads, 0, s>>>(
-                    rows, B, j + 2, Vf, L, wf, part, nullptr);
+                k_split_act<<<blocks_for(L), 256, 0, s>>>(L, B, w, wf, ac);
+                k_multidot_ff_tiled<<<dim3((unsigned)((j + 2 + kMdTile - 1) / kMdTile), (unsigned)nchunk),
+                                      kDotThreads, 0, s>>>(rows, B, j + 2, Vf, L, wf, part, nullptr, ac);
                 k_reduce_h<<<blocks_for((int64_t)(j + 2) * B), 256, 0, s>>>(nchunk, j + 2, j + 1, B, part, ht,
                                                                            hft, Hb, j, mmax, nullptr);
                 k_reorth_flag<<<1, 128, 0, s>>>(j + 1, B, ht, dskip);
-                k_gs_update_ff<<<blocks_for(L), 256, 0, s>>>(rows, B, j + 1, Vf, L, hft, wf, nullptr);
+                k_gs_update_ff<<<blocks_for(L), 256, 0, s>>>(rows, B, j + 1, Vf, L, hft, wf, nullptr, ac);
             }
             {   // pass 2 (skipped on the device when pass 1 kept enough of w)
                 Prof pr(HEOM_KC_KRYLOV_VECTOR, s, 0.0, 0.0);
                 pr.kernels = 3;
-                k_multidot_ff<<<dim3((unsigned)(j + 1), (unsigned)nchunk), kDotThreads, 0, s>>>(
-                    rows, B, j + 1, Vf, L, wf, part, dskip);
+                k_multidot_ff_tiled<<<dim3((unsigned)((j + 1 + kMdTile - 1) / kMdTile), (unsigned)nchunk),
+                                      kDotThreads, 0, s>>>(rows, B, j + 1, Vf, L, wf, part, dskip, ac);
                 k_reduce_h<<<blocks_for((int64_t)(j + 1) * B), 256, 0, s>>>(nchunk, j + 1, j + 1, B, part, ht,
                                                                            hft, Hb, j, mmax, dskip);
-                k_gs_update_ff<<<blocks_for(L), 256, 0, s>>>(rows, B, j + 1, Vf, L, hft, wf, dskip);
+                k_gs_update_ff<<<blocks_for(L), 256, 0, s>>>(rows, B, j + 1, Vf, L, hft, wf, dskip, ac);
             }
             {   // h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j} (FP64 and split)
-                Prof pr(HEOM_KC_KRYLOV_VECTOR, s, (double)L, 4.0 * L * 16);
+                Prof pr(HEOM_KC_KRYLOV_VECTOR, s, Lg, 4.0 * Lg * 16);
                 pr.kernels = 3;
-                k_colnorm_part_ff<<<dim3((unsigned)nchunk, (unsigned)B), kDotThreads, 0, s>>>(rows, B, wf, npart);
+                k_colnorm_part_ff<<<dim3((unsigned)nchunk, (unsigned)B), kDotThreads, 0, s>>>(rows, B, wf, npart, ac);
                 k_colnorm_fin<<<blocks_for(B), 256, 0, s>>>(nchunk, B, npart, nrm, Hb, j, mmax);
-                k_scale_ff<<<blocks_for(L), 256, 0, s>>>(L, B, wf, nrm, w);
+                k_scale_ff<<<blocks_for(L), 256, 0, s>>>(L, B, wf, nrm, w, ac);
             }
         } else {
             {   // classical Gram-Schmidt in FP64, as above

@@ -632,7 +632,7 @@ inline int tile_var_of(const DevView<R> &v, int64_t B) {
 // (N d^2 B < 2^31), every ADO range within its shared-memory budget.
 template <class R>
 inline bool tile_ok(const DevView<R> &v, int64_t B) {
-    if (B < 16 || B < v.tile_min_b || v.n_sets != 1 || v.n_ranges < 1) return false;
+    if (B < 16 || B < v.tile_min_b || v.n_sets != 1 || v.n_ranges < 1 || v.set_cap) return false;
     if (sizeof(R) == 4 && (B & 1)) return false;
     if ((double)v.N * v.d2 * (double)B >= 2147483647.0) return false;
     if (v.range_terms > kRangeTerms || v.range_slots > kRangeSlots) return false;

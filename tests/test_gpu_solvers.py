@@ -234,6 +234,31 @@ def test_dos_parameter_sets_shifted(heom):
         assert np.abs(A[j, idx] - Ao).max() < 1e-7 * np.abs(Ao).max(), j
 
 
+def test_dos_two_parameter_sets_shifted(heom):
+    """Two parameter sets (four Krylov processes, a column count the single-set persistent
+    Arnoldi would take): each set's A(w) against the oracle's sparse-LU DOS of that set, so a
+    solve that used one set's coefficients for every column fails."""
+    import torch
+    models = [W.siam_model(tier=2, U=u, mu=mu, eps=e) for u, mu, e in
+              ((10.0, 1.0, -5.0), (3.0, 0.2, -1.5))]
+    even = heom.build_hierarchy(heom.problem_from_model(models[0], 1))
+    _set_params_of(heom, even, models, 1)
+    odd = heom.build_hierarchy(heom.problem_from_model(models[0], -1))
+    _set_params_of(heom, odd, models, -1)
+    x = torch.zeros((even.n_ado, 4, 4, 2), dtype=torch.complex128, device="cuda")
+    heom.steady(even, x, tol=1e-10, max_iter=3000, prec=heom.FP64)
+    om = np.array([-9.0, -2.5, 0.0, 4.0, 11.0])
+    A, st, stats = heom.spectrum(odd, x, models[0].fermion_baths[0][0], om, tol=1e-9,
+                                 max_iter=1500, prec=heom.SHIFTED)
+    assert st == heom.OK and A.shape == (2, 5)
+    for j, m in enumerate(models):
+        prob = hy.model_to_problem(m)
+        h = hy.problem_hierarchy(prob)
+        Xo = so.steady_state(lv.build_matrix(prob, h), 4)
+        Ao = so.dos(lv.build_matrix(hy.model_to_problem(m, -1), h), Xo, m.fermion_baths[0][0], om)
+        assert np.abs(A[j] - Ao).max() < 1e-7 * np.abs(Ao).max(), j
+
+
 def test_current_matches_oracle(heom):
     """Lead currents from the tier-1 ADOs of GPU stationary states (one parameter set, then
     three biases batched as parameter sets) against the oracle's current of its own sparse-LU
