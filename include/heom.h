@@ -75,11 +75,14 @@ typedef enum {
     HEOM_FP32 = 1,   /* complex FP32 storage and arithmetic                            */
     HEOM_MIXED = 2,  /* solvers: FP32 inner Krylov solves inside FP64 iterative
                         refinement; FP64 residuals, dot products and normalisation      */
-    HEOM_SHIFTED = 3 /* heom_spectrum: one Arnoldi process per right-hand side serves
+    HEOM_SHIFTED = 3, /* heom_spectrum: one Arnoldi process per right-hand side serves
                         every frequency (the shifted systems share one Krylov space):
                         apply, Gram-Schmidt and rotation chains in float-float (about
                         48 significant bits), Hessenberg matrix, rotations and solutions
                         FP64; residual per frequency from its shifted Hessenberg problem */
+    HEOM_FP64_STRICT = 4 /* heom_steady: FP64 storage and arithmetic in every step, the
+                        single-column solve included (never the float-float persistent
+                        kernel): the plain reference path                                */
 } heom_prec;
 
 /* One bath = one coupling operator + its exponent list (Fig. 1b). */
@@ -306,8 +309,10 @@ heom_status heom_evolve_noalloc(heom_hier *h, void *ados, int64_t batch, double 
  * trace). x0: optional device warm start (complex128, NULL for a cold start); a column whose
  * x0 has a residual ||b - A x0|| above ||b|| starts from zero instead. x_out:
  * device complex128 [N][d][d][batch]. Converged when ||M x||_2 / ||x||_2 <= tol for x
- * normalised to Tr rho_sys = 1. prec: HEOM_FP64 (plain FP64 BiCGStab) or HEOM_MIXED
- * (FP32 BiCGStab corrections inside FP64 iterative refinement). stats: host array of
+ * normalised to Tr rho_sys = 1. prec: HEOM_FP64 (FP64 BiCGStab; a single column runs in one
+ * cooperative launch whose applies are float-float), HEOM_FP64_STRICT (FP64 BiCGStab, FP64
+ * applies everywhere) or HEOM_MIXED (FP32 BiCGStab corrections inside FP64 iterative
+ * refinement). stats: host array of
  * batch entries or NULL. Returns HEOM_ENOCONV if any column missed tol within max_iter
  * Krylov iterations. Synchronises s. */
 heom_status heom_steady(heom_hier *h, const void *x0, void *x_out, int64_t batch, double tol,
@@ -393,11 +398,24 @@ heom_status heom_set_tile_config(heom_hier *h, int ctas_per_sm, int variant);
  * s_q = +1 for nu = +1 and -1 for nu = -1 ((-1)^{delta_{nu,-}}). x: device complex128
  * [N][d][d][batch] stationary states of the even-parity hierarchy h (columns = parameter
  * sets or repeats); baths: host [n_baths] indices of the lead's baths in the order given
- * to heom_build_hierarchy; I_out: host [batch]. A conductance is the difference quotient of
- * currents at neighbouring biases (a batched stationary solve over the biases, then this
- * call). Synchronises s. */
+ * to heom_build_hierarchy; I_out: host [batch]. heom_conductance forms conductances from
+ * currents at neighbouring biases. Synchronises s. */
 heom_status heom_current(const heom_hier *h, const void *x, int64_t batch, const int *baths,
                          int n_baths, double *I_out, heom_stream s);
+
+/* Differential conductance G = dI_alpha / dPhi (Methods, electronic current; Example 1's
+ * conductance) as difference quotients over bias pairs: h holds 2 P parameter sets
+ * (heom_set_params), set 2k at bias Phi_k and set 2k + 1 at Phi_k + dphi[k] (the exponents of
+ * the leads follow the bias through their chemical potentials). One batched stationary solve
+ * of all 2 P sets (tol, max_iter, prec as heom_steady), the current of the lead made of
+ * `baths` for every set (as heom_current), then G_out[k] = (I_{2k+1} - I_{2k}) / dphi[k].
+ * dphi: host [P], finite and non-zero; G_out: host [P]; I_out: host [2 P] or NULL; stats:
+ * host [2 P] or NULL (the stationary solves). Allocates the 2 P stationary states for the call.
+ * Returns heom_steady's status (the quotients are still formed on HEOM_ENOCONV /
+ * HEOM_EBREAKDOWN: see stats). Synchronises s. */
+heom_status heom_conductance(heom_hier *h, const double *dphi, const int *baths, int n_baths,
+                             double tol, int max_iter, int prec, double *G_out, double *I_out,
+                             heom_solve_stats *stats, heom_stream s);
 
 /* ---------------------------------------------------------------- learned warm start */
 

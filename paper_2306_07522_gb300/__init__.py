@@ -24,7 +24,7 @@ _lib = C.CDLL(LIBRARY_PATH)
 # ------------------------------------------------------------------------- ABI types
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EBREAKDOWN, ENOTSUP, ETIMEOUT = range(8)
 BOSON_R, BOSON_I, BOSON_RI, FERMION = range(4)
-FP64, FP32, MIXED, SHIFTED = range(4)
+FP64, FP32, MIXED, SHIFTED, FP64_STRICT = range(5)
 KERNEL_CLASSES = ("apply", "rk4", "krylov_apply_fp32", "krylov_apply_fp64", "krylov_vector",
                   "residual_fp64", "other")
 APPLY_CLASSES = ("apply", "rk4", "krylov_apply_fp32", "krylov_apply_fp64", "residual_fp64")
@@ -86,6 +86,7 @@ _sig = {
                               _P, _P],
     "heom_current": [_P, _P, C.c_int64, _P, C.c_int, _P, _P],
     "heom_psd": [_P, _P, _P, _P, C.c_int64, C.c_double, C.c_int, _P, _P, _P],
+    "heom_conductance": [_P, _P, _P, C.c_int, C.c_double, C.c_int, C.c_int, _P, _P, _P, _P],
     "heom_autotune": [_P, C.c_int64, C.c_int, _P, _P, _P, _P, _P, _P],
     "heom_set_tile_config": [_P, C.c_int, C.c_int],
     "heom_mlp_create": [C.c_int, _P, C.c_uint64, C.POINTER(_P)],
@@ -588,6 +589,24 @@ def current(h: Hierarchy, x, baths, stream=None) -> np.ndarray:
     _check(_lib.heom_current(h.handle, _dptr(x), B, _ptr(idx), len(idx), _ptr(out), _stream(stream)),
            "heom_current")
     return out
+
+
+def conductance(h: Hierarchy, dphi, baths, tol: float = 1e-10, max_iter: int = 4000,
+                prec: int = FP64, stream=None, raise_on_error: bool = True):
+    """heom_conductance over bias pairs (sets 2k, 2k + 1 of h): returns (G [P], I [2 P],
+    status, stats)."""
+    d = np.ascontiguousarray(dphi, np.float64)
+    if d.shape != (h.n_sets // 2,) or h.n_sets % 2:
+        raise ValueError("dphi needs one entry per bias pair (n_sets / 2)")
+    idx = np.ascontiguousarray(baths, np.int32)
+    G = np.zeros(len(d))
+    I = np.zeros(h.n_sets)
+    stats = (SolveStats * h.n_sets)()
+    st = _lib.heom_conductance(h.handle, _ptr(d), _ptr(idx), len(idx), tol, max_iter, prec,
+                               _ptr(G), _ptr(I), C.cast(stats, C.c_void_p), _stream(stream))
+    if raise_on_error:
+        _check(st, "heom_conductance")
+    return G, I, st, _stats_list(stats)
 
 
 # ------------------------------------------------------------------------- launch accounting

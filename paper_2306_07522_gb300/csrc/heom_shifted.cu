@@ -640,7 +640,9 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
         // them within 60 % of the free device memory
         size_t free_b = 0, total_b = 0;
         if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
-            free_b += h->ws.bytes;  // the hierarchy's own workspace is reused (or grown)
+            // the hierarchy's own workspace is reused (or grown), or else the largest one the
+            // library keeps cached on this device
+            free_b += std::max(h->ws.bytes, ws_cached_max(h->device));
             const double per_step = 32.0 * (double)L + 88.0 * (double)S + 64.0 * (double)B;
             const double fixed = 64.0 * (double)L + 48.0 * (double)S + (double)(64 * 2 + 2) * B * 16.0;
             const double avail = 0.6 * (double)free_b - fixed;

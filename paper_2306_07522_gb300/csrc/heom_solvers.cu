@@ -834,7 +834,7 @@ template <class RI>
 heom_status refine_solve(heom_hier *h, const cx<double> *b64, cx<double> *x64, int64_t B,
                          const cx<double> *shift64, double aug, bool x_zero, double tol,
                          int max_iter, Solve &res, cudaStream_t s,
-                         const std::vector<int> *only = nullptr) {
+                         const std::vector<int> *only = nullptr, bool strict = false) {
     const int64_t rows = h->N * h->d2, L = rows * B;
     const size_t bytes = align_up(L * sizeof(cx<double>)) + align_up(15 * L * sizeof(cx<RI>)) +
                          2 * align_up(B * sizeof(cx<RI>));
@@ -935,7 +935,7 @@ heom_status refine_solve(heom_hier *h, const cx<double> *b64, cx<double> *x64, i
         const double inner_tol = plain ? std::max(0.5 * tol / worst, 1e-10) : 1e-4;
         inner_max = std::min(inner_max, plain ? kInnerCap64 : kInnerCap);
         SolveOut o;
-        if (B == 1 && persist_ok<RI>(h)) {
+        if (B == 1 && !strict && persist_ok<RI>(h)) {
             // one column: the whole BiCGStab solve is one cooperative launch
             o.iters.assign(1, 0);
             o.status.assign(1, HEOM_OK);
@@ -984,8 +984,9 @@ __global__ void k_zero_cols(int64_t total, cx<double> *x, int64_t B, const int *
 heom_status solve_system(heom_hier *h, const cx<double> *b64, cx<double> *x64, int64_t B,
                          const cx<double> *shift64, double aug, bool x_zero, double tol,
                          int max_iter, int prec, Solve &res, cudaStream_t s) {
-    if (prec != HEOM_MIXED)
-        return refine_solve<double>(h, b64, x64, B, shift64, aug, x_zero, tol, max_iter, res, s);
+    if (prec != HEOM_MIXED)  // HEOM_FP64_STRICT: no float-float persistent solve
+        return refine_solve<double>(h, b64, x64, B, shift64, aug, x_zero, tol, max_iter, res, s,
+                                    nullptr, prec == HEOM_FP64_STRICT);
     heom_status st = refine_solve<float>(h, b64, x64, B, shift64, aug, x_zero, tol, max_iter, res, s);
     if (st != HEOM_OK) return st;
     // columns whose FP32 corrections broke down (near-singular systems whose FP32 BiCGStab
@@ -1188,9 +1189,10 @@ extern "C" heom_status heom_steady(heom_hier *h, const void *x0, void *x_out, in
                                    double tol, int max_iter, int prec, heom_solve_stats *stats,
                                    heom_stream s) {
     if (!h || !x_out || batch < 1 || batch % h->n_sets != 0 || !(tol > 0) || max_iter < 1 ||
-        (prec != HEOM_FP64 && prec != HEOM_MIXED) || batch > 65535LL * 32 || h->parity != 1) {
+        (prec != HEOM_FP64 && prec != HEOM_MIXED && prec != HEOM_FP64_STRICT) ||
+        batch > 65535LL * 32 || h->parity != 1) {
         set_error("heom_steady: need an even-parity hierarchy, x_out, batch >= 1 (multiple of "
-                  "n_sets), tol > 0, max_iter >= 1, prec FP64 or MIXED");
+                  "n_sets), tol > 0, max_iter >= 1, prec FP64, FP64_STRICT or MIXED");
         return HEOM_EINVAL;
     }
     HEOM_DEVICE(h->device);
@@ -1594,4 +1596,37 @@ extern "C" heom_status heom_current(const heom_hier *h, const void *x, int64_t b
     dfree(buf);
     if (e != cudaSuccess) return cuda_fail(e, "heom_current");
     return HEOM_OK;
+}
+
+extern "C" heom_status heom_conductance(heom_hier *h, const double *dphi, const int *baths, int n_baths,
+                                        double tol, int max_iter, int prec, double *G_out, double *I_out,
+                                        heom_solve_stats *stats, heom_stream s) {
+    using namespace heom;
+    if (!h || !dphi || !G_out || h->n_sets < 2 || (h->n_sets & 1) || h->parity != 1) {
+        set_error("heom_conductance: need an even-parity hierarchy holding bias pairs (an even "
+                  "number >= 2 of parameter sets), dphi[n_sets / 2] and G_out");
+        return HEOM_EINVAL;
+    }
+    const int64_t B = h->n_sets, npair = B / 2;
+    for (int64_t k = 0; k < npair; ++k)
+        if (!(std::isfinite(dphi[k]) && dphi[k] != 0.0)) {
+            set_error("heom_conductance: dphi[%lld] must be finite and non-zero", (long long)k);
+            return HEOM_EINVAL;
+        }
+    HEOM_DEVICE(h->device);
+    DBuf xbuf;
+    heom_status st = dalloc(xbuf, (size_t)h->N * h->d2 * B * sizeof(cx<double>));
+    if (st != HEOM_OK) return st;
+    std::vector<heom_solve_stats> ss(B);
+    st = heom_steady(h, nullptr, xbuf.p, B, tol, max_iter, prec, ss.data(), s);
+    std::vector<double> I(B, 0.0);
+    const heom_status sc = (st == HEOM_OK || st == HEOM_ENOCONV || st == HEOM_EBREAKDOWN)
+                               ? heom_current(h, xbuf.p, B, baths, n_baths, I.data(), s)
+                               : st;
+    dfree(xbuf);
+    if (sc != HEOM_OK) return sc;
+    for (int64_t k = 0; k < npair; ++k) G_out[k] = (I[2 * k + 1] - I[2 * k]) / dphi[k];
+    if (I_out) for (int64_t b = 0; b < B; ++b) I_out[b] = I[b];
+    if (stats) for (int64_t b = 0; b < B; ++b) stats[b] = ss[b];
+    return st;
 }

@@ -359,3 +359,22 @@ def test_spectrum_batched_over_hierarchies_of_different_shapes(heom):
         Xo = so.steady_state(lv.build_matrix(prob, h), m.d)
         Ao = so.dos(lv.build_matrix(hy.model_to_problem(m, -1), h), Xo, m.fermion_baths[0][0], om)
         assert np.abs(As[i] - Ao).max() < 1e-8 * np.abs(Ao).max()
+
+
+def test_steady_fp64_strict_matches_oracle(heom):
+    """HEOM_FP64_STRICT (FP64 applies everywhere, no float-float persistent kernel): one column
+    and two columns against the oracle's sparse-LU stationary state, SIAM tier 2."""
+    import torch
+    m = W.siam_model(tier=2)
+    prob = hy.model_to_problem(m)
+    h = hy.problem_hierarchy(prob)
+    M = lv.build_matrix(prob, h)
+    Xo = so.steady_state(M, 4)
+    g = heom.build_hierarchy(heom.problem_from_model(m))
+    for shape in ((h.n_ado, 4, 4), (h.n_ado, 4, 4, 2)):
+        x = torch.zeros(shape, dtype=torch.complex128, device="cuda")
+        st, stats = heom.steady(g, x, tol=1e-10, max_iter=4000, prec=heom.FP64_STRICT)
+        assert st == heom.OK and all(s_["residual"] <= 1e-10 for s_ in stats)
+        X = x.cpu().numpy()
+        X = X if X.ndim == 3 else X[..., 1]
+        assert np.abs(X - Xo).max() < 1e-8 * np.abs(Xo).max()
