@@ -414,7 +414,6 @@ heom::DevView<double> heom_hier::view64() const {
     v.tile_var = tile_var;
     v.ado_tier = has_caps ? (const int32_t *)d_ado_tier.p : nullptr;
     v.set_cap = has_caps ? (const int32_t *)d_set_cap.p : nullptr;
-    v.act_sets = (has_caps && has_act) ? (const int32_t *)d_act_sets.p : nullptr;
     v.pers_ado = (const int32_t *)d_pers_ado.p; v.pers_ranges = pers_ranges;
     v.pers_terms = pers_terms; v.pers_slots = pers_slots; v.pers_ados = pers_ados;
     return v;
@@ -442,7 +441,6 @@ heom::DevView<float> heom_hier::view32() const {
     v.tile_var = tile_var;
     v.ado_tier = has_caps ? (const int32_t *)d_ado_tier.p : nullptr;
     v.set_cap = has_caps ? (const int32_t *)d_set_cap.p : nullptr;
-    v.act_sets = (has_caps && has_act) ? (const int32_t *)d_act_sets.p : nullptr;
     v.pers_ado = (const int32_t *)d_pers_ado.p; v.pers_ranges = pers_ranges;
     v.pers_terms = pers_terms; v.pers_slots = pers_slots; v.pers_ados = pers_ados;
     return v;
@@ -459,7 +457,7 @@ void free_all(heom_hier *h) {
                     &h->d_sdiag32, &h->d_tdval64, &h->d_floor64, &h->d_floor32, &h->ws,
                     &h->ws_small,
                     &h->d_t_ptr, &h->d_t_src, &h->d_t_val64, &h->d_t_val32, &h->d_cta_ado,
-                    &h->d_pers_ado, &h->d_ar_ado, &h->ws_pers, &h->d_ado_tier, &h->d_set_cap, &h->d_act_sets};
+                    &h->d_pers_ado, &h->d_ar_ado, &h->ws_pers, &h->d_ado_tier, &h->d_set_cap};
     for (DBuf *b : bufs) heom::dfree(*b);
 }
 
@@ -1147,7 +1145,6 @@ extern "C" heom_status heom_set_params(heom_hier *h, int n_sets, const heom_c64 
     // a new set count invalidates per-set truncation tiers
     h->has_caps = h->has_act = false;
     heom::dfree(h->d_set_cap);
-    heom::dfree(h->d_act_sets);
     return upload_params(h, n_sets, H, coef, rate);
 }
 
@@ -1160,7 +1157,6 @@ extern "C" heom_status heom_set_truncation(heom_hier *h, const int *tier_b, cons
     if (!tier_b && !tier_f) {  // remove
         h->has_caps = h->has_act = false;
         heom::dfree(h->d_set_cap);
-        heom::dfree(h->d_act_sets);
         return HEOM_OK;
     }
     if (!tier_b || !tier_f) {
@@ -1198,15 +1194,14 @@ extern "C" heom_status heom_set_truncation(heom_hier *h, const int *tier_b, cons
     for (int s = 1; s < h->n_sets; ++s)
         mono = mono && tier_b[s] <= tier_b[s - 1] && tier_f[s] <= tier_f[s - 1];
     h->has_act = false;
-    heom::dfree(h->d_act_sets);
-    if (mono) {  // per row (d2 rows per ADO), so kernels index it without a division
-        std::vector<int32_t> act((size_t)h->N * h->d2);
+    h->act_ado.clear();
+    if (mono) {
+        h->act_ado.resize(h->N);
         for (int64_t n = 0; n < h->N; ++n) {
             int k = 0;
             while (k < h->n_sets && (at[n] & 0xffff) <= tier_f[k] && (at[n] >> 16) <= tier_b[k]) ++k;
-            for (int e = 0; e < h->d2; ++e) act[(size_t)n * h->d2 + e] = k;
+            h->act_ado[n] = k;
         }
-        if ((st = upload(h->d_act_sets, act)) != HEOM_OK) return st;
         h->has_act = true;
     }
     HEOM_CUDA(cudaStreamSynchronize(0));

@@ -119,10 +119,6 @@ struct DevView {
     // and holds every other ADO at zero (the apply writes zero there).
     const int32_t *ado_tier;  // [N]
     const int32_t *set_cap;   // [n_sets]
-    // When the sets' truncation tiers do not increase from one set to the next, the sets that
-    // keep the ADO of row r (= r / d2) are sets 0 .. act_sets[r]-1, so the columns of a vector
-    // that can be nonzero in row r are a leading block (null otherwise).
-    const int32_t *act_sets;  // [N d2]
 };
 
 // Whether ADO n lies beyond the truncation of parameter set s.
@@ -192,7 +188,10 @@ struct heom_hier {
     int max_terms = 0, max_entries = 0;
     heom::DBuf d_cta_ado, d_pers_ado;
     heom::DBuf d_ado_tier, d_set_cap;    // per-set truncation (heom_set_truncation)
-    heom::DBuf d_act_sets;               // leading sets that keep each row's ADO (monotone caps)
+    // When the sets' truncation tiers do not increase from one set to the next, the sets that
+    // keep ADO n are sets 0 .. act_ado[n]-1 (has_act), so the columns of a vector that can be
+    // nonzero in its rows are a leading block.
+    std::vector<int32_t> act_ado;
     bool has_act = false;
     int64_t kept_rowsets = 0;            // sum over rows of the sets that keep the row's ADO
     bool has_caps = false;

@@ -25,17 +25,22 @@ namespace {
 
 constexpr int kDotThreads = 256;
 
-// Columns of a [rows][B] vector that can be nonzero in a row: with truncated parameter sets
-// ordered deepest first (heom_set_truncation), row r's are columns 0 .. act[r] * cps - 1 (cps
-// columns per set); the other entries of every Krylov vector are zero and the float-float
-// Gram-Schmidt kernels neither read nor write them. act = null: every column.
-struct ActCols {
-    const int32_t *act;
-    int64_t cps;
-    __device__ __forceinline__ bool on(int64_t row, int64_t b) const {
-        return !act || b < (int64_t)__ldg(act + row) * cps;
-    }
+// Work chunks of the float-float Gram-Schmidt kernels: rows row0 .. row1-1 of the [rows][B]
+// vectors, whose columns 0 .. acols-1 can be nonzero (acols < B where parameter sets are
+// truncated below the rows' ADOs, sets ordered deepest first; the other entries of every
+// Krylov vector are zero and no Gram-Schmidt kernel reads or writes them). In a chunk the
+// first T = (256 / acols) acols threads of a block each own one column, col = tid % acols,
+// and rows row0 + tid / acols, stepping by 256 / acols: only active entries get threads.
+struct GsChunk {
+    int32_t row0, row1, acols, pad;
 };
+
+__device__ __forceinline__ bool chunk_lane(const GsChunk &ch, int &col, int &rstep, int64_t &row) {
+    rstep = kDotThreads / ch.acols;
+    col = threadIdx.x % ch.acols;
+    row = ch.row0 + threadIdx.x / ch.acols;
+    return (int)threadIdx.x < rstep * ch.acols;
+}
 
 // Hessenberg matrices of all columns, column-major: entry (i, j) of column b's matrix at
 // Hb[(j (mmax + 1) + i) B + b], so that one Hessenberg column is contiguous.
@@ -106,82 +111,73 @@ __global__ void __launch_bounds__(kDotThreads) k_multidot(int64_t rows, int64_t 
     }
 }
 
-// wf[t] = split(w[t]); entries outside the active columns (ac) are left alone: only the
-// float-float Gram-Schmidt kernels read wf, and they skip the same entries.
+// wf[t] = split(w[t])
 __global__ void k_split(int64_t total, const cx<double> *__restrict__ w, float4 *__restrict__ wf) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x)
         wf[t] = ff_split(w[t]);
 }
-__global__ void k_split_act(int64_t total, int64_t B, const cx<double> *__restrict__ w,
-                            float4 *__restrict__ wf, ActCols ac) {
-    // the grid stride is a multiple of B (B divides the block): the column is fixed per thread
-    const int64_t t_first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x, b = t_first % B, rstep = stride / B;
-    int64_t row = t_first / B;
-    for (int64_t t = t_first; t < total; t += stride, row += rstep)
-        if (ac.on(row, b)) wf[t] = ff_split(w[t]);
+
+// wf = split(w) on the active entries of the chunks (blocks stride over the chunks)
+__global__ void __launch_bounds__(kDotThreads) k_split_chunks(int64_t B, const cx<double> *__restrict__ w,
+                                                              float4 *__restrict__ wf,
+                                                              const GsChunk *__restrict__ chunks, int nch) {
+    for (int c = blockIdx.x; c < nch; c += gridDim.x) {
+        const GsChunk ch = chunks[c];
+        int col, rstep;
+        int64_t row;
+        if (!chunk_lane(ch, col, rstep, row)) continue;
+        for (; row < ch.row1; row += rstep) {
+            const int64_t t = row * B + col;
+            wf[t] = ff_split(w[t]);
+        }
+    }
 }
 
-// Float-float partial dot products over a chunk of rows: part[c][i][b] = sum_{rows of chunk
-// c} conj(V_i[row][b]) w[row][b] (FP64 result), the basis vectors taken kMdTile at a time:
-// block (tile, chunk) reads its chunk of w once for the tile's basis vectors, with one
-// float-float accumulator pair per basis vector; the tile's loads of an element are
-// independent, so they are in flight together. B must be a power of two dividing the block
-// (checked by the caller), so every thread keeps one column. Entries outside the active
-// columns (ac) are neither read nor summed.
+// Float-float partial dot products over a chunk: part[c][i][b] = sum_{rows of chunk c}
+// conj(V_i[row][b]) w[row][b] (FP64 result; zero for the chunk's inactive columns), the basis
+// vectors taken kMdTile at a time: block (tile, chunk) reads its chunk of w once for the
+// tile's basis vectors, with one float-float accumulator pair per basis vector; the tile's
+// loads of an element are independent, so they are in flight together. Every thread sums its
+// own column's entries in a fixed order, and the per-column sum over the threads runs in a
+// fixed order too: the result is deterministic.
 constexpr int kMdTile = 8;
-__global__ void __launch_bounds__(kDotThreads) k_multidot_ff_tiled(int64_t rows, int64_t B, int nv,
+__global__ void __launch_bounds__(kDotThreads) k_multidot_ff_tiled(int64_t B, int nv,
                                                                    const float4 *__restrict__ Vf,
                                                                    int64_t vstride,
                                                                    const float4 *__restrict__ wf,
                                                                    cx<double> *__restrict__ part,
-                                                                   const int *__restrict__ skip, ActCols ac) {
+                                                                   const int *__restrict__ skip,
+                                                                   const GsChunk *__restrict__ chunks) {
     if (skip && *skip) return;
-    const int i0 = blockIdx.x * kMdTile, c = blockIdx.y, nc = gridDim.y;
+    const int i0 = blockIdx.x * kMdTile, c = blockIdx.y;
     const int nt = min(kMdTile, nv - i0);
-    const int64_t L = rows * B;
-    const int64_t t0 = L * c / nc, t1 = L * (c + 1) / nc;
+    const GsChunk ch = chunks[c];
     __shared__ double sre[kMdTile][kDotThreads], sim[kMdTile][kDotThreads];
-    const int64_t tb = t0 - t0 % B;
-    // B divides the block: this thread's column is tid % B, its row advances by kDotThreads / B
-    const int64_t cb = threadIdx.x % B, rstep = kDotThreads / B;
-    int64_t row = (tb + threadIdx.x) / B;
     float rh[kMdTile], rl[kMdTile], ih[kMdTile], il[kMdTile];
 #pragma unroll
     for (int k = 0; k < kMdTile; ++k) rh[k] = rl[k] = ih[k] = il[k] = 0.f;
     const float4 *V0 = Vf + (int64_t)i0 * vstride;
-    // the active column counts of the chunk's rows, staged in shared memory 1,024 rows at a
-    // time, so that no element's loads wait on a load of its row's count
-    __shared__ int s_act[1024];
-    const int64_t r_first = tb / B, r_end = (t1 + B - 1) / B;
-    for (int64_t ra = r_first; ra < r_end; ra += 1024) {
-        const int64_t rb = min(r_end, ra + 1024);
-        if (ac.act) {
-            __syncthreads();
-            for (int64_t r = ra + threadIdx.x; r < rb; r += kDotThreads)
-                s_act[r - ra] = (int)(__ldg(ac.act + r) * ac.cps);
-            __syncthreads();
-        }
-        int64_t t = ra * B + threadIdx.x;
-        row = ra + threadIdx.x / B;
-    for (; t < rb * B && t < t1; t += kDotThreads, row += rstep) {
-        if (t < t0 || (ac.act && cb >= s_act[row - ra])) continue;
-        const float4 x = wf[t];
-        float4 a[kMdTile];
+    int col, rstep;
+    int64_t row;
+    if (chunk_lane(ch, col, rstep, row)) {
+        for (; row < ch.row1; row += rstep) {
+            const int64_t t = row * B + col;
+            const float4 x = wf[t];
+            float4 a[kMdTile];
 #pragma unroll
-        for (int k = 0; k < kMdTile; ++k)
-            if (k < nt) a[k] = V0[(int64_t)k * vstride + t];
+            for (int k = 0; k < kMdTile; ++k)
+                if (k < nt) a[k] = V0[(int64_t)k * vstride + t];
 #pragma unroll
-        for (int k = 0; k < kMdTile; ++k) {
-            if (k < nt) {  // conj(a) x
-                ff_mac(rh[k], rl[k], a[k].x, a[k].z, x.x, x.z);
-                ff_mac(rh[k], rl[k], a[k].y, a[k].w, x.y, x.w);
-                ff_mac(ih[k], il[k], a[k].x, a[k].z, x.y, x.w);
-                ff_mac(ih[k], il[k], -a[k].y, -a[k].w, x.x, x.z);
+            for (int k = 0; k < kMdTile; ++k) {
+                if (k < nt) {  // conj(a) x
+                    ff_mac(rh[k], rl[k], a[k].x, a[k].z, x.x, x.z);
+                    ff_mac(rh[k], rl[k], a[k].y, a[k].w, x.y, x.w);
+                    ff_mac(ih[k], il[k], a[k].x, a[k].z, x.y, x.w);
+                    ff_mac(ih[k], il[k], -a[k].y, -a[k].w, x.x, x.z);
+                }
             }
         }
-    }
     }
 #pragma unroll
     for (int k = 0; k < kMdTile; ++k) {
@@ -189,65 +185,64 @@ __global__ void __launch_bounds__(kDotThreads) k_multidot_ff_tiled(int64_t rows,
         sim[k][threadIdx.x] = (double)ih[k] + (double)il[k];
     }
     __syncthreads();
-    for (int st = kDotThreads >> 1; st >= B; st >>= 1) {
-        if (threadIdx.x < st)
-#pragma unroll
-            for (int k = 0; k < kMdTile; ++k) {
-                sre[k][threadIdx.x] += sre[k][threadIdx.x + st];
-                sim[k][threadIdx.x] += sim[k][threadIdx.x + st];
-            }
-        __syncthreads();
-    }
-    if (threadIdx.x < B)
-        for (int k = 0; k < nt; ++k)
-            part[((int64_t)c * nv + i0 + k) * B + threadIdx.x] =
-                cx<double>{sre[k][threadIdx.x], sim[k][threadIdx.x]};
-}
-
-// wf[row][b] -= sum_i V_i[row][b] h_i[b] in float-float (hf = split h)
-__global__ void k_gs_update_ff(int64_t rows, int64_t B, int nv, const float4 *__restrict__ Vf,
-                               int64_t vstride, const float4 *__restrict__ hf,
-                               float4 *__restrict__ wf, const int *__restrict__ skip, ActCols ac) {
-    if (skip && *skip) return;
-    const int64_t total = rows * B;
-    // the grid stride is a multiple of B (B divides the block): the column is fixed per thread
-    const int64_t t_first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x, b = t_first % B, rstep = stride / B;
-    int64_t row = t_first / B;
-    // the next element's active count is loaded one element ahead
-    int64_t act_next = (ac.act && t_first < total) ? (int64_t)__ldg(ac.act + row) * ac.cps : B;
-    for (int64_t t = t_first; t < total; t += stride, row += rstep) {
-        const int64_t act_here = act_next;
-        if (ac.act && t + stride < total) act_next = (int64_t)__ldg(ac.act + row + rstep) * ac.cps;
-        if (b >= act_here) continue;
-        const float4 w0 = wf[t];
-        float rh = w0.x, rl = w0.z, ih = w0.y, il = w0.w;
-        for (int i = 0; i < nv; ++i) {
-            const float4 h = hf[(int64_t)i * B + b];
-            const float4 v = Vf[(int64_t)i * vstride + t];
-            // -= v h: re -= v.re h.re - v.im h.im, im -= v.re h.im + v.im h.re
-            ff_mac(rh, rl, -v.x, -v.z, h.x, h.z);
-            ff_mac(rh, rl, v.y, v.w, h.y, h.w);
-            ff_mac(ih, il, -v.x, -v.z, h.y, h.w);
-            ff_mac(ih, il, -v.y, -v.w, h.x, h.z);
+    if (threadIdx.x < B) {
+        const int per = kDotThreads / ch.acols;
+        for (int k = 0; k < nt; ++k) {
+            double re = 0.0, im = 0.0;
+            if ((int)threadIdx.x < ch.acols)
+                for (int q = 0; q < per; ++q) {
+                    re += sre[k][threadIdx.x + q * ch.acols];
+                    im += sim[k][threadIdx.x + q * ch.acols];
+                }
+            part[((int64_t)c * nv + i0 + k) * B + threadIdx.x] = cx<double>{re, im};
         }
-        ff_norm(rh, rl);
-        ff_norm(ih, il);
-        wf[t] = make_float4(rh, ih, rl, il);
     }
 }
 
-// Partial squared column norms (FP64) of a float-float vector over a chunk of rows.
-__global__ void __launch_bounds__(kDotThreads) k_colnorm_part_ff(int64_t rows, int64_t B,
-                                                                 const float4 *__restrict__ wf,
-                                                                 double *__restrict__ part, ActCols ac) {
-    const int c = blockIdx.x, nc = gridDim.x;
+// wf[row][b] -= sum_i V_i[row][b] h_i[b] in float-float (hf = split h), on the active
+// entries of the chunks (blocks stride over the chunks)
+__global__ void __launch_bounds__(kDotThreads) k_gs_update_ff(int64_t B, int nv, const float4 *__restrict__ Vf,
+                                                              int64_t vstride, const float4 *__restrict__ hf,
+                                                              float4 *__restrict__ wf, const int *__restrict__ skip,
+                                                              const GsChunk *__restrict__ chunks, int nch) {
+    if (skip && *skip) return;
+    for (int c = blockIdx.x; c < nch; c += gridDim.x) {
+        const GsChunk ch = chunks[c];
+        int col, rstep;
+        int64_t row;
+        if (!chunk_lane(ch, col, rstep, row)) continue;
+        for (; row < ch.row1; row += rstep) {
+            const int64_t t = row * B + col;
+            const float4 w0 = wf[t];
+            float rh = w0.x, rl = w0.z, ih = w0.y, il = w0.w;
+            for (int i = 0; i < nv; ++i) {
+                const float4 h = hf[(int64_t)i * B + col];
+                const float4 v = Vf[(int64_t)i * vstride + t];
+                // -= v h: re -= v.re h.re - v.im h.im, im -= v.re h.im + v.im h.re
+                ff_mac(rh, rl, -v.x, -v.z, h.x, h.z);
+                ff_mac(rh, rl, v.y, v.w, h.y, h.w);
+                ff_mac(ih, il, -v.x, -v.z, h.y, h.w);
+                ff_mac(ih, il, -v.y, -v.w, h.x, h.z);
+            }
+            ff_norm(rh, rl);
+            ff_norm(ih, il);
+            wf[t] = make_float4(rh, ih, rl, il);
+        }
+    }
+}
+
+// Partial squared column norms (FP64) of a float-float vector over a chunk: part[c][b];
+// grid (chunk, b); zero for the chunk's inactive columns.
+__global__ void __launch_bounds__(kDotThreads) k_colnorm_part_ff(int64_t B, const float4 *__restrict__ wf,
+                                                                 double *__restrict__ part,
+                                                                 const GsChunk *__restrict__ chunks) {
+    const int c = blockIdx.x;
     const int64_t b = blockIdx.y;
-    const int64_t r0 = rows * c / nc, r1 = rows * (c + 1) / nc;
+    const GsChunk ch = chunks[c];
     __shared__ double sh[kDotThreads];
     double acc = 0.0;
-    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x)
-        if (ac.on(r, b)) acc += norm2(ff_join(wf[r * B + b]));
+    if (b < ch.acols)
+        for (int64_t r = ch.row0 + threadIdx.x; r < ch.row1; r += blockDim.x) acc += norm2(ff_join(wf[r * B + b]));
     sh[threadIdx.x] = acc;
     __syncthreads();
     for (int k = blockDim.x >> 1; k > 0; k >>= 1) {
@@ -258,19 +253,24 @@ __global__ void __launch_bounds__(kDotThreads) k_colnorm_part_ff(int64_t rows, i
 }
 
 // v = w / nrm[b] in FP64 (for the apply) and its float-float split (for Gram-Schmidt); in
-// place on wf. nrm = 0 leaves zeros (exact invariant subspace).
-__global__ void k_scale_ff(int64_t total, int64_t B, float4 *__restrict__ wf,
-                           const double *__restrict__ nrm, cx<double> *__restrict__ v, ActCols ac) {
-    // the grid stride is a multiple of B (B divides the block): the column is fixed per thread
-    const int64_t t_first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x, b = t_first % B, rstep = stride / B;
-    int64_t row = t_first / B;
-    const double n = b < B ? nrm[b] : 0.0;
-    for (int64_t t = t_first; t < total; t += stride, row += rstep) {
-        if (!ac.on(row, b)) continue;  // zero in v and wf already
-        const cx<double> x = n > 0.0 ? (1.0 / n) * ff_join(wf[t]) : cx<double>{0.0, 0.0};
-        v[t] = x;
-        wf[t] = ff_split(x);
+// place on wf, on the active entries of the chunks (the others stay zero in v). nrm = 0
+// leaves zeros (exact invariant subspace).
+__global__ void __launch_bounds__(kDotThreads) k_scale_ff(int64_t B, float4 *__restrict__ wf,
+                                                          const double *__restrict__ nrm,
+                                                          cx<double> *__restrict__ v,
+                                                          const GsChunk *__restrict__ chunks, int nch) {
+    for (int c = blockIdx.x; c < nch; c += gridDim.x) {
+        const GsChunk ch = chunks[c];
+        int col, rstep;
+        int64_t row;
+        if (!chunk_lane(ch, col, rstep, row)) continue;
+        const double n = nrm[col];
+        for (; row < ch.row1; row += rstep) {
+            const int64_t t = row * B + col;
+            const cx<double> x = n > 0.0 ? (1.0 / n) * ff_join(wf[t]) : cx<double>{0.0, 0.0};
+            v[t] = x;
+            wf[t] = ff_split(x);
+        }
     }
 }
 
@@ -668,14 +668,37 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
                  oy = take((size_t)S * mmax * 16), ocb = take((size_t)S * mmax * 16),
                  ox0 = take((size_t)S * d2 * 16), ores = take((size_t)S * 8),
                  osh = take((size_t)S * 16), oco = take((size_t)S * 4);
-    // row chunks of the partial dot products: enough blocks to fill the GPU (three per SM) with
-    // one tile of basis vectors
+    // row chunks of the FP64 partial dot products
     const int nchunk = (int)std::max<int64_t>(1, std::min<int64_t>(456, L / 4096));
-    const size_t opart = take((size_t)nchunk * (mmax + 2) * B * 16), oskip = take(sizeof(int));
-    const size_t onp = take((size_t)nchunk * B * 8);
-    // float-float Gram-Schmidt (B a power of two up to the block size): a split copy of the
-    // basis and of h
-    const bool ffgs = B <= kDotThreads && (kDotThreads % B) == 0;
+    // float-float Gram-Schmidt (B up to the block size): a split copy of the basis and of h,
+    // and its work chunks -- runs of ADOs whose rows have the same active columns (all B
+    // unless parameter sets are truncated deepest first), cut into pieces of about
+    // 1/456 of the active entries so that one tile of basis vectors fills the GPU
+    const bool ffgs = B <= kDotThreads;
+    std::vector<GsChunk> chunks;
+    int64_t act_total = 0;
+    if (ffgs) {
+        const int64_t cps = B / h->n_sets;
+        auto acols_of = [&](int64_t n) { return h->has_act ? (int)(h->act_ado[n] * cps) : (int)B; };
+        for (int64_t n = 0; n < h->N; ++n) act_total += (int64_t)d2 * acols_of(n);
+        const int64_t target = std::max<int64_t>(4096, act_total / 456);
+        for (int64_t n = 0; n < h->N;) {
+            const int a = acols_of(n);
+            int64_t n1 = n;
+            while (n1 < h->N && acols_of(n1) == a) ++n1;
+            if (a > 0) {
+                const int64_t r0 = n * d2, r1 = n1 * d2, step = std::max<int64_t>(1, target / a);
+                for (int64_t r = r0; r < r1; r += step)
+                    chunks.push_back(GsChunk{(int32_t)r, (int32_t)std::min(r1, r + step), a, 0});
+            }
+            n = n1;
+        }
+    }
+    const int nch = (int)chunks.size();
+    const int npc = std::max(nchunk, nch);
+    const size_t opart = take((size_t)npc * (mmax + 2) * B * 16), oskip = take(sizeof(int));
+    const size_t onp = take((size_t)npc * B * 8);
+    const size_t och = take((size_t)std::max(nch, 1) * sizeof(GsChunk));
     const size_t oVf = ffgs ? take((size_t)(mmax + 1) * L * 16) : 0,
                  ohf = ffgs ? take((size_t)(mmax + 2) * B * 16) : 0;
     // every shift's triangular factor (strict upper part) for the final solve, for up to mp
@@ -728,12 +751,14 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
     }
     const DevView<double> v = h->view64();
     const bool tiled = tile_ok(v, B);
-    const ActCols ac{v.act_sets, v.act_sets ? B / h->n_sets : 0};
+    const GsChunk *dch = (const GsChunk *)(base + och);
+    if (nch > 0) HEOM_CUDA(memcpy_counted((void *)dch, chunks.data(), nch * sizeof(GsChunk), cudaMemcpyHostToDevice, s));
+    const int gsb = std::max(1, std::min(nch, 152 * 8));  // blocks of the chunk-striding kernels
     // elements of one vector that can be nonzero (truncated sets: the kept rows of each
     // column), and the ADO-applies of one apply: the work and the algorithmic bytes counted
     const int64_t cps = B / h->n_sets;
     const double Lk = h->has_caps ? (double)h->kept_rowsets * cps : (double)L;
-    const double Lg = ac.act ? Lk : (double)L;  // what the Gram-Schmidt kernels stream
+    const double Lg = ffgs ? (double)act_total : (double)L;  // what the Gram-Schmidt kernels stream
     TileArgs<double> ta{};
     ta.v = v;
     ta.B = B;
@@ -771,29 +796,29 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
                 // itself), from which k_reorth_flag decides on the device whether pass 2 runs
                 Prof pr(HEOM_KC_KRYLOV_VECTOR, s, (double)(j + 1) * Lg, (2.0 * (j + 1) + 5.0) * Lg * 16);
                 pr.kernels = 5;
-                k_split_act<<<blocks_for(L), 256, 0, s>>>(L, B, w, wf, ac);
-                k_multidot_ff_tiled<<<dim3((unsigned)((j + 2 + kMdTile - 1) / kMdTile), (unsigned)nchunk),
-                                      kDotThreads, 0, s>>>(rows, B, j + 2, Vf, L, wf, part, nullptr, ac);
-                k_reduce_h<<<blocks_for((int64_t)(j + 2) * B), 256, 0, s>>>(nchunk, j + 2, j + 1, B, part, ht,
+                k_split_chunks<<<gsb, kDotThreads, 0, s>>>(B, w, wf, dch, nch);
+                k_multidot_ff_tiled<<<dim3((unsigned)((j + 2 + kMdTile - 1) / kMdTile), (unsigned)nch),
+                                      kDotThreads, 0, s>>>(B, j + 2, Vf, L, wf, part, nullptr, dch);
+                k_reduce_h<<<blocks_for((int64_t)(j + 2) * B), 256, 0, s>>>(nch, j + 2, j + 1, B, part, ht,
                                                                            hft, Hb, j, mmax, nullptr);
                 k_reorth_flag<<<1, 128, 0, s>>>(j + 1, B, ht, dskip);
-                k_gs_update_ff<<<blocks_for(L), 256, 0, s>>>(rows, B, j + 1, Vf, L, hft, wf, nullptr, ac);
+                k_gs_update_ff<<<gsb, kDotThreads, 0, s>>>(B, j + 1, Vf, L, hft, wf, nullptr, dch, nch);
             }
             {   // pass 2 (skipped on the device when pass 1 kept enough of w)
                 Prof pr(HEOM_KC_KRYLOV_VECTOR, s, 0.0, 0.0);
                 pr.kernels = 3;
-                k_multidot_ff_tiled<<<dim3((unsigned)((j + 1 + kMdTile - 1) / kMdTile), (unsigned)nchunk),
-                                      kDotThreads, 0, s>>>(rows, B, j + 1, Vf, L, wf, part, dskip, ac);
-                k_reduce_h<<<blocks_for((int64_t)(j + 1) * B), 256, 0, s>>>(nchunk, j + 1, j + 1, B, part, ht,
+                k_multidot_ff_tiled<<<dim3((unsigned)((j + 1 + kMdTile - 1) / kMdTile), (unsigned)nch),
+                                      kDotThreads, 0, s>>>(B, j + 1, Vf, L, wf, part, dskip, dch);
+                k_reduce_h<<<blocks_for((int64_t)(j + 1) * B), 256, 0, s>>>(nch, j + 1, j + 1, B, part, ht,
                                                                            hft, Hb, j, mmax, dskip);
-                k_gs_update_ff<<<blocks_for(L), 256, 0, s>>>(rows, B, j + 1, Vf, L, hft, wf, dskip, ac);
+                k_gs_update_ff<<<gsb, kDotThreads, 0, s>>>(B, j + 1, Vf, L, hft, wf, dskip, dch, nch);
             }
             {   // h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j} (FP64 and split)
                 Prof pr(HEOM_KC_KRYLOV_VECTOR, s, Lg, 4.0 * Lg * 16);
                 pr.kernels = 3;
-                k_colnorm_part_ff<<<dim3((unsigned)nchunk, (unsigned)B), kDotThreads, 0, s>>>(rows, B, wf, npart, ac);
-                k_colnorm_fin<<<blocks_for(B), 256, 0, s>>>(nchunk, B, npart, nrm, Hb, j, mmax);
-                k_scale_ff<<<blocks_for(L), 256, 0, s>>>(L, B, wf, nrm, w, ac);
+                k_colnorm_part_ff<<<dim3((unsigned)nch, (unsigned)B), kDotThreads, 0, s>>>(B, wf, npart, dch);
+                k_colnorm_fin<<<blocks_for(B), 256, 0, s>>>(nch, B, npart, nrm, Hb, j, mmax);
+                k_scale_ff<<<gsb, kDotThreads, 0, s>>>(B, wf, nrm, w, dch, nch);
             }
         } else {
             {   // classical Gram-Schmidt in FP64, as above
