@@ -703,6 +703,45 @@ def run_apply_only(args):
                       "autotune": tune}))
 
 
+def run_spectra_only(args):
+    """Profiling case of the batched-spectra step: the first --sets of the 64 drawn sets (deepest
+    first), --n-omega frequencies, at most --max-iter Arnoldi steps; --steps steps after
+    --warmup, timed with CUDA events."""
+    import numpy as np
+    import torch
+
+    import paper_2306_07522_gb300 as heom
+    import workloads as W
+    draws = c3_draws()
+    # the first sets of each tier, deepest first, so every tier is present
+    pick = sorted([d for t in (4, 3, 2) for d in [x for x in draws if x["tier"] == t][:max(1, args.sets // 3)]],
+                  key=lambda d: -d["tier"])[:args.sets]
+    models = c3_models(pick)
+    even, odd = c3_build(heom, pick, models)
+    om = np.asarray(W.omega_grid(args.n_omega))
+    dop = models[0].fermion_baths[0][0]
+    x = torch.zeros((even.n_ado, 4, 4, len(pick)), dtype=torch.complex128, device="cuda")
+
+    def step():
+        heom.steady(even, x, tol=TOL, max_iter=4000, prec=heom.MIXED, raise_on_error=False)
+        return heom.spectrum(odd, x, dop, om, tol=TOL, max_iter=args.max_iter, prec=heom.SHIFTED,
+                             raise_on_error=False)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        A, st, stats = step()
+    b.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"case": "batched spectra (profiling)", "sets": len(pick),
+                      "tiers": [d["tier"] for d in pick], "n_omega": len(om),
+                      "arnoldi_steps": stats[0]["iterations"], "status": st,
+                      "ms_per_step": round(a.elapsed_time(b) / max(args.steps, 1), 2)}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -711,13 +750,19 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--quick", action="store_true",
                     help="timed steps only (no plain-path, e2e or CPU-baseline legs)")
-    ap.add_argument("--only", choices=["apply"], default=None,
-                    help="kernel micro-benchmark (for profiling) instead of the step benchmark")
+    ap.add_argument("--only", choices=["apply", "spectra"], default=None,
+                    help="profiling cases: the apply alone, or a reduced batched-spectra step")
+    ap.add_argument("--sets", type=int, default=8, help="--only spectra: parameter sets")
+    ap.add_argument("--n-omega", type=int, default=256, help="--only spectra: frequencies")
+    ap.add_argument("--max-iter", type=int, default=2000, help="--only spectra: Arnoldi steps")
     ap.add_argument("--batch", type=int, default=2000)
     ap.add_argument("--prec", choices=["fp32", "fp64"], default="fp32")
     args = ap.parse_args()
     if args.only == "apply":
         run_apply_only(args)
+        return
+    if args.only == "spectra":
+        run_spectra_only(args)
         return
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -467,6 +467,21 @@ heom_status heom_warm_start_features(const heom_hier *h, const void *x, int64_t 
 heom_status heom_warm_start(const heom_hier *h, heom_mlp *net, const float *params, int64_t n_sets,
                             void *x_out, heom_stream s);
 
+/* Selected elements as features: f (device FP32 [n_sets][2 n_elems]) holds Re and Im of
+ * element elems[k] (device int64 [n_elems], flat indices n d^2 + r d + c of the ADO vector) of
+ * every column of x (device complex128 [N][d][d][n_sets]). A network that predicts them can
+ * cover whole ADO vectors: the elements a caller lists are those that vary over its training
+ * states (the others vanish in every state, by the symmetry of the model). Synchronises s. */
+heom_status heom_gather_elements(const heom_hier *h, const void *x, int64_t n_sets,
+                                 const int64_t *elems, int64_t n_elems, float *f, heom_stream s);
+/* x_out (device complex128 [N][d][d][n_sets]) = the network's prediction for the parameter
+ * rows params (device FP32 [n_sets][n_in]) written to the listed elements (layout as
+ * heom_gather_elements; the network has 2 n_elems outputs), every other element zero: a
+ * whole-vector warm start for heom_steady. Synchronises s. */
+heom_status heom_warm_start_elements(const heom_hier *h, heom_mlp *net, const float *params,
+                                     int64_t n_sets, const int64_t *elems, int64_t n_elems,
+                                     void *x_out, heom_stream s);
+
 /* ---------------------------------------------------------------- launch accounting */
 
 /* Measurement support for benchmarks; the paper has no counterpart. While enabled, every

@@ -99,6 +99,8 @@ _sig = {
     "heom_mlp_train_step": [_P, _P, _P, C.c_int64, C.c_float, _P, _P],
     "heom_warm_start_features": [_P, _P, C.c_int64, _P, C.c_int, _P],
     "heom_warm_start": [_P, _P, _P, C.c_int64, _P, _P],
+    "heom_gather_elements": [_P, _P, C.c_int64, _P, C.c_int64, _P, _P],
+    "heom_warm_start_elements": [_P, _P, _P, C.c_int64, _P, C.c_int64, _P, _P],
     "heom_release_workspace_cache": [],
     "heom_profile_enable": [C.c_int],
     "heom_profile_read": [C.c_int, _P, _P, _P, _P],
@@ -737,4 +739,29 @@ def warm_start(h: "Hierarchy", net: Mlp, params, x_out, stream=None):
         raise ValueError("params must have one row per column of x_out")
     _check(_lib.heom_warm_start(h.handle, net.handle, _dptr(params), n_sets, _dptr(x_out),
                                 _stream(stream)), "heom_warm_start")
+    return x_out
+
+
+def gather_elements(h: Hierarchy, x, elems, stream=None):
+    """Features (torch float32 [n_sets][2 n_elems]) of the listed elements (torch int64, CUDA)
+    of states x (N, d, d[, n_sets], complex128)."""
+    import torch
+    _need_c128(x, "x")
+    n_sets = _batch_of(h, x)
+    f = torch.empty((n_sets, 2 * elems.numel()), dtype=torch.float32, device=x.device)
+    _check(_lib.heom_gather_elements(h.handle, _dptr(x), n_sets, _dptr(elems), elems.numel(),
+                                     _dptr(f), _stream(stream)), "heom_gather_elements")
+    return f
+
+
+def warm_start_elements(h: Hierarchy, net: Mlp, params, elems, x_out, stream=None):
+    """x_out (N, d, d[, n_sets], complex128) = net's prediction for params on the listed
+    elements, zero elsewhere."""
+    _need_c128(x_out, "x_out")
+    n_sets = _batch_of(h, x_out)
+    if params.shape[0] != n_sets:
+        raise ValueError("params must have one row per column of x_out")
+    _check(_lib.heom_warm_start_elements(h.handle, net.handle, _dptr(params), n_sets, _dptr(elems),
+                                         elems.numel(), _dptr(x_out), _stream(stream)),
+           "heom_warm_start_elements")
     return x_out

@@ -619,3 +619,88 @@ extern "C" heom_status heom_warm_start(const heom_hier *h, heom_mlp *net, const 
     heom::dfree(y);
     return r;
 }
+
+// ------------------------------------------------------------------ selected elements
+namespace heom {
+namespace {
+// f[s][2k], f[s][2k+1] = Re, Im of element elems[k] of column s (to_x = 0), or the reverse
+// (to_x = 1: x already zeroed by the caller)
+__global__ void k_elements(int64_t n_sets, const int64_t *__restrict__ elems, int64_t n_el,
+                           cx<double> *__restrict__ x, float *__restrict__ f, int to_x) {
+    const int64_t total = n_sets * n_el;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = i / n_el, k = i - s * n_el;
+        const int64_t e = elems[k] * n_sets + s;
+        float *fp = f + s * 2 * n_el + 2 * k;
+        if (to_x) {
+            x[e] = cx<double>{(double)fp[0], (double)fp[1]};
+        } else {
+            fp[0] = (float)x[e].re;
+            fp[1] = (float)x[e].im;
+        }
+    }
+}
+
+heom_status elements_call(const heom_hier *h, void *x, const int64_t *elems, int64_t n_el, float *f,
+                          int64_t n_sets, int to_x, cudaStream_t st, const char *who) {
+    std::vector<int64_t> he((size_t)n_el);
+    HEOM_CUDA(memcpy_counted(he.data(), elems, (size_t)n_el * 8, cudaMemcpyDeviceToHost, st));
+    HEOM_CUDA(cudaStreamSynchronize(st));
+    const int64_t total = h->N * h->d2;
+    for (int64_t k = 0; k < n_el; ++k)
+        if (he[k] < 0 || he[k] >= total) {
+            set_error("%s: element index %lld outside [0, N d^2 = %lld)", who, (long long)he[k], (long long)total);
+            return HEOM_EINVAL;
+        }
+    Prof pr(HEOM_KC_OTHER, st, (double)n_sets * n_el);
+    k_elements<<<nblk(n_sets * n_el), 256, 0, st>>>(n_sets, elems, n_el, (cx<double> *)x, f, to_x);
+    HEOM_CUDA(cudaGetLastError());
+    HEOM_CUDA(cudaStreamSynchronize(st));
+    return HEOM_OK;
+}
+}  // namespace
+}  // namespace heom
+
+extern "C" heom_status heom_gather_elements(const heom_hier *h, const void *x, int64_t n_sets,
+                                            const int64_t *elems, int64_t n_elems, float *f,
+                                            heom_stream s) {
+    if (!h || !x || !elems || !f || n_sets < 1 || n_elems < 1) {
+        set_error("heom_gather_elements: need a hierarchy, x, elems[n_elems >= 1], f and n_sets >= 1");
+        return HEOM_EINVAL;
+    }
+    HEOM_DEVICE(h->device);
+    return heom::elements_call(h, const_cast<void *>(x), elems, n_elems, f, n_sets, 0, (cudaStream_t)s,
+                               "heom_gather_elements");
+}
+
+extern "C" heom_status heom_warm_start_elements(const heom_hier *h, heom_mlp *net, const float *params,
+                                                int64_t n_sets, const int64_t *elems, int64_t n_elems,
+                                                void *x_out, heom_stream s) {
+    if (!h || !net || !params || !elems || !x_out || n_sets < 1 || n_elems < 1) {
+        set_error("heom_warm_start_elements: need a hierarchy, a network, params, elems[n_elems >= 1], "
+                  "x_out and n_sets >= 1");
+        return HEOM_EINVAL;
+    }
+    const int nf = net->width[net->n_layers];
+    if ((int64_t)nf != 2 * n_elems) {
+        set_error("heom_warm_start_elements: the network has %d outputs, 2 n_elems = %lld needed", nf,
+                  (long long)(2 * n_elems));
+        return HEOM_EINVAL;
+    }
+    HEOM_DEVICE(h->device);
+    cudaStream_t st = (cudaStream_t)s;
+    heom::DBuf y;
+    heom_status r = heom::dalloc(y, (size_t)n_sets * nf * 4);
+    if (r != HEOM_OK) return r;
+    if ((r = heom_mlp_forward(net, params, (float *)y.p, n_sets, s)) != HEOM_OK) { heom::dfree(y); return r; }
+    const size_t bytes = (size_t)h->N * h->d2 * n_sets * sizeof(heom::cx<double>);
+    if (cudaMemsetAsync(x_out, 0, bytes, st) != cudaSuccess) {
+        heom::dfree(y);
+        set_error("heom_warm_start_elements: memset");
+        return HEOM_ECUDA;
+    }
+    r = heom::elements_call(h, x_out, elems, n_elems, (float *)y.p, n_sets, 1, st, "heom_warm_start_elements");
+    heom::dfree(y);
+    return r;
+}

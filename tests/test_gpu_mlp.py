@@ -180,3 +180,33 @@ def test_warm_start_gain_on_held_out_solves(heom):
     assert np.mean(err_net) < 0.05
     assert np.mean(err_net) < 0.25 * np.mean(err_mean)
     assert np.mean(warm) <= np.mean(cold) + 1.0
+
+
+def test_element_features_round_trip(heom):
+    """heom_gather_elements reads the listed elements of every column; heom_warm_start_elements
+    writes a network's outputs to the same elements and zero elsewhere (checked against the
+    network's own forward pass); an out-of-range element index is refused."""
+    import torch
+    m = W.siam_model(tier=2)
+    g = heom.build_hierarchy(heom.problem_from_model(m, 1))
+    X = W.random_ado_vector(g.n_ado, 4, 3, seed=71)
+    x = torch.from_numpy(X).cuda()
+    elems = torch.tensor([0, 5, 17, 16 * g.n_ado - 1], dtype=torch.int64, device="cuda")
+    f = heom.gather_elements(g, x, elems).cpu().numpy()
+    flat = X.reshape(-1, 3)
+    for k, e in enumerate(elems.cpu().numpy()):
+        assert np.array_equal(f[:, 2 * k], flat[e].real.astype(np.float32))
+        assert np.array_equal(f[:, 2 * k + 1], flat[e].imag.astype(np.float32))
+    net = heom.Mlp([5, 16, 8], seed=3)
+    params = torch.randn(3, 5, dtype=torch.float32, device="cuda")
+    y = net.forward(params).cpu().numpy()
+    x0 = torch.empty((g.n_ado, 4, 4, 3), dtype=torch.complex128, device="cuda")
+    heom.warm_start_elements(g, net, params, elems, x0)
+    got = x0.cpu().numpy().reshape(-1, 3)
+    want = np.zeros_like(got)
+    for k, e in enumerate(elems.cpu().numpy()):
+        want[e] = y[:, 2 * k] + 1j * y[:, 2 * k + 1]
+    assert np.array_equal(got, want)
+    bad = torch.tensor([16 * g.n_ado], dtype=torch.int64, device="cuda")
+    with pytest.raises(heom.HeomError):
+        heom.gather_elements(g, x, bad)
