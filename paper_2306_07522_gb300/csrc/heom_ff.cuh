@@ -39,4 +39,52 @@ __device__ __forceinline__ void ff_norm(float &sh, float &sl) {
     sh = s;
 }
 
+// ---------------------------------------------------------------- packed float-float pairs
+// The same arithmetic on two values at once with GB300's packed FP32 instructions
+// ({add,sub,mul,fma}.rn.f32x2): a float2 holds the high (or low) words of two float-float
+// numbers, typically the real and imaginary parts of one complex value.
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mov.b64 rc, {%6, %7};\n\tfma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+// (H, L) += (Ah + Al)(Bh + Bl) elementwise, dropping Al*Bl; nBh = -Bh is passed in (it is
+// formed once per operand and reused) so that no separate negation is issued: -p = Ah * nBh
+// exactly, the product error is fma(Ah, Bh, -p), and H + p = H - (-p) is Knuth's two-sum.
+__device__ __forceinline__ void ff2_mac(float2 &H, float2 &L, float2 Ah, float2 Al, float2 Bh, float2 Bl,
+                                        float2 nBh) {
+    const float2 np = f2_mul(Ah, nBh);
+    float2 e = f2_fma(Ah, Bh, np);
+    e = f2_fma(Ah, Bl, e);
+    e = f2_fma(Al, Bh, e);
+    const float2 s = f2_sub(H, np);
+    const float2 bb = f2_sub(s, H);
+    const float2 t = f2_sub(f2_sub(H, f2_sub(s, bb)), f2_add(np, bb));
+    H = s;
+    L = f2_add(L, f2_add(t, e));
+}
+
 }  // namespace heom

@@ -274,6 +274,317 @@ __global__ void __launch_bounds__(kDotThreads) k_scale_ff(int64_t B, float4 *__r
     }
 }
 
+// ---------------------------------------------------------------- delayed reorthogonalisation
+// Arnoldi with classical Gram-Schmidt reorthogonalised one step late (DCGS2: Swirydowicz,
+// Langou, Thomas, Yamazaki, "Low synchronization Gram-Schmidt and GMRES algorithms", 2020),
+// per batch column. After step j-1 the slots hold q_0 .. q_{j-1} (final, orthonormal) and
+// p_j, the new vector after one projection, normalised: M q_{j-1} = Q_j h' + nu p_j with
+// h' = Hb(0..j-1, j-1) and nu = Hb(j, j-1) provisional. Step j applies M to p_j (z = M p_j)
+// and then, with ONE read of the basis for the dot products and one for the update:
+//   a = Q_j^H p_j, c = Q_j^H z, e = p_j^H z, f = p_j^H p_j         (k_dots2_ff_tiled)
+//   sigma = sqrt(f - |a|^2), q_j = (p_j - Q_j a) / sigma            (p_j = Q_j a + sigma q_j)
+//   Hb(0..j-1, j-1) += nu a, Hb(j, j-1) = nu sigma                  (column j-1 final)
+//   t = Q_{j+1}^H z = (c, (e - a^H c) / sigma)
+//   Hb(0..j, j) = (t - Hb(0..j, 0..j-1) a) / sigma                   (M q_j = (z - M Q_j a) / sigma)
+//   w = (z - Q_{j+1} t) / sigma, nu' = |w|, p_{j+1} = w / nu'        (k_update2_ff, k_scale_ff)
+// so every vector is projected out twice, as in two-pass classical Gram-Schmidt, at the
+// memory traffic of one pass; column j of Hb becomes final one step later. q_0 = p_0 = b /
+// beta exactly (step 0 takes sigma = 1).
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+// (h, l) * (sh + sl) for a float-float real scale, normalised
+__device__ __forceinline__ void ff_scale(float &h, float &l, float sh, float sl) {
+    const float p = h * sh;
+    float e = fmaf(h, sh, -p);
+    e = fmaf(h, sl, e);
+    e = fmaf(l, sh, e);
+    h = p + e;
+    l = e - (h - p);
+}
+
+// part[c][i][r][b] = sum over chunk c of conj(V_i) x_r for x_0 = p (= slot nv - 1 of the
+// basis) and x_1 = z: the two dot-product sets of one step in one read of the basis, tiled
+// kD2Tile basis vectors per block as in k_multidot_ff_tiled (deterministic, per-column fixed
+// order, zero for the chunk's inactive columns).
+constexpr int kD2Tile = 6;
+__global__ void __launch_bounds__(kDotThreads, 2) k_dots2_ff_tiled(int64_t B, int nv, const float4 *__restrict__ Vf,
+                                                                int64_t vstride, const float4 *__restrict__ zf,
+                                                                cx<double> *__restrict__ part,
+                                                                const GsChunk *__restrict__ chunks) {
+    const int i0 = blockIdx.x * kD2Tile, c = blockIdx.y;
+    const int nt = min(kD2Tile, nv - i0);
+    const GsChunk ch = chunks[c];
+    const float4 *pf = Vf + (int64_t)(nv - 1) * vstride;
+    __shared__ double sre[kD2Tile][kDotThreads], sim[kD2Tile][kDotThreads];
+    // accumulators of <V_k, x_r> as packed (re, im) pairs: high and low words
+    float2 H[kD2Tile][2], L[kD2Tile][2];
+#pragma unroll
+    for (int k = 0; k < kD2Tile; ++k)
+#pragma unroll
+        for (int r = 0; r < 2; ++r) H[k][r] = L[k][r] = make_float2(0.f, 0.f);
+    const float4 *V0 = Vf + (int64_t)i0 * vstride;
+    int col, rstep;
+    int64_t row;
+    if (chunk_lane(ch, col, rstep, row)) {
+        for (; row < ch.row1; row += rstep) {
+            const int64_t t = row * B + col;
+            // conj(a) x = a.re (x.re, x.im) + a.im (x.im, -x.re): the two packed products
+            float2 XH[2], XL[2], nXH[2], YH[2], YL[2], nYH[2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const float4 x = r ? zf[t] : pf[t];
+                XH[r] = make_float2(x.x, x.y);
+                XL[r] = make_float2(x.z, x.w);
+                nXH[r] = make_float2(-x.x, -x.y);
+                YH[r] = make_float2(x.y, -x.x);
+                YL[r] = make_float2(x.w, -x.z);
+                nYH[r] = make_float2(-x.y, x.x);
+            }
+            float4 a[kD2Tile];
+#pragma unroll
+            for (int k = 0; k < kD2Tile; ++k)
+                if (k < nt) a[k] = V0[(int64_t)k * vstride + t];
+#pragma unroll
+            for (int k = 0; k < kD2Tile; ++k) {
+                if (k < nt) {
+                    const float2 ARh = make_float2(a[k].x, a[k].x), ARl = make_float2(a[k].z, a[k].z);
+                    const float2 AIh = make_float2(a[k].y, a[k].y), AIl = make_float2(a[k].w, a[k].w);
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) {
+                        ff2_mac(H[k][r], L[k][r], ARh, ARl, XH[r], XL[r], nXH[r]);
+                        ff2_mac(H[k][r], L[k][r], AIh, AIl, YH[r], YL[r], nYH[r]);
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        if (r) __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kD2Tile; ++k) {
+            sre[k][threadIdx.x] = (double)H[k][r].x + (double)L[k][r].x;
+            sim[k][threadIdx.x] = (double)H[k][r].y + (double)L[k][r].y;
+        }
+        __syncthreads();
+        if (threadIdx.x < B) {
+            const int per = kDotThreads / ch.acols;
+            for (int k = 0; k < nt; ++k) {
+                double re = 0.0, im = 0.0;
+                if ((int)threadIdx.x < ch.acols)
+                    for (int q = 0; q < per; ++q) {
+                        re += sre[k][threadIdx.x + q * ch.acols];
+                        im += sim[k][threadIdx.x + q * ch.acols];
+                    }
+                part[(((int64_t)c * nv + i0 + k) * 2 + r) * B + threadIdx.x] = cx<double>{re, im};
+            }
+        }
+    }
+}
+
+// D[i][r][b] = sum_c part[c][i][r][b]
+__global__ void k_reduce_dots2(int nc, int nv, int64_t B, const cx<double> *__restrict__ part,
+                               cx<double> *__restrict__ D) {
+    const int64_t n = (int64_t)nv * 2 * B;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        cx<double> acc{0.0, 0.0};
+        for (int c = 0; c < nc; ++c) acc = acc + part[(int64_t)c * n + t];
+        D[t] = acc;
+    }
+}
+
+// The scalars of step j for column b = blockIdx.x (see the comment above): sigma, the final
+// column j-1 and the provisional column j of Hb, and the update's coefficients: cfa[i][b] =
+// a_i (FP32: the correction Q_j a is at the level of the lost orthogonality, so its FP32
+// error is far below float-float rounding; as two packed pairs), cft[i][b] = t_i (float-float,
+// i <= j; three float4 in the form the packed update takes), rsig[b] = 1 / sigma (float-float;
+// 0 when p_j lies in span(Q_j): the columns from there on are zero).
+__global__ void __launch_bounds__(256) k_dcgs_coef(int j, int mmax, int64_t B, const cx<double> *__restrict__ D,
+                                                   cx<double> *__restrict__ Hb, float4 *__restrict__ cfa,
+                                                   float4 *__restrict__ cft, float2 *__restrict__ rsig) {
+    const int64_t b = blockIdx.x;
+    __shared__ double s_aa[256], s_re[256], s_im[256];
+    __shared__ double s_sig, s_inv, s_nu;
+    __shared__ cx<double> s_tj;
+    auto Da = [&](int i) { return D[((int64_t)i * 2 + 0) * B + b]; };
+    auto Dc = [&](int i) { return D[((int64_t)i * 2 + 1) * B + b]; };
+    double aa = 0.0, re = 0.0, im = 0.0;
+    for (int i = threadIdx.x; i < j; i += blockDim.x) {
+        const cx<double> a = Da(i), c = Dc(i);
+        aa += norm2(a);
+        re += a.re * c.re + a.im * c.im;  // conj(a) c
+        im += a.re * c.im - a.im * c.re;
+    }
+    s_aa[threadIdx.x] = aa;
+    s_re[threadIdx.x] = re;
+    s_im[threadIdx.x] = im;
+    __syncthreads();
+    for (int k = blockDim.x >> 1; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) {
+            s_aa[threadIdx.x] += s_aa[threadIdx.x + k];
+            s_re[threadIdx.x] += s_re[threadIdx.x + k];
+            s_im[threadIdx.x] += s_im[threadIdx.x + k];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double sig = 1.0;
+        if (j > 0) {
+            const double s2 = Da(j).re - s_aa[0];
+            sig = s2 > 0.0 ? std::sqrt(s2) : 0.0;
+        }
+        const double inv = sig > 0.0 ? 1.0 / sig : 0.0;
+        const cx<double> e = Dc(j);
+        s_sig = sig;
+        s_inv = inv;
+        s_nu = j > 0 ? Hb[hb_at(j, j - 1, mmax, B, b)].re : 0.0;
+        s_tj = inv * cx<double>{e.re - s_re[0], e.im - s_im[0]};
+        const float h = (float)inv;
+        rsig[b] = make_float2(h, (float)(inv - (double)h));
+    }
+    __syncthreads();
+    const double sig = s_sig, inv = s_inv, nu = s_nu;
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+        // row i of Hb(0..j, 0..j-1) a, with column j-1 corrected first
+        cx<double> acc{0.0, 0.0};
+        for (int k = i > 0 ? i - 1 : 0; k < j - 1; ++k) acc = acc + Hb[hb_at(i, k, mmax, B, b)] * Da(k);
+        if (j > 0) {
+            cx<double> hc;
+            if (i < j) {
+                hc = Hb[hb_at(i, j - 1, mmax, B, b)] + nu * Da(i);
+            } else {
+                hc = cx<double>{nu * sig, 0.0};
+            }
+            Hb[hb_at(i, j - 1, mmax, B, b)] = hc;
+            acc = acc + hc * Da(j - 1);
+        }
+        const cx<double> ti = i < j ? Dc(i) : s_tj;
+        Hb[hb_at(i, j, mmax, B, b)] = inv * (ti - acc);
+        // w -= v t as w += (v.re, v.re) * B1 + (v.im, v.im) * B2 with B1 = -t and
+        // B2 = (t.im, -t.re), high and low words, and the negated high words
+        const float4 f = ff_split(ti);
+        float4 *rec = cft + ((int64_t)i * B + b) * 3;
+        rec[0] = make_float4(-f.x, -f.y, -f.z, -f.w);
+        rec[1] = make_float4(f.y, -f.x, f.w, -f.z);
+        rec[2] = make_float4(f.x, f.y, -f.y, f.x);
+        if (i < j) {  // Q a as (v.re, v.re) * (a.re, a.im) + (v.im, v.im) * (-a.im, a.re)
+            const cx<double> a = Da(i);
+            cfa[(int64_t)i * B + b] = make_float4((float)a.re, (float)a.im, -(float)a.im, (float)a.re);
+        }
+    }
+}
+
+// The update of step j on the active entries (blocks stride over the chunks): slot j of the
+// basis turns from p_j into q_j = (p_j - Q_j a) / sigma (float-float and FP64), slot j + 1
+// from z into w = (z - Q_j t - q_j t_j) / sigma (float-float); npart[c][b] = the chunk's
+// part of |w|^2 (per column in a fixed order; zero for inactive columns). A thread takes
+// kUpRows of its rows at a time, so each coefficient record it loads serves them all; the
+// multiply-adds run on packed (re, im) pairs.
+constexpr int kUpRows = 4;
+__global__ void __launch_bounds__(kDotThreads, 2) k_update2_ff(int64_t B, int j, float4 *__restrict__ Vf,
+                                                            int64_t vstride, cx<double> *__restrict__ q64,
+                                                            const float4 *__restrict__ cfa,
+                                                            const float4 *__restrict__ cft,
+                                                            const float2 *__restrict__ rsig,
+                                                            double *__restrict__ npart,
+                                                            const GsChunk *__restrict__ chunks, int nch) {
+    float4 *pf = Vf + (int64_t)j * vstride, *zf = Vf + (int64_t)(j + 1) * vstride;
+    __shared__ double sh[kDotThreads];
+    for (int c = blockIdx.x; c < nch; c += gridDim.x) {
+        const GsChunk ch = chunks[c];
+        int col, rstep;
+        int64_t row;
+        double acc = 0.0;
+        if (chunk_lane(ch, col, rstep, row)) {
+            const float2 rs = rsig[col];
+            const float4 *tjr = cft + ((int64_t)j * B + col) * 3;
+            const float4 tj = make_float4(-tjr[0].x, -tjr[0].y, -tjr[0].z, -tjr[0].w);  // t_j
+            for (; row < ch.row1; row += (int64_t)kUpRows * rstep) {
+                int64_t tt[kUpRows];
+                bool ok[kUpRows];
+                float2 WH[kUpRows], WL[kUpRows], CA[kUpRows];
+#pragma unroll
+                for (int g = 0; g < kUpRows; ++g) {
+                    const int64_t r = row + (int64_t)g * rstep;
+                    ok[g] = r < ch.row1;
+                    tt[g] = (ok[g] ? r : row) * B + col;
+                    const float4 z = zf[tt[g]];
+                    WH[g] = make_float2(z.x, z.y);
+                    WL[g] = make_float2(z.z, z.w);
+                    CA[g] = make_float2(0.f, 0.f);
+                }
+                for (int i = 0; i < j; ++i) {
+                    const float4 *rec = cft + ((int64_t)i * B + col) * 3;
+                    const float4 r0 = rec[0], r1 = rec[1], r2 = rec[2], a = cfa[(int64_t)i * B + col];
+                    const float2 B1h = make_float2(r0.x, r0.y), B1l = make_float2(r0.z, r0.w);
+                    const float2 B2h = make_float2(r1.x, r1.y), B2l = make_float2(r1.z, r1.w);
+                    const float2 nB1h = make_float2(r2.x, r2.y), nB2h = make_float2(r2.z, r2.w);
+                    const float2 A1 = make_float2(a.x, a.y), A2 = make_float2(a.z, a.w);
+                    const float4 *Vi = Vf + (int64_t)i * vstride;
+                    float4 v[kUpRows];
+#pragma unroll
+                    for (int g = 0; g < kUpRows; ++g) v[g] = Vi[tt[g]];
+#pragma unroll
+                    for (int g = 0; g < kUpRows; ++g) {
+                        const float2 VRh = make_float2(v[g].x, v[g].x), VRl = make_float2(v[g].z, v[g].z);
+                        const float2 VIh = make_float2(v[g].y, v[g].y), VIl = make_float2(v[g].w, v[g].w);
+                        ff2_mac(WH[g], WL[g], VRh, VRl, B1h, B1l, nB1h);
+                        ff2_mac(WH[g], WL[g], VIh, VIl, B2h, B2l, nB2h);
+                        CA[g] = f2_fma(VRh, A1, CA[g]);
+                        CA[g] = f2_fma(VIh, A2, CA[g]);
+                    }
+                }
+#pragma unroll
+                for (int g = 0; g < kUpRows; ++g) {
+                    if (!ok[g]) continue;
+                    const int64_t t = tt[g];
+                    const float4 p = pf[t];
+                    // q = (p - Q a) / sigma
+                    float qrh, qrl, qih, qil, er, ei;
+                    two_sum(p.x, -CA[g].x, qrh, er);
+                    two_sum(p.y, -CA[g].y, qih, ei);
+                    qrl = p.z + er;
+                    qil = p.w + ei;
+                    ff_norm(qrh, qrl);
+                    ff_norm(qih, qil);
+                    ff_scale(qrh, qrl, rs.x, rs.y);
+                    ff_scale(qih, qil, rs.x, rs.y);
+                    // w = (z - Q t - q t_j) / sigma
+                    float rh = WH[g].x, rl = WL[g].x, ih = WH[g].y, il = WL[g].y;
+                    ff_mac(rh, rl, -qrh, -qrl, tj.x, tj.z);
+                    ff_mac(rh, rl, qih, qil, tj.y, tj.w);
+                    ff_mac(ih, il, -qrh, -qrl, tj.y, tj.w);
+                    ff_mac(ih, il, -qih, -qil, tj.x, tj.z);
+                    ff_norm(rh, rl);
+                    ff_norm(ih, il);
+                    ff_scale(rh, rl, rs.x, rs.y);
+                    ff_scale(ih, il, rs.x, rs.y);
+                    pf[t] = make_float4(qrh, qih, qrl, qil);
+                    q64[t] = cx<double>{(double)qrh + (double)qrl, (double)qih + (double)qil};
+                    const float4 w = make_float4(rh, ih, rl, il);
+                    zf[t] = w;
+                    acc += norm2(ff_join(w));
+                }
+            }
+        }
+        sh[threadIdx.x] = acc;
+        __syncthreads();
+        if (threadIdx.x < B) {
+            double s = 0.0;
+            if ((int)threadIdx.x < ch.acols) {
+                const int per = kDotThreads / ch.acols;
+                for (int q = 0; q < per; ++q) s += sh[threadIdx.x + q * ch.acols];
+            }
+            npart[(int64_t)c * B + threadIdx.x] = s;
+        }
+        __syncthreads();
+    }
+}
+
 // h[i][b] = sum_c part[c][i][b] for i < nv (and its float-float split hf when hf is not
 // null); Hb(i, j)[b] += h[i][b] for i < nh (column j of
 // the Hessenberg matrix accumulates both Gram-Schmidt passes; entry nh, when nv > nh, is the
@@ -300,9 +611,11 @@ __global__ void k_reduce_h(int nc, int nv, int nh, int64_t B, const cx<double> *
 // Whether the second Gram-Schmidt pass can be skipped: after one classical pass the vector
 // keeps norm^2 = |w|^2 - sum_i |h_i|^2 (V orthonormal); when that is at least kKeep^2 |w|^2
 // for every column, the orthogonality lost in the pass is at most about eps / kKeep per step
-// and a second pass would change nothing measurable. skip = 1 in that case.
+// and a second pass would change nothing measurable. skip = 1 in that case; ran[j] records
+// whether pass 2 of step j runs (the work accounting reads it back).
 constexpr double kKeep2 = 0.05 * 0.05;
-__global__ void k_reorth_flag(int nh, int64_t B, const cx<double> *__restrict__ h, int *__restrict__ skip) {
+__global__ void k_reorth_flag(int nh, int64_t B, const cx<double> *__restrict__ h, int *__restrict__ skip,
+                              int *__restrict__ ran, int j) {
     __shared__ int need;
     if (threadIdx.x == 0) need = 0;
     __syncthreads();
@@ -316,7 +629,10 @@ __global__ void k_reorth_flag(int nh, int64_t B, const cx<double> *__restrict__ 
         if (lane == 0 && !(w2 - sacc >= kKeep2 * w2)) need = 1;  // also when not finite
     }
     __syncthreads();
-    if (threadIdx.x == 0) *skip = need ? 0 : 1;
+    if (threadIdx.x == 0) {
+        *skip = need ? 0 : 1;
+        ran[j] = need;
+    }
 }
 
 // w[row][b] -= sum_i V_i[row][b] h[i][b]
@@ -643,7 +959,7 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
             // the hierarchy's own workspace is reused (or grown), or else the largest one the
             // library keeps cached on this device
             free_b += std::max(h->ws.bytes, ws_cached_max(h->device));
-            const double per_step = 32.0 * (double)L + 88.0 * (double)S + 64.0 * (double)B;
+            const double per_step = 32.0 * (double)L + 88.0 * (double)S + (64.0 + 32.0 * 456) * (double)B;
             const double fixed = 64.0 * (double)L + 48.0 * (double)S + (double)(64 * 2 + 2) * B * 16.0;
             const double avail = 0.6 * (double)free_b - fixed;
             const int fit = avail > per_step ? (int)std::min(2.0e9, avail / per_step) - 1 : 0;
@@ -696,11 +1012,16 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
     }
     const int nch = (int)chunks.size();
     const int npc = std::max(nchunk, nch);
-    const size_t opart = take((size_t)npc * (mmax + 2) * B * 16), oskip = take(sizeof(int));
+    const size_t opart = take((size_t)npc * (mmax + 2) * 2 * B * 16), oskip = take(sizeof(int)),
+                 oran = take((size_t)mmax * sizeof(int));
     const size_t onp = take((size_t)npc * B * 8);
     const size_t och = take((size_t)std::max(nch, 1) * sizeof(GsChunk));
     const size_t oVf = ffgs ? take((size_t)(mmax + 1) * L * 16) : 0,
                  ohf = ffgs ? take((size_t)(mmax + 2) * B * 16) : 0;
+    // the delayed-reorthogonalisation scalars: dots D [mmax+1][2][B], coefficients
+    const size_t oD = ffgs ? take((size_t)(mmax + 1) * 2 * B * 16) : 0,
+                 ocfa = ffgs ? take((size_t)(mmax + 1) * B * 16) : 0,
+                 ocft = ffgs ? take((size_t)(mmax + 1) * B * 48) : 0, orsig = ffgs ? take((size_t)B * 8) : 0;
     // every shift's triangular factor (strict upper part) for the final solve, for up to mp
     // steps when that fits 1 GiB (more steps solve by walking the rotation chains instead)
     const bool pers = ffgs && arnoldi_persistent_ok(h, B, mmax);
@@ -725,9 +1046,12 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
     int *dco = (int *)(base + oco);
     cx<double> *part = (cx<double> *)(base + opart);
     double *npart = (double *)(base + onp);
-    int *dskip = (int *)(base + oskip);
+    int *dskip = (int *)(base + oskip), *dran = (int *)(base + oran);
     float4 *Vf = ffgs ? (float4 *)(base + oVf) : nullptr;
     float4 *hft = ffgs ? (float4 *)(base + ohf) : nullptr;
+    cx<double> *dD = ffgs ? (cx<double> *)(base + oD) : nullptr;
+    float2 *rsig = ffgs ? (float2 *)(base + orsig) : nullptr;
+    float4 *cfa = ffgs ? (float4 *)(base + ocfa) : nullptr, *cft = ffgs ? (float4 *)(base + ocft) : nullptr;
     cx<double> *Rst = keepR ? (cx<double> *)(base + oR) : nullptr;
     float2 *rot_cf = pers ? (float2 *)(base + orcf) : nullptr;
     float4 *rot_sf = pers ? (float4 *)(base + orsf) : nullptr;
@@ -776,6 +1100,12 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
         }
         m = j_done = psteps;
     }
+    const int j_pers = m;  // steps taken by the persistent kernel (accounted there)
+    // delayed reorthogonalisation from the first step (after the persistent kernel's steps
+    // the basis is already final: the two-pass step continues it); Hessenberg column j is
+    // final only after step j + 1, so the shifts' QR and the solution stay one column behind
+    const bool dcgs = ffgs && m == 0 && mmax >= 3;
+    const int lag = dcgs ? 1 : 0;
     for (int j = m; j < mmax && !done; ++j) {
         const cx<double> *vj = V + (int64_t)j * L;
         cx<double> *w = V + (int64_t)(j + 1) * L;  // the new vector is built in place
@@ -790,7 +1120,23 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
                 HEOM_CUDA(launch_apply(v, vj, w, B, mods, s));
             }
         }
-        if (ffgs) {
+        if (dcgs) {
+            // one read of the basis for the dots, one for the update (see k_dots2_ff_tiled)
+            float4 *zf = Vf + (int64_t)(j + 1) * L;
+            {
+                Prof pr(HEOM_KC_KRYLOV_VECTOR, s, (double)(j + 1) * Lg, (2.0 * j + 12.0) * Lg * 16);
+                pr.kernels = 8;
+                k_split_chunks<<<gsb, kDotThreads, 0, s>>>(B, w, zf, dch, nch);
+                k_dots2_ff_tiled<<<dim3((unsigned)((j + 1 + kD2Tile - 1) / kD2Tile), (unsigned)nch), kDotThreads,
+                                   0, s>>>(B, j + 1, Vf, L, zf, part, dch);
+                k_reduce_dots2<<<blocks_for((int64_t)(j + 1) * 2 * B), 256, 0, s>>>(nch, j + 1, B, part, dD);
+                k_dcgs_coef<<<(unsigned)B, 256, 0, s>>>(j, mmax, B, dD, Hb, cfa, cft, rsig);
+                k_update2_ff<<<gsb, kDotThreads, 0, s>>>(B, j, Vf, L, V + (int64_t)j * L, cfa, cft, rsig, npart,
+                                                         dch, nch);
+                k_colnorm_fin<<<blocks_for(B), 256, 0, s>>>(nch, B, npart, nrm, Hb, j, mmax);
+                k_scale_ff<<<gsb, kDotThreads, 0, s>>>(B, zf, nrm, w, dch, nch);
+            }
+        } else if (ffgs) {
             float4 *wf = Vf + (int64_t)(j + 1) * L;
             {   // classical Gram-Schmidt in float-float; pass 1 also yields |w|^2 (w's dot with
                 // itself), from which k_reorth_flag decides on the device whether pass 2 runs
@@ -801,10 +1147,11 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
                                       kDotThreads, 0, s>>>(B, j + 2, Vf, L, wf, part, nullptr, dch);
                 k_reduce_h<<<blocks_for((int64_t)(j + 2) * B), 256, 0, s>>>(nch, j + 2, j + 1, B, part, ht,
                                                                            hft, Hb, j, mmax, nullptr);
-                k_reorth_flag<<<1, 128, 0, s>>>(j + 1, B, ht, dskip);
+                k_reorth_flag<<<1, 128, 0, s>>>(j + 1, B, ht, dskip, dran, j);
                 k_gs_update_ff<<<gsb, kDotThreads, 0, s>>>(B, j + 1, Vf, L, hft, wf, nullptr, dch, nch);
             }
-            {   // pass 2 (skipped on the device when pass 1 kept enough of w)
+            {   // pass 2 (skipped on the device when pass 1 kept enough of w; its work is
+                // added to the accounting from the device's record after the solve)
                 Prof pr(HEOM_KC_KRYLOV_VECTOR, s, 0.0, 0.0);
                 pr.kernels = 3;
                 k_multidot_ff_tiled<<<dim3((unsigned)((j + 1 + kMdTile - 1) / kMdTile), (unsigned)nch),
@@ -828,7 +1175,7 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
                     rows, B, j + 2, V, L, w, part, nullptr);
                 k_reduce_h<<<blocks_for((int64_t)(j + 2) * B), 256, 0, s>>>(nchunk, j + 2, j + 1, B, part, ht,
                                                                            nullptr, Hb, j, mmax, nullptr);
-                k_reorth_flag<<<1, 128, 0, s>>>(j + 1, B, ht, dskip);
+                k_reorth_flag<<<1, 128, 0, s>>>(j + 1, B, ht, dskip, dran, j);
                 k_gs_update<<<blocks_for(L), 256, 0, s>>>(rows, B, j + 1, V, L, ht, w, nullptr);
             }
             {
@@ -850,13 +1197,14 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
         }
         HEOM_CUDA(cudaGetLastError());
         m = j + 1;
-        if (m % check == 0 || m == mmax) {
+        if ((m % check == 0 || m == mmax) && m - lag > j_done) {
+            const int mf = m - lag;  // the final Hessenberg columns
             {   // every shift's Givens QR catches up with the new Hessenberg columns
-                Prof pr(HEOM_KC_OTHER, s, (double)S * (m - j_done), 0.0);
-                k_shift_steps<<<(unsigned)((S + 63) / 64), 64, 0, s>>>(j_done, m, mmax, B, S, Hb, dsh, dco,
+                Prof pr(HEOM_KC_OTHER, s, (double)S * (mf - j_done), 0.0);
+                k_shift_steps<<<(unsigned)((S + 63) / 64), 64, 0, s>>>(j_done, mf, mmax, B, S, Hb, dsh, dco,
                                                                       rot_c, rot_s, rdiag, g, beta, dres);
             }
-            j_done = m;
+            j_done = mf;
             HEOM_CUDA(memcpy_counted(hres.data(), dres, S * 8, cudaMemcpyDeviceToHost, s));
             HEOM_CUDA(cudaStreamSynchronize(s));
             double worst = 0.0;
@@ -865,32 +1213,42 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
             check = std::min(check + 5, 20);
         }
     }
-    if (keepR && m <= mp && m > 0) {
+    const int mf = j_done;  // the Hessenberg columns the shifts' QR has taken in
+    if (keepR && mf <= mp && mf > 0) {
         // R from the stored rotations (all columns at once), then back substitution
-        Prof pr(HEOM_KC_OTHER, s, (double)S, (double)S * m * 16);
-        pr.kernels = m > 1 ? 2 : 1;
-        if (m > 1)
-            k_shift_rform<<<dim3((unsigned)((S + 63) / 64), (unsigned)(m - 1)), 64, 0, s>>>(
-                m, mmax, rtri, B, S, Hb, dsh, dco, rot_c, rot_s, Rst);
-        const size_t smb = (size_t)3 * kBsShifts * m * sizeof(cx<double>);
+        Prof pr(HEOM_KC_OTHER, s, (double)S, (double)S * mf * 16);
+        pr.kernels = mf > 1 ? 2 : 1;
+        if (mf > 1)
+            k_shift_rform<<<dim3((unsigned)((S + 63) / 64), (unsigned)(mf - 1)), 64, 0, s>>>(
+                mf, mmax, rtri, B, S, Hb, dsh, dco, rot_c, rot_s, Rst);
+        const size_t smb = (size_t)3 * kBsShifts * mf * sizeof(cx<double>);
         if (smb > 48 * 1024)
             HEOM_CUDA(cudaFuncSetAttribute(k_shift_backsub, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
         k_shift_backsub<<<(unsigned)((S + kBsShifts - 1) / kBsShifts), 32, smb, s>>>(
-            m, mmax, rtri, B, S, d2, dco, Rst, rdiag, g, V, L, dx0);
+            mf, mmax, rtri, B, S, d2, dco, Rst, rdiag, g, V, L, dx0);
     } else {
-        Prof pr(HEOM_KC_OTHER, s, (double)S, (double)S * m * 16);
-        const size_t smb = (size_t)m * kSolveThreads * (3 * sizeof(cx<double>) + sizeof(double));
+        Prof pr(HEOM_KC_OTHER, s, (double)S, (double)S * mf * 16);
+        const size_t smb = (size_t)mf * kSolveThreads * (3 * sizeof(cx<double>) + sizeof(double));
         if (smb <= (size_t)kSolveSmemMax) {
             if (smb > 48 * 1024)
                 HEOM_CUDA(cudaFuncSetAttribute(k_shift_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
             k_shift_solve<<<(unsigned)((S + kSolveThreads - 1) / kSolveThreads), kSolveThreads, smb, s>>>(
-                m, mmax, B, S, d2, Hb, dsh, dco, rot_c, rot_s, rdiag, g, V, L, dx0);
+                mf, mmax, B, S, d2, Hb, dsh, dco, rot_c, rot_s, rdiag, g, V, L, dx0);
         } else {
-            k_shift_solve_long<<<(unsigned)((S + 63) / 64), 64, 0, s>>>(m, mmax, B, S, d2, Hb, dsh, dco, rot_c,
+            k_shift_solve_long<<<(unsigned)((S + 63) / 64), 64, 0, s>>>(mf, mmax, B, S, d2, Hb, dsh, dco, rot_c,
                                                                         rot_s, rdiag, g, gw, y, V, L, dx0);
         }
     }
     HEOM_CUDA(cudaGetLastError());
+    if (prof_on() && !dcgs && m > j_pers) {
+        // the second Gram-Schmidt passes that ran: j + 1 basis vectors read by the dots and
+        // by the update, w read twice and written once
+        std::vector<int> ran((size_t)m);
+        HEOM_CUDA(cudaMemcpyAsync(ran.data(), dran, (size_t)m * sizeof(int), cudaMemcpyDeviceToHost, s));
+        HEOM_CUDA(cudaStreamSynchronize(s));
+        for (int j = j_pers; j < m; ++j)
+            if (ran[j]) prof_add(HEOM_KC_KRYLOV_VECTOR, (double)(j + 1) * Lg, (2.0 * (j + 1) + 3.0) * Lg * 16);
+    }
     x0.resize((size_t)S * d2);
     res.resize(S);
     HEOM_CUDA(memcpy_counted(x0.data(), dx0, (size_t)S * d2 * 16, cudaMemcpyDeviceToHost, s));
