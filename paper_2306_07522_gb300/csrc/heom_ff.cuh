@@ -39,6 +39,22 @@ __device__ __forceinline__ void ff_norm(float &sh, float &sl) {
     sh = s;
 }
 
+// Knuth's two-sum: s + e = a + b exactly
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+// (h, l) * (sh + sl) for a float-float real scale, normalised
+__device__ __forceinline__ void ff_scale(float &h, float &l, float sh, float sl) {
+    const float p = h * sh;
+    float e = fmaf(h, sh, -p);
+    e = fmaf(h, sl, e);
+    e = fmaf(l, sh, e);
+    h = p + e;
+    l = e - (h - p);
+}
+
 // ---------------------------------------------------------------- packed float-float pairs
 // The same arithmetic on two values at once with GB300's packed FP32 instructions
 // ({add,sub,mul,fma}.rn.f32x2): a float2 holds the high (or low) words of two float-float

@@ -383,6 +383,17 @@ std::vector<cx<R>> to_cx(const std::vector<heom_c64> &v) {
     return o;
 }
 
+// float-float {hi.re, hi.im, lo.re, lo.im} of each value (hi = nearest float, lo = the
+// nearest float to the rest)
+std::vector<float4> to_ff(const std::vector<heom_c64> &v) {
+    std::vector<float4> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) {
+        const float hr = (float)v[i].re, hi = (float)v[i].im;
+        o[i] = make_float4(hr, hi, (float)(v[i].re - (double)hr), (float)(v[i].im - (double)hi));
+    }
+    return o;
+}
+
 // bosonic (a, b) of D X = a V X - b X V for one exponent of the given kind
 void boson_ab(int kind, heom_c64 c, heom_c64 &a, heom_c64 &b) {
     if (kind == HEOM_BOSON_R) { a = c; b = c; }
@@ -416,6 +427,9 @@ heom::DevView<double> heom_hier::view64() const {
     v.set_cap = has_caps ? (const int32_t *)d_set_cap.p : nullptr;
     v.pers_ado = (const int32_t *)d_pers_ado.p; v.pers_ranges = pers_ranges;
     v.pers_terms = pers_terms; v.pers_slots = pers_slots; v.pers_ados = pers_ados;
+    v.op_rvalf = (const float4 *)d_op_rvalff.p; v.op_cvalf = (const float4 *)d_op_cvalff.p;
+    v.s_valf = (const float4 *)d_svalff.p; v.coefLf = (const float4 *)d_coefLff.p;
+    v.coefRf = (const float4 *)d_coefRff.p; v.ratef = (const float4 *)d_rateff.p;
     return v;
 }
 
@@ -457,7 +471,9 @@ void free_all(heom_hier *h) {
                     &h->d_sdiag32, &h->d_tdval64, &h->d_floor64, &h->d_floor32, &h->ws,
                     &h->ws_small,
                     &h->d_t_ptr, &h->d_t_src, &h->d_t_val64, &h->d_t_val32, &h->d_cta_ado,
-                    &h->d_pers_ado, &h->d_ar_ado, &h->ws_pers, &h->d_ado_tier, &h->d_set_cap};
+                    &h->d_pers_ado, &h->d_ar_ado, &h->ws_pers, &h->d_ado_tier, &h->d_set_cap,
+                    &h->d_op_rvalff, &h->d_op_cvalff, &h->d_svalff, &h->d_coefLff, &h->d_coefRff,
+                    &h->d_rateff};
     for (DBuf *b : bufs) heom::dfree(*b);
 }
 
@@ -728,7 +744,8 @@ heom_status upload_params(heom_hier *h, int n_sets, const heom_c64 *H, const heo
 #define UP(buf, vec) if ((st = upload(h->buf, vec)) != HEOM_OK) return st
     UP(d_cta_ado, ranges); UP(d_pers_ado, pranges); UP(d_ar_ado, arranges);
     UP(d_s_ptr, sptr); UP(d_s_src, ssrc);
-    UP(d_sval64, to_cx<double>(sval)); UP(d_sval32, to_cx<float>(sval));
+    UP(d_sval64, to_cx<double>(sval)); UP(d_sval32, to_cx<float>(sval)); UP(d_svalff, to_ff(sval));
+    UP(d_coefLff, to_ff(cl)); UP(d_coefRff, to_ff(cr)); UP(d_rateff, to_ff(rt));
     UP(d_sdiag64, to_cx<double>(sd)); UP(d_sdiag32, to_cx<float>(sd));
     UP(d_tdval64, to_cx<double>(tdval));
     UP(d_coefL64, to_cx<double>(cl)); UP(d_coefL32, to_cx<float>(cl));
@@ -1044,6 +1061,7 @@ heom_status build_impl(int d, const heom_c64 *H, int n_baths, const heom_bath *b
         UP(d_op_rptr, orp); UP(d_op_rcol, orc); UP(d_op_cptr, ocp); UP(d_op_crow, ocr);
         UP(d_op_rval64, to_cx<double>(orv)); UP(d_op_cval64, to_cx<double>(ocv));
         UP(d_op_rval32, to_cx<float>(orv)); UP(d_op_cval32, to_cx<float>(ocv));
+        UP(d_op_rvalff, to_ff(orv)); UP(d_op_cvalff, to_ff(ocv));
         // per-element term lists of every operator slot (tiled kernels)
         std::vector<int32_t> tp(1, 0), tsrc;
         std::vector<heom_c64> tval;

@@ -119,6 +119,9 @@ struct DevView {
     // and holds every other ADO at zero (the apply writes zero there).
     const int32_t *ado_tier;  // [N]
     const int32_t *set_cap;   // [n_sets]
+    // Float-float copies {hi.re, hi.im, lo.re, lo.im} of the FP64 tables for the float-float
+    // apply (FP64 view only; null in the FP32 view)
+    const float4 *op_rvalf, *op_cvalf, *s_valf, *coefLf, *coefRf, *ratef;
 };
 
 // Whether ADO n lies beyond the truncation of parameter set s.
@@ -178,7 +181,7 @@ struct heom_hier {
     // device tables
     heom::DBuf d_row_ptr, d_ent, d_occ_ptr, d_occ;
     heom::DBuf d_op_rptr, d_op_rcol, d_op_cptr, d_op_crow, d_op_rval64, d_op_cval64,
-        d_op_rval32, d_op_cval32;
+        d_op_rval32, d_op_cval32, d_op_rvalff, d_op_cvalff;
     heom::DBuf d_s_ptr, d_s_src;
     heom::DBuf d_tdval64;                   // [n_drive][nS] system-term values of -i[H_k, .]
     int nS = 0;                             // system terms (all elements)
@@ -202,9 +205,10 @@ struct heom_hier {
     int pers_ranges = 0, pers_terms = 0, pers_slots = 0, pers_ados = 0;
     heom::DBuf d_ar_ado;        // ADO ranges of the persistent Arnoldi (elements weighted)
     int ar_ranges = 0, ar_terms = 0, ar_slots = 0, ar_ados = 0;
-    // device parameters (per set), both precisions
+    // device parameters (per set), both precisions and float-float
     heom::DBuf d_sval64, d_sval32, d_coefL64, d_coefL32, d_coefR64, d_coefR32, d_rate64,
-        d_rate32, d_sdiag64, d_sdiag32, d_floor64, d_floor32;
+        d_rate32, d_sdiag64, d_sdiag32, d_floor64, d_floor32, d_svalff, d_coefLff, d_coefRff,
+        d_rateff;
     // solver workspace (grown on demand)
     heom::DBuf ws;
     heom::DBuf ws_small;

@@ -252,8 +252,8 @@ __global__ void __launch_bounds__(kDotThreads) k_colnorm_part_ff(int64_t B, cons
     if (threadIdx.x == 0) part[(int64_t)c * B + b] = sh[0];
 }
 
-// v = w / nrm[b] in FP64 (for the apply) and its float-float split (for Gram-Schmidt); in
-// place on wf, on the active entries of the chunks (the others stay zero in v). nrm = 0
+// v = w / nrm[b] in FP64 (for the FP64 apply; skipped when v is null) and its float-float
+// split (for Gram-Schmidt and the float-float apply); in place on wf, on the active entries of the chunks (the others stay zero in v). nrm = 0
 // leaves zeros (exact invariant subspace).
 __global__ void __launch_bounds__(kDotThreads) k_scale_ff(int64_t B, float4 *__restrict__ wf,
                                                           const double *__restrict__ nrm,
@@ -268,9 +268,105 @@ __global__ void __launch_bounds__(kDotThreads) k_scale_ff(int64_t B, float4 *__r
         for (; row < ch.row1; row += rstep) {
             const int64_t t = row * B + col;
             const cx<double> x = n > 0.0 ? (1.0 / n) * ff_join(wf[t]) : cx<double>{0.0, 0.0};
-            v[t] = x;
+            if (v) v[t] = x;
             wf[t] = ff_split(x);
         }
+    }
+}
+
+// ---------------------------------------------------------------- float-float apply
+// (H, L) += c x for float-float complex c, x ({hi.re, hi.im, lo.re, lo.im}):
+// (re, im) += (c.re, c.re) (x.re, x.im) + (c.im, c.im) (-x.im, x.re) in packed pairs.
+__device__ __forceinline__ void cmac_ff(float2 &H, float2 &L, float4 c, float4 x) {
+    ff2_mac(H, L, make_float2(c.x, c.x), make_float2(c.z, c.z), make_float2(x.x, x.y), make_float2(x.z, x.w),
+            make_float2(-x.x, -x.y));
+    ff2_mac(H, L, make_float2(c.y, c.y), make_float2(c.w, c.w), make_float2(-x.y, x.x), make_float2(-x.w, x.z),
+            make_float2(x.y, -x.x));
+}
+__device__ __forceinline__ float4 ff_pack(float2 H, float2 L) {
+    float rh = H.x, rl = L.x, ih = H.y, il = L.y;
+    ff_norm(rh, rl);
+    ff_norm(ih, il);
+    return make_float4(rh, ih, rl, il);
+}
+// c x for float-float complex values
+__device__ __forceinline__ float4 cmul_ff(float4 c, float4 x) {
+    float2 H = make_float2(0.f, 0.f), L = H;
+    cmac_ff(H, L, c, x);
+    return ff_pack(H, L);
+}
+// -i m a for a float-float complex a and a small integer m: (m a.im, -m a.re)
+__device__ __forceinline__ float4 mul_mi_ff(float m, float4 a) {
+    float rh = a.y, rl = a.w, ih = -a.x, il = -a.z;
+    ff_scale(rh, rl, m, 0.f);
+    ff_scale(ih, il, m, 0.f);
+    return make_float4(rh, ih, rl, il);
+}
+
+// Y = M X in float-float for batched columns of several parameter sets (column b belongs to
+// set b / cps): Eq. HEOM at every (ADO n, element e, column b), the terms in the order of the
+// per-element FP64 apply, every product a float-float one (unit roundoff 2^-48 instead of
+// FP64's 2^-53, at FP32 issue rates). An ADO beyond its column's set truncation is written
+// as zero, and neighbours beyond it are skipped (their entries are zero).
+__global__ void __launch_bounds__(256, 3) k_apply_ff(DevView<double> v, const float4 *__restrict__ X,
+                                                  float4 *__restrict__ Y, int64_t B, int64_t cps) {
+    const int d = v.d, d2 = v.d2;
+    const int64_t total = v.N * d2 * B;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = t / B, b = t - row * B, n = row / d2;
+        const int e = (int)(row - n * d2), set = (int)(b / cps);
+        if (beyond_cap(v, n, set)) {
+            Y[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+            continue;
+        }
+        const int r = e / d, c = e - r * d;
+        const float4 *Xn = X + n * d2 * B + b;
+        float2 H = make_float2(0.f, 0.f), L = H;
+        {   // damping: -sum_k count_k rate_k x
+            float2 DH = H, DL = H;
+            const int o1 = __ldg(v.occ_ptr + n + 1);
+            for (int o = __ldg(v.occ_ptr + n); o < o1; ++o) {
+                const int packed = __ldg(reinterpret_cast<const int *>(v.occ) + o);
+                const int k = (int)(int16_t)(packed & 0xffff);
+                const float cnt = (float)(int16_t)(packed >> 16);
+                const float4 rt = v.ratef[(int64_t)set * v.K + k];
+                ff2_mac(DH, DL, make_float2(cnt, cnt), make_float2(0.f, 0.f), make_float2(rt.x, rt.y),
+                        make_float2(rt.z, rt.w), make_float2(-rt.x, -rt.y));
+            }
+            const float4 dm = ff_pack(DH, DL);
+            cmac_ff(H, L, make_float4(-dm.x, -dm.y, -dm.z, -dm.w), Xn[(int64_t)e * B]);
+        }
+        const float4 *sv = v.s_valf + (int64_t)set * v.nS;
+        for (int j = __ldg(v.s_ptr + e), j1 = __ldg(v.s_ptr + e + 1); j < j1; ++j)
+            cmac_ff(H, L, sv[j], Xn[(int64_t)__ldg(v.s_src + j) * B]);
+        const int t1 = __ldg(v.row_ptr + n + 1);
+        for (int q = __ldg(v.row_ptr + n); q < t1; ++q) {
+            const int4 raw = __ldg(reinterpret_cast<const int4 *>(v.ent) + q);
+            const int nb = raw.x;
+            if (beyond_cap(v, (int64_t)nb, set)) continue;
+            const int op = (int)(int16_t)(raw.y & 0xffff);
+            const int k = (int)(int16_t)(raw.y >> 16);
+            const int dir = (int)(int16_t)(raw.z & 0xffff);
+            const float ml = (float)(int16_t)(raw.z >> 16);
+            const float mr = (float)(int16_t)(raw.w & 0xffff);
+            float4 cl, cr;  // -i * mult * (a | b)
+            if (dir > 0) {
+                cl = make_float4(0.f, -ml, 0.f, 0.f);
+                cr = make_float4(0.f, -mr, 0.f, 0.f);
+            } else {
+                const int64_t pk = (int64_t)set * v.K + k;
+                cl = mul_mi_ff(ml, v.coefLf[pk]);
+                cr = mul_mi_ff(mr, v.coefRf[pk]);
+            }
+            const float4 *Xb = X + (int64_t)nb * d2 * B + b;
+            const int base = op * (d + 1);
+            for (int j = __ldg(v.op_rptr + base + r), j1 = __ldg(v.op_rptr + base + r + 1); j < j1; ++j)
+                cmac_ff(H, L, cmul_ff(cl, v.op_rvalf[j]), Xb[(int64_t)(__ldg(v.op_rcol + j) * d + c) * B]);
+            for (int j = __ldg(v.op_cptr + base + c), j1 = __ldg(v.op_cptr + base + c + 1); j < j1; ++j)
+                cmac_ff(H, L, cmul_ff(cr, v.op_cvalf[j]), Xb[(int64_t)(r * d + __ldg(v.op_crow + j)) * B]);
+        }
+        Y[t] = ff_pack(H, L);
     }
 }
 
@@ -290,21 +386,6 @@ __global__ void __launch_bounds__(kDotThreads) k_scale_ff(int64_t B, float4 *__r
 // so every vector is projected out twice, as in two-pass classical Gram-Schmidt, at the
 // memory traffic of one pass; column j of Hb becomes final one step later. q_0 = p_0 = b /
 // beta exactly (step 0 takes sigma = 1).
-
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-}
-// (h, l) * (sh + sl) for a float-float real scale, normalised
-__device__ __forceinline__ void ff_scale(float &h, float &l, float sh, float sl) {
-    const float p = h * sh;
-    float e = fmaf(h, sh, -p);
-    e = fmaf(h, sl, e);
-    e = fmaf(l, sh, e);
-    h = p + e;
-    l = e - (h - p);
-}
 
 // part[c][i][r][b] = sum over chunk c of conj(V_i) x_r for x_0 = p (= slot nv - 1 of the
 // basis) and x_1 = z: the two dot-product sets of one step in one read of the basis, tiled
@@ -479,7 +560,8 @@ __global__ void __launch_bounds__(256) k_dcgs_coef(int j, int mmax, int64_t B, c
 }
 
 // The update of step j on the active entries (blocks stride over the chunks): slot j of the
-// basis turns from p_j into q_j = (p_j - Q_j a) / sigma (float-float and FP64), slot j + 1
+// basis turns from p_j into q_j = (p_j - Q_j a) / sigma (float-float; FP64 in its first
+// q64_rows rows, the rows the solution is formed from), slot j + 1
 // from z into w = (z - Q_j t - q_j t_j) / sigma (float-float); npart[c][b] = the chunk's
 // part of |w|^2 (per column in a fixed order; zero for inactive columns). A thread takes
 // kUpRows of its rows at a time, so each coefficient record it loads serves them all; the
@@ -487,6 +569,7 @@ __global__ void __launch_bounds__(256) k_dcgs_coef(int j, int mmax, int64_t B, c
 constexpr int kUpRows = 4;
 __global__ void __launch_bounds__(kDotThreads, 2) k_update2_ff(int64_t B, int j, float4 *__restrict__ Vf,
                                                             int64_t vstride, cx<double> *__restrict__ q64,
+                                                            int64_t q64_rows,
                                                             const float4 *__restrict__ cfa,
                                                             const float4 *__restrict__ cft,
                                                             const float2 *__restrict__ rsig,
@@ -564,7 +647,7 @@ __global__ void __launch_bounds__(kDotThreads, 2) k_update2_ff(int64_t B, int j,
                     ff_scale(rh, rl, rs.x, rs.y);
                     ff_scale(ih, il, rs.x, rs.y);
                     pf[t] = make_float4(qrh, qih, qrl, qil);
-                    q64[t] = cx<double>{(double)qrh + (double)qrl, (double)qih + (double)qil};
+                    if (t < q64_rows * B) q64[t] = cx<double>{(double)qrh + (double)qrl, (double)qih + (double)qil};
                     const float4 w = make_float4(rh, ih, rl, il);
                     zf[t] = w;
                     acc += norm2(ff_join(w));
@@ -1111,7 +1194,10 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
         cx<double> *w = V + (int64_t)(j + 1) * L;  // the new vector is built in place
         {   // w = M v_j
             Prof pr(HEOM_KC_KRYLOV_APPLY64, s, Lk / h->d2, 2.0 * Lk * 16);
-            if (tiled) {
+            if (dcgs) {  // float-float, from and into the float-float basis
+                const int64_t grid = std::min<int64_t>((L + 255) / 256, 152 * 16);
+                k_apply_ff<<<(unsigned)grid, 256, 0, s>>>(v, Vf + (int64_t)j * L, Vf + (int64_t)(j + 1) * L, B, cps);
+            } else if (tiled) {
                 ta.x = vj;
                 ta.out = w;
                 HEOM_CUDA((launch_tile<double, TM_STORE>(ta, s)));
@@ -1124,17 +1210,16 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
             // one read of the basis for the dots, one for the update (see k_dots2_ff_tiled)
             float4 *zf = Vf + (int64_t)(j + 1) * L;
             {
-                Prof pr(HEOM_KC_KRYLOV_VECTOR, s, (double)(j + 1) * Lg, (2.0 * j + 12.0) * Lg * 16);
-                pr.kernels = 8;
-                k_split_chunks<<<gsb, kDotThreads, 0, s>>>(B, w, zf, dch, nch);
+                Prof pr(HEOM_KC_KRYLOV_VECTOR, s, (double)(j + 1) * Lg, (2.0 * j + 8.0) * Lg * 16);
+                pr.kernels = 6;
                 k_dots2_ff_tiled<<<dim3((unsigned)((j + 1 + kD2Tile - 1) / kD2Tile), (unsigned)nch), kDotThreads,
                                    0, s>>>(B, j + 1, Vf, L, zf, part, dch);
                 k_reduce_dots2<<<blocks_for((int64_t)(j + 1) * 2 * B), 256, 0, s>>>(nch, j + 1, B, part, dD);
                 k_dcgs_coef<<<(unsigned)B, 256, 0, s>>>(j, mmax, B, dD, Hb, cfa, cft, rsig);
-                k_update2_ff<<<gsb, kDotThreads, 0, s>>>(B, j, Vf, L, V + (int64_t)j * L, cfa, cft, rsig, npart,
-                                                         dch, nch);
+                k_update2_ff<<<gsb, kDotThreads, 0, s>>>(B, j, Vf, L, V + (int64_t)j * L, (int64_t)d2, cfa, cft,
+                                                         rsig, npart, dch, nch);
                 k_colnorm_fin<<<blocks_for(B), 256, 0, s>>>(nch, B, npart, nrm, Hb, j, mmax);
-                k_scale_ff<<<gsb, kDotThreads, 0, s>>>(B, zf, nrm, w, dch, nch);
+                k_scale_ff<<<gsb, kDotThreads, 0, s>>>(B, zf, nrm, nullptr, dch, nch);
             }
         } else if (ffgs) {
             float4 *wf = Vf + (int64_t)(j + 1) * L;
