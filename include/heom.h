@@ -181,7 +181,7 @@ heom_status heom_set_params(heom_hier *h, int n_sets, const heom_c64 *H,
  * stationary states, spectra -- computes
  * set s's own, shallower hierarchy, and parameter sets of different depths share one batched
  * call. Input vectors must be zero beyond a set's tiers (the solvers' are); the apply writes
- * zero there. Tables are not rebuilt. NULL, NULL removes the truncation; heom_set_params
+ * zero there and reads nothing there. Tables are not rebuilt. NULL, NULL removes the truncation; heom_set_params
  * removes it too. Errors: HEOM_EINVAL for tiers out of range or one NULL array. */
 heom_status heom_set_truncation(heom_hier *h, const int *tier_b, const int *tier_f);
 

@@ -61,38 +61,6 @@ constexpr int kPartStride = 2 * 2 * (kArMaxSteps + 2) * kArMaxB + kArMaxB + 2;  
 
 __device__ __forceinline__ float4 ld_l2_f4(const float4 *p) { return __ldcg(p); }
 
-// (h, l) += (bh, bl), float-float sum by Knuth's two-sum, renormalised
-__device__ __forceinline__ void ff_add(float &h, float &l, float bh, float bl) {
-    const float s = h + bh;
-    const float bb = s - h;
-    const float t = (h - (s - bb)) + (bh - bb) + l + bl;
-    h = s + t;
-    l = t - (h - s);
-}
-
-// One Givens step of a rotation chain in float-float: h <- c a - conj(s) h, with c real
-// {hi, lo}, s, a, h complex {re hi, im hi, re lo, im lo}.
-__device__ __forceinline__ float4 ff_rot_step(float2 c, float4 s, float4 a, float4 h) {
-    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
-    ff_mac(rh, rl, c.x, c.y, a.x, a.z);
-    ff_mac(rh, rl, -s.x, -s.z, h.x, h.z);
-    ff_mac(rh, rl, -s.y, -s.w, h.y, h.w);
-    ff_mac(ih, il, c.x, c.y, a.y, a.w);
-    ff_mac(ih, il, -s.x, -s.z, h.y, h.w);
-    ff_mac(ih, il, s.y, s.w, h.x, h.z);
-    ff_norm(rh, rl);
-    ff_norm(ih, il);
-    return make_float4(rh, ih, rl, il);
-}
-
-// acc += c x (complex float-float; acc = {re hi, im hi, re lo, im lo})
-__device__ __forceinline__ void ff_cmac(float &rh, float &rl, float &ih, float &il, const float4 &c,
-                                        const float4 &x) {
-    ff_mac(rh, rl, c.x, c.z, x.x, x.z);
-    ff_mac(rh, rl, -c.y, -c.w, x.y, x.w);
-    ff_mac(ih, il, c.x, c.z, x.y, x.w);
-    ff_mac(ih, il, c.y, c.w, x.x, x.z);
-}
 
 // Partial dot products conj(V_i) w over the CTA's own elements for i < nv (w is V_nv-1 +1
 // slot when self is wanted), into this CTA's slot of part: warp per i, lanes over own

@@ -55,6 +55,39 @@ __device__ __forceinline__ void ff_scale(float &h, float &l, float sh, float sl)
     l = e - (h - p);
 }
 
+// (h, l) += (bh, bl), float-float sum by Knuth's two-sum, renormalised
+__device__ __forceinline__ void ff_add(float &h, float &l, float bh, float bl) {
+    const float s = h + bh;
+    const float bb = s - h;
+    const float t = (h - (s - bb)) + (bh - bb) + l + bl;
+    h = s + t;
+    l = t - (h - s);
+}
+
+// One Givens step of a rotation chain in float-float: h <- c a - conj(s) h, with c real
+// {hi, lo}, s, a, h complex {re hi, im hi, re lo, im lo}.
+__device__ __forceinline__ float4 ff_rot_step(float2 c, float4 s, float4 a, float4 h) {
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    ff_mac(rh, rl, c.x, c.y, a.x, a.z);
+    ff_mac(rh, rl, -s.x, -s.z, h.x, h.z);
+    ff_mac(rh, rl, -s.y, -s.w, h.y, h.w);
+    ff_mac(ih, il, c.x, c.y, a.y, a.w);
+    ff_mac(ih, il, -s.x, -s.z, h.y, h.w);
+    ff_mac(ih, il, s.y, s.w, h.x, h.z);
+    ff_norm(rh, rl);
+    ff_norm(ih, il);
+    return make_float4(rh, ih, rl, il);
+}
+
+// acc += c x (complex float-float; acc = {re hi, im hi, re lo, im lo})
+__device__ __forceinline__ void ff_cmac(float &rh, float &rl, float &ih, float &il, const float4 &c,
+                                        const float4 &x) {
+    ff_mac(rh, rl, c.x, c.z, x.x, x.z);
+    ff_mac(rh, rl, -c.y, -c.w, x.y, x.w);
+    ff_mac(ih, il, c.x, c.z, x.y, x.w);
+    ff_mac(ih, il, c.y, c.w, x.x, x.z);
+}
+
 // ---------------------------------------------------------------- packed float-float pairs
 // The same arithmetic on two values at once with GB300's packed FP32 instructions
 // ({add,sub,mul,fma}.rn.f32x2): a float2 holds the high (or low) words of two float-float

@@ -54,7 +54,8 @@ __device__ __forceinline__ cx<R> damping_of(const DevView<R> &v, int64_t n, int 
 // X points at the start of the ADO vector ([N][d2][B]). Zero for an ADO beyond the
 // truncation of the column's parameter set (heom_set_truncation): with the input zero there
 // too, this is the apply of that set's own, shallower hierarchy, whose ADOs are those of this
-// one within the set's tiers, in the same relative order.
+// one within the set's tiers, in the same relative order (neighbours beyond the tiers are
+// not read: their couplings are the ones the truncation drops).
 template <class R>
 __device__ __forceinline__ cx<R> apply_point(const DevView<R> &v, const cx<R> *__restrict__ X,
                                              int64_t n, int e, int64_t b, int64_t B, int set,
@@ -74,6 +75,7 @@ __device__ __forceinline__ cx<R> apply_point(const DevView<R> &v, const cx<R> *_
     for (int t = __ldg(v.row_ptr + n); t < t1; ++t) {
         const int4 raw = __ldg(reinterpret_cast<const int4 *>(v.ent) + t);
         const int nb = raw.x;
+        if (beyond_cap(v, (int64_t)nb, set)) continue;  // not in the set's hierarchy
         const int op = (int)(int16_t)(raw.y & 0xffff);
         const int k = (int)(int16_t)(raw.y >> 16);
         const int dir = (int)(int16_t)(raw.z & 0xffff);

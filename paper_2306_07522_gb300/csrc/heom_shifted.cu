@@ -559,14 +559,27 @@ __global__ void __launch_bounds__(256) k_dcgs_coef(int j, int mmax, int64_t B, c
     }
 }
 
+// 16-byte asynchronous global -> shared copies (each thread copies and later reads only its
+// own slots, so completion of its own groups is all the ordering it needs)
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // The update of step j on the active entries (blocks stride over the chunks): slot j of the
 // basis turns from p_j into q_j = (p_j - Q_j a) / sigma (float-float; FP64 in its first
-// q64_rows rows, the rows the solution is formed from), slot j + 1
-// from z into w = (z - Q_j t - q_j t_j) / sigma (float-float); npart[c][b] = the chunk's
-// part of |w|^2 (per column in a fixed order; zero for inactive columns). A thread takes
-// kUpRows of its rows at a time, so each coefficient record it loads serves them all; the
+// q64_rows rows, the rows the solution is formed from), slot j + 1 from z into
+// w = (z - Q_j t - q_j t_j) / sigma (float-float); npart[c][b] = the chunk's part of |w|^2
+// (per column in a fixed order; zero for inactive columns). A thread takes kUpRows of its
+// rows at a time, so each coefficient record it loads serves them all, and streams their
+// basis entries through a per-thread ring of kUpDepth stages in shared memory filled by
+// asynchronous copies, so kUpDepth x kUpRows loads are in flight while it computes; the
 // multiply-adds run on packed (re, im) pairs.
-constexpr int kUpRows = 4;
+constexpr int kUpRows = 4, kUpDepth = 4;
+constexpr size_t kUpSmem = (size_t)kUpDepth * kUpRows * kDotThreads * sizeof(float4);
 __global__ void __launch_bounds__(kDotThreads, 2) k_update2_ff(int64_t B, int j, float4 *__restrict__ Vf,
                                                             int64_t vstride, cx<double> *__restrict__ q64,
                                                             int64_t q64_rows,
@@ -575,8 +588,10 @@ __global__ void __launch_bounds__(kDotThreads, 2) k_update2_ff(int64_t B, int j,
                                                             const float2 *__restrict__ rsig,
                                                             double *__restrict__ npart,
                                                             const GsChunk *__restrict__ chunks, int nch) {
+    extern __shared__ float4 ring[];  // [kUpDepth][kUpRows][kDotThreads]
     float4 *pf = Vf + (int64_t)j * vstride, *zf = Vf + (int64_t)(j + 1) * vstride;
     __shared__ double sh[kDotThreads];
+    auto slot = [&](int i, int g) { return ring + ((size_t)((i % kUpDepth) * kUpRows + g) * kDotThreads + threadIdx.x); };
     for (int c = blockIdx.x; c < nch; c += gridDim.x) {
         const GsChunk ch = chunks[c];
         int col, rstep;
@@ -594,33 +609,44 @@ __global__ void __launch_bounds__(kDotThreads, 2) k_update2_ff(int64_t B, int j,
                 for (int g = 0; g < kUpRows; ++g) {
                     const int64_t r = row + (int64_t)g * rstep;
                     ok[g] = r < ch.row1;
-                    tt[g] = (ok[g] ? r : row) * B + col;
+                    tt[g] = (ok[g] ? r : row) * B + col;  // a valid address for the idle rows
                     const float4 z = zf[tt[g]];
                     WH[g] = make_float2(z.x, z.y);
                     WL[g] = make_float2(z.z, z.w);
                     CA[g] = make_float2(0.f, 0.f);
                 }
+                auto issue = [&](int i) {
+                    const float4 *Vi = Vf + (int64_t)i * vstride;
+#pragma unroll
+                    for (int g = 0; g < kUpRows; ++g) cp_async16(slot(i, g), Vi + tt[g]);
+                };
+#pragma unroll
+                for (int q = 0; q < kUpDepth - 1; ++q) {
+                    if (q < j) issue(q);
+                    cp_async_commit();
+                }
                 for (int i = 0; i < j; ++i) {
+                    if (i + kUpDepth - 1 < j) issue(i + kUpDepth - 1);
+                    cp_async_commit();
+                    cp_async_wait<kUpDepth - 1>();  // the group of basis vector i has landed
                     const float4 *rec = cft + ((int64_t)i * B + col) * 3;
                     const float4 r0 = rec[0], r1 = rec[1], r2 = rec[2], a = cfa[(int64_t)i * B + col];
                     const float2 B1h = make_float2(r0.x, r0.y), B1l = make_float2(r0.z, r0.w);
                     const float2 B2h = make_float2(r1.x, r1.y), B2l = make_float2(r1.z, r1.w);
                     const float2 nB1h = make_float2(r2.x, r2.y), nB2h = make_float2(r2.z, r2.w);
                     const float2 A1 = make_float2(a.x, a.y), A2 = make_float2(a.z, a.w);
-                    const float4 *Vi = Vf + (int64_t)i * vstride;
-                    float4 v[kUpRows];
-#pragma unroll
-                    for (int g = 0; g < kUpRows; ++g) v[g] = Vi[tt[g]];
 #pragma unroll
                     for (int g = 0; g < kUpRows; ++g) {
-                        const float2 VRh = make_float2(v[g].x, v[g].x), VRl = make_float2(v[g].z, v[g].z);
-                        const float2 VIh = make_float2(v[g].y, v[g].y), VIl = make_float2(v[g].w, v[g].w);
+                        const float4 v = *slot(i, g);
+                        const float2 VRh = make_float2(v.x, v.x), VRl = make_float2(v.z, v.z);
+                        const float2 VIh = make_float2(v.y, v.y), VIl = make_float2(v.w, v.w);
                         ff2_mac(WH[g], WL[g], VRh, VRl, B1h, B1l, nB1h);
                         ff2_mac(WH[g], WL[g], VIh, VIl, B2h, B2l, nB2h);
                         CA[g] = f2_fma(VRh, A1, CA[g]);
                         CA[g] = f2_fma(VIh, A2, CA[g]);
                     }
                 }
+                cp_async_wait<0>();
 #pragma unroll
                 for (int g = 0; g < kUpRows; ++g) {
                     if (!ok[g]) continue;
@@ -794,13 +820,18 @@ __global__ void k_scale_by(int64_t total, int64_t B, const cx<double> *__restric
 // Per-shift arrays are [S][mmax] (rot_c, rot_s, rdiag: the diagonal R(j, j) for the back
 // substitution) and [S][mmax+1] (g); shift [S], col_of [S] (the batch column of shift k),
 // res [S].
+// With Hbf (the float-float split of Hb's columns j0 .. j1-1) the chain runs in float-float
+// from the split rotations rcf, rsf, which the kernel also writes (FP32 pipe: GB300 issues
+// FP64 at 1/64 of the FP32 rate); the new rotation itself and g stay FP64.
 __global__ void __launch_bounds__(64) k_shift_steps(int j0, int j1, int mmax, int64_t B, int64_t S,
                                                     const cx<double> *__restrict__ Hb,
                                                     const cx<double> *__restrict__ shift,
                                                     const int *__restrict__ col_of,
                                                     double *__restrict__ rot_c, cx<double> *__restrict__ rot_s,
                                                     cx<double> *__restrict__ rdiag, cx<double> *__restrict__ g,
-                                                    const double *__restrict__ beta, double *__restrict__ res) {
+                                                    const double *__restrict__ beta, double *__restrict__ res,
+                                                    const float4 *__restrict__ Hbf, float2 *__restrict__ rot_cf,
+                                                    float4 *__restrict__ rot_sf) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= S) return;
     const int64_t b = col_of[k];
@@ -808,20 +839,46 @@ __global__ void __launch_bounds__(64) k_shift_steps(int j0, int j1, int mmax, in
     double *rc = rot_c + k * mmax;
     cx<double> *rs = rot_s + k * mmax;
     cx<double> *gk = g + k * (mmax + 1);
+    float2 *rcf = Hbf ? rot_cf + k * mmax : nullptr;
+    float4 *rsf = Hbf ? rot_sf + k * mmax : nullptr;
+    const float4 shf = ff_split(shk);
     for (int j = j0; j < j1; ++j) {
         // (the chain is walked from the stored rotations; see the comment above)
-        cx<double> hj = Hb[hb_at(0, j, mmax, B, b)];
-        if (j == 0) hj = hj + shk;
-        for (int i = 0; i < j; ++i) {
-            cx<double> hi1 = Hb[hb_at(i + 1, j, mmax, B, b)];
-            if (i + 1 == j) hi1 = hi1 + shk;
-            hj = rc[i] * hi1 - conj(rs[i]) * hj;
+        cx<double> hj;
+        if (Hbf) {
+            float4 h = Hbf[hb_at(0, j, mmax, B, b)];
+            if (j == 0) {
+                ff_add(h.x, h.z, shf.x, shf.z);
+                ff_add(h.y, h.w, shf.y, shf.w);
+            }
+            for (int i = 0; i < j; ++i) {
+                float4 hi1 = Hbf[hb_at(i + 1, j, mmax, B, b)];
+                if (i + 1 == j) {
+                    ff_add(hi1.x, hi1.z, shf.x, shf.z);
+                    ff_add(hi1.y, hi1.w, shf.y, shf.w);
+                }
+                h = ff_rot_step(rcf[i], rsf[i], hi1, h);
+            }
+            hj = ff_join(h);
+        } else {
+            hj = Hb[hb_at(0, j, mmax, B, b)];
+            if (j == 0) hj = hj + shk;
+            for (int i = 0; i < j; ++i) {
+                cx<double> hi1 = Hb[hb_at(i + 1, j, mmax, B, b)];
+                if (i + 1 == j) hi1 = hi1 + shk;
+                hj = rc[i] * hi1 - conj(rs[i]) * hj;
+            }
         }
         double c;
         cx<double> sn, r;
         givens_rot(hj, Hb[hb_at(j + 1, j, mmax, B, b)], c, sn, r);
         rc[j] = c;
         rs[j] = sn;
+        if (Hbf) {
+            const float ch = __double2float_rn(c);
+            rcf[j] = make_float2(ch, __double2float_rn(c - (double)ch));
+            rsf[j] = ff_split(sn);
+        }
         rdiag[k * mmax + j] = r;
         const cx<double> gj = gk[j];
         gk[j] = c * gj;
@@ -1013,6 +1070,79 @@ __global__ void k_shift_solve_long(int m, int mmax, int64_t B, int64_t S, int d2
     }
 }
 
+// The same solve in float-float (any m): R(i, l) regenerated by the float-float chains from
+// Hbf and the split rotations, y_l = g_l / R(l, l) in FP64 (one division per column), the
+// back substitution's updates of g and x0 = V_0 y from the float-float tier-0 rows of the
+// basis (Vf). Work arrays gw [S][mmax+1] and y [S][mmax] hold float-float values.
+__global__ void __launch_bounds__(64) k_shift_solve_ff(int m, int mmax, int64_t B, int64_t S, int d2,
+                                                       const float4 *__restrict__ Hbf,
+                                                       const cx<double> *__restrict__ shift,
+                                                       const int *__restrict__ col_of,
+                                                       const float2 *__restrict__ rot_cf,
+                                                       const float4 *__restrict__ rot_sf,
+                                                       const cx<double> *__restrict__ rdiag,
+                                                       const cx<double> *__restrict__ g, float4 *__restrict__ gw,
+                                                       float4 *__restrict__ y, const float4 *__restrict__ Vf,
+                                                       int64_t vstride, cx<double> *__restrict__ x0) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= S) return;
+    const int64_t b = col_of[k];
+    const float4 shf = ff_split(shift[k]);
+    const float2 *rcf = rot_cf + k * mmax;
+    const float4 *rsf = rot_sf + k * mmax;
+    float4 *gk = gw + k * (mmax + 1);
+    float4 *yk = y + k * mmax;
+    for (int i = 0; i < m; ++i) gk[i] = ff_split(g[k * (mmax + 1) + i]);
+    for (int l = m - 1; l >= 0; --l) {
+        const cx<double> yl = cdiv(ff_join(gk[l]), rdiag[k * mmax + l]);
+        const float4 yf = ff_split(yl);
+        yk[l] = yf;
+        const float4 nyf = make_float4(-yf.x, -yf.y, -yf.z, -yf.w);
+        float4 carry = Hbf[hb_at(0, l, mmax, B, b)];
+        if (l == 0) {
+            ff_add(carry.x, carry.z, shf.x, shf.z);
+            ff_add(carry.y, carry.w, shf.y, shf.w);
+        }
+        for (int i = 0; i < l; ++i) {
+            float4 a1 = Hbf[hb_at(i + 1, l, mmax, B, b)];
+            if (i + 1 == l) {
+                ff_add(a1.x, a1.z, shf.x, shf.z);
+                ff_add(a1.y, a1.w, shf.y, shf.w);
+            }
+            const float2 c = rcf[i];
+            const float4 sn = rsf[i];
+            // R(i, l) = c carry + s a1; carry <- c a1 - conj(s) carry
+            float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+            ff_mac(rh, rl, c.x, c.y, carry.x, carry.z);
+            ff_mac(ih, il, c.x, c.y, carry.y, carry.w);
+            ff_cmac(rh, rl, ih, il, sn, a1);
+            ff_norm(rh, rl);
+            ff_norm(ih, il);
+            carry = ff_rot_step(c, sn, a1, carry);
+            // g_i -= R(i, l) y_l
+            float4 gi = gk[i];
+            float gr = gi.x, grl = gi.z, gim = gi.y, gil = gi.w;
+            ff_cmac(gr, grl, gim, gil, make_float4(rh, ih, rl, il), nyf);
+            ff_norm(gr, grl);
+            ff_norm(gim, gil);
+            gk[i] = make_float4(gr, gim, grl, gil);
+        }
+    }
+    for (int e = 0; e < d2; ++e) {
+        float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+        for (int l = 0; l < m; ++l) ff_cmac(rh, rl, ih, il, Vf[(int64_t)l * vstride + (int64_t)e * B + b], yk[l]);
+        x0[k * d2 + e] = cx<double>{(double)rh + (double)rl, (double)ih + (double)il};
+    }
+}
+
+// Hbf = float-float split of Hessenberg columns j0 .. j1-1 (rows 0 .. mmax)
+__global__ void k_split_hb(int j0, int j1, int mmax, int64_t B, const cx<double> *__restrict__ Hb,
+                           float4 *__restrict__ Hbf) {
+    const int64_t n = (int64_t)(j1 - j0) * (mmax + 1) * B, off = (int64_t)j0 * (mmax + 1) * B;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        Hbf[off + t] = ff_split(Hb[off + t]);
+}
+
 // g[k][0] = beta of shift k's column
 __global__ void k_init_g(int64_t S, int mmax, const int *__restrict__ col_of,
                          const double *__restrict__ beta, cx<double> *__restrict__ g) {
@@ -1042,7 +1172,7 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
             // the hierarchy's own workspace is reused (or grown), or else the largest one the
             // library keeps cached on this device
             free_b += std::max(h->ws.bytes, ws_cached_max(h->device));
-            const double per_step = 32.0 * (double)L + 88.0 * (double)S + (64.0 + 32.0 * 456) * (double)B;
+            const double per_step = 32.0 * (double)L + 112.0 * (double)S + (64.0 + 32.0 * 456) * (double)B;
             const double fixed = 64.0 * (double)L + 48.0 * (double)S + (double)(64 * 2 + 2) * B * 16.0;
             const double avail = 0.6 * (double)free_b - fixed;
             const int fit = avail > per_step ? (int)std::min(2.0e9, avail / per_step) - 1 : 0;
@@ -1052,6 +1182,9 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
                 return HEOM_ENOMEM;
             }
             mmax = std::min(mmax, fit);
+            // the Hessenberg matrices (FP64 and float-float split) grow as mmax^2: within a
+            // tenth of the free memory
+            while (mmax > 8 && 32.0 * (double)B * (mmax + 1.0) * mmax > 0.1 * (double)free_b) mmax -= 8;
         }
     }
     // device memory: basis V [mmax+1][L] (the new vector is formed in its slot), Hb
@@ -1094,11 +1227,21 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
         }
     }
     const int nch = (int)chunks.size();
-    const int npc = std::max(nchunk, nch);
+    // the update's chunks: the same runs cut about 8x finer (its blocks stride over them, one
+    // wave of resident blocks, so that the last chunks balance across the SMs)
+    std::vector<GsChunk> uchunks;
+    for (const GsChunk &c0 : chunks) {
+        const int64_t rows_c = c0.row1 - c0.row0, ustep = std::max<int64_t>(1, (rows_c + 7) / 8);
+        for (int64_t r = c0.row0; r < c0.row1; r += ustep)
+            uchunks.push_back(GsChunk{(int32_t)r, (int32_t)std::min<int64_t>(c0.row1, r + ustep), c0.acols, 0});
+    }
+    const int nuch = (int)uchunks.size();
+    const int npc = std::max(nchunk, nch);  // partial-dot chunks
     const size_t opart = take((size_t)npc * (mmax + 2) * 2 * B * 16), oskip = take(sizeof(int)),
                  oran = take((size_t)mmax * sizeof(int));
-    const size_t onp = take((size_t)npc * B * 8);
-    const size_t och = take((size_t)std::max(nch, 1) * sizeof(GsChunk));
+    const size_t onp = take((size_t)std::max(npc, nuch) * B * 8);
+    const size_t och = take((size_t)std::max(nch, 1) * sizeof(GsChunk)),
+                 ouch = take((size_t)std::max(nuch, 1) * sizeof(GsChunk));
     const size_t oVf = ffgs ? take((size_t)(mmax + 1) * L * 16) : 0,
                  ohf = ffgs ? take((size_t)(mmax + 2) * B * 16) : 0;
     // the delayed-reorthogonalisation scalars: dots D [mmax+1][2][B], coefficients
@@ -1113,7 +1256,8 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
     const bool keepR = (double)S * (double)rtri * 16.0 <= (double)(1ull << 30);
     const size_t oR = keepR ? take((size_t)S * std::max<int64_t>(rtri, 1) * 16) : 0;
     // the persistent Arnoldi's float-float copies of the rotations
-    const size_t orcf = pers ? take((size_t)S * mmax * 8) : 0, orsf = pers ? take((size_t)S * mmax * 16) : 0;
+    const size_t orcf = ffgs ? take((size_t)S * mmax * 8) : 0, orsf = ffgs ? take((size_t)S * mmax * 16) : 0;
+    const size_t ohbf = ffgs ? take((size_t)(mmax + 1) * mmax * B * 16) : 0;
     heom_status st = ensure_ws(h->ws, off);
     if (st != HEOM_OK) return st;
     char *base = (char *)h->ws.p;
@@ -1136,8 +1280,9 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
     float2 *rsig = ffgs ? (float2 *)(base + orsig) : nullptr;
     float4 *cfa = ffgs ? (float4 *)(base + ocfa) : nullptr, *cft = ffgs ? (float4 *)(base + ocft) : nullptr;
     cx<double> *Rst = keepR ? (cx<double> *)(base + oR) : nullptr;
-    float2 *rot_cf = pers ? (float2 *)(base + orcf) : nullptr;
-    float4 *rot_sf = pers ? (float4 *)(base + orsf) : nullptr;
+    float2 *rot_cf = ffgs ? (float2 *)(base + orcf) : nullptr;
+    float4 *rot_sf = ffgs ? (float4 *)(base + orsf) : nullptr;
+    float4 *Hbf = ffgs ? (float4 *)(base + ohbf) : nullptr;
     HEOM_CUDA(memcpy_counted(dsh, shift.data(), S * 16, cudaMemcpyHostToDevice, s));
     HEOM_CUDA(memcpy_counted(dco, col_of.data(), S * 4, cudaMemcpyHostToDevice, s));
     HEOM_CUDA(cudaMemsetAsync(Hb, 0, (size_t)(mmax + 1) * mmax * B * 16, s));
@@ -1160,7 +1305,19 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
     const bool tiled = tile_ok(v, B);
     const GsChunk *dch = (const GsChunk *)(base + och);
     if (nch > 0) HEOM_CUDA(memcpy_counted((void *)dch, chunks.data(), nch * sizeof(GsChunk), cudaMemcpyHostToDevice, s));
+    const GsChunk *duch = (const GsChunk *)(base + ouch);
+    if (nuch > 0)
+        HEOM_CUDA(memcpy_counted((void *)duch, uchunks.data(), nuch * sizeof(GsChunk), cudaMemcpyHostToDevice, s));
     const int gsb = std::max(1, std::min(nch, 152 * 8));  // blocks of the chunk-striding kernels
+    int gsu = 1;  // the update's grid: its resident blocks (one wave)
+    if (ffgs) {
+        HEOM_CUDA(cudaFuncSetAttribute(k_update2_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUpSmem));
+        int occ = 0, dev = 0, sms = 0;
+        HEOM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update2_ff, kDotThreads, kUpSmem));
+        HEOM_CUDA(cudaGetDevice(&dev));
+        HEOM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        gsu = std::max(1, std::min(nuch, std::max(occ, 1) * sms));
+    }
     // elements of one vector that can be nonzero (truncated sets: the kept rows of each
     // column), and the ADO-applies of one apply: the work and the algorithmic bytes counted
     const int64_t cps = B / h->n_sets;
@@ -1216,9 +1373,9 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
                                    0, s>>>(B, j + 1, Vf, L, zf, part, dch);
                 k_reduce_dots2<<<blocks_for((int64_t)(j + 1) * 2 * B), 256, 0, s>>>(nch, j + 1, B, part, dD);
                 k_dcgs_coef<<<(unsigned)B, 256, 0, s>>>(j, mmax, B, dD, Hb, cfa, cft, rsig);
-                k_update2_ff<<<gsb, kDotThreads, 0, s>>>(B, j, Vf, L, V + (int64_t)j * L, (int64_t)d2, cfa, cft,
-                                                         rsig, npart, dch, nch);
-                k_colnorm_fin<<<blocks_for(B), 256, 0, s>>>(nch, B, npart, nrm, Hb, j, mmax);
+                k_update2_ff<<<gsu, kDotThreads, kUpSmem, s>>>(B, j, Vf, L, V + (int64_t)j * L, (int64_t)d2, cfa,
+                                                               cft, rsig, npart, duch, nuch);
+                k_colnorm_fin<<<blocks_for(B), 256, 0, s>>>(nuch, B, npart, nrm, Hb, j, mmax);
                 k_scale_ff<<<gsb, kDotThreads, 0, s>>>(B, zf, nrm, nullptr, dch, nch);
             }
         } else if (ffgs) {
@@ -1284,10 +1441,17 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
         m = j + 1;
         if ((m % check == 0 || m == mmax) && m - lag > j_done) {
             const int mf = m - lag;  // the final Hessenberg columns
-            {   // every shift's Givens QR catches up with the new Hessenberg columns
+            {   // every shift's Givens QR catches up with the new Hessenberg columns (chains in
+                // float-float with the delayed-reorthogonalisation process)
                 Prof pr(HEOM_KC_OTHER, s, (double)S * (mf - j_done), 0.0);
-                k_shift_steps<<<(unsigned)((S + 63) / 64), 64, 0, s>>>(j_done, mf, mmax, B, S, Hb, dsh, dco,
-                                                                      rot_c, rot_s, rdiag, g, beta, dres);
+                if (dcgs) {
+                    pr.kernels = 2;
+                    k_split_hb<<<blocks_for((int64_t)(mf - j_done) * (mmax + 1) * B), 256, 0, s>>>(j_done, mf, mmax,
+                                                                                                 B, Hb, Hbf);
+                }
+                k_shift_steps<<<(unsigned)((S + 63) / 64), 64, 0, s>>>(
+                    j_done, mf, mmax, B, S, Hb, dsh, dco, rot_c, rot_s, rdiag, g, beta, dres,
+                    dcgs ? Hbf : nullptr, rot_cf, rot_sf);
             }
             j_done = mf;
             HEOM_CUDA(memcpy_counted(hres.data(), dres, S * 8, cudaMemcpyDeviceToHost, s));
@@ -1319,6 +1483,10 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
                 HEOM_CUDA(cudaFuncSetAttribute(k_shift_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
             k_shift_solve<<<(unsigned)((S + kSolveThreads - 1) / kSolveThreads), kSolveThreads, smb, s>>>(
                 mf, mmax, B, S, d2, Hb, dsh, dco, rot_c, rot_s, rdiag, g, V, L, dx0);
+        } else if (dcgs) {
+            k_shift_solve_ff<<<(unsigned)((S + 63) / 64), 64, 0, s>>>(mf, mmax, B, S, d2, Hbf, dsh, dco, rot_cf,
+                                                                      rot_sf, rdiag, g, (float4 *)gw, (float4 *)y,
+                                                                      Vf, L, dx0);
         } else {
             k_shift_solve_long<<<(unsigned)((S + 63) / 64), 64, 0, s>>>(mf, mmax, B, S, d2, Hb, dsh, dco, rot_c,
                                                                         rot_s, rdiag, g, gw, y, V, L, dx0);
