@@ -307,24 +307,33 @@ __device__ __forceinline__ float4 mul_mi_ff(float m, float4 a) {
 // set b / cps): Eq. HEOM at every (ADO n, element e, column b), the terms in the order of the
 // per-element FP64 apply, every product a float-float one (unit roundoff 2^-48 instead of
 // FP64's 2^-53, at FP32 issue rates). An ADO beyond its column's set truncation is written
-// as zero, and neighbours beyond it are skipped (their entries are zero).
+// as zero, and neighbours beyond it are skipped (their entries are zero). A thread takes CPT
+// adjacent columns of one parameter set (cps a multiple of CPT), so the decoding of the
+// neighbour entries and every coefficient product serve all of them; operator values of +-1
+// (fermionic annihilators with their Jordan-Wigner signs) skip the coefficient product.
+template <int CPT>
 __global__ void __launch_bounds__(256, 3) k_apply_ff(DevView<double> v, const float4 *__restrict__ X,
-                                                  float4 *__restrict__ Y, int64_t B, int64_t cps) {
+                                                     float4 *__restrict__ Y, int64_t B, int64_t cps) {
     const int d = v.d, d2 = v.d2;
-    const int64_t total = v.N * d2 * B;
+    const int64_t BT = B / CPT, total = v.N * d2 * BT;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t row = t / B, b = t - row * B, n = row / d2;
+        const int64_t row = t / BT, b = (t - row * BT) * CPT, n = row / d2;
         const int e = (int)(row - n * d2), set = (int)(b / cps);
+        float4 *Yo = Y + row * B + b;
         if (beyond_cap(v, n, set)) {
-            Y[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < CPT; ++u) Yo[u] = make_float4(0.f, 0.f, 0.f, 0.f);
             continue;
         }
+        const int cap = v.set_cap ? v.set_cap[set] : 0x7fffffff;
         const int r = e / d, c = e - r * d;
         const float4 *Xn = X + n * d2 * B + b;
-        float2 H = make_float2(0.f, 0.f), L = H;
+        float2 H[CPT], L[CPT];
+#pragma unroll
+        for (int u = 0; u < CPT; ++u) H[u] = L[u] = make_float2(0.f, 0.f);
         {   // damping: -sum_k count_k rate_k x
-            float2 DH = H, DL = H;
+            float2 DH = make_float2(0.f, 0.f), DL = DH;
             const int o1 = __ldg(v.occ_ptr + n + 1);
             for (int o = __ldg(v.occ_ptr + n); o < o1; ++o) {
                 const int packed = __ldg(reinterpret_cast<const int *>(v.occ) + o);
@@ -334,17 +343,25 @@ __global__ void __launch_bounds__(256, 3) k_apply_ff(DevView<double> v, const fl
                 ff2_mac(DH, DL, make_float2(cnt, cnt), make_float2(0.f, 0.f), make_float2(rt.x, rt.y),
                         make_float2(rt.z, rt.w), make_float2(-rt.x, -rt.y));
             }
-            const float4 dm = ff_pack(DH, DL);
-            cmac_ff(H, L, make_float4(-dm.x, -dm.y, -dm.z, -dm.w), Xn[(int64_t)e * B]);
+            const float4 dm = ff_pack(DH, DL), ndm = make_float4(-dm.x, -dm.y, -dm.z, -dm.w);
+#pragma unroll
+            for (int u = 0; u < CPT; ++u) cmac_ff(H[u], L[u], ndm, Xn[(int64_t)e * B + u]);
         }
         const float4 *sv = v.s_valf + (int64_t)set * v.nS;
-        for (int j = __ldg(v.s_ptr + e), j1 = __ldg(v.s_ptr + e + 1); j < j1; ++j)
-            cmac_ff(H, L, sv[j], Xn[(int64_t)__ldg(v.s_src + j) * B]);
+        for (int j = __ldg(v.s_ptr + e), j1 = __ldg(v.s_ptr + e + 1); j < j1; ++j) {
+            const float4 cv = sv[j];
+            const float4 *xs = Xn + (int64_t)__ldg(v.s_src + j) * B;
+#pragma unroll
+            for (int u = 0; u < CPT; ++u) cmac_ff(H[u], L[u], cv, xs[u]);
+        }
         const int t1 = __ldg(v.row_ptr + n + 1);
         for (int q = __ldg(v.row_ptr + n); q < t1; ++q) {
             const int4 raw = __ldg(reinterpret_cast<const int4 *>(v.ent) + q);
             const int nb = raw.x;
-            if (beyond_cap(v, (int64_t)nb, set)) continue;
+            if (v.set_cap) {  // neighbours beyond the set's tiers are not in its hierarchy
+                const int tn = __ldg(v.ado_tier + nb);
+                if ((tn & 0xffff) > (cap & 0xffff) || (tn >> 16) > (cap >> 16)) continue;
+            }
             const int op = (int)(int16_t)(raw.y & 0xffff);
             const int k = (int)(int16_t)(raw.y >> 16);
             const int dir = (int)(int16_t)(raw.z & 0xffff);
@@ -361,12 +378,27 @@ __global__ void __launch_bounds__(256, 3) k_apply_ff(DevView<double> v, const fl
             }
             const float4 *Xb = X + (int64_t)nb * d2 * B + b;
             const int base = op * (d + 1);
-            for (int j = __ldg(v.op_rptr + base + r), j1 = __ldg(v.op_rptr + base + r + 1); j < j1; ++j)
-                cmac_ff(H, L, cmul_ff(cl, v.op_rvalf[j]), Xb[(int64_t)(__ldg(v.op_rcol + j) * d + c) * B]);
-            for (int j = __ldg(v.op_cptr + base + c), j1 = __ldg(v.op_cptr + base + c + 1); j < j1; ++j)
-                cmac_ff(H, L, cmul_ff(cr, v.op_cvalf[j]), Xb[(int64_t)(r * d + __ldg(v.op_crow + j)) * B]);
+            for (int j = __ldg(v.op_rptr + base + r), j1 = __ldg(v.op_rptr + base + r + 1); j < j1; ++j) {
+                const float4 ov = v.op_rvalf[j];
+                const float4 cf = ov.y == 0.f && ov.z == 0.f && ov.w == 0.f && (ov.x == 1.f || ov.x == -1.f)
+                                      ? make_float4(ov.x * cl.x, ov.x * cl.y, ov.x * cl.z, ov.x * cl.w)
+                                      : cmul_ff(cl, ov);
+                const float4 *xs = Xb + (int64_t)(__ldg(v.op_rcol + j) * d + c) * B;
+#pragma unroll
+                for (int u = 0; u < CPT; ++u) cmac_ff(H[u], L[u], cf, xs[u]);
+            }
+            for (int j = __ldg(v.op_cptr + base + c), j1 = __ldg(v.op_cptr + base + c + 1); j < j1; ++j) {
+                const float4 ov = v.op_cvalf[j];
+                const float4 cf = ov.y == 0.f && ov.z == 0.f && ov.w == 0.f && (ov.x == 1.f || ov.x == -1.f)
+                                      ? make_float4(ov.x * cr.x, ov.x * cr.y, ov.x * cr.z, ov.x * cr.w)
+                                      : cmul_ff(cr, ov);
+                const float4 *xs = Xb + (int64_t)(r * d + __ldg(v.op_crow + j)) * B;
+#pragma unroll
+                for (int u = 0; u < CPT; ++u) cmac_ff(H[u], L[u], cf, xs[u]);
+            }
         }
-        Y[t] = ff_pack(H, L);
+#pragma unroll
+        for (int u = 0; u < CPT; ++u) Yo[u] = ff_pack(H[u], L[u]);
     }
 }
 
@@ -374,18 +406,19 @@ __global__ void __launch_bounds__(256, 3) k_apply_ff(DevView<double> v, const fl
 // Arnoldi with classical Gram-Schmidt reorthogonalised one step late (DCGS2: Swirydowicz,
 // Langou, Thomas, Yamazaki, "Low synchronization Gram-Schmidt and GMRES algorithms", 2020),
 // per batch column. After step j-1 the slots hold q_0 .. q_{j-1} (final, orthonormal) and
-// p_j, the new vector after one projection, normalised: M q_{j-1} = Q_j h' + nu p_j with
-// h' = Hb(0..j-1, j-1) and nu = Hb(j, j-1) provisional. Step j applies M to p_j (z = M p_j)
-// and then, with ONE read of the basis for the dot products and one for the update:
+// p_j, the new vector after one projection and not normalised: M q_{j-1} = Q_j h' + p_j with
+// h' = Hb(0..j-1, j-1) provisional. Step j applies M to p_j (z = M p_j) and then, with ONE
+// read of the basis for the dot products and one for the update:
 //   a = Q_j^H p_j, c = Q_j^H z, e = p_j^H z, f = p_j^H p_j         (k_dots2_ff_tiled)
 //   sigma = sqrt(f - |a|^2), q_j = (p_j - Q_j a) / sigma            (p_j = Q_j a + sigma q_j)
-//   Hb(0..j-1, j-1) += nu a, Hb(j, j-1) = nu sigma                  (column j-1 final)
+//   Hb(0..j-1, j-1) += a, Hb(j, j-1) = sigma                        (column j-1 final)
 //   t = Q_{j+1}^H z = (c, (e - a^H c) / sigma)
 //   Hb(0..j, j) = (t - Hb(0..j, 0..j-1) a) / sigma                   (M q_j = (z - M Q_j a) / sigma)
-//   w = (z - Q_{j+1} t) / sigma, nu' = |w|, p_{j+1} = w / nu'        (k_update2_ff, k_scale_ff)
+//   p_{j+1} = (z - Q_{j+1} t) / sigma                               (k_update2_ff)
 // so every vector is projected out twice, as in two-pass classical Gram-Schmidt, at the
-// memory traffic of one pass; column j of Hb becomes final one step later. q_0 = p_0 = b /
-// beta exactly (step 0 takes sigma = 1).
+// memory traffic of one pass, and no separate normalisation pass is needed (sigma of the next
+// step is the subdiagonal entry); column j of Hb becomes final one step later. q_0 = p_0 =
+// b / beta exactly (step 0 takes sigma = 1).
 
 // part[c][i][r][b] = sum over chunk c of conj(V_i) x_r for x_0 = p (= slot nv - 1 of the
 // basis) and x_1 = z: the two dot-product sets of one step in one read of the basis, tiled
@@ -522,7 +555,7 @@ __global__ void __launch_bounds__(256) k_dcgs_coef(int j, int mmax, int64_t B, c
         const cx<double> e = Dc(j);
         s_sig = sig;
         s_inv = inv;
-        s_nu = j > 0 ? Hb[hb_at(j, j - 1, mmax, B, b)].re : 0.0;
+        s_nu = j > 0 ? 1.0 : 0.0;  // p_j is the previous step's w itself, not normalised
         s_tj = inv * cx<double>{e.re - s_re[0], e.im - s_im[0]};
         const float h = (float)inv;
         rsig[b] = make_float2(h, (float)(inv - (double)h));
@@ -572,8 +605,8 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // The update of step j on the active entries (blocks stride over the chunks): slot j of the
 // basis turns from p_j into q_j = (p_j - Q_j a) / sigma (float-float; FP64 in its first
 // q64_rows rows, the rows the solution is formed from), slot j + 1 from z into
-// w = (z - Q_j t - q_j t_j) / sigma (float-float); npart[c][b] = the chunk's part of |w|^2
-// (per column in a fixed order; zero for inactive columns). A thread takes kUpRows of its
+// w = (z - Q_j t - q_j t_j) / sigma (float-float), which is p_{j+1} as it stands: it is not
+// normalised (the next step's sigma is the exact subdiagonal entry). A thread takes kUpRows of its
 // rows at a time, so each coefficient record it loads serves them all, and streams their
 // basis entries through a per-thread ring of kUpDepth stages in shared memory filled by
 // asynchronous copies, so kUpDepth x kUpRows loads are in flight while it computes; the
@@ -586,17 +619,14 @@ __global__ void __launch_bounds__(kDotThreads, 2) k_update2_ff(int64_t B, int j,
                                                             const float4 *__restrict__ cfa,
                                                             const float4 *__restrict__ cft,
                                                             const float2 *__restrict__ rsig,
-                                                            double *__restrict__ npart,
                                                             const GsChunk *__restrict__ chunks, int nch) {
     extern __shared__ float4 ring[];  // [kUpDepth][kUpRows][kDotThreads]
     float4 *pf = Vf + (int64_t)j * vstride, *zf = Vf + (int64_t)(j + 1) * vstride;
-    __shared__ double sh[kDotThreads];
     auto slot = [&](int i, int g) { return ring + ((size_t)((i % kUpDepth) * kUpRows + g) * kDotThreads + threadIdx.x); };
     for (int c = blockIdx.x; c < nch; c += gridDim.x) {
         const GsChunk ch = chunks[c];
         int col, rstep;
         int64_t row;
-        double acc = 0.0;
         if (chunk_lane(ch, col, rstep, row)) {
             const float2 rs = rsig[col];
             const float4 *tjr = cft + ((int64_t)j * B + col) * 3;
@@ -674,23 +704,10 @@ __global__ void __launch_bounds__(kDotThreads, 2) k_update2_ff(int64_t B, int j,
                     ff_scale(ih, il, rs.x, rs.y);
                     pf[t] = make_float4(qrh, qih, qrl, qil);
                     if (t < q64_rows * B) q64[t] = cx<double>{(double)qrh + (double)qrl, (double)qih + (double)qil};
-                    const float4 w = make_float4(rh, ih, rl, il);
-                    zf[t] = w;
-                    acc += norm2(ff_join(w));
+                    zf[t] = make_float4(rh, ih, rl, il);
                 }
             }
         }
-        sh[threadIdx.x] = acc;
-        __syncthreads();
-        if (threadIdx.x < B) {
-            double s = 0.0;
-            if ((int)threadIdx.x < ch.acols) {
-                const int per = kDotThreads / ch.acols;
-                for (int q = 0; q < per; ++q) s += sh[threadIdx.x + q * ch.acols];
-            }
-            npart[(int64_t)c * B + threadIdx.x] = s;
-        }
-        __syncthreads();
     }
 }
 
@@ -1353,7 +1370,12 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
             Prof pr(HEOM_KC_KRYLOV_APPLY64, s, Lk / h->d2, 2.0 * Lk * 16);
             if (dcgs) {  // float-float, from and into the float-float basis
                 const int64_t grid = std::min<int64_t>((L + 255) / 256, 152 * 16);
-                k_apply_ff<<<(unsigned)grid, 256, 0, s>>>(v, Vf + (int64_t)j * L, Vf + (int64_t)(j + 1) * L, B, cps);
+                if (cps % 2 == 0)
+                    k_apply_ff<2><<<(unsigned)grid, 256, 0, s>>>(v, Vf + (int64_t)j * L, Vf + (int64_t)(j + 1) * L, B,
+                                                                 cps);
+                else
+                    k_apply_ff<1><<<(unsigned)grid, 256, 0, s>>>(v, Vf + (int64_t)j * L, Vf + (int64_t)(j + 1) * L, B,
+                                                                 cps);
             } else if (tiled) {
                 ta.x = vj;
                 ta.out = w;
@@ -1367,16 +1389,14 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
             // one read of the basis for the dots, one for the update (see k_dots2_ff_tiled)
             float4 *zf = Vf + (int64_t)(j + 1) * L;
             {
-                Prof pr(HEOM_KC_KRYLOV_VECTOR, s, (double)(j + 1) * Lg, (2.0 * j + 8.0) * Lg * 16);
-                pr.kernels = 6;
+                Prof pr(HEOM_KC_KRYLOV_VECTOR, s, (double)(j + 1) * Lg, (2.0 * j + 6.0) * Lg * 16);
+                pr.kernels = 4;
                 k_dots2_ff_tiled<<<dim3((unsigned)((j + 1 + kD2Tile - 1) / kD2Tile), (unsigned)nch), kDotThreads,
                                    0, s>>>(B, j + 1, Vf, L, zf, part, dch);
                 k_reduce_dots2<<<blocks_for((int64_t)(j + 1) * 2 * B), 256, 0, s>>>(nch, j + 1, B, part, dD);
                 k_dcgs_coef<<<(unsigned)B, 256, 0, s>>>(j, mmax, B, dD, Hb, cfa, cft, rsig);
                 k_update2_ff<<<gsu, kDotThreads, kUpSmem, s>>>(B, j, Vf, L, V + (int64_t)j * L, (int64_t)d2, cfa,
-                                                               cft, rsig, npart, duch, nuch);
-                k_colnorm_fin<<<blocks_for(B), 256, 0, s>>>(nuch, B, npart, nrm, Hb, j, mmax);
-                k_scale_ff<<<gsb, kDotThreads, 0, s>>>(B, zf, nrm, nullptr, dch, nch);
+                                                               cft, rsig, duch, nuch);
             }
         } else if (ffgs) {
             float4 *wf = Vf + (int64_t)(j + 1) * L;
