@@ -114,11 +114,11 @@ void release_cached(int device) {  // device < 0: every device
 }
 }  // namespace
 
-size_t ws_cached_max(int device) {
+size_t ws_cached_total(int device) {
     std::lock_guard<std::mutex> lk(g_ws_mu);
     size_t m = 0;
     for (const WsEntry &e : g_ws_cache)
-        if (e.device == device) m = std::max(m, e.buf.bytes);
+        if (e.device == device) m += e.buf.bytes;
     return m;
 }
 

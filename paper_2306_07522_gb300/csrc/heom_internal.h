@@ -265,7 +265,7 @@ long long wait_limit_cycles();               // bound of device-side waits (heom
 void dfree(DBuf &b);
 heom_status ensure_ws(DBuf &b, size_t bytes);  // grows b, from the workspace cache when it can
 void ws_release(DBuf &b, int device);           // hands b to the workspace cache
-size_t ws_cached_max(int device);               // largest cached workspace on a device
+size_t ws_cached_total(int device);             // bytes of the cached workspaces on a device
 void ws_release_all();
 
 // bounds of one ADO range of the persistent tiled kernel (shared-memory budget)

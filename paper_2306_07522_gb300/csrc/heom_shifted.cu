@@ -304,22 +304,23 @@ __device__ __forceinline__ float4 mul_mi_ff(float m, float4 a) {
 }
 
 // Y = M X in float-float for batched columns of several parameter sets (column b belongs to
-// set b / cps): Eq. HEOM at every (ADO n, element e, column b), the terms in the order of the
+// set set_of[b]): Eq. HEOM at every (ADO n, element e, column b), the terms in the order of the
 // per-element FP64 apply, every product a float-float one (unit roundoff 2^-48 instead of
 // FP64's 2^-53, at FP32 issue rates). An ADO beyond its column's set truncation is written
 // as zero, and neighbours beyond it are skipped (their entries are zero). A thread takes CPT
-// adjacent columns of one parameter set (cps a multiple of CPT), so the decoding of the
+// adjacent columns of one parameter set (set_of equal on each aligned CPT columns), so the decoding of the
 // neighbour entries and every coefficient product serve all of them; operator values of +-1
 // (fermionic annihilators with their Jordan-Wigner signs) skip the coefficient product.
 template <int CPT>
 __global__ void __launch_bounds__(256, 3) k_apply_ff(DevView<double> v, const float4 *__restrict__ X,
-                                                     float4 *__restrict__ Y, int64_t B, int64_t cps) {
+                                                     float4 *__restrict__ Y, int64_t B,
+                                                     const int *__restrict__ set_of) {
     const int d = v.d, d2 = v.d2;
     const int64_t BT = B / CPT, total = v.N * d2 * BT;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t row = t / BT, b = (t - row * BT) * CPT, n = row / d2;
-        const int e = (int)(row - n * d2), set = (int)(b / cps);
+        const int e = (int)(row - n * d2), set = set_of[b];
         float4 *Yo = Y + row * B + b;
         if (beyond_cap(v, n, set)) {
 #pragma unroll
@@ -837,7 +838,8 @@ __global__ void k_scale_by(int64_t total, int64_t B, const cx<double> *__restric
 // Per-shift arrays are [S][mmax] (rot_c, rot_s, rdiag: the diagonal R(j, j) for the back
 // substitution) and [S][mmax+1] (g); shift [S], col_of [S] (the batch column of shift k),
 // res [S].
-// With Hbf (the float-float split of Hb's columns j0 .. j1-1) the chain runs in float-float
+// With klist, the S shifts taken are klist[0 .. S-1]. With Hbf (the float-float split of Hb's
+// columns j0 .. j1-1) the chain runs in float-float
 // from the split rotations rcf, rsf, which the kernel also writes (FP32 pipe: GB300 issues
 // FP64 at 1/64 of the FP32 rate); the new rotation itself and g stay FP64.
 __global__ void __launch_bounds__(64) k_shift_steps(int j0, int j1, int mmax, int64_t B, int64_t S,
@@ -848,9 +850,10 @@ __global__ void __launch_bounds__(64) k_shift_steps(int j0, int j1, int mmax, in
                                                     cx<double> *__restrict__ rdiag, cx<double> *__restrict__ g,
                                                     const double *__restrict__ beta, double *__restrict__ res,
                                                     const float4 *__restrict__ Hbf, float2 *__restrict__ rot_cf,
-                                                    float4 *__restrict__ rot_sf) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= S) return;
+                                                    float4 *__restrict__ rot_sf, const int *__restrict__ klist) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= S) return;
+    const int64_t k = klist ? klist[t] : t;
     const int64_t b = col_of[k];
     const cx<double> shk = shift[k];
     double *rc = rot_c + k * mmax;
@@ -1090,7 +1093,8 @@ __global__ void k_shift_solve_long(int m, int mmax, int64_t B, int64_t S, int d2
 // The same solve in float-float (any m): R(i, l) regenerated by the float-float chains from
 // Hbf and the split rotations, y_l = g_l / R(l, l) in FP64 (one division per column), the
 // back substitution's updates of g and x0 = V_0 y from the float-float tier-0 rows of the
-// basis (Vf). Work arrays gw [S][mmax+1] and y [S][mmax] hold float-float values.
+// basis (Vf), for the S shifts klist[0 .. S-1]. Work arrays gw [S][mmax+1] and y [S][mmax]
+// (indexed by shift) hold float-float values.
 __global__ void __launch_bounds__(64) k_shift_solve_ff(int m, int mmax, int64_t B, int64_t S, int d2,
                                                        const float4 *__restrict__ Hbf,
                                                        const cx<double> *__restrict__ shift,
@@ -1100,9 +1104,11 @@ __global__ void __launch_bounds__(64) k_shift_solve_ff(int m, int mmax, int64_t 
                                                        const cx<double> *__restrict__ rdiag,
                                                        const cx<double> *__restrict__ g, float4 *__restrict__ gw,
                                                        float4 *__restrict__ y, const float4 *__restrict__ Vf,
-                                                       int64_t vstride, cx<double> *__restrict__ x0) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= S) return;
+                                                       int64_t vstride, cx<double> *__restrict__ x0,
+                                                       const int *__restrict__ klist) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= S) return;
+    const int64_t k = klist[t];
     const int64_t b = col_of[k];
     const float4 shf = ff_split(shift[k]);
     const float2 *rcf = rot_cf + k * mmax;
@@ -1160,6 +1166,31 @@ __global__ void k_split_hb(int j0, int j1, int mmax, int64_t B, const cx<double>
         Hbf[off + t] = ff_split(Hb[off + t]);
 }
 
+// Column compaction of the Krylov state when parameter sets leave the shift-invariant process
+// (all their shifts converged): column c of the new layout is column map[c] of the old one.
+// The basis (nslots slots of rows x Bo entries into rows x Bn), the Hessenberg matrices (ne
+// entries (i, j) per column) and beta move; nothing else is per column.
+__global__ void k_compact_basis(int64_t nslots, int64_t rows, int64_t Bo, int64_t Bn, const int *__restrict__ map,
+                                const float4 *__restrict__ src, float4 *__restrict__ dst) {
+    const int64_t total = nslots * rows * Bn;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t sr = t / Bn, c = t - sr * Bn;  // sr = slot * rows + row
+        dst[t] = src[sr * Bo + map[c]];
+    }
+}
+__global__ void k_compact_hb(int64_t ne, int64_t Bo, int64_t Bn, const int *__restrict__ map,
+                             const cx<double> *__restrict__ src, cx<double> *__restrict__ dst,
+                             const double *__restrict__ beta, double *__restrict__ beta_out) {
+    const int64_t total = ne * Bn;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = t / Bn, c = t - e * Bn;
+        dst[t] = src[e * Bo + map[c]];
+        if (e == 0) beta_out[c] = beta[map[c]];
+    }
+}
+
 // g[k][0] = beta of shift k's column
 __global__ void k_init_g(int64_t S, int mmax, const int *__restrict__ col_of,
                          const double *__restrict__ beta, cx<double> *__restrict__ g) {
@@ -1171,6 +1202,244 @@ __global__ void k_init_g(int64_t S, int mmax, const int *__restrict__ col_of,
 int blocks_for(int64_t n) { return (int)std::min<int64_t>(std::max<int64_t>((n + 255) / 256, 1), 152 * 16); }
 
 }  // namespace
+
+// Work chunks of the float-float Gram-Schmidt kernels for a column layout in which ADO n has
+// acols[n] active (leading) columns: runs of ADOs with equal counts, cut into pieces of about
+// 1/456 of the active entries (at least 4096) so that one tile of basis vectors fills the GPU,
+// and the update's pieces, the same cut about 8x finer (its blocks stride over them in one
+// wave of resident blocks, so that the last pieces balance across the SMs). Returns the
+// active entries; *runs = the number of runs.
+static int64_t make_chunks(const std::vector<int> &acols, int d2, std::vector<GsChunk> &ch, std::vector<GsChunk> &uch,
+                    int *runs) {
+    ch.clear();
+    uch.clear();
+    const int64_t N = (int64_t)acols.size();
+    int64_t act = 0;
+    for (int64_t n = 0; n < N; ++n) act += (int64_t)d2 * acols[(size_t)n];
+    const int64_t target = std::max<int64_t>(4096, act / 456);
+    int nr = 0;
+    for (int64_t n = 0; n < N;) {
+        const int a = acols[(size_t)n];
+        int64_t n1 = n;
+        while (n1 < N && acols[(size_t)n1] == a) ++n1;
+        ++nr;
+        if (a > 0) {
+            const int64_t r0 = n * d2, r1 = n1 * d2, step = std::max<int64_t>(1, target / a);
+            for (int64_t r = r0; r < r1; r += step)
+                ch.push_back(GsChunk{(int32_t)r, (int32_t)std::min(r1, r + step), a, 0});
+        }
+        n = n1;
+    }
+    for (const GsChunk &c0 : ch) {
+        const int64_t rows_c = c0.row1 - c0.row0, ustep = std::max<int64_t>(1, (rows_c + 7) / 8);
+        for (int64_t r = c0.row0; r < c0.row1; r += ustep)
+            uch.push_back(GsChunk{(int32_t)r, (int32_t)std::min<int64_t>(c0.row1, r + ustep), c0.acols, 0});
+    }
+    if (runs) *runs = nr;
+    return act;
+}
+
+// Device buffers of the delayed-reorthogonalisation process (see shifted_gmres).
+struct DcgsBufs {
+    float4 *VA, *VB;             // two float-float bases of (mmax + 1) x rows x B entries
+    cx<double> *Hb, *Hb2;        // Hessenberg matrices and their compaction target
+    float4 *Hbf;                 // float-float split of the final Hessenberg columns
+    double *beta, *beta2;        // ||b|| per column and its compaction target
+    cx<double> *part, *D;        // partial and reduced dot products
+    float4 *cfa, *cft;           // update coefficients
+    float2 *rsig;                // 1 / sigma per column
+    const cx<double> *shift;     // [S]
+    int *col_of;                 // [S] current column of each shift
+    double *rot_c;
+    cx<double> *rot_s, *rdiag, *g;
+    double *res;                 // [S] residual estimates
+    float2 *rot_cf;
+    float4 *rot_sf, *gw, *y;
+    cx<double> *x0;              // [S][d2]
+    GsChunk *ch, *uch;           // chunk tables (capacities ch_cap, uch_cap)
+    int ch_cap, uch_cap;
+    int *klist, *kfroz, *set_of, *map;
+};
+
+// The shift-invariant Arnoldi process with delayed reorthogonalisation for B columns, from
+// v_0 = b / beta in VA slot 0 (g and beta set), with every shift's Givens QR advanced at the
+// convergence checks (every 10 steps). A parameter set all of whose shifts have converged
+// leaves the process: its shifts' tier-0 blocks are solved at once from the columns so far,
+// and when enough columns have left (at least 1/16 of them) the remaining columns are
+// compacted into a narrower layout (basis, Hessenberg matrices, beta; the shifts' own arrays
+// stay), so the later steps stream only the columns still running. Ends with the final solve
+// of the shifts still running; *steps = the Arnoldi steps taken (applies).
+static heom_status dcgs_process(heom_hier *h, int64_t B, int64_t S, int mmax, double tol, std::vector<int> col_of,
+                         DcgsBufs &bf, int *steps, cudaStream_t s) {
+    const int64_t rows = h->N * h->d2;
+    const int d2 = h->d2;
+    const int64_t cps = B / h->n_sets;
+    const DevView<double> v = h->view64();
+    int dev = 0, sms = 0, occ = 0;
+    HEOM_CUDA(cudaGetDevice(&dev));
+    HEOM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    HEOM_CUDA(cudaFuncSetAttribute(k_update2_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUpSmem));
+    HEOM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update2_ff, kDotThreads, kUpSmem));
+    std::vector<int> cur((size_t)B);  // original column of each current column
+    for (int64_t c = 0; c < B; ++c) cur[(size_t)c] = (int)c;
+    std::vector<int> act((size_t)S);  // shifts still running
+    for (int64_t k = 0; k < S; ++k) act[(size_t)k] = (int)k;
+    int64_t Bc = B, Lc = rows * B;
+    float4 *Vc = bf.VA, *Vo = bf.VB;
+    cx<double> *Hc = bf.Hb, *Ho = bf.Hb2;
+    double *bc = bf.beta, *bo = bf.beta2;
+    std::vector<GsChunk> ch, uch;
+    int nch = 0, nuch = 0, gsu = 1;
+    double Lg = 0.0;
+    // chunk tables and sets of the current layout: ADO n keeps the current columns whose set is
+    // below act_ado[n] (a leading block: columns stay in set order)
+    auto relayout = [&]() -> heom_status {
+        std::vector<int> set_c((size_t)Bc), acols((size_t)h->N);
+        for (int64_t c = 0; c < Bc; ++c) set_c[(size_t)c] = (int)(cur[(size_t)c] / cps);
+        for (int64_t n = 0; n < h->N; ++n)
+            acols[(size_t)n] = h->has_act ? (int)(std::lower_bound(set_c.begin(), set_c.end(), h->act_ado[n]) -
+                                                  set_c.begin())
+                                          : (int)Bc;
+        Lg = (double)make_chunks(acols, d2, ch, uch, nullptr);
+        nch = (int)ch.size();
+        nuch = (int)uch.size();
+        if (nch > bf.ch_cap || nuch > bf.uch_cap) {
+            set_error("shift-invariant solver: chunk table overflow");
+            return HEOM_EINVAL;
+        }
+        if (nch) HEOM_CUDA(memcpy_counted(bf.ch, ch.data(), nch * sizeof(GsChunk), cudaMemcpyHostToDevice, s));
+        if (nuch) HEOM_CUDA(memcpy_counted(bf.uch, uch.data(), nuch * sizeof(GsChunk), cudaMemcpyHostToDevice, s));
+        HEOM_CUDA(memcpy_counted(bf.set_of, set_c.data(), Bc * sizeof(int), cudaMemcpyHostToDevice, s));
+        gsu = std::max(1, std::min(nuch, std::max(occ, 1) * sms));
+        return HEOM_OK;
+    };
+    auto upload_shifts = [&]() -> heom_status {
+        HEOM_CUDA(memcpy_counted(bf.klist, act.data(), act.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+        HEOM_CUDA(memcpy_counted(bf.col_of, col_of.data(), S * sizeof(int), cudaMemcpyHostToDevice, s));
+        return HEOM_OK;
+    };
+    // final solve of the listed shifts from the first mf Hessenberg columns
+    auto solve_shifts = [&](const int *klist, int64_t nk, int mf) -> heom_status {
+        if (nk == 0 || mf == 0) return HEOM_OK;
+        Prof pr(HEOM_KC_OTHER, s, (double)nk, (double)nk * mf * 16);
+        k_shift_solve_ff<<<(unsigned)((nk + 63) / 64), 64, 0, s>>>(mf, mmax, Bc, nk, d2, bf.Hbf, bf.shift, bf.col_of,
+                                                                   bf.rot_cf, bf.rot_sf, bf.rdiag, bf.g, bf.gw, bf.y,
+                                                                   Vc, Lc, bf.x0, klist);
+        HEOM_CUDA(cudaGetLastError());
+        return HEOM_OK;
+    };
+    heom_status st = relayout();
+    if (st != HEOM_OK) return st;
+    st = upload_shifts();
+    if (st != HEOM_OK) return st;
+    std::vector<double> hres((size_t)S, 1.0);
+    int m = 0, j_done = 0;
+    for (int j = 0; j < mmax; ++j) {
+        float4 *zf = Vc + (int64_t)(j + 1) * Lc;
+        {   // z = M p_j, float-float from and into the basis
+            Prof pr(HEOM_KC_KRYLOV_APPLY64, s, Lg / d2, 2.0 * Lg * 16);
+            const int64_t grid = std::min<int64_t>((Lc + 255) / 256, 152 * 16);
+            if (cps % 2 == 0)
+                k_apply_ff<2><<<(unsigned)grid, 256, 0, s>>>(v, Vc + (int64_t)j * Lc, zf, Bc, bf.set_of);
+            else
+                k_apply_ff<1><<<(unsigned)grid, 256, 0, s>>>(v, Vc + (int64_t)j * Lc, zf, Bc, bf.set_of);
+        }
+        {   // one read of the basis for the dots, one for the update
+            Prof pr(HEOM_KC_KRYLOV_VECTOR, s, (double)(j + 1) * Lg, (2.0 * j + 6.0) * Lg * 16);
+            pr.kernels = 4;
+            k_dots2_ff_tiled<<<dim3((unsigned)((j + 1 + kD2Tile - 1) / kD2Tile), (unsigned)nch), kDotThreads, 0, s>>>(
+                Bc, j + 1, Vc, Lc, zf, bf.part, bf.ch);
+            k_reduce_dots2<<<blocks_for((int64_t)(j + 1) * 2 * Bc), 256, 0, s>>>(nch, j + 1, Bc, bf.part, bf.D);
+            k_dcgs_coef<<<(unsigned)Bc, 256, 0, s>>>(j, mmax, Bc, bf.D, Hc, bf.cfa, bf.cft, bf.rsig);
+            k_update2_ff<<<gsu, kDotThreads, kUpSmem, s>>>(Bc, j, Vc, Lc, nullptr, 0, bf.cfa, bf.cft, bf.rsig, bf.uch,
+                                                           nuch);
+        }
+        HEOM_CUDA(cudaGetLastError());
+        m = j + 1;
+        if ((m % 10 != 0 && m != mmax) || m - 1 <= j_done) continue;
+        const int mf = m - 1;  // column m - 1 of Hb becomes final only at the next step
+        {   // the running shifts' Givens QR catches up with the new final columns
+            Prof pr(HEOM_KC_OTHER, s, (double)act.size() * (mf - j_done), 0.0);
+            pr.kernels = 2;
+            k_split_hb<<<blocks_for((int64_t)(mf - j_done) * (mmax + 1) * Bc), 256, 0, s>>>(j_done, mf, mmax, Bc, Hc,
+                                                                                          bf.Hbf);
+            k_shift_steps<<<(unsigned)((act.size() + 63) / 64), 64, 0, s>>>(
+                j_done, mf, mmax, Bc, (int64_t)act.size(), Hc, bf.shift, bf.col_of, bf.rot_c, bf.rot_s, bf.rdiag, bf.g,
+                bc, bf.res, bf.Hbf, bf.rot_cf, bf.rot_sf, bf.klist);
+        }
+        j_done = mf;
+        HEOM_CUDA(memcpy_counted(hres.data(), bf.res, S * 8, cudaMemcpyDeviceToHost, s));
+        HEOM_CUDA(cudaStreamSynchronize(s));
+        // a column is done when all its running shifts are; a parameter set when all its columns are
+        std::vector<char> done_c((size_t)Bc, 1);
+        bool all = true;
+        for (int k : act)
+            if (!(hres[(size_t)k] <= tol)) {
+                done_c[(size_t)col_of[(size_t)k]] = 0;
+                all = false;
+            }
+        if (all || m == mmax) break;
+        std::vector<char> leave((size_t)Bc, 0);
+        int64_t n_leave = 0;
+        for (int64_t c0 = 0; c0 < Bc;) {  // runs of one set
+            int64_t c1 = c0;
+            bool d = true;
+            while (c1 < Bc && cur[(size_t)c1] / cps == cur[(size_t)c0] / cps) {
+                d = d && done_c[(size_t)c1];
+                ++c1;
+            }
+            if (d) {
+                for (int64_t c = c0; c < c1; ++c) leave[(size_t)c] = 1;
+                n_leave += c1 - c0;
+            }
+            c0 = c1;
+        }
+        if (n_leave == 0 || n_leave < Bc / 16) continue;
+        // the leaving shifts: tier-0 blocks from the mf final columns, in the current layout
+        std::vector<int> kf, keep;
+        for (int k : act) (leave[(size_t)col_of[(size_t)k]] ? kf : keep).push_back(k);
+        HEOM_CUDA(memcpy_counted(bf.kfroz, kf.data(), kf.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+        st = solve_shifts(bf.kfroz, (int64_t)kf.size(), mf);
+        if (st != HEOM_OK) return st;
+        // compact the running columns (slots 0 .. m: q_0 .. q_{m-1} and p_m)
+        std::vector<int> map, inv((size_t)Bc, -1);
+        for (int64_t c = 0; c < Bc; ++c)
+            if (!leave[(size_t)c]) {
+                inv[(size_t)c] = (int)map.size();
+                map.push_back((int)c);
+            }
+        const int64_t Bn = (int64_t)map.size(), Ln = rows * Bn;
+        HEOM_CUDA(memcpy_counted(bf.map, map.data(), Bn * sizeof(int), cudaMemcpyHostToDevice, s));
+        {
+            Prof pr(HEOM_KC_OTHER, s, (double)(m + 1) * Ln, 2.0 * (m + 1) * Ln * 16);
+            pr.kernels = 3;
+            k_compact_basis<<<blocks_for((int64_t)(m + 1) * Ln), 256, 0, s>>>(m + 1, rows, Bc, Bn, bf.map, Vc, Vo);
+            const int64_t ne = (int64_t)(mmax + 1) * mmax;
+            k_compact_hb<<<blocks_for(ne * Bn), 256, 0, s>>>(ne, Bc, Bn, bf.map, Hc, Ho, bc, bo);
+            k_split_hb<<<blocks_for((int64_t)j_done * (mmax + 1) * Bn), 256, 0, s>>>(0, j_done, mmax, Bn, Ho, bf.Hbf);
+        }
+        HEOM_CUDA(cudaGetLastError());
+        std::swap(Vc, Vo);
+        std::swap(Hc, Ho);
+        std::swap(bc, bo);
+        std::vector<int> cur_n((size_t)Bn);
+        for (int64_t c = 0; c < Bn; ++c) cur_n[(size_t)c] = cur[(size_t)map[(size_t)c]];
+        cur.swap(cur_n);
+        for (int k : keep) col_of[(size_t)k] = inv[(size_t)col_of[(size_t)k]];
+        for (int k : kf) col_of[(size_t)k] = 0;  // no longer read
+        act.swap(keep);
+        Bc = Bn;
+        Lc = Ln;
+        st = relayout();
+        if (st != HEOM_OK) return st;
+        st = upload_shifts();
+        if (st != HEOM_OK) return st;
+    }
+    st = solve_shifts(bf.klist, (int64_t)act.size(), j_done);
+    if (st != HEOM_OK) return st;
+    *steps = m;
+    return HEOM_OK;
+}
 
 // Shift-invariant GMRES for B right-hand sides (columns of bvec, [rows][B], FP64) with S
 // shifts in total: shift k (value shift[k], host) belongs to column col_of[k]. Returns the
@@ -1186,9 +1455,9 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
         // them within 60 % of the free device memory
         size_t free_b = 0, total_b = 0;
         if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
-            // the hierarchy's own workspace is reused (or grown), or else the largest one the
-            // library keeps cached on this device
-            free_b += std::max(h->ws.bytes, ws_cached_max(h->device));
+            // the hierarchy's own workspace is reused (or grown), and the workspaces the library
+            // keeps cached on this device are freed when an allocation needs their memory
+            free_b += h->ws.bytes + ws_cached_total(h->device);
             const double per_step = 32.0 * (double)L + 112.0 * (double)S + (64.0 + 32.0 * 456) * (double)B;
             const double fixed = 64.0 * (double)L + 48.0 * (double)S + (double)(64 * 2 + 2) * B * 16.0;
             const double avail = 0.6 * (double)free_b - fixed;
@@ -1224,41 +1493,29 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
     // unless parameter sets are truncated deepest first), cut into pieces of about
     // 1/456 of the active entries so that one tile of basis vectors fills the GPU
     const bool ffgs = B <= kDotThreads;
-    std::vector<GsChunk> chunks;
+    std::vector<GsChunk> chunks, uchunks;
     int64_t act_total = 0;
+    int runs = 0;
     if (ffgs) {
         const int64_t cps = B / h->n_sets;
-        auto acols_of = [&](int64_t n) { return h->has_act ? (int)(h->act_ado[n] * cps) : (int)B; };
-        for (int64_t n = 0; n < h->N; ++n) act_total += (int64_t)d2 * acols_of(n);
-        const int64_t target = std::max<int64_t>(4096, act_total / 456);
-        for (int64_t n = 0; n < h->N;) {
-            const int a = acols_of(n);
-            int64_t n1 = n;
-            while (n1 < h->N && acols_of(n1) == a) ++n1;
-            if (a > 0) {
-                const int64_t r0 = n * d2, r1 = n1 * d2, step = std::max<int64_t>(1, target / a);
-                for (int64_t r = r0; r < r1; r += step)
-                    chunks.push_back(GsChunk{(int32_t)r, (int32_t)std::min(r1, r + step), a, 0});
-            }
-            n = n1;
-        }
+        std::vector<int> acols((size_t)h->N);
+        for (int64_t n = 0; n < h->N; ++n) acols[(size_t)n] = h->has_act ? (int)(h->act_ado[n] * cps) : (int)B;
+        act_total = make_chunks(acols, d2, chunks, uchunks, &runs);
     }
     const int nch = (int)chunks.size();
-    // the update's chunks: the same runs cut about 8x finer (its blocks stride over them, one
-    // wave of resident blocks, so that the last chunks balance across the SMs)
-    std::vector<GsChunk> uchunks;
-    for (const GsChunk &c0 : chunks) {
-        const int64_t rows_c = c0.row1 - c0.row0, ustep = std::max<int64_t>(1, (rows_c + 7) / 8);
-        for (int64_t r = c0.row0; r < c0.row1; r += ustep)
-            uchunks.push_back(GsChunk{(int32_t)r, (int32_t)std::min<int64_t>(c0.row1, r + ustep), c0.acols, 0});
-    }
     const int nuch = (int)uchunks.size();
-    const int npc = std::max(nchunk, nch);  // partial-dot chunks
+    // chunk-table capacity for every later column layout (compaction only merges runs)
+    const int ch_cap = std::max(nch, 456 + runs + 1), uch_cap = 8 * ch_cap;
+    const int npc = std::max(nchunk, ch_cap);  // partial-dot chunks
     const size_t opart = take((size_t)npc * (mmax + 2) * 2 * B * 16), oskip = take(sizeof(int)),
                  oran = take((size_t)mmax * sizeof(int));
     const size_t onp = take((size_t)std::max(npc, nuch) * B * 8);
-    const size_t och = take((size_t)std::max(nch, 1) * sizeof(GsChunk)),
-                 ouch = take((size_t)std::max(nuch, 1) * sizeof(GsChunk));
+    const size_t och = take((size_t)ch_cap * sizeof(GsChunk)), ouch = take((size_t)uch_cap * sizeof(GsChunk));
+    // column compaction (delayed-reorthogonalisation process): second Hessenberg and beta
+    // arrays, shift lists, the set of each column, the column map
+    const size_t oHb2 = ffgs ? take((size_t)(mmax + 1) * mmax * B * 16) : 0,
+                 obeta2 = take((size_t)B * 8), okl = take((size_t)S * 4), okf = take((size_t)S * 4),
+                 oset = take((size_t)B * 4), omap = take((size_t)B * 4);
     const size_t oVf = ffgs ? take((size_t)(mmax + 1) * L * 16) : 0,
                  ohf = ffgs ? take((size_t)(mmax + 2) * B * 16) : 0;
     // the delayed-reorthogonalisation scalars: dots D [mmax+1][2][B], coefficients
@@ -1322,19 +1579,9 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
     const bool tiled = tile_ok(v, B);
     const GsChunk *dch = (const GsChunk *)(base + och);
     if (nch > 0) HEOM_CUDA(memcpy_counted((void *)dch, chunks.data(), nch * sizeof(GsChunk), cudaMemcpyHostToDevice, s));
-    const GsChunk *duch = (const GsChunk *)(base + ouch);
-    if (nuch > 0)
-        HEOM_CUDA(memcpy_counted((void *)duch, uchunks.data(), nuch * sizeof(GsChunk), cudaMemcpyHostToDevice, s));
+    const GsChunk *duch = (const GsChunk *)(base + ouch);  // filled by the process's layout
     const int gsb = std::max(1, std::min(nch, 152 * 8));  // blocks of the chunk-striding kernels
-    int gsu = 1;  // the update's grid: its resident blocks (one wave)
-    if (ffgs) {
-        HEOM_CUDA(cudaFuncSetAttribute(k_update2_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUpSmem));
-        int occ = 0, dev = 0, sms = 0;
-        HEOM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update2_ff, kDotThreads, kUpSmem));
-        HEOM_CUDA(cudaGetDevice(&dev));
-        HEOM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        gsu = std::max(1, std::min(nuch, std::max(occ, 1) * sms));
-    }
+
     // elements of one vector that can be nonzero (truncated sets: the kept rows of each
     // column), and the ADO-applies of one apply: the work and the algorithmic bytes counted
     const int64_t cps = B / h->n_sets;
@@ -1362,21 +1609,55 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
     // the basis is already final: the two-pass step continues it); Hessenberg column j is
     // final only after step j + 1, so the shifts' QR and the solution stay one column behind
     const bool dcgs = ffgs && m == 0 && mmax >= 3;
-    const int lag = dcgs ? 1 : 0;
+    if (dcgs) {
+        DcgsBufs bf{};
+        bf.VA = Vf;
+        bf.VB = reinterpret_cast<float4 *>(V);  // the FP64 basis is not needed past v_0
+        bf.Hb = Hb;
+        bf.Hb2 = (cx<double> *)(base + oHb2);
+        bf.Hbf = Hbf;
+        bf.beta = beta;
+        bf.beta2 = (double *)(base + obeta2);
+        bf.part = part;
+        bf.D = dD;
+        bf.cfa = cfa;
+        bf.cft = cft;
+        bf.rsig = rsig;
+        bf.shift = dsh;
+        bf.col_of = dco;
+        bf.rot_c = rot_c;
+        bf.rot_s = rot_s;
+        bf.rdiag = rdiag;
+        bf.g = g;
+        bf.res = dres;
+        bf.rot_cf = rot_cf;
+        bf.rot_sf = rot_sf;
+        bf.gw = (float4 *)gw;
+        bf.y = (float4 *)y;
+        bf.x0 = dx0;
+        bf.ch = const_cast<GsChunk *>(dch);
+        bf.uch = const_cast<GsChunk *>(duch);
+        bf.ch_cap = ch_cap;
+        bf.uch_cap = uch_cap;
+        bf.klist = (int *)(base + okl);
+        bf.kfroz = (int *)(base + okf);
+        bf.set_of = (int *)(base + oset);
+        bf.map = (int *)(base + omap);
+        st = dcgs_process(h, B, S, mmax, tol, col_of, bf, steps, s);
+        if (st != HEOM_OK) return st;
+        x0.resize((size_t)S * d2);
+        res.resize(S);
+        HEOM_CUDA(memcpy_counted(x0.data(), dx0, (size_t)S * d2 * 16, cudaMemcpyDeviceToHost, s));
+        HEOM_CUDA(memcpy_counted(res.data(), dres, S * 8, cudaMemcpyDeviceToHost, s));
+        HEOM_CUDA(cudaStreamSynchronize(s));
+        return HEOM_OK;
+    }
     for (int j = m; j < mmax && !done; ++j) {
         const cx<double> *vj = V + (int64_t)j * L;
         cx<double> *w = V + (int64_t)(j + 1) * L;  // the new vector is built in place
         {   // w = M v_j
             Prof pr(HEOM_KC_KRYLOV_APPLY64, s, Lk / h->d2, 2.0 * Lk * 16);
-            if (dcgs) {  // float-float, from and into the float-float basis
-                const int64_t grid = std::min<int64_t>((L + 255) / 256, 152 * 16);
-                if (cps % 2 == 0)
-                    k_apply_ff<2><<<(unsigned)grid, 256, 0, s>>>(v, Vf + (int64_t)j * L, Vf + (int64_t)(j + 1) * L, B,
-                                                                 cps);
-                else
-                    k_apply_ff<1><<<(unsigned)grid, 256, 0, s>>>(v, Vf + (int64_t)j * L, Vf + (int64_t)(j + 1) * L, B,
-                                                                 cps);
-            } else if (tiled) {
+            if (tiled) {
                 ta.x = vj;
                 ta.out = w;
                 HEOM_CUDA((launch_tile<double, TM_STORE>(ta, s)));
@@ -1385,20 +1666,7 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
                 HEOM_CUDA(launch_apply(v, vj, w, B, mods, s));
             }
         }
-        if (dcgs) {
-            // one read of the basis for the dots, one for the update (see k_dots2_ff_tiled)
-            float4 *zf = Vf + (int64_t)(j + 1) * L;
-            {
-                Prof pr(HEOM_KC_KRYLOV_VECTOR, s, (double)(j + 1) * Lg, (2.0 * j + 6.0) * Lg * 16);
-                pr.kernels = 4;
-                k_dots2_ff_tiled<<<dim3((unsigned)((j + 1 + kD2Tile - 1) / kD2Tile), (unsigned)nch), kDotThreads,
-                                   0, s>>>(B, j + 1, Vf, L, zf, part, dch);
-                k_reduce_dots2<<<blocks_for((int64_t)(j + 1) * 2 * B), 256, 0, s>>>(nch, j + 1, B, part, dD);
-                k_dcgs_coef<<<(unsigned)B, 256, 0, s>>>(j, mmax, B, dD, Hb, cfa, cft, rsig);
-                k_update2_ff<<<gsu, kDotThreads, kUpSmem, s>>>(B, j, Vf, L, V + (int64_t)j * L, (int64_t)d2, cfa,
-                                                               cft, rsig, duch, nuch);
-            }
-        } else if (ffgs) {
+        if (ffgs) {
             float4 *wf = Vf + (int64_t)(j + 1) * L;
             {   // classical Gram-Schmidt in float-float; pass 1 also yields |w|^2 (w's dot with
                 // itself), from which k_reorth_flag decides on the device whether pass 2 runs
@@ -1459,19 +1727,13 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
         }
         HEOM_CUDA(cudaGetLastError());
         m = j + 1;
-        if ((m % check == 0 || m == mmax) && m - lag > j_done) {
-            const int mf = m - lag;  // the final Hessenberg columns
-            {   // every shift's Givens QR catches up with the new Hessenberg columns (chains in
-                // float-float with the delayed-reorthogonalisation process)
+        if ((m % check == 0 || m == mmax) && m > j_done) {
+            const int mf = m;
+            {   // every shift's Givens QR catches up with the new Hessenberg columns
                 Prof pr(HEOM_KC_OTHER, s, (double)S * (mf - j_done), 0.0);
-                if (dcgs) {
-                    pr.kernels = 2;
-                    k_split_hb<<<blocks_for((int64_t)(mf - j_done) * (mmax + 1) * B), 256, 0, s>>>(j_done, mf, mmax,
-                                                                                                 B, Hb, Hbf);
-                }
-                k_shift_steps<<<(unsigned)((S + 63) / 64), 64, 0, s>>>(
-                    j_done, mf, mmax, B, S, Hb, dsh, dco, rot_c, rot_s, rdiag, g, beta, dres,
-                    dcgs ? Hbf : nullptr, rot_cf, rot_sf);
+                k_shift_steps<<<(unsigned)((S + 63) / 64), 64, 0, s>>>(j_done, mf, mmax, B, S, Hb, dsh, dco, rot_c,
+                                                                      rot_s, rdiag, g, beta, dres, nullptr, nullptr,
+                                                                      nullptr, nullptr);
             }
             j_done = mf;
             HEOM_CUDA(memcpy_counted(hres.data(), dres, S * 8, cudaMemcpyDeviceToHost, s));
@@ -1503,17 +1765,13 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
                 HEOM_CUDA(cudaFuncSetAttribute(k_shift_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
             k_shift_solve<<<(unsigned)((S + kSolveThreads - 1) / kSolveThreads), kSolveThreads, smb, s>>>(
                 mf, mmax, B, S, d2, Hb, dsh, dco, rot_c, rot_s, rdiag, g, V, L, dx0);
-        } else if (dcgs) {
-            k_shift_solve_ff<<<(unsigned)((S + 63) / 64), 64, 0, s>>>(mf, mmax, B, S, d2, Hbf, dsh, dco, rot_cf,
-                                                                      rot_sf, rdiag, g, (float4 *)gw, (float4 *)y,
-                                                                      Vf, L, dx0);
         } else {
             k_shift_solve_long<<<(unsigned)((S + 63) / 64), 64, 0, s>>>(mf, mmax, B, S, d2, Hb, dsh, dco, rot_c,
                                                                         rot_s, rdiag, g, gw, y, V, L, dx0);
         }
     }
     HEOM_CUDA(cudaGetLastError());
-    if (prof_on() && !dcgs && m > j_pers) {
+    if (prof_on() && m > j_pers) {
         // the second Gram-Schmidt passes that ran: j + 1 basis vectors read by the dots and
         // by the update, w read twice and written once
         std::vector<int> ran((size_t)m);
