@@ -742,6 +742,36 @@ def run_spectra_only(args):
                       "ms_per_step": round(a.elapsed_time(b) / max(args.steps, 1), 2)}))
 
 
+def run_steady_only(args):
+    """Profiling case of the stationary half of the step: the batched mixed-precision
+    stationary solve of all 64 drawn sets (tier-4 structure, each set at its own tier),
+    --steps solves after --warmup, timed with CUDA events; per-set iterations printed."""
+    import torch
+
+    import paper_2306_07522_gb300 as heom
+    draws = c3_draws()
+    models = c3_models(draws)
+    even, odd = c3_build(heom, draws, models)
+    x = torch.zeros((even.n_ado, 4, 4, N_SETS), dtype=torch.complex128, device="cuda")
+
+    def step():
+        return heom.steady(even, x, tol=TOL, max_iter=4000, prec=heom.MIXED, raise_on_error=False)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        st, stats = step()
+    b.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"case": "batched stationary states (profiling)", "sets": N_SETS, "status": st,
+                      "iterations": [s["iterations"] for s in stats],
+                      "refinements": [s["refinements"] for s in stats],
+                      "ms_per_step": round(a.elapsed_time(b) / max(args.steps, 1), 2)}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -750,8 +780,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--quick", action="store_true",
                     help="timed steps only (no plain-path, e2e or CPU-baseline legs)")
-    ap.add_argument("--only", choices=["apply", "spectra"], default=None,
-                    help="profiling cases: the apply alone, or a reduced batched-spectra step")
+    ap.add_argument("--only", choices=["apply", "spectra", "steady"], default=None,
+                    help="profiling cases: the apply alone, a reduced batched-spectra step, or the stationary solve")
     ap.add_argument("--sets", type=int, default=8, help="--only spectra: parameter sets")
     ap.add_argument("--n-omega", type=int, default=256, help="--only spectra: frequencies")
     ap.add_argument("--max-iter", type=int, default=2000, help="--only spectra: Arnoldi steps")
@@ -763,6 +793,9 @@ def main():
         return
     if args.only == "spectra":
         run_spectra_only(args)
+        return
+    if args.only == "steady":
+        run_steady_only(args)
         return
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -38,11 +38,19 @@ __device__ __forceinline__ void reduce_add(double (&val)[NV], double *const (&ds
     }
 }
 
+// The parameter set of batch column b: (map ? map[b] : b) / cps, where map gives the original
+// column of each column of a compacted working layout (null: the layout is the original).
+struct ColSets {
+    int64_t cps;
+    const int *map;
+    __host__ __device__ ColSets(int64_t c, const int *m = nullptr) : cps(c), map(m) {}
+};
+
 #define COLUMN_PROLOGUE                                                    \
     const int64_t b = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;      \
     const bool inb = b < B;                                                \
     const int64_t rows = v.N * v.d2;                                       \
-    const int set = inb ? (int)(b / cps) : 0;                              \
+    const int set = inb ? (int)((cps.map ? (int64_t)cps.map[b] : b) / cps.cps) : 0; \
     (void)set;
 
 #define ROW_LOOP _Pragma("unroll 4") \
@@ -61,7 +69,7 @@ template <class R>
 __global__ void __launch_bounds__(256) k_rk4_stage(DevView<R> v, const cx<R> *__restrict__ z_in,
                                                    cx<R> *__restrict__ z_out, cx<R> *y,
                                                    cx<R> *__restrict__ acc, int64_t B,
-                                                   int64_t cps, R dt, int stage) {
+                                                   ColSets cps, R dt, int stage) {
     COLUMN_PROLOGUE
     if (!inb) return;
     ROW_LOOP {
@@ -116,7 +124,7 @@ template <class R>
 __global__ void __launch_bounds__(256) k_bicg_init(DevView<R> v, const cx<R> *__restrict__ bb,
                                                    const cx<R> *__restrict__ x, cx<R> *r,
                                                    cx<R> *rh, cx<R> *p, cx<R> *vv, int64_t B,
-                                                   int64_t cps, ApplyMods<R> mods, int x_zero,
+                                                   ColSets cps, ApplyMods<R> mods, int x_zero,
                                                    ColState *st) {
     COLUMN_PROLOGUE
     const bool act = inb && st[b].active;
@@ -169,7 +177,7 @@ template <class R>
 __global__ void __launch_bounds__(256) k_bicg_p(DevView<R> v, const cx<R> *__restrict__ r,
                                                 cx<R> *p, const cx<R> *__restrict__ vv,
                                                 cx<R> *__restrict__ ph, cx<R> *rh, int64_t B,
-                                                int64_t cps, const cx<R> *shift, int precond,
+                                                ColSets cps, const cx<R> *shift, int precond,
                                                 ColState *st) {
     COLUMN_PROLOGUE
     __shared__ ColScalars<R> sc[32];
@@ -217,7 +225,7 @@ template <class R>
 __global__ void __launch_bounds__(256) k_bicg_apply(DevView<R> v, const cx<R> *__restrict__ in,
                                                     cx<R> *__restrict__ out,
                                                     const cx<R> *__restrict__ w, int64_t B,
-                                                    int64_t cps, ApplyMods<R> mods, int mode,
+                                                    ColSets cps, ApplyMods<R> mods, int mode,
                                                     ColState *st) {
     COLUMN_PROLOGUE
     const bool act = inb && st[b].active;
@@ -265,7 +273,7 @@ __global__ void __launch_bounds__(256) k_bicg_apply(DevView<R> v, const cx<R> *_
 // alpha = rho / (rh, v); s = r - alpha v (in place in r); sh = P^-1 s
 template <class R>
 __global__ void __launch_bounds__(256) k_bicg_s(DevView<R> v, cx<R> *r, const cx<R> *__restrict__ vv,
-                                                cx<R> *__restrict__ sh, int64_t B, int64_t cps,
+                                                cx<R> *__restrict__ sh, int64_t B, ColSets cps,
                                                 const cx<R> *shift, int precond, ColState *st) {
     COLUMN_PROLOGUE
     __shared__ ColScalars<R> sc[32];
@@ -369,7 +377,7 @@ __global__ void __launch_bounds__(256) k_bicg_x(int64_t rows, cx<R> *x, const cx
 __global__ void __launch_bounds__(256) k_residual64(DevView<double> v, const cx<double> *__restrict__ bb,
                                                     const cx<double> *__restrict__ x,
                                                     cx<double> *__restrict__ r, int64_t B,
-                                                    int64_t cps, ApplyMods<double> mods,
+                                                    ColSets cps, ApplyMods<double> mods,
                                                     ColState *st) {
     COLUMN_PROLOGUE
     const bool act = inb && st[b].active;
@@ -426,7 +434,7 @@ __global__ void k_accum(int64_t rows, cx<double> *__restrict__ x, const cx<RI> *
 
 // per column: |M x|^2 and |x|^2 (FP64, no shift, no augmentation) into out[2*b], out[2*b+1]
 __global__ void __launch_bounds__(256) k_apply_norms(DevView<double> v, const cx<double> *__restrict__ x,
-                                                     int64_t B, int64_t cps, double *out) {
+                                                     int64_t B, ColSets cps, double *out) {
     COLUMN_PROLOGUE
     double mx = 0, xx = 0;
     if (inb) {
@@ -554,8 +562,9 @@ constexpr int kStallIters = 96;
 //
 // The solver works on a compact copy of the active columns ([rows][Bc] with Bc <= B) and
 // re-compacts whenever the still-active columns fall to 60 % of the working width, so that
-// iteration cost follows the columns that still iterate (frequencies converge at different
-// iterations). Converged solutions are scattered back into x. Workspace: 13 vectors of
+// iteration cost follows the columns that still iterate (frequencies and parameter sets
+// converge at different iterations; the kernels find each compact column's parameter set
+// through the column map). Converged solutions are scattered back into x. Workspace: 13 vectors of
 // rows x B (two sets of x, r, rh, p, v and the scratch ph, sh, t).
 template <class R>
 heom_status bicgstab(heom_hier *h, const cx<R> *bvec, cx<R> *x, int64_t B, const cx<R> *shift,
@@ -567,16 +576,16 @@ heom_status bicgstab(heom_hier *h, const cx<R> *bvec, cx<R> *x, int64_t B, const
     cx<R> *set_a[5], *set_b[5];
     for (int i = 0; i < 5; ++i) { set_a[i] = work + i * L; set_b[i] = work + (5 + i) * L; }
     cx<R> *ph = work + 10 * L, *sh = work + 11 * L, *t = work + 12 * L;
-    const bool compact = h->n_sets == 1;
+    const int64_t cps_g = B / h->n_sets;  // columns per parameter set in the caller's layout
     out.iters.assign(B, 0);
     out.status.assign(B, HEOM_OK);
     out.res.assign(B, 0.0);
     // the initial column set
     std::vector<int> cols, alive;  // global column of each compact column; its activity
     for (int64_t b = 0; b < B; ++b)
-        if (!compact || active[b]) { cols.push_back((int)b); alive.push_back(active[b] != 0); }
+        if (active[b]) { cols.push_back((int)b); alive.push_back(1); }
     if (cols.empty()) return HEOM_OK;
-    if (compact && sizeof(R) == 4 && (cols.size() & 1) && (int64_t)cols.size() < B) {
+    if (sizeof(R) == 4 && (cols.size() & 1) && (int64_t)cols.size() < B) {
         for (int64_t b = 0; b < B; ++b)  // an even width keeps the float4 column loads aligned
             if (!active[b]) { cols.push_back((int)b); alive.push_back(0); break; }
     }
@@ -612,7 +621,7 @@ heom_status bicgstab(heom_hier *h, const cx<R> *bvec, cx<R> *x, int64_t B, const
         ApplyMods<R> mods{shc, aug};
         Prof pr(HEOM_KC_KRYLOV_VECTOR, s, (double)rows * Bc, (x_zero ? 5.0 : 6.0) * rows * Bc * sizeof(cx<R>));
         k_bicg_init<R><<<gd.grid, gd.block, 0, s>>>(v, t, cur[0], cur[1], cur[2], cur[3], cur[4],
-                                                    Bc, Bc, mods, x_zero, st);
+                                                    Bc, ColSets(cps_g, d_map), mods, x_zero, st);
     }
     HEOM_CUDA(cudaGetLastError());
     std::vector<ColState> hs(Bc);
@@ -650,7 +659,7 @@ heom_status bicgstab(heom_hier *h, const cx<R> *bvec, cx<R> *x, int64_t B, const
     } graph_release{gexec, gcap};
     while (n_act > 0 && it < max_iter) {
         // ---- re-compaction when the active columns fall to 60 % of the working width
-        if (compact && n_act <= 0.6 * Bc && Bc - n_act >= 16) {
+        if (n_act <= 0.6 * Bc && Bc - n_act >= 16) {
             std::vector<int> keep;
             for (int64_t j = 0; j < Bc; ++j)
                 if (alive[j]) keep.push_back((int)j);
@@ -706,7 +715,7 @@ heom_status bicgstab(heom_hier *h, const cx<R> *bvec, cx<R> *x, int64_t B, const
         ta.st = st;
         ta.B = Bc;
         cx<R> *xw = cur[0], *r = cur[1], *rh = cur[2], *p = cur[3], *vv = cur[4];
-        const int64_t cps = Bc / h->n_sets;
+        const ColSets cps(cps_g, d_map);  // compact column -> the caller's column -> set
         const double u_vec = (double)rows * Bc, u_app = (double)h->N * Bc;
         const double sz = sizeof(cx<R>), e_vec = u_vec * sz;
         // one iteration: five kernels on stream q (event brackets when accounting is on)
