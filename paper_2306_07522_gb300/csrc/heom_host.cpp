@@ -1205,9 +1205,13 @@ extern "C" heom_status heom_set_truncation(heom_hier *h, const int *tier_b, cons
     // caps that never increase from one set to the next: each ADO is kept by a leading run of
     // sets, whose length the Gram-Schmidt kernels use to skip the columns held at zero
     h->kept_rowsets = 0;
+    h->set_kept.assign((size_t)h->n_sets, 0);
     for (int64_t n = 0; n < h->N; ++n)
         for (int s = 0; s < h->n_sets; ++s)
-            if ((at[n] & 0xffff) <= tier_f[s] && (at[n] >> 16) <= tier_b[s]) h->kept_rowsets += h->d2;
+            if ((at[n] & 0xffff) <= tier_f[s] && (at[n] >> 16) <= tier_b[s]) {
+                h->kept_rowsets += h->d2;
+                ++h->set_kept[(size_t)s];
+            }
     bool mono = true;
     for (int s = 1; s < h->n_sets; ++s)
         mono = mono && tier_b[s] <= tier_b[s - 1] && tier_f[s] <= tier_f[s - 1];

@@ -197,6 +197,11 @@ struct heom_hier {
     std::vector<int32_t> act_ado;
     bool has_act = false;
     int64_t kept_rowsets = 0;            // sum over rows of the sets that keep the row's ADO
+    std::vector<int64_t> set_kept;       // ADOs kept by each set (per-set truncation)
+    // ADOs a parameter set keeps (all of them without per-set truncation)
+    int64_t kept_of_set(int s) const {
+        return has_caps && (size_t)s < set_kept.size() ? set_kept[(size_t)s] : N;
+    }
     bool has_caps = false;
     int n_ranges = 0, range_terms = 0, range_slots = 0, range_ados = 0;
     int tile_per_sm = 2;        // tiled kernel: ADO ranges per SM (autotuned)

@@ -71,11 +71,15 @@ __device__ __forceinline__ cx<R> apply_point(const DevView<R> &v, const cx<R> *_
     for (int j = __ldg(v.s_ptr + e), j1 = __ldg(v.s_ptr + e + 1); j < j1; ++j)
         fma_to(acc, ldc(sv + j), Xn[(int64_t)__ldg(v.s_src + j) * B]);
     // couplings to the neighbouring ADOs
+    const int cap = v.set_cap ? __ldg(v.set_cap + set) : 0;
     const int t1 = __ldg(v.row_ptr + n + 1);
     for (int t = __ldg(v.row_ptr + n); t < t1; ++t) {
         const int4 raw = __ldg(reinterpret_cast<const int4 *>(v.ent) + t);
         const int nb = raw.x;
-        if (beyond_cap(v, (int64_t)nb, set)) continue;  // not in the set's hierarchy
+        if (v.set_cap) {  // a neighbour beyond the set's tiers is not in its hierarchy
+            const int tn = __ldg(v.ado_tier + nb);
+            if ((tn & 0xffff) > (cap & 0xffff) || (tn >> 16) > (cap >> 16)) continue;
+        }
         const int op = (int)(int16_t)(raw.y & 0xffff);
         const int k = (int)(int16_t)(raw.y >> 16);
         const int dir = (int)(int16_t)(raw.z & 0xffff);

@@ -716,7 +716,11 @@ heom_status bicgstab(heom_hier *h, const cx<R> *bvec, cx<R> *x, int64_t B, const
         ta.B = Bc;
         cx<R> *xw = cur[0], *r = cur[1], *rh = cur[2], *p = cur[3], *vv = cur[4];
         const ColSets cps(cps_g, d_map);  // compact column -> the caller's column -> set
-        const double u_vec = (double)rows * Bc, u_app = (double)h->N * Bc;
+        // ADO-applies: the ADOs each running column's set keeps (idle padding columns excluded)
+        double u_app = 0.0;
+        for (int64_t j = 0; j < Bc; ++j)
+            if (alive[(size_t)j]) u_app += (double)h->kept_of_set((int)(cols[(size_t)j] / cps_g));
+        const double u_vec = (double)rows * Bc;
         const double sz = sizeof(cx<R>), e_vec = u_vec * sz;
         // one iteration: five kernels on stream q (event brackets when accounting is on)
         auto launch_iter = [&](cudaStream_t q, bool prof, bool set_attr) -> cudaError_t {
@@ -884,10 +888,15 @@ heom_status refine_solve(heom_hier *h, const cx<double> *b64, cx<double> *x64, i
     for (int sweep = 0; sweep <= max_sweeps; ++sweep) {
         HEOM_CUDA(memcpy_counted(d_flags, active.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
         int n_on = 0;
-        for (int a : active) n_on += a != 0;
+        double u_res = 0.0;  // ADO-applies of the residual: the ADOs each active column's set keeps
+        for (int64_t b = 0; b < B; ++b)
+            if (active[(size_t)b]) {
+                ++n_on;
+                u_res += (double)h->kept_of_set((int)(b / cps));
+            }
         { Prof pr(HEOM_KC_OTHER, s, (double)B);
           k_state_init<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(st_out, B, d_flags); }
-        { Prof pr(HEOM_KC_RESIDUAL64, s, (double)h->N * n_on, 3.0 * rows * n_on * sizeof(cx<double>));
+        { Prof pr(HEOM_KC_RESIDUAL64, s, u_res, 3.0 * rows * n_on * sizeof(cx<double>));
           if (tile_ok(v64, B)) {
               TileArgs<double> ta{};
               ta.v = v64; ta.x = x64; ta.out = r64; ta.w = b64; ta.shift = shift64; ta.aug = aug;
