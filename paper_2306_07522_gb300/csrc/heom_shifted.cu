@@ -253,8 +253,8 @@ __global__ void __launch_bounds__(kDotThreads) k_colnorm_part_ff(int64_t B, cons
 }
 
 // v = w / nrm[b] in FP64 (for the FP64 apply; skipped when v is null) and its float-float
-// split (for Gram-Schmidt), in place on wf, on the active entries of the chunks (the others
-// stay zero in v). nrm = 0 leaves zeros (exact invariant subspace).
+// split (for Gram-Schmidt and the float-float apply); in place on wf, on the active entries of the chunks (the others stay zero in v). nrm = 0
+// leaves zeros (exact invariant subspace).
 __global__ void __launch_bounds__(kDotThreads) k_scale_ff(int64_t B, float4 *__restrict__ wf,
                                                           const double *__restrict__ nrm,
                                                           cx<double> *__restrict__ v,
