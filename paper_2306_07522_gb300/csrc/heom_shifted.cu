@@ -1468,9 +1468,9 @@ heom_status shifted_gmres(heom_hier *h, const cx<double> *bvec, int64_t B,
                 return HEOM_ENOMEM;
             }
             mmax = std::min(mmax, fit);
-            // the Hessenberg matrices (FP64 and float-float split) grow as mmax^2: within a
-            // tenth of the free memory
-            while (mmax > 8 && 32.0 * (double)B * (mmax + 1.0) * mmax > 0.1 * (double)free_b) mmax -= 8;
+            // the Hessenberg matrices (FP64, its compaction target and the float-float split)
+            // grow as mmax^2: within a tenth of the free memory
+            while (mmax > 8 && 48.0 * (double)B * (mmax + 1.0) * mmax > 0.1 * (double)free_b) mmax -= 8;
         }
     }
     // device memory: basis V [mmax+1][L] (the new vector is formed in its slot), Hb
