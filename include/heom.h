@@ -498,8 +498,10 @@ typedef enum {
     HEOM_KC_APPLY = 0,           /* heom_apply                                       */
     HEOM_KC_RK4 = 1,             /* fused RK4 stages (one apply each)                */
     HEOM_KC_KRYLOV_APPLY32 = 2,  /* apply + dot products inside FP32 BiCGStab         */
-    HEOM_KC_KRYLOV_APPLY64 = 3,  /* apply + dot products inside FP64 BiCGStab         */
-    HEOM_KC_KRYLOV_VECTOR = 4,   /* BiCGStab vector updates and start-up              */
+    HEOM_KC_KRYLOV_APPLY64 = 3,  /* FP64 BiCGStab applies; the Arnoldi applies (FP64
+                                    or float-float)                                  */
+    HEOM_KC_KRYLOV_VECTOR = 4,   /* BiCGStab vector updates and start-up; Arnoldi
+                                    Gram-Schmidt                                      */
     HEOM_KC_RESIDUAL64 = 5,      /* FP64 residual applies (refinement, final norms)   */
     HEOM_KC_OTHER = 6,           /* right-hand sides, scaling, normalisation          */
     HEOM_KC_COUNT = 7
